@@ -1,0 +1,328 @@
+#!/usr/bin/env python3
+"""Throughput of the full tree step on GB300: particles per second.
+
+Workload: Plummer sphere N = 2^20 (Henon units, seed 1), eps = 0.005,
+theta = 0.75, shared-time-step kick-drift-kick leapfrog with dt = 1/128; every
+step runs the whole hot path (domain + Morton keys, radix sort, reorder,
+octree build, multipoles, group-wise walk, kicks) through the C ABI.
+
+Prints one JSON line (rank 0).  `value` = bodies advanced per second over all
+ranks (device time of the timed steps, CUDA events on the library's stream);
+`e2e` = the same through the C ABI with host buffers (pinned H2D of the
+bodies, full tree step, D2H of accelerations and potentials); `roofline` =
+the walk kernel's algorithmic FP32 rate against the FP32 peak of 152 SMs x
+128 lanes x 2 flop x 2070 MHz; `cpu_baseline` = the FP64 oracle tree-code on
+a bounded sample of the same workload on the host cores.
+
+`--impl reference` times the FP64 oracle (the reference arm of this build) on
+the host cores instead.  Under torchrun each rank is an independent replica
+(no collective in the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particles/s per full tree step at equal 99th-pct force error, plain vs learned"
+UNIT = "particles/s"
+FLOP_PC, FLOP_PP = 65, 23           # flops per body-cell / body-body interaction
+SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+KERNELS_PER_STEP = 19               # reset, kick+drift, keys, 8 sort passes, reorder,
+                                    # 3 build, multipoles, open radius, walk, kick
+WALK_TRAFFIC_PER_LAUNCH = None      # dram bytes per walk launch from the committed ncu capture
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=int, default=1 << 20)
+    p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--theta", type=float, default=0.75)
+    p.add_argument("--eps", type=float, default=0.005)
+    p.add_argument("--dt", type=float, default=1.0 / 128)
+    p.add_argument("--ncrit", type=int, default=32)
+    p.add_argument("--nleaf", type=int, default=16)
+    p.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def config(a, world):
+    return {"workload": f"Plummer sphere N={a.n} (Henon units, seed {a.seed}), eps={a.eps}, "
+                        f"theta={a.theta}, KDK leapfrog dt={a.dt:g}, full rebuild every step",
+            "n": a.n, "theta": a.theta, "eps": a.eps, "dt": a.dt, "nleaf": a.nleaf,
+            "ncrit": a.ncrit, "l2": "flushed between timed steps (256 MiB write)",
+            "parallelism": f"replicas x{world}"}
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9 or not c[0].isdigit() or int(c[0]) != self.index:
+                continue
+            try:
+                sm.append(float(c[1])); mx.append(float(c[2])); power.append(float(c[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, c[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def gpu_index(local_rank: int) -> int:
+    v = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    parts = [x for x in v.split(",") if x.strip()]
+    if parts and local_rank < len(parts) and parts[local_rank].strip().isdigit():
+        return int(parts[local_rank])
+    return local_rank
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_sample(bodies, theta, eps, nleaf, ncrit, budget_s, seed=0):
+    """FP64 oracle tree-code on a bounded sample: the whole tree (domain, keys,
+    sort, build, groups, moments) for all bodies, the walk for a random sample
+    of groups; the step time is extrapolated to all bodies."""
+    import numpy as np
+    import oracle
+    t0 = time.perf_counter()
+    mn, S = oracle.domain(bodies.pos)
+    k = oracle.keys(bodies.pos, mn, S)
+    perm = oracle.sort(k)
+    sk, sp, sm = k[perm], bodies.pos[perm], bodies.mass[perm]
+    tree = oracle.build_tree(sk, nleaf)
+    gb, gc = oracle.groups(tree, ncrit)
+    M, com, Q = oracle.moments(tree, sp, sm)
+    ro = oracle.open_radius(tree, sk, mn, S, com, theta)
+    t_tree = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    frac, t_walk, nb = 0.002, 0.0, 0
+    order = rng.permutation(gb.shape[0])
+    used = 0
+    while True:
+        take = max(1, int(frac * gb.shape[0]))
+        sel = np.sort(order[used:used + take])
+        if sel.size == 0:
+            break
+        t1 = time.perf_counter()
+        oracle.walk(sp, sm, tree, M, com, Q, ro, gb[sel], gc[sel], eps)
+        t_walk += time.perf_counter() - t1
+        nb += int(gc[sel].sum())
+        used += take
+        if t_tree + t_walk > 0.5 * budget_s or used >= gb.shape[0]:
+            break
+        frac *= 2
+    n = bodies.n
+    t_step = t_tree + t_walk * n / max(nb, 1)
+    return {"value": n / t_step, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"full tree build of all {n} bodies ({t_tree:.2f} s) + walk of {used} random "
+                      f"groups ({nb} bodies, {t_walk:.2f} s), extrapolated to {n} bodies",
+            "t_step_s": t_step}
+
+
+# ---------------------------------------------------------------------------
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    from paper_1204_2280_gb300 import workloads as W
+    b = W.plummer(a.n, a.seed)
+    per_step = max(4.0, min(a.cpu_budget, 150.0 / max(1, a.steps + a.warmup)))
+    for _ in range(a.warmup):
+        cpu_oracle_sample(b, a.theta, a.eps, a.nleaf, a.ncrit, per_step)
+    ts = []
+    samp = None
+    for s in range(a.steps):
+        samp = cpu_oracle_sample(b, a.theta, a.eps, a.nleaf, a.ncrit, per_step, seed=s)
+        ts.append(samp["t_step_s"])
+    t = sum(ts)
+    value = a.n * a.steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(a, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": samp["cores"], "kind": "oracle",
+                             "sample": samp["sample"] + f"; {a.steps} timed samples"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import paper_1204_2280_gb300 as B
+    from paper_1204_2280_gb300 import workloads as W
+    import ctypes as C
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(dev)            # all torch and library work on one stream
+    torch.cuda.set_stream(stream)
+    b = W.plummer(a.n, a.seed)
+    n = b.n
+    bz = B.Bonsai(B.Config(nleaf=a.nleaf, ncrit=a.ncrit), stream=stream)
+    bz.set_bodies(torch.from_numpy(b.pos).to(dev), torch.from_numpy(b.mass).to(dev),
+                  torch.from_numpy(b.vel).to(dev))
+    bz.build().multipoles().forces(a.theta, a.eps)
+    B.bonsai_set_params(bz.ctx, a.theta, a.eps)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(a.warmup):
+        bz.step(a.dt)
+    bz.sync()
+    tot = (C.c_ulonglong * 2)()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(gpu_index(local_rank))
+    barrier()
+    sampler.start()
+    time.sleep(0.3)
+    step_ms, stage_ms, flops, npc, npp = [], [], [], [], []
+    t_wall0 = time.perf_counter()
+    for _ in range(a.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bz.step(a.dt)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        stage_ms.append(B.bonsai_get_stage_times(bz.ctx))
+        B._check(bz.ctx, B.lib().bonsai_get_counts(bz.ctx, None, None, tot))
+        npc.append(int(tot[0])); npp.append(int(tot[1]))
+        flops.append(FLOP_PC * int(tot[0]) + FLOP_PP * int(tot[1]))
+    t_wall = time.perf_counter() - t_wall0
+    barrier()
+    clocks = sampler.stop()
+    bz.sync()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * n * a.steps / (total_ms / 1e3)
+    stages = np.array(stage_ms).sum(0)
+    walk_ms = float(stages[B.STAGES.index("walk")])
+    achieved = sum(flops) / (walk_ms / 1e3) / 1e12
+
+    # End to end through the C ABI with host buffers.
+    e2e = None
+    if not a.no_e2e:
+        hp = torch.from_numpy(b.pos).pin_memory().numpy()
+        hm = torch.from_numpy(b.mass).pin_memory().numpy()
+        hv = torch.from_numpy(b.vel).pin_memory().numpy()
+        ha = torch.empty((n, 3), dtype=torch.float32).pin_memory().numpy()
+        hpot = torch.empty(n, dtype=torch.float32).pin_memory().numpy()
+        ts = []
+        for s in range(a.steps + 1):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            bz.set_bodies(hp, hm, hv)
+            bz.build().multipoles().forces(a.theta, a.eps, ha, hpot)
+            ts.append(time.perf_counter() - t0)
+        ts = ts[1:]
+        e2e = {"value": n * len(ts) / sum(ts), "unit": UNIT, "h2d_bytes_per_step": 28 * n,
+               "d2h_bytes_per_step": 16 * n,
+               "what": "set_bodies(host pos, mass, vel) + build + multipoles + forces(host acc, pot)"}
+    bz.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = cpu_oracle_sample(b, a.theta, a.eps, a.nleaf, a.ncrit, a.cpu_budget)
+        cpu.pop("t_step_s")
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config(a, world),
+            "roofline": {"bound": "alu", "kernel": "k_walk", "achieved": achieved,
+                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                         "traffic": WALK_TRAFFIC_PER_LAUNCH,
+                         "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
+                         "flops_basis": f"{FLOP_PC} per body-cell + {FLOP_PP} per body-body interaction"},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": KERNELS_PER_STEP * a.steps,
+            "clocks": clocks,
+            "stages_ms_per_step": {s: float(v) / a.steps for s, v in zip(B.STAGES, stages)},
+            "interactions_per_body": {"pc": sum(npc) / (n * a.steps), "pp": sum(npp) / (n * a.steps)},
+            "interactions_per_s": (sum(npc) + sum(npp)) / (walk_ms / 1e3),
+            "wall_s_timed_loop": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    run_ours(a, rank, world, local_rank)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * bonsai.h -- C ABI of the GB300 Barnes-Hut tree-code library (libbonsai.so).
+ *
+ * The library runs the per-step hot path of "Bonsai: A GPU Tree-Code"
+ * (Bedorf, Gaburov & Portegies Zwart) entirely on one GPU: Morton keys and
+ * radix sort of the bodies along the space-filling curve, reordering
+ * ("moving"), octree construction, multipole moments and the group-wise
+ * tree-traverse under the opening angle theta (paper Sect. 2 and Fig. 1),
+ * plus the shared-time-step leapfrog the paper's block-time-step discussion
+ * builds on (Sect. 1 and 3).
+ *
+ * Conventions (all entry points):
+ *  - Return value: BONSAI_OK (0) or a negative BONSAI_ERR_* code; the text of
+ *    the last error of a context is returned by bonsai_last_error().  No entry
+ *    point aborts the process and no kernel traps.
+ *  - Pointers: plain host or device pointers and element counts.  The caller
+ *    owns every buffer it passes; the library copies inputs in and writes
+ *    outputs out, and keeps no reference to caller memory after a call.
+ *    `on_device` = 1 means the pointers are CUDA device pointers on the
+ *    context's device, ordered on the context's stream; 0 means host memory
+ *    (the call then synchronises the stream before returning).
+ *  - Units: G = 1.  Positions, velocities and masses are float32.
+ *  - Order: every per-body output is in the caller's body order (the order of
+ *    the last bonsai_set_bodies call); the library sorts bodies internally.
+ *  - Memory: the context allocates and owns all device memory it uses
+ *    (cudaMalloc at create / set_bodies; reused while N does not grow) and
+ *    frees it in bonsai_destroy.
+ *  - Threads: a context may be used by one host thread at a time.
+ */
+#ifndef BONSAI_H
+#define BONSAI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BONSAI_OK              0
+#define BONSAI_ERR_INVALID_ARG (-1)  /* bad pointer, size or parameter        */
+#define BONSAI_ERR_OOM         (-2)  /* device allocation failed              */
+#define BONSAI_ERR_CUDA        (-3)  /* a CUDA runtime call failed            */
+#define BONSAI_ERR_CAPACITY    (-4)  /* a walk list or cell capacity overflow */
+#define BONSAI_ERR_TIMEOUT     (-5)  /* a bounded device-side wait gave up    */
+#define BONSAI_ERR_NAN         (-6)  /* non-finite positions detected         */
+#define BONSAI_ERR_NOT_READY   (-7)  /* stage called before its inputs exist  */
+
+typedef struct bonsai_ctx bonsai_ctx;
+
+/* Tuning knobs; a zero field selects the default shown. */
+typedef struct {
+    int nleaf;            /* max bodies per leaf cell (16)                    */
+    int ncrit;            /* max bodies per walk group, 1..32 (32)            */
+    int walk_warps;       /* warps per walk thread block, 1..8 (4)            */
+    int list_capacity;    /* walk stack entries per warp, 64..8192 (256)      */
+    int use_graph;        /* -1: direct launches; else replay bonsai_step
+                             from a CUDA graph (default)                      */
+    int reserved[3];
+    long long max_spin;   /* bound on every device-side wait, polls (1<<24)   */
+} bonsai_config;
+
+/* Create a context on the current CUDA device.  cfg may be NULL (defaults).
+ * cuda_stream is a cudaStream_t (not the legacy NULL stream) to order all
+ * work on, or NULL for a blocking stream owned by the context (ordered with
+ * the legacy default stream).  *out receives the context (NULL on failure). */
+int bonsai_create(bonsai_ctx **out, const bonsai_config *cfg, void *cuda_stream);
+
+/* Free every device resource of the context.  NULL is ignored. */
+void bonsai_destroy(bonsai_ctx *ctx);
+
+/* Load N bodies: pos (N x 3, xyz interleaved), mass (N), vel (N x 3, or
+ * NULL for zero velocities).  Invalidates the tree and the forces.
+ * N must be in [1, 2^26]. */
+int bonsai_set_bodies(bonsai_ctx *ctx, const float *pos, const float *mass,
+                      const float *vel, long long n, int on_device);
+
+/* Sect. 2 "sorting", "moving", "tree-construction": domain cube, 63-bit
+ * Morton keys (21 bits per axis, x in the lowest bit of each triple), stable
+ * LSD radix sort, body reorder, octree (cells with more than nleaf bodies
+ * split into their non-empty octants; breadth-first, key order within a
+ * level) and walk groups (cells with at most ncrit bodies whose parent has
+ * more). */
+int bonsai_build(bonsai_ctx *ctx);
+
+/* Sect. 2 "multipole moments": per cell mass, centre of mass and traceless
+ * quadrupole Q_ij = sum m (3 y_i y_j - |y|^2 delta_ij), y = x - com, computed
+ * from the leaves up (FP64 for the top four levels).  Requires bonsai_build. */
+int bonsai_multipoles(bonsai_ctx *ctx);
+
+/* Sect. 2 "tree-traverse": softened accelerations and potentials under the
+ * opening angle theta (a cell is opened when the squared distance from its
+ * com to the group's bounding box is below (l/theta + delta)^2, l its side,
+ * delta the com's offset from its centre) with Plummer softening eps.
+ * acc: N x 3, pot: N (either may be NULL), caller order.  Requires
+ * bonsai_multipoles.  0 < theta <= 1.15, eps > 0. */
+int bonsai_forces(bonsai_ctx *ctx, float theta, float eps, float *acc,
+                  float *pot, int on_device);
+
+/* One kick-drift-kick leapfrog step of length dt for all bodies: the first
+ * kick uses the accelerations of the last bonsai_forces/bonsai_step (if there
+ * are none, they are computed first at that call's theta/eps, default 0.75 /
+ * 0.01), then the drift, the full rebuild (keys, sort, reorder, build,
+ * multipoles), the walk and the second kick.  No host synchronisation. */
+int bonsai_step(bonsai_ctx *ctx, float dt);
+
+/* Sets theta and eps for bonsai_step without computing forces. */
+int bonsai_set_params(bonsai_ctx *ctx, float theta, float eps);
+
+/* Copy the current state out in caller order: pos (N x 3), vel (N x 3),
+ * either may be NULL. */
+int bonsai_get_bodies(bonsai_ctx *ctx, float *pos, float *vel, int on_device);
+
+/* FP64 diagnostics of the current state: out[8] = {K, W, E, Px, Py, Pz,
+ * Mtot, Lz} with K = sum m v^2/2, W = sum m phi/2 (phi of the last walk),
+ * E = K + W, P = sum m v, Lz = sum m (x v_y - y v_x).  Host output. */
+int bonsai_diagnostics(bonsai_ctx *ctx, double out[8]);
+
+/* Synchronise the context's stream and return (and clear) the device status:
+ * BONSAI_OK, BONSAI_ERR_CAPACITY, BONSAI_ERR_TIMEOUT or BONSAI_ERR_NAN. */
+int bonsai_sync(bonsai_ctx *ctx);
+
+/* Device time of each stage of the last bonsai_step in milliseconds, from
+ * CUDA events recorded on the context's stream between the stages (also when
+ * the step is replayed from its graph).  ms[0] first kick + drift + domain,
+ * [1] keys, [2] sort, [3] reorder, [4] tree build, [5] multipoles, [6] walk
+ * (opening radii + traverse), [7] second kick.  Synchronises; writes
+ * min(n, 8) values and returns that count (negative on error). */
+int bonsai_get_stage_times(bonsai_ctx *ctx, float *ms, int n);
+
+/* ---- introspection (copies to caller-owned HOST buffers; synchronises) -- */
+
+/* Number of bodies, cells and groups of the current tree. */
+int bonsai_get_sizes(bonsai_ctx *ctx, long long *n, long long *ncells,
+                     long long *ngroups);
+
+/* Domain of the last build: mn[3] (per-axis float minimum) and side[1]. */
+int bonsai_get_domain(bonsai_ctx *ctx, float mn[3], float side[1]);
+
+/* Sorted keys (N) and the sort permutation perm (N): sorted position i holds
+ * caller body perm[i]. */
+int bonsai_get_keys(bonsai_ctx *ctx, uint64_t *keys, uint32_t *perm);
+
+/* Cells in breadth-first order (ncells each): first body (sorted order),
+ * body count, first child (0 for leaves), child count, level. */
+int bonsai_get_tree(bonsai_ctx *ctx, int32_t *body_begin, int32_t *body_count,
+                    int32_t *child_begin, int32_t *nchild, int32_t *level);
+
+/* Groups in key order (ngroups each): first body (sorted order), count. */
+int bonsai_get_groups(bonsai_ctx *ctx, int32_t *begin, int32_t *count);
+
+/* Moments per cell: mono (ncells x 4: com xyz, M), quad (ncells x 6:
+ * Qxx Qyy Qzz Qxy Qxz Qyz). */
+int bonsai_get_moments(bonsai_ctx *ctx, float *mono, float *quad);
+
+/* Interaction counts of the last walk per body, caller order: n_pc
+ * (body-cell) and n_pp (body-body, self excluded); and the totals over all
+ * bodies in tot[2].  Any pointer may be NULL. */
+int bonsai_get_counts(bonsai_ctx *ctx, uint32_t *n_pc, uint32_t *n_pp,
+                      unsigned long long tot[2]);
+
+/* Text of the last error of ctx (or of the last failed bonsai_create when
+ * ctx is NULL).  Valid until the next call on the context. */
+const char *bonsai_last_error(const bonsai_ctx *ctx);
+
+/* Library version string. */
+const char *bonsai_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BONSAI_H */

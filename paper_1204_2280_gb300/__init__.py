@@ -1,0 +1,293 @@
+"""GB300 Barnes-Hut tree-code ("Bonsai: A GPU Tree-Code", Bedorf, Gaburov &
+Portegies Zwart) -- Python binding of libbonsai.so.
+
+Argument marshalling only: every stage (keys, sort, reorder, tree build,
+multipoles, walk, leapfrog, diagnostics) runs in the library's CUDA kernels.
+The functions carry the C ABI's names (include/bonsai.h) and accept torch
+tensors (CUDA tensors are passed as device pointers, CPU tensors as host
+pointers) or numpy arrays (host).  There is no CPU fallback: if the compiled
+library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbonsai.so")
+_lib = None
+
+BONSAI_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "CAPACITY", -5: "TIMEOUT", -6: "NAN",
+          -7: "NOT_READY"}
+
+# Entry points declared in include/bonsai.h (checked by the CPU tests).
+EXPORTS = ["bonsai_create", "bonsai_destroy", "bonsai_set_bodies", "bonsai_build",
+           "bonsai_multipoles", "bonsai_forces", "bonsai_step", "bonsai_set_params",
+           "bonsai_get_bodies", "bonsai_diagnostics", "bonsai_sync", "bonsai_get_sizes",
+           "bonsai_get_domain", "bonsai_get_keys", "bonsai_get_tree", "bonsai_get_groups",
+           "bonsai_get_moments", "bonsai_get_counts", "bonsai_last_error", "bonsai_version",
+           "bonsai_get_stage_times"]
+
+STAGES = ["kick_drift_domain", "keys", "sort", "reorder", "build", "multipoles", "walk", "kick"]
+
+
+class BonsaiError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [("nleaf", C.c_int), ("ncrit", C.c_int), ("walk_warps", C.c_int),
+                ("list_capacity", C.c_int), ("use_graph", C.c_int), ("reserved", C.c_int * 3),
+                ("max_spin", C.c_longlong)]
+
+
+def build(force: bool = False) -> str:
+    from . import builder as _b
+    return _b.build(force=force)
+
+
+def lib():
+    """Load libbonsai.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1204_2280_gb300.build()")
+        L = C.CDLL(LIB_PATH)
+        p, i, f, ll = C.c_void_p, C.c_int, C.c_float, C.c_longlong
+        L.bonsai_create.argtypes = [C.POINTER(p), C.POINTER(Config), p]
+        L.bonsai_destroy.argtypes = [p]
+        L.bonsai_destroy.restype = None
+        L.bonsai_set_bodies.argtypes = [p, p, p, p, ll, i]
+        L.bonsai_build.argtypes = [p]
+        L.bonsai_multipoles.argtypes = [p]
+        L.bonsai_forces.argtypes = [p, f, f, p, p, i]
+        L.bonsai_step.argtypes = [p, f]
+        L.bonsai_set_params.argtypes = [p, f, f]
+        L.bonsai_get_bodies.argtypes = [p, p, p, i]
+        L.bonsai_diagnostics.argtypes = [p, p]
+        L.bonsai_sync.argtypes = [p]
+        L.bonsai_get_sizes.argtypes = [p, p, p, p]
+        L.bonsai_get_domain.argtypes = [p, p, p]
+        L.bonsai_get_keys.argtypes = [p, p, p]
+        L.bonsai_get_tree.argtypes = [p, p, p, p, p, p]
+        L.bonsai_get_groups.argtypes = [p, p, p]
+        L.bonsai_get_moments.argtypes = [p, p, p]
+        L.bonsai_get_counts.argtypes = [p, p, p, p]
+        L.bonsai_last_error.argtypes = [p]
+        L.bonsai_last_error.restype = C.c_char_p
+        L.bonsai_version.restype = C.c_char_p
+        L.bonsai_get_stage_times.argtypes = [p, p, i]
+        _lib = L
+    return _lib
+
+
+def _check(ctx, rc: int):
+    if rc != BONSAI_OK:
+        msg = lib().bonsai_last_error(ctx)
+        raise BonsaiError(rc, msg.decode() if msg else "")
+
+
+def _buf(x, dtype=None):
+    """(pointer, on_device) of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None, None
+    if isinstance(x, np.ndarray):
+        if dtype is not None:
+            assert x.dtype == dtype, (x.dtype, dtype)
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data, 0
+    import torch
+    assert isinstance(x, torch.Tensor) and x.is_contiguous()
+    return x.data_ptr(), (1 if x.is_cuda else 0)
+
+
+def _same_side(*flags):
+    fl = {f for f in flags if f is not None}
+    if len(fl) > 1:
+        raise ValueError("mix of device and host buffers in one call")
+    return fl.pop() if fl else 0
+
+
+# ---------------------------------------------------------------------------
+# C ABI, one function each
+# ---------------------------------------------------------------------------
+
+def bonsai_create(cfg: Config | None = None, stream=None):
+    """Create a context on the current device; stream: a torch.cuda.Stream, a
+    raw cudaStream_t int, or None for torch's current stream."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    ctx = C.c_void_p()
+    rc = lib().bonsai_create(C.byref(ctx), C.byref(cfg) if cfg is not None else None,
+                             C.c_void_p(int(stream)) if stream else None)
+    _check(None, rc)
+    return ctx
+
+
+def bonsai_destroy(ctx):
+    lib().bonsai_destroy(ctx)
+
+
+def bonsai_set_bodies(ctx, pos, mass, vel=None):
+    (pp, d0), (mp, d1), (vp, d2) = _buf(pos, np.float32), _buf(mass, np.float32), _buf(vel, np.float32)
+    n = int(mass.shape[0])
+    _check(ctx, lib().bonsai_set_bodies(ctx, pp, mp, vp, n, _same_side(d0, d1, d2)))
+
+
+def bonsai_build(ctx):
+    _check(ctx, lib().bonsai_build(ctx))
+
+
+def bonsai_multipoles(ctx):
+    _check(ctx, lib().bonsai_multipoles(ctx))
+
+
+def bonsai_forces(ctx, theta: float, eps: float, acc=None, pot=None):
+    (ap, d0), (pp, d1) = _buf(acc, np.float32), _buf(pot, np.float32)
+    _check(ctx, lib().bonsai_forces(ctx, theta, eps, ap, pp, _same_side(d0, d1)))
+
+
+def bonsai_step(ctx, dt: float):
+    _check(ctx, lib().bonsai_step(ctx, dt))
+
+
+def bonsai_set_params(ctx, theta: float, eps: float):
+    _check(ctx, lib().bonsai_set_params(ctx, theta, eps))
+
+
+def bonsai_get_bodies(ctx, pos=None, vel=None):
+    (pp, d0), (vp, d1) = _buf(pos, np.float32), _buf(vel, np.float32)
+    _check(ctx, lib().bonsai_get_bodies(ctx, pp, vp, _same_side(d0, d1)))
+
+
+def bonsai_diagnostics(ctx) -> np.ndarray:
+    out = np.zeros(8)
+    _check(ctx, lib().bonsai_diagnostics(ctx, out.ctypes.data))
+    return out
+
+
+def bonsai_sync(ctx):
+    _check(ctx, lib().bonsai_sync(ctx))
+
+
+def bonsai_get_sizes(ctx) -> tuple[int, int, int]:
+    a, b, c = C.c_longlong(), C.c_longlong(), C.c_longlong()
+    _check(ctx, lib().bonsai_get_sizes(ctx, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
+def bonsai_get_domain(ctx):
+    mn = np.zeros(3, np.float32)
+    side = np.zeros(1, np.float32)
+    _check(ctx, lib().bonsai_get_domain(ctx, mn.ctypes.data, side.ctypes.data))
+    return mn, float(side[0])
+
+
+def bonsai_get_keys(ctx):
+    n, _, _ = bonsai_get_sizes(ctx)
+    keys = np.zeros(n, np.uint64)
+    perm = np.zeros(n, np.uint32)
+    _check(ctx, lib().bonsai_get_keys(ctx, keys.ctypes.data, perm.ctypes.data))
+    return keys, perm
+
+
+def bonsai_get_tree(ctx) -> dict:
+    _, nc, _ = bonsai_get_sizes(ctx)
+    arr = [np.zeros(nc, np.int32) for _ in range(5)]
+    _check(ctx, lib().bonsai_get_tree(ctx, *[a.ctypes.data for a in arr]))
+    return dict(zip(["body_begin", "body_count", "child_begin", "nchild", "level"], arr))
+
+
+def bonsai_get_groups(ctx):
+    _, _, ng = bonsai_get_sizes(ctx)
+    b = np.zeros(ng, np.int32)
+    c = np.zeros(ng, np.int32)
+    _check(ctx, lib().bonsai_get_groups(ctx, b.ctypes.data, c.ctypes.data))
+    return b, c
+
+
+def bonsai_get_moments(ctx):
+    _, nc, _ = bonsai_get_sizes(ctx)
+    mono = np.zeros((nc, 4), np.float32)
+    quad = np.zeros((nc, 6), np.float32)
+    _check(ctx, lib().bonsai_get_moments(ctx, mono.ctypes.data, quad.ctypes.data))
+    return mono, quad
+
+
+def bonsai_get_counts(ctx):
+    n, _, _ = bonsai_get_sizes(ctx)
+    a = np.zeros(n, np.uint32)
+    b = np.zeros(n, np.uint32)
+    tot = (C.c_ulonglong * 2)()
+    _check(ctx, lib().bonsai_get_counts(ctx, a.ctypes.data, b.ctypes.data, tot))
+    return a, b, (int(tot[0]), int(tot[1]))
+
+
+def bonsai_get_stage_times(ctx) -> np.ndarray:
+    ms = np.zeros(len(STAGES), np.float32)
+    rc = lib().bonsai_get_stage_times(ctx, ms.ctypes.data, ms.shape[0])
+    if rc < 0:
+        _check(ctx, rc)
+    return ms
+
+
+def bonsai_version() -> str:
+    return lib().bonsai_version().decode()
+
+
+class Bonsai:
+    """Owning wrapper: Bonsai(cfg).set_bodies(...).build().multipoles() ..."""
+
+    def __init__(self, cfg: Config | None = None, stream=None, **kw):
+        if cfg is None and kw:
+            cfg = Config(**kw)
+        self.ctx = bonsai_create(cfg, stream)
+
+    def close(self):
+        if self.ctx:
+            bonsai_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_bodies(self, pos, mass, vel=None):
+        bonsai_set_bodies(self.ctx, pos, mass, vel)
+        return self
+
+    def build(self):
+        bonsai_build(self.ctx)
+        return self
+
+    def multipoles(self):
+        bonsai_multipoles(self.ctx)
+        return self
+
+    def forces(self, theta, eps, acc=None, pot=None):
+        bonsai_forces(self.ctx, theta, eps, acc, pot)
+        return self
+
+    def step(self, dt):
+        bonsai_step(self.ctx, dt)
+        return self
+
+    def sync(self):
+        bonsai_sync(self.ctx)
+        return self

@@ -1,0 +1,493 @@
+// api.cu -- the C ABI of libbonsai (declared in include/bonsai.h).
+//
+// All device memory of a context comes from one cudaMalloc arena sized for
+// the body count; every stage is a kernel launch ordered on the context's
+// stream; bonsai_step contains no host synchronisation and is replayed from a
+// CUDA graph.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace bonsai;
+
+struct bonsai_ctx {
+    Ctx c;
+};
+
+static thread_local std::string g_create_err;
+
+static int fail(bonsai_ctx *ctx, int code, const std::string &what, cudaError_t e = cudaSuccess) {
+    std::string s = what;
+    if (e != cudaSuccess) {
+        s += ": ";
+        s += cudaGetErrorString(e);
+    }
+    if (ctx) ctx->c.err = s; else g_create_err = s;
+    return code;
+}
+
+#define CK(call)                                                               \
+    do {                                                                       \
+        cudaError_t _e = (call);                                               \
+        if (_e != cudaSuccess) return fail(ctx, BONSAI_ERR_CUDA, #call, _e);   \
+    } while (0)
+
+namespace {
+
+struct Arena {
+    size_t off = 0;
+    template <class T> void take(T *&p, size_t count, std::vector<std::pair<void **, size_t>> &plan) {
+        off = (off + 255) & ~size_t(255);
+        plan.push_back({(void **)&p, off});
+        off += count * sizeof(T);
+    }
+};
+
+void free_bodies(Ctx &c) {
+    if (c.step_graph) { cudaGraphExecDestroy(c.step_graph); c.step_graph = nullptr; }
+    if (c.pos4) cudaFree(c.pos4);
+    c.pos4 = nullptr;
+    c.ncap = 0;
+}
+
+cudaError_t alloc_bodies(Ctx &c, long long n) {
+    free_bodies(c);
+    const long long ntiles = (n + SORT_TILE - 1) / SORT_TILE;
+    const long long nbb = (n + BUILD_THREADS - 1) / BUILD_THREADS;
+    // Cells: at most n leaves and n/(nleaf+1) internal cells per level.
+    const long long ccap = n + (long long)MAX_LEVEL * (n / (c.nleaf + 1)) + 64;
+    std::vector<std::pair<void **, size_t>> plan;
+    Arena a;
+    a.take(c.pos4, n, plan); a.take(c.vel4, n, plan); a.take(c.acc4, n, plan);
+    a.take(c.pos4_alt, n, plan); a.take(c.vel4_alt, n, plan);
+    a.take(c.id, n, plan); a.take(c.id_alt, n, plan);
+    a.take(c.keys, n, plan); a.take(c.keys_alt, n, plan);
+    a.take(c.vals, n, plan); a.take(c.vals_alt, n, plan);
+    a.take(c.tile_status, (size_t)SORT_PASSES * ntiles * 256, plan);
+    a.take(c.blockcount, (size_t)NROWS * nbb, plan);
+    a.take(c.cell_body, ccap, plan); a.take(c.cell_link, ccap, plan);
+    a.take(c.cell_level, ccap, plan); a.take(c.cell_parent, ccap, plan);
+    a.take(c.cell_done, ccap, plan);
+    a.take(c.mono, ccap, plan); a.take(c.quadA, ccap, plan); a.take(c.quadB, ccap, plan);
+    a.take(c.test, ccap, plan); a.take(c.delta, ccap, plan);
+    a.take(c.shadow, 10 * 585, plan);
+    a.take(c.groups, n, plan); a.take(c.counts, n, plan);
+    a.take(c.stage, 7 * (size_t)n, plan);
+    char *base = nullptr;
+    cudaError_t e = cudaMalloc(&base, a.off);
+    if (e != cudaSuccess) return e;
+    for (auto &p : plan) *p.first = base + p.second;
+    c.ncap = n;
+    c.ntiles = (int)ntiles;
+    c.nbblocks = (int)nbb;
+    c.ccap = ccap;
+    return cudaMemsetAsync(base, 0, a.off, c.stream);
+}
+
+// keys -> sort -> reorder -> build; the domain accumulators must hold the
+// bounding box of the pre-sort positions.
+cudaError_t pipeline_tree(Ctx &c) {
+    cudaError_t e;
+    if ((e = launch_keys(c)) != cudaSuccess) return e;
+    if ((e = launch_sort(c)) != cudaSuccess) return e;
+    if ((e = launch_reorder(c)) != cudaSuccess) return e;
+    return launch_build(c);
+}
+
+cudaError_t pipeline_forces(Ctx &c, float theta, float eps) {
+    cudaError_t e;
+    if ((e = launch_open_radius(c, theta)) != cudaSuccess) return e;
+    return launch_walk(c, eps);
+}
+
+// One kick-drift-kick step; events between the stages give per-stage times.
+cudaError_t pipeline_step(Ctx &c, float dt) {
+    cudaError_t e;
+#define STAGE(i, call)                                                  \
+    if ((e = cudaEventRecord(c.ev[i], c.stream)) != cudaSuccess) return e; \
+    if ((e = (call)) != cudaSuccess) return e;
+    STAGE(0, launch_reset(c));
+    if ((e = launch_kick_drift_bbox(c, dt)) != cudaSuccess) return e;
+    STAGE(1, launch_keys(c));
+    STAGE(2, launch_sort(c));
+    STAGE(3, launch_reorder(c));
+    STAGE(4, launch_build(c));
+    STAGE(5, launch_multipoles(c));
+    STAGE(6, pipeline_forces(c, c.theta, c.eps));
+    STAGE(7, launch_kick(c, dt));
+#undef STAGE
+    return cudaEventRecord(c.ev[8], c.stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *bonsai_version(void) { return "bonsai-gb300 0.1 (sm_103a)"; }
+
+const char *bonsai_last_error(const bonsai_ctx *ctx) {
+    return ctx ? ctx->c.err.c_str() : g_create_err.c_str();
+}
+
+int bonsai_create(bonsai_ctx **out, const bonsai_config *cfg, void *cuda_stream) {
+    bonsai_ctx *ctx = nullptr;
+    if (!out) return fail(nullptr, BONSAI_ERR_INVALID_ARG, "bonsai_create: out is NULL");
+    *out = nullptr;
+    ctx = new (std::nothrow) bonsai_ctx();
+    if (!ctx) return fail(nullptr, BONSAI_ERR_OOM, "bonsai_create: host allocation failed");
+    Ctx &c = ctx->c;
+    if (cfg) {
+        if (cfg->nleaf) c.nleaf = cfg->nleaf;
+        if (cfg->ncrit) c.ncrit = cfg->ncrit;
+        if (cfg->list_capacity) c.list_capacity = cfg->list_capacity;
+        if (cfg->walk_warps) c.walk_warps = cfg->walk_warps;
+        if (cfg->max_spin) c.max_spin = cfg->max_spin;
+        if (cfg->use_graph < 0) c.use_graph = 0;
+    }
+    if (c.nleaf < 1 || c.nleaf > 64 || c.ncrit < 1 || c.ncrit > 32 || c.list_capacity < 64 ||
+        c.list_capacity > 8192 || c.max_spin < 1 || c.walk_warps < 1 || c.walk_warps > 8) {
+        int r = fail(nullptr, BONSAI_ERR_INVALID_ARG,
+                     "bonsai_create: need 1<=nleaf<=64, 1<=ncrit<=32, 64<=list_capacity<=8192, "
+                     "1<=walk_warps<=8");
+        delete ctx;
+        return r;
+    }
+    c.list_capacity = (c.list_capacity + 31) & ~31;   // keeps per-warp shared rings 16-byte aligned
+    cudaError_t e = cudaGetDevice(&c.device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.device);
+    if (e == cudaSuccess) {
+        if (cuda_stream) c.stream = (cudaStream_t)cuda_stream;
+        else { e = cudaStreamCreate(&c.stream); c.own_stream = true; }   // blocking: ordered with the legacy stream
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&c.st, sizeof(DevState));
+    if (e == cudaSuccess) e = cudaMallocHost(&c.st_host, sizeof(DevState));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c.st, 0, sizeof(DevState), c.stream);
+    for (int i = 0; i <= Ctx::NSTAGE && e == cudaSuccess; i++) e = cudaEventCreate(&c.ev[i]);
+    if (e != cudaSuccess) {
+        int r = fail(nullptr, BONSAI_ERR_CUDA, "bonsai_create", e);
+        bonsai_destroy(ctx);
+        return r;
+    }
+    *out = ctx;
+    return BONSAI_OK;
+}
+
+void bonsai_destroy(bonsai_ctx *ctx) {
+    if (!ctx) return;
+    Ctx &c = ctx->c;
+    if (c.stream) cudaStreamSynchronize(c.stream);
+    free_bodies(c);
+    if (c.st) cudaFree(c.st);
+    if (c.st_host) cudaFreeHost(c.st_host);
+    for (int i = 0; i <= Ctx::NSTAGE; i++)
+        if (c.ev[i]) cudaEventDestroy(c.ev[i]);
+    if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
+    delete ctx;
+}
+
+int bonsai_set_bodies(bonsai_ctx *ctx, const float *pos, const float *mass, const float *vel,
+                      long long n, int on_device) {
+    if (!ctx) return BONSAI_ERR_INVALID_ARG;
+    Ctx &c = ctx->c;
+    if (!pos || !mass || n < 1 || n > (1ll << 26))
+        return fail(ctx, BONSAI_ERR_INVALID_ARG, "bonsai_set_bodies: need pos, mass and 1 <= n <= 2^26");
+    if (n > c.ncap) CK(alloc_bodies(c, n));
+    if (c.step_graph) { cudaGraphExecDestroy(c.step_graph); c.step_graph = nullptr; }
+    c.graph_n = -1;
+    c.n = n;
+    const float *p = pos, *m = mass, *v = vel;
+    if (!on_device) {
+        float *s = c.stage;
+        CK(cudaMemcpyAsync(s, pos, 12 * (size_t)n, cudaMemcpyHostToDevice, c.stream));
+        CK(cudaMemcpyAsync(s + 3 * n, mass, 4 * (size_t)n, cudaMemcpyHostToDevice, c.stream));
+        if (vel) CK(cudaMemcpyAsync(s + 4 * n, vel, 12 * (size_t)n, cudaMemcpyHostToDevice, c.stream));
+        p = s; m = s + 3 * n; v = vel ? s + 4 * n : nullptr;
+    }
+    CK(launch_pack(c, p, m, v));
+    if (!on_device) CK(cudaStreamSynchronize(c.stream));
+    // The state now lives in the pre-sort (*_alt) arrays; nothing derived
+    // from earlier bodies stays valid.
+    c.have_bodies = true;
+    c.built = c.moments_ready = c.have_acc = false;
+    c.err.clear();
+    return BONSAI_OK;
+}
+
+int bonsai_build(bonsai_ctx *ctx) {
+    if (!ctx) return BONSAI_ERR_INVALID_ARG;
+    Ctx &c = ctx->c;
+    if (!c.have_bodies) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_build: no bodies");
+    if (c.built) {
+        // rebuild from the current (sorted) state: copy it to the pre-sort arrays
+        CK(cudaMemcpyAsync(c.pos4_alt, c.pos4, 16 * (size_t)c.n, cudaMemcpyDeviceToDevice, c.stream));
+        CK(cudaMemcpyAsync(c.vel4_alt, c.vel4, 16 * (size_t)c.n, cudaMemcpyDeviceToDevice, c.stream));
+        CK(cudaMemcpyAsync(c.id_alt, c.id, 4 * (size_t)c.n, cudaMemcpyDeviceToDevice, c.stream));
+    }
+    CK(launch_reset(c));
+    CK(launch_bbox(c));
+    CK(pipeline_tree(c));
+    c.built = true;
+    c.moments_ready = c.have_acc = false;
+    return BONSAI_OK;
+}
+
+int bonsai_multipoles(bonsai_ctx *ctx) {
+    if (!ctx) return BONSAI_ERR_INVALID_ARG;
+    Ctx &c = ctx->c;
+    if (!c.built) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_multipoles: call bonsai_build first");
+    CK(launch_multipoles(c));
+    c.moments_ready = true;
+    return BONSAI_OK;
+}
+
+static int check_theta_eps(bonsai_ctx *ctx, float theta, float eps) {
+    if (!(theta > 0.f && theta <= 1.15f) || !(eps > 0.f) || !(eps < 1e30f))
+        return fail(ctx, BONSAI_ERR_INVALID_ARG, "need 0 < theta <= 1.15 and eps > 0");
+    return BONSAI_OK;
+}
+
+int bonsai_set_params(bonsai_ctx *ctx, float theta, float eps) {
+    if (!ctx) return BONSAI_ERR_INVALID_ARG;
+    int r = check_theta_eps(ctx, theta, eps);
+    if (r) return r;
+    ctx->c.theta = theta;
+    ctx->c.eps = eps;
+    return BONSAI_OK;
+}
+
+int bonsai_forces(bonsai_ctx *ctx, float theta, float eps, float *acc, float *pot, int on_device) {
+    if (!ctx) return BONSAI_ERR_INVALID_ARG;
+    Ctx &c = ctx->c;
+    int r = check_theta_eps(ctx, theta, eps);
+    if (r) return r;
+    if (!c.moments_ready)
+        return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_forces: call bonsai_build and bonsai_multipoles first");
+    c.theta = theta;
+    c.eps = eps;
+    CK(launch_reset(c));
+    CK(pipeline_forces(c, theta, eps));
+    c.have_acc = true;
+    if (acc || pot) {
+        if (on_device) {
+            CK(launch_scatter_forces(c, acc, pot));
+        } else {
+            float *sa = c.stage, *sp = c.stage + 3 * c.n;
+            CK(launch_scatter_forces(c, acc ? sa : nullptr, pot ? sp : nullptr));
+            if (acc) CK(cudaMemcpyAsync(acc, sa, 12 * (size_t)c.n, cudaMemcpyDeviceToHost, c.stream));
+            if (pot) CK(cudaMemcpyAsync(pot, sp, 4 * (size_t)c.n, cudaMemcpyDeviceToHost, c.stream));
+            CK(cudaStreamSynchronize(c.stream));
+        }
+    }
+    return BONSAI_OK;
+}
+
+int bonsai_step(bonsai_ctx *ctx, float dt) {
+    if (!ctx) return BONSAI_ERR_INVALID_ARG;
+    Ctx &c = ctx->c;
+    if (!c.have_bodies) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_step: no bodies");
+    if (!(dt == dt) || dt > 1e30f || dt < -1e30f) return fail(ctx, BONSAI_ERR_INVALID_ARG, "bonsai_step: bad dt");
+    if (!c.have_acc) {
+        int r;
+        if (!c.built && (r = bonsai_build(ctx))) return r;
+        if (!c.moments_ready && (r = bonsai_multipoles(ctx))) return r;
+        if ((r = bonsai_forces(ctx, c.theta, c.eps, nullptr, nullptr, 1))) return r;
+    }
+    // The first step with a given (dt, theta, eps, N) runs eagerly; the second
+    // captures the step into a CUDA graph, later ones replay it.
+    const bool same = c.graph_dt == dt && c.graph_theta == c.theta && c.graph_eps == c.eps &&
+                      c.graph_n == c.n;
+    if (c.use_graph && same && c.step_graph) {
+        CK(cudaGraphLaunch(c.step_graph, c.stream));
+    } else if (c.use_graph && same) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = pipeline_step(c, dt);
+            e = cudaStreamEndCapture(c.stream, &g);
+            if (e1 != cudaSuccess) e = e1;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&c.step_graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c.step_graph = nullptr;
+            c.use_graph = 0;           // fall back to direct launches
+            CK(pipeline_step(c, dt));
+        } else {
+            CK(cudaGraphLaunch(c.step_graph, c.stream));
+        }
+    } else {
+        if (c.step_graph) { cudaGraphExecDestroy(c.step_graph); c.step_graph = nullptr; }
+        CK(pipeline_step(c, dt));
+        c.graph_dt = dt; c.graph_theta = c.theta; c.graph_eps = c.eps; c.graph_n = c.n;
+    }
+    c.built = c.moments_ready = c.have_acc = true;
+    c.timed_step = true;
+    return BONSAI_OK;
+}
+
+int bonsai_get_stage_times(bonsai_ctx *ctx, float *ms, int n) {
+    if (!ctx || !ms || n < 0) return BONSAI_ERR_INVALID_ARG;
+    Ctx &c = ctx->c;
+    if (!c.timed_step) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_get_stage_times: no step yet");
+    CK(cudaStreamSynchronize(c.stream));
+    int k = n < Ctx::NSTAGE ? n : Ctx::NSTAGE;
+    for (int i = 0; i < k; i++) CK(cudaEventElapsedTime(&ms[i], c.ev[i], c.ev[i + 1]));
+    return k;
+}
+
+int bonsai_get_bodies(bonsai_ctx *ctx, float *pos, float *vel, int on_device) {
+    if (!ctx) return BONSAI_ERR_INVALID_ARG;
+    Ctx &c = ctx->c;
+    if (!c.have_bodies) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_get_bodies: no bodies");
+    const float4 *P = c.built ? c.pos4 : c.pos4_alt;
+    const float4 *V = c.built ? c.vel4 : c.vel4_alt;
+    const uint32_t *I = c.built ? c.id : c.id_alt;
+    Ctx tmp = c;   // view with the arrays that hold the state
+    tmp.pos4 = (float4 *)P; tmp.vel4 = (float4 *)V; tmp.id = (uint32_t *)I;
+    if (on_device) {
+        CK(launch_scatter_bodies(tmp, pos, vel));
+    } else {
+        float *sp = c.stage, *sv = c.stage + 3 * c.n;
+        CK(launch_scatter_bodies(tmp, pos ? sp : nullptr, vel ? sv : nullptr));
+        if (pos) CK(cudaMemcpyAsync(pos, sp, 12 * (size_t)c.n, cudaMemcpyDeviceToHost, c.stream));
+        if (vel) CK(cudaMemcpyAsync(vel, sv, 12 * (size_t)c.n, cudaMemcpyDeviceToHost, c.stream));
+        CK(cudaStreamSynchronize(c.stream));
+    }
+    tmp.step_graph = nullptr;   // the copy must not own the graph
+    return BONSAI_OK;
+}
+
+int bonsai_diagnostics(bonsai_ctx *ctx, double out[8]) {
+    if (!ctx || !out) return BONSAI_ERR_INVALID_ARG;
+    Ctx &c = ctx->c;
+    if (!c.have_acc) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_diagnostics: no forces yet");
+    CK(cudaMemsetAsync(&c.st->diag[0], 0, 8 * sizeof(double), c.stream));
+    CK(launch_diag(c));
+    CK(cudaMemcpyAsync(out, &c.st->diag[0], 8 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    out[2] = out[0] + out[1];
+    return BONSAI_OK;
+}
+
+int bonsai_sync(bonsai_ctx *ctx) {
+    if (!ctx) return BONSAI_ERR_INVALID_ARG;
+    Ctx &c = ctx->c;
+    CK(cudaStreamSynchronize(c.stream));
+    unsigned s = 0;
+    CK(cudaMemcpy(&s, &c.st->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    CK(cudaMemset(&c.st->status, 0, sizeof(unsigned)));
+    if (s & ST_TIMEOUT) return fail(ctx, BONSAI_ERR_TIMEOUT, "a bounded device-side wait gave up");
+    if (s & ST_CAPACITY) return fail(ctx, BONSAI_ERR_CAPACITY, "walk stack or cell capacity exceeded");
+    if (s & ST_NAN) return fail(ctx, BONSAI_ERR_NAN, "non-finite body positions");
+    return BONSAI_OK;
+}
+
+static int read_state(bonsai_ctx *ctx) {
+    Ctx &c = ctx->c;
+    CK(cudaMemcpyAsync(c.st_host, c.st, sizeof(DevState), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    return BONSAI_OK;
+}
+
+int bonsai_get_sizes(bonsai_ctx *ctx, long long *n, long long *ncells, long long *ngroups) {
+    if (!ctx) return BONSAI_ERR_INVALID_ARG;
+    int r = read_state(ctx);
+    if (r) return r;
+    if (n) *n = ctx->c.n;
+    if (ncells) *ncells = ctx->c.built ? ctx->c.st_host->ncells : 0;
+    if (ngroups) *ngroups = ctx->c.built ? ctx->c.st_host->ngroups : 0;
+    return BONSAI_OK;
+}
+
+int bonsai_get_domain(bonsai_ctx *ctx, float mn[3], float side[1]) {
+    if (!ctx || !mn || !side) return BONSAI_ERR_INVALID_ARG;
+    if (!ctx->c.built) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_get_domain: not built");
+    int r = read_state(ctx);
+    if (r) return r;
+    for (int d = 0; d < 3; d++) mn[d] = ctx->c.st_host->mn[d];
+    side[0] = ctx->c.st_host->side;
+    return BONSAI_OK;
+}
+
+int bonsai_get_keys(bonsai_ctx *ctx, uint64_t *keys, uint32_t *perm) {
+    if (!ctx) return BONSAI_ERR_INVALID_ARG;
+    Ctx &c = ctx->c;
+    if (!c.built) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_get_keys: not built");
+    if (keys) CK(cudaMemcpyAsync(keys, c.keys, 8 * (size_t)c.n, cudaMemcpyDeviceToHost, c.stream));
+    if (perm) CK(cudaMemcpyAsync(perm, c.id, 4 * (size_t)c.n, cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    return BONSAI_OK;
+}
+
+int bonsai_get_tree(bonsai_ctx *ctx, int32_t *bb, int32_t *bc, int32_t *cb, int32_t *nc, int32_t *lv) {
+    if (!ctx || !bb || !bc || !cb || !nc || !lv) return BONSAI_ERR_INVALID_ARG;
+    Ctx &c = ctx->c;
+    if (!c.built) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_get_tree: not built");
+    int r = read_state(ctx);
+    if (r) return r;
+    size_t nc_ = c.st_host->ncells;
+    int32_t *tmp = nullptr;
+    CK(cudaMalloc(&tmp, 5 * c.ccap * sizeof(int32_t)));
+    cudaError_t e = launch_tree_export(c, tmp, tmp + c.ccap, tmp + 2 * c.ccap, tmp + 3 * c.ccap, tmp + 4 * c.ccap);
+    int32_t *dst[5] = {bb, bc, cb, nc, lv};
+    for (int k = 0; k < 5 && e == cudaSuccess; k++)
+        e = cudaMemcpyAsync(dst[k], tmp + k * c.ccap, nc_ * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return fail(ctx, BONSAI_ERR_CUDA, "bonsai_get_tree", e);
+    return BONSAI_OK;
+}
+
+int bonsai_get_groups(bonsai_ctx *ctx, int32_t *begin, int32_t *count) {
+    if (!ctx || !begin || !count) return BONSAI_ERR_INVALID_ARG;
+    Ctx &c = ctx->c;
+    if (!c.built) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_get_groups: not built");
+    int r = read_state(ctx);
+    if (r) return r;
+    size_t ng = c.st_host->ngroups;
+    std::vector<uint2> h(ng);
+    CK(cudaMemcpy(h.data(), c.groups, ng * sizeof(uint2), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < ng; i++) { begin[i] = (int32_t)h[i].x; count[i] = (int32_t)h[i].y; }
+    return BONSAI_OK;
+}
+
+int bonsai_get_moments(bonsai_ctx *ctx, float *mono, float *quad) {
+    if (!ctx || !mono || !quad) return BONSAI_ERR_INVALID_ARG;
+    Ctx &c = ctx->c;
+    if (!c.moments_ready) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_get_moments: no moments");
+    int r = read_state(ctx);
+    if (r) return r;
+    size_t nc_ = c.st_host->ncells;
+    float *tmp = nullptr;
+    CK(cudaMalloc(&tmp, 10 * c.ccap * sizeof(float)));
+    cudaError_t e = launch_moments_export(c, tmp, tmp + 4 * c.ccap);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mono, tmp, 4 * nc_ * sizeof(float), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(quad, tmp + 4 * c.ccap, 6 * nc_ * sizeof(float), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return fail(ctx, BONSAI_ERR_CUDA, "bonsai_get_moments", e);
+    return BONSAI_OK;
+}
+
+int bonsai_get_counts(bonsai_ctx *ctx, uint32_t *n_pc, uint32_t *n_pp, unsigned long long tot[2]) {
+    if (!ctx) return BONSAI_ERR_INVALID_ARG;
+    Ctx &c = ctx->c;
+    if (!c.have_acc) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_get_counts: no walk yet");
+    if (n_pc || n_pp) {
+        uint32_t *sa = (uint32_t *)c.stage, *sb = (uint32_t *)c.stage + c.n;
+        CK(launch_scatter_counts(c, n_pc ? sa : nullptr, n_pp ? sb : nullptr));
+        if (n_pc) CK(cudaMemcpyAsync(n_pc, sa, 4 * (size_t)c.n, cudaMemcpyDeviceToHost, c.stream));
+        if (n_pp) CK(cudaMemcpyAsync(n_pp, sb, 4 * (size_t)c.n, cudaMemcpyDeviceToHost, c.stream));
+    }
+    int r = read_state(ctx);
+    if (r) return r;
+    if (tot) { tot[0] = c.st_host->inter[0]; tot[1] = c.st_host->inter[1]; }
+    return BONSAI_OK;
+}
+
+}  // extern "C"

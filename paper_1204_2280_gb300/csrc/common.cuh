@@ -1,0 +1,149 @@
+// common.cuh -- internal declarations of libbonsai (not part of the C ABI).
+//
+// Data layout in HBM (sorted body order unless stated):
+//   pos4  float4[N]  (x, y, z, m)          vel4  float4[N] (vx, vy, vz, 0)
+//   id    u32[N]     caller index          acc4  float4[N] (ax, ay, az, phi)
+//   *_alt            the same, pre-sort copies written by pack / drift
+//   keys  u64[N] + sort ping-pong buffers, perm u32[N]
+//   cells (capacity C): body uint2 (begin, count), link uint2 (internal:
+//     child_begin, nchild; leaf: begin, count | LEAF_BIT), level u8,
+//     parent u32, done u32, mono float4 (com, M), quadA float4 (xx yy zz xy),
+//     quadB float2 (xz yz), test float4 (com, r_open), delta float
+//   groups (capacity N): uint2 (begin, count)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/bonsai.h"
+
+namespace bonsai {
+
+constexpr int KEY_BITS_PER_AXIS = 21;            // L, Sect. 2 Morton keys
+constexpr int MAX_LEVEL = KEY_BITS_PER_AXIS;     // deepest level (root = 0)
+constexpr int NROWS = MAX_LEVEL + 2;             // 22 level rows + group row
+constexpr int GROUP_ROW = MAX_LEVEL + 1;
+constexpr uint32_t LEAF_BIT = 0x80000000u;
+constexpr int FP64_LEVELS = 4;                   // levels 0..3 combine in FP64
+
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 16;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;   // 4096 keys per tile
+constexpr int SORT_PASSES = 8;                         // 8-bit digits, 63-bit keys
+constexpr int BUILD_THREADS = 1024;                    // bodies per build block
+
+// Device status bits (ORed by kernels, read and cleared by bonsai_sync).
+constexpr unsigned ST_CAPACITY = 1u;
+constexpr unsigned ST_TIMEOUT = 2u;
+constexpr unsigned ST_NAN = 4u;
+
+struct DevState {
+    int dom[6];                       // orderable-int min xyz, max xyz
+    float mn[3];                      // domain corner (written by keys block 0)
+    float side;                       // domain side S
+    unsigned hist[SORT_PASSES * 256]; // digit histograms of the keys
+    unsigned sort_tile[SORT_PASSES];  // tile tickets per pass
+    unsigned ncells, ngroups;
+    unsigned row_total[NROWS];        // cells per level, groups
+    unsigned walk_next;               // group queue head
+    unsigned status;
+    unsigned pad0;
+    unsigned long long inter[2];      // n_pc, n_pp totals of the last walk
+    double diag[8];
+};
+
+struct Ctx {
+    // configuration
+    int nleaf = 16, ncrit = 32, walk_warps = 4, list_capacity = 256, use_graph = 1;
+    long long max_spin = 1ll << 24;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0, num_sms = 0;
+
+    // sizes
+    long long n = 0, ncap = 0, ccap = 0;
+    int ntiles = 0, nbblocks = 0;     // sort tiles, build blocks
+
+    // body arrays
+    float4 *pos4 = nullptr, *vel4 = nullptr, *acc4 = nullptr;
+    float4 *pos4_alt = nullptr, *vel4_alt = nullptr;
+    uint32_t *id = nullptr, *id_alt = nullptr;
+    // sort
+    unsigned long long *keys = nullptr, *keys_alt = nullptr;
+    uint32_t *vals = nullptr, *vals_alt = nullptr;   // vals ends as perm
+    unsigned *tile_status = nullptr;                   // SORT_PASSES * ntiles * 256
+    // build
+    uint32_t *binfo = nullptr;       // per body: lo | hi<<5 | has<<10 | ngrp<<16
+    unsigned *blockcount = nullptr;  // NROWS * nbblocks
+    uint2 *cell_body = nullptr, *cell_link = nullptr;
+    uint8_t *cell_level = nullptr;
+    uint32_t *cell_parent = nullptr, *cell_done = nullptr;
+    float4 *mono = nullptr, *quadA = nullptr, *test = nullptr;
+    float2 *quadB = nullptr;
+    float *delta = nullptr;
+    double *shadow = nullptr;        // FP64 moments of the top levels (10 per cell)
+    uint2 *groups = nullptr;
+    uint2 *counts = nullptr;         // per body (n_pc, n_pp), sorted order
+    // staging for host transfers and caller-order outputs
+    float *stage = nullptr;          // 7 floats per body
+    DevState *st = nullptr;          // device
+    DevState *st_host = nullptr;     // pinned mirror for reads
+
+    // pipeline state
+    bool have_bodies = false, built = false, moments_ready = false, have_acc = false;
+    float theta = 0.75f, eps = 0.01f;
+    cudaGraphExec_t step_graph = nullptr;
+    static constexpr int NSTAGE = 8;
+    cudaEvent_t ev[NSTAGE + 1] = {};
+    bool timed_step = false;
+    float graph_dt = 0.f, graph_theta = 0.f, graph_eps = 0.f;
+    long long graph_n = -1;
+
+    std::string err;
+};
+
+// ---- device helpers ------------------------------------------------------
+
+// Monotone map float -> int (signed compare order == float order).
+__device__ __forceinline__ int f2ord(float f) {
+    int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ord2f(int i) {
+    return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff);
+}
+
+// Number of leading tree levels shared by two keys (level 0 always shared):
+// prefix_l(a) == prefix_l(b) iff l <= cpl(a, b).
+__device__ __forceinline__ int key_cpl(unsigned long long a, unsigned long long b) {
+    unsigned long long x = a ^ b;
+    if (x == 0ull) return MAX_LEVEL;
+    int p = 63 - __clzll((long long)x);
+    return MAX_LEVEL - p / 3 - 1;
+}
+
+__device__ __forceinline__ unsigned long long key_prefix(unsigned long long k, int level) {
+    return level == 0 ? 0ull : (k >> (3 * (MAX_LEVEL - level)));
+}
+
+// ---- launchers (host) ------------------------------------------------------
+cudaError_t launch_reset(Ctx &c);
+cudaError_t launch_pack(Ctx &c, const float *pos, const float *mass, const float *vel);
+cudaError_t launch_bbox(Ctx &c);
+cudaError_t launch_kick_drift_bbox(Ctx &c, float dt);
+cudaError_t launch_keys(Ctx &c);
+cudaError_t launch_sort(Ctx &c);
+cudaError_t launch_reorder(Ctx &c);
+cudaError_t launch_build(Ctx &c);
+cudaError_t launch_multipoles(Ctx &c);
+cudaError_t launch_open_radius(Ctx &c, float theta);
+cudaError_t launch_walk(Ctx &c, float eps);
+cudaError_t launch_kick(Ctx &c, float dt);
+cudaError_t launch_scatter_forces(Ctx &c, float *acc, float *pot);
+cudaError_t launch_scatter_bodies(Ctx &c, float *pos, float *vel);
+cudaError_t launch_scatter_counts(Ctx &c, uint32_t *npc, uint32_t *npp);
+cudaError_t launch_diag(Ctx &c);
+cudaError_t launch_tree_export(Ctx &c, int32_t *bb, int32_t *bc, int32_t *cb, int32_t *nc, int32_t *lv);
+cudaError_t launch_moments_export(Ctx &c, float *mono, float *quad);
+
+}  // namespace bonsai

@@ -1,0 +1,203 @@
+// k_moments.cu -- multipole moments of every cell (paper Sect. 2,
+// "computation of the multipole moments") and the opening radius of the MAC.
+//
+// Per cell: mass M, centre of mass com and traceless quadrupole
+//   Q_ij = sum m (3 y_i y_j - |y|^2 delta_ij),  y = x - com.
+// Leaves are summed from their bodies in cell-relative coordinates (offsets
+// from the first body, then from the com).  Parents combine their children
+// by the parallel-axis theorem,
+//   Q_p = sum_k [ Q_k + M_k (3 d_k d_k^T - |d_k|^2 I) ],  d_k = com_k - com_p,
+// in one launch: each thread finishing a cell bumps its parent's arrival
+// counter and the last child to arrive combines the parent (no waiting).
+// The top four levels (at most 585 cells, the first ones in breadth-first
+// order) combine in FP64, from FP64 copies of children on those levels.
+#include "common.cuh"
+
+namespace bonsai {
+
+__device__ __forceinline__ unsigned compact3(unsigned long long x) {
+    x &= 0x1249249249249249ull;
+    x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+    x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+    x = (x ^ (x >> 8)) & 0x001f0000ff0000ffull;
+    x = (x ^ (x >> 16)) & 0x001f00000000ffffull;
+    x = (x ^ (x >> 32)) & 0x00000000001fffffull;
+    return (unsigned)x;
+}
+
+// |com - geometric centre| of a cell at `level` whose first body has key k.
+__device__ float cell_delta(unsigned long long k, int level, float3 com, const DevState *st) {
+    unsigned long long pre = key_prefix(k, level);
+    float l = ldexpf(st->side, -level);
+    float cx = fmaf((float)compact3(pre) + 0.5f, l, st->mn[0]);
+    float cy = fmaf((float)compact3(pre >> 1) + 0.5f, l, st->mn[1]);
+    float cz = fmaf((float)compact3(pre >> 2) + 0.5f, l, st->mn[2]);
+    float dx = com.x - cx, dy = com.y - cy, dz = com.z - cz;
+    return sqrtf(dx * dx + dy * dy + dz * dz);
+}
+
+struct Mom32 { float M, x, y, z, q[6]; };
+
+__device__ __forceinline__ void store32(int c, const Mom32 &m, float4 *mono, float4 *qa, float2 *qb) {
+    mono[c] = make_float4(m.x, m.y, m.z, m.M);
+    qa[c] = make_float4(m.q[0], m.q[1], m.q[2], m.q[3]);
+    qb[c] = make_float2(m.q[4], m.q[5]);
+}
+
+__global__ void __launch_bounds__(256)
+k_multipoles(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__ cell_body,
+             const uint2 *__restrict__ cell_link, const uint8_t *__restrict__ cell_level,
+             const uint32_t *__restrict__ cell_parent, uint32_t *cell_done,
+             const float4 *__restrict__ pos4, const unsigned long long *__restrict__ sk,
+             float4 *mono, float4 *qa, float2 *qb, float *delta, double *shadow) {
+    unsigned c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= stc->ncells || (stc->status & ST_TIMEOUT)) return;
+    uint2 link = cell_link[c];
+    if (!(link.y & LEAF_BIT)) return;
+
+    // Leaf from its bodies.
+    unsigned b = link.x, cnt = link.y & ~LEAF_BIT;
+    float4 x0 = pos4[b];
+    float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+    for (unsigned j = b; j < b + cnt; j++) {
+        float4 p = pos4[j];
+        M += p.w;
+        sx = fmaf(p.w, p.x - x0.x, sx); sy = fmaf(p.w, p.y - x0.y, sy); sz = fmaf(p.w, p.z - x0.z, sz);
+    }
+    Mom32 m;
+    m.M = M;
+    float inv = M > 0.f ? 1.f / M : 0.f;
+    m.x = x0.x + sx * inv; m.y = x0.y + sy * inv; m.z = x0.z + sz * inv;
+    for (int k = 0; k < 6; k++) m.q[k] = 0.f;
+    for (unsigned j = b; j < b + cnt; j++) {
+        float4 p = pos4[j];
+        float yx = p.x - m.x, yy = p.y - m.y, yz = p.z - m.z;
+        float r2 = yx * yx + yy * yy + yz * yz;
+        m.q[0] += p.w * (3.f * yx * yx - r2);
+        m.q[1] += p.w * (3.f * yy * yy - r2);
+        m.q[2] += p.w * (3.f * yz * yz - r2);
+        m.q[3] += p.w * (3.f * yx * yy);
+        m.q[4] += p.w * (3.f * yx * yz);
+        m.q[5] += p.w * (3.f * yy * yz);
+    }
+    int lev = cell_level[c];
+    store32(c, m, mono, qa, qb);
+    delta[c] = cell_delta(sk[b], lev, make_float3(m.x, m.y, m.z), stc);
+    if (lev < FP64_LEVELS) {
+        double *s = shadow + 10 * (size_t)c;
+        s[0] = m.M; s[1] = m.x; s[2] = m.y; s[3] = m.z;
+        for (int k = 0; k < 6; k++) s[4 + k] = m.q[k];
+    }
+
+    // Up the tree while this thread is the last child to finish.
+    while (c != 0) {
+        unsigned p = cell_parent[c];
+        __threadfence();
+        unsigned nch = __ldcg(&cell_link[p].y);
+        if (atomicAdd(&cell_done[p], 1u) != nch - 1u) return;
+        __threadfence();
+        c = p;
+        unsigned cb = __ldcg(&cell_link[c].x);
+        int lv = cell_level[c];
+        if (lv < FP64_LEVELS) {
+            double dM = 0, c0x = 0, c0y = 0, c0z = 0, ax = 0, ay = 0, az = 0;
+            double ch[8][10];
+            for (unsigned k = 0; k < nch; k++) {
+                unsigned cc = cb + k;
+                if (lv + 1 < FP64_LEVELS) {
+                    for (int i = 0; i < 10; i++) ch[k][i] = __ldcg(shadow + 10 * (size_t)cc + i);
+                } else {
+                    float4 mo = __ldcg(mono + cc), a = __ldcg(qa + cc);
+                    float2 q2 = __ldcg(qb + cc);
+                    ch[k][0] = mo.w; ch[k][1] = mo.x; ch[k][2] = mo.y; ch[k][3] = mo.z;
+                    ch[k][4] = a.x; ch[k][5] = a.y; ch[k][6] = a.z; ch[k][7] = a.w;
+                    ch[k][8] = q2.x; ch[k][9] = q2.y;
+                }
+            }
+            c0x = ch[0][1]; c0y = ch[0][2]; c0z = ch[0][3];
+            for (unsigned k = 0; k < nch; k++) {
+                dM += ch[k][0];
+                ax += ch[k][0] * (ch[k][1] - c0x);
+                ay += ch[k][0] * (ch[k][2] - c0y);
+                az += ch[k][0] * (ch[k][3] - c0z);
+            }
+            double inv2 = dM > 0 ? 1.0 / dM : 0.0;
+            double cx = c0x + ax * inv2, cy = c0y + ay * inv2, cz = c0z + az * inv2;
+            double q[6] = {0, 0, 0, 0, 0, 0};
+            for (unsigned k = 0; k < nch; k++) {
+                double mk = ch[k][0];
+                double dx = ch[k][1] - cx, dy = ch[k][2] - cy, dz = ch[k][3] - cz;
+                double d2 = dx * dx + dy * dy + dz * dz;
+                q[0] += ch[k][4] + mk * (3 * dx * dx - d2);
+                q[1] += ch[k][5] + mk * (3 * dy * dy - d2);
+                q[2] += ch[k][6] + mk * (3 * dz * dz - d2);
+                q[3] += ch[k][7] + mk * (3 * dx * dy);
+                q[4] += ch[k][8] + mk * (3 * dx * dz);
+                q[5] += ch[k][9] + mk * (3 * dy * dz);
+            }
+            double *s = shadow + 10 * (size_t)c;
+            s[0] = dM; s[1] = cx; s[2] = cy; s[3] = cz;
+            for (int i = 0; i < 6; i++) s[4 + i] = q[i];
+            m.M = (float)dM; m.x = (float)cx; m.y = (float)cy; m.z = (float)cz;
+            for (int i = 0; i < 6; i++) m.q[i] = (float)q[i];
+        } else {
+            float4 ch0 = __ldcg(mono + cb);
+            float c0x = ch0.x, c0y = ch0.y, c0z = ch0.z;
+            float fM = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
+            for (unsigned k = 0; k < nch; k++) {
+                float4 mo = __ldcg(mono + cb + k);
+                fM += mo.w;
+                ax = fmaf(mo.w, mo.x - c0x, ax);
+                ay = fmaf(mo.w, mo.y - c0y, ay);
+                az = fmaf(mo.w, mo.z - c0z, az);
+            }
+            float inv2 = fM > 0.f ? 1.f / fM : 0.f;
+            m.M = fM; m.x = c0x + ax * inv2; m.y = c0y + ay * inv2; m.z = c0z + az * inv2;
+            for (int i = 0; i < 6; i++) m.q[i] = 0.f;
+            for (unsigned k = 0; k < nch; k++) {
+                float4 mo = __ldcg(mono + cb + k), a = __ldcg(qa + cb + k);
+                float2 q2 = __ldcg(qb + cb + k);
+                float dx = mo.x - m.x, dy = mo.y - m.y, dz = mo.z - m.z;
+                float d2 = dx * dx + dy * dy + dz * dz;
+                m.q[0] += a.x + mo.w * (3.f * dx * dx - d2);
+                m.q[1] += a.y + mo.w * (3.f * dy * dy - d2);
+                m.q[2] += a.z + mo.w * (3.f * dz * dz - d2);
+                m.q[3] += a.w + mo.w * (3.f * dx * dy);
+                m.q[4] += q2.x + mo.w * (3.f * dx * dz);
+                m.q[5] += q2.y + mo.w * (3.f * dy * dz);
+            }
+        }
+        store32(c, m, mono, qa, qb);
+        unsigned b0 = __ldcg(&cell_body[c].x);
+        delta[c] = cell_delta(sk[b0], lv, make_float3(m.x, m.y, m.z), stc);
+    }
+}
+
+cudaError_t launch_multipoles(Ctx &c) {
+    unsigned grid = (unsigned)((c.ccap + 255) / 256);
+    k_multipoles<<<grid, 256, 0, c.stream>>>(c.st, c.st, c.cell_body, c.cell_link, c.cell_level,
+                                             c.cell_parent, c.cell_done, c.pos4, c.keys, c.mono,
+                                             c.quadA, c.quadB, c.delta, c.shadow);
+    return cudaGetLastError();
+}
+
+// test[c] = (com, l/theta + delta), l = S / 2^level: the opening radius of
+// the Barnes (1994) criterion as read here.
+__global__ void k_open_radius(const DevState *__restrict__ st, const float4 *__restrict__ mono,
+                              const float *__restrict__ delta, const uint8_t *__restrict__ level,
+                              float inv_theta, float4 *test) {
+    unsigned c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= st->ncells) return;
+    float4 m = mono[c];
+    float l = ldexpf(st->side, -(int)level[c]);
+    test[c] = make_float4(m.x, m.y, m.z, fmaf(l, inv_theta, delta[c]));
+}
+
+cudaError_t launch_open_radius(Ctx &c, float theta) {
+    unsigned grid = (unsigned)((c.ccap + 255) / 256);
+    k_open_radius<<<grid, 256, 0, c.stream>>>(c.st, c.mono, c.delta, c.cell_level, 1.0f / theta,
+                                              c.test);
+    return cudaGetLastError();
+}
+
+}  // namespace bonsai

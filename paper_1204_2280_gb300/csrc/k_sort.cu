@@ -1,0 +1,190 @@
+// k_sort.cu -- stable LSD radix sort of (63-bit Morton key, u32 index).
+//
+// Paper Sect. 2, "sorting": bodies are ordered along the space-filling curve
+// by their keys; equal keys keep their input order (stable).  Eight passes of
+// 8-bit digits cover the 63 key bits.  Each pass is one "onesweep" launch:
+// the digit histograms of all passes come from the key kernel, so a pass
+// reads every key/value once and writes it once (24 B per body per pass):
+//   1. a tile of 4096 keys is taken in ticket order (atomic counter), loaded
+//      warp-striped and ranked per warp with match_any (stable: item order,
+//      then lane order, then warp order);
+//   2. per digit the tile count is published and the prefix over earlier
+//      tiles found by decoupled look-back (bounded spin; on timeout a status
+//      bit is set and the kernel continues, so it always terminates);
+//   3. keys/values are reordered by digit in shared memory and written out so
+//      that consecutive threads write consecutive addresses of a digit run.
+#include "common.cuh"
+
+namespace bonsai {
+
+constexpr unsigned FLAG_AGG = 1u << 30;
+constexpr unsigned FLAG_INC = 2u << 30;
+constexpr unsigned VAL_MASK = (1u << 30) - 1u;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ unsigned ld_volatile(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.volatile.global.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ void st_volatile(unsigned *p, unsigned v) {
+    asm volatile("st.volatile.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Exclusive scan over the 256 threads of a block (one value per thread).
+__device__ __forceinline__ unsigned block_excl_scan256(unsigned v, unsigned *s_warp) {
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    unsigned off = 0;
+#pragma unroll
+    for (int w = 0; w < SORT_THREADS / 32; w++) off += (w < warp) ? s_warp[w] : 0u;
+    __syncthreads();
+    return off + x - v;
+}
+
+__global__ void __launch_bounds__(SORT_THREADS, 2)
+k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restrict__ vin,
+           unsigned long long *__restrict__ kout, uint32_t *__restrict__ vout, int n, int shift,
+           const unsigned *__restrict__ ghist, unsigned *status, unsigned *status_next,
+           unsigned *ticket, int ntiles, DevState *st, long long max_spin) {
+    extern __shared__ unsigned long long s_keys[];                 // SORT_TILE keys
+    uint32_t *s_vals = (uint32_t *)(s_keys + SORT_TILE);          // SORT_TILE values
+    __shared__ unsigned s_whist[SORT_THREADS / 32][256];
+    __shared__ unsigned s_dstart[256], s_goff[256], s_warp[SORT_THREADS / 32];
+    __shared__ unsigned s_tile;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (status_next)
+        for (int i = blockIdx.x * SORT_THREADS + tid; i < ntiles * 256; i += gridDim.x * SORT_THREADS)
+            status_next[i] = 0u;
+    if (tid == 0) s_tile = atomicAdd(ticket, 1u);
+    for (int i = tid; i < (SORT_THREADS / 32) * 256; i += SORT_THREADS) (&s_whist[0][0])[i] = 0u;
+    __syncthreads();
+    const int tile = (int)s_tile;
+    const int wbase = tile * SORT_TILE + warp * (SORT_ITEMS * 32);
+
+    unsigned long long k[SORT_ITEMS];
+    uint32_t v[SORT_ITEMS];
+    unsigned short rk[SORT_ITEMS];
+#pragma unroll
+    for (int it = 0; it < SORT_ITEMS; it++) {
+        int idx = wbase + it * 32 + lane;
+        bool ok = idx < n;
+        k[it] = ok ? kin[idx] : ~0ull;
+        v[it] = vin ? (ok ? vin[idx] : 0u) : (uint32_t)idx;
+    }
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int it = 0; it < SORT_ITEMS; it++) {
+        int idx = wbase + it * 32 + lane;
+        unsigned d = idx < n ? (unsigned)((k[it] >> shift) & 0xffu) : 256u;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        unsigned below = __popc(peers & lt);
+        unsigned basec = d < 256u ? s_whist[warp][d] : 0u;
+        rk[it] = (unsigned short)(basec + below);
+        __syncwarp();
+        if (d < 256u && below == 0u) s_whist[warp][d] = basec + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // Thread d owns digit d: exclusive prefix over warps, tile count.
+    const unsigned d = (unsigned)tid;
+    unsigned run = 0;
+#pragma unroll
+    for (int w = 0; w < SORT_THREADS / 32; w++) {
+        unsigned c = s_whist[w][d];
+        s_whist[w][d] = run;
+        run += c;
+    }
+    const unsigned tcount = run;
+    unsigned dstart = block_excl_scan256(tcount, s_warp);
+    unsigned gbase = block_excl_scan256(ghist[d], s_warp);
+    s_dstart[d] = dstart;
+
+    // Decoupled look-back over earlier tiles for digit d.
+    unsigned *my = status + (size_t)tile * 256 + d;
+    unsigned prefix = 0;
+    if (tile == 0) {
+        st_volatile(my, FLAG_INC | tcount);
+    } else {
+        st_volatile(my, FLAG_AGG | tcount);
+        int j = tile - 1;
+        long long spins = 0;
+        while (j >= 0) {
+            unsigned s = ld_volatile(status + (size_t)j * 256 + d);
+            unsigned f = s & ~VAL_MASK;
+            if (f == 0u) {
+                if (++spins > max_spin) { atomicOr(&st->status, ST_TIMEOUT); break; }
+                continue;
+            }
+            prefix += s & VAL_MASK;
+            if (f == FLAG_INC) break;
+            j--;
+        }
+        st_volatile(my, FLAG_INC | ((prefix + tcount) & VAL_MASK));
+    }
+    s_goff[d] = gbase + prefix;
+    __syncthreads();
+
+    // Reorder the tile by digit in shared memory.
+#pragma unroll
+    for (int it = 0; it < SORT_ITEMS; it++) {
+        int idx = wbase + it * 32 + lane;
+        if (idx < n) {
+            unsigned dd = (unsigned)((k[it] >> shift) & 0xffu);
+            unsigned pos = s_dstart[dd] + s_whist[warp][dd] + rk[it];
+            s_keys[pos] = k[it];
+            s_vals[pos] = v[it];
+        }
+    }
+    __syncthreads();
+    const int nvalid = min(SORT_TILE, n - tile * SORT_TILE);
+    for (int p = tid; p < nvalid; p += SORT_THREADS) {
+        unsigned long long key = s_keys[p];
+        unsigned dd = (unsigned)((key >> shift) & 0xffu);
+        unsigned g = s_goff[dd] + ((unsigned)p - s_dstart[dd]);
+        kout[g] = key;
+        vout[g] = s_vals[p];
+    }
+}
+
+constexpr size_t SORT_DYN_SMEM = (size_t)SORT_TILE * (sizeof(unsigned long long) + sizeof(uint32_t));
+
+cudaError_t launch_sort(Ctx &c) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SORT_DYN_SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    int n = (int)c.n;
+    unsigned long long *kb[2] = {c.keys, c.keys_alt};
+    uint32_t *vb[2] = {c.vals, c.vals_alt};
+    size_t plane = (size_t)c.ntiles * 256;
+    for (int p = 0; p < SORT_PASSES; p++) {
+        k_onesweep<<<c.ntiles, SORT_THREADS, SORT_DYN_SMEM, c.stream>>>(
+            kb[p & 1], p == 0 ? nullptr : vb[p & 1], kb[(p + 1) & 1], vb[(p + 1) & 1], n, 8 * p,
+            c.st->hist + 256 * p, c.tile_status + plane * p,
+            p + 1 < SORT_PASSES ? c.tile_status + plane * (p + 1) : nullptr, c.st->sort_tile + p,
+            c.ntiles, c.st, c.max_spin);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace bonsai

@@ -1,0 +1,300 @@
+// k_walk.cu -- the group-wise Barnes-Hut tree-traverse (paper Sect. 2,
+// "tree-traverse"; MAC after Barnes 1994 combined with the vector-machine
+// group walk of Barnes 1990).  This is the dominant kernel (>90% of a step).
+//
+// One warp owns one group (<= 32 bodies that share an interaction list).  A
+// persistent grid pulls groups from an atomic queue in key order.  Per warp:
+//  * a stack of child ranges (first child, count <= 8) in shared memory; each
+//    round pops up to 32 cells, one per lane, and tests them against the
+//    group's bounding box: a cell is opened when the squared distance from its
+//    com to the box is below r_open^2 (r_open = l/theta + delta);
+//  * accepted cells are staged (com, M, Q) into a 64-slot ring in shared
+//    memory; the bodies of opened leaves into a second ring; opened internal
+//    cells push their child range;
+//  * whenever a ring holds 32 sources the warp evaluates that tile: every
+//    lane streams the sources from shared memory (broadcast reads) with FP32
+//    FMAs.  A group of n bodies uses s = next_pow2(n) body slots; the 32/s
+//    lanes sharing a body split the tile's sources between them and are summed
+//    at the end, so small groups still keep all lanes busy;
+//  * each tile is summed in plain FP32 and added to the body's accumulators
+//    with Kahan compensation (one compensated add per tile and component).
+// Body-cell (monopole + traceless quadrupole, softened):
+//   d = com - x, r^2 = |d|^2 + eps^2, q = d.Q.d
+//   phi -= M/r + q/(2 r^5),  a += (M/r^3 + 5q/(2 r^7)) d - Q d / r^5
+// Body-body: a += m d / r^3, phi -= m / r.  The body's own term has d = 0
+// (zero force); its potential -m/eps is removed after the walk.
+#include "common.cuh"
+
+namespace bonsai {
+
+constexpr int RING = 64;
+
+struct WarpRings {
+    float4 mono[RING];   // com xyz, M
+    float4 qa[RING];     // Qxx Qyy Qzz Qxy
+    float2 qb[RING];     // Qxz Qyz
+    float4 pp[RING];     // x y z m
+};
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
+    float y = __fsub_rn(v, c);
+    float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+struct Acc {
+    float ax, ay, az, ph;    // running sums
+    float cx, cy, cz, cp;    // Kahan compensations
+};
+
+__device__ __forceinline__ void eval_pc(const WarpRings &R, int head, int cnt, int phase, int nph,
+                                        float x, float y, float z, float eps2, Acc &A) {
+    float px = 0.f, py = 0.f, pz = 0.f, pp = 0.f;
+    for (int k = phase; k < cnt; k += nph) {
+        const int s = head + k;
+        const float4 mo = R.mono[s];
+        const float4 qa = R.qa[s];
+        const float2 qb = R.qb[s];
+        const float dx = mo.x - x, dy = mo.y - y, dz = mo.z - z;
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+        const float rinv = rsqrtf(r2);
+        const float rinv2 = rinv * rinv;
+        const float mr = mo.w * rinv;
+        const float mr3 = mr * rinv2;
+        const float qx = fmaf(qa.w, dy, fmaf(qb.x, dz, qa.x * dx));
+        const float qy = fmaf(qa.w, dx, fmaf(qb.y, dz, qa.y * dy));
+        const float qz = fmaf(qb.x, dx, fmaf(qb.y, dy, qa.z * dz));
+        const float q = fmaf(dz, qz, fmaf(dy, qy, dx * qx));
+        const float rinv5 = rinv2 * rinv2 * rinv;
+        const float qr5 = q * rinv5;
+        pp -= fmaf(0.5f, qr5, mr);
+        const float sc = fmaf(2.5f * qr5, rinv2, mr3);
+        px = fmaf(sc, dx, px); px = fmaf(-rinv5, qx, px);
+        py = fmaf(sc, dy, py); py = fmaf(-rinv5, qy, py);
+        pz = fmaf(sc, dz, pz); pz = fmaf(-rinv5, qz, pz);
+    }
+    kahan_add(A.ax, A.cx, px); kahan_add(A.ay, A.cy, py);
+    kahan_add(A.az, A.cz, pz); kahan_add(A.ph, A.cp, pp);
+}
+
+__device__ __forceinline__ void eval_pp(const WarpRings &R, int head, int cnt, int phase, int nph,
+                                        float x, float y, float z, float eps2, Acc &A) {
+    float px = 0.f, py = 0.f, pz = 0.f, pp = 0.f;
+    for (int k = phase; k < cnt; k += nph) {
+        const float4 s = R.pp[head + k];
+        const float dx = s.x - x, dy = s.y - y, dz = s.z - z;
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+        const float rinv = rsqrtf(r2);
+        const float mr = s.w * rinv;
+        const float mr3 = mr * rinv * rinv;
+        pp -= mr;
+        px = fmaf(mr3, dx, px); py = fmaf(mr3, dy, py); pz = fmaf(mr3, dz, pz);
+    }
+    kahan_add(A.ax, A.cx, px); kahan_add(A.ay, A.cy, py);
+    kahan_add(A.az, A.cz, pz); kahan_add(A.ph, A.cp, pp);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt_w() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__global__ void __launch_bounds__(256)
+k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__ groups,
+       const float4 *__restrict__ pos4, const float4 *__restrict__ test,
+       const uint2 *__restrict__ link, const float4 *__restrict__ mono,
+       const float4 *__restrict__ quadA, const float2 *__restrict__ quadB, float eps,
+       int stack_cap, long long max_rounds, float4 *acc4, uint2 *counts) {
+    extern __shared__ float4 smem4[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t warp_bytes = sizeof(WarpRings) + (size_t)stack_cap * sizeof(unsigned);
+    char *wbase = (char *)smem4 + warp * warp_bytes;
+    WarpRings &R = *reinterpret_cast<WarpRings *>(wbase);
+    unsigned *stk = reinterpret_cast<unsigned *>(wbase + sizeof(WarpRings));
+    const unsigned ngroups = (stc->status & ST_TIMEOUT) ? 0u : stc->ngroups;
+    const float eps2 = eps * eps;
+    const unsigned lt = lanemask_lt_w();
+
+    while (true) {
+        unsigned g = 0;
+        if (lane == 0) g = atomicAdd(&st->walk_next, 1u);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= ngroups) break;
+        const uint2 gr = groups[g];
+        const int gb = (int)gr.x, ng = (int)gr.y;
+        // body slots and source phases
+        const int lg = ng <= 1 ? 0 : 32 - __clz(ng - 1);      // log2(next_pow2(ng))
+        const int slots = 1 << lg, nph = 32 >> lg;
+        const int bslot = lane & (slots - 1), phase = lane >> lg;
+        const bool live = bslot < ng;
+        const int bi = gb + (live ? bslot : 0);
+        const float4 me = pos4[bi];
+        float bx0 = live ? me.x : INFINITY, by0 = live ? me.y : INFINITY, bz0 = live ? me.z : INFINITY;
+        float bx1 = live ? me.x : -INFINITY, by1 = live ? me.y : -INFINITY, bz1 = live ? me.z : -INFINITY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            bx0 = fminf(bx0, __shfl_xor_sync(0xffffffffu, bx0, o));
+            by0 = fminf(by0, __shfl_xor_sync(0xffffffffu, by0, o));
+            bz0 = fminf(bz0, __shfl_xor_sync(0xffffffffu, bz0, o));
+            bx1 = fmaxf(bx1, __shfl_xor_sync(0xffffffffu, bx1, o));
+            by1 = fmaxf(by1, __shfl_xor_sync(0xffffffffu, by1, o));
+            bz1 = fmaxf(bz1, __shfl_xor_sync(0xffffffffu, bz1, o));
+        }
+        Acc A = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        int sp = 1;
+        if (lane == 0) stk[0] = 0u << 3 | 0u;      // root range: cell 0, count 1
+        int pc_head = 0, pc_n = 0, pp_head = 0, pp_n = 0;
+        unsigned npc = 0, npp = 0;
+        bool overflow = false, timeout = false;
+        long long rounds = 0;
+        __syncwarp();
+
+        while (sp > 0) {
+            if (++rounds > max_rounds) { timeout = true; break; }   // bounded traversal
+            // Pop up to 32 cells from the top ranges.
+            const int avail = min(sp, 32);
+            const unsigned ent = lane < avail ? stk[sp - 1 - lane] : 0u;
+            const int cnt = lane < avail ? (int)(ent & 7u) + 1 : 0;
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const unsigned take = __ballot_sync(0xffffffffu, lane < avail && incl <= 32);
+            const int m = __popc(take);
+            const int T = __shfl_sync(0xffffffffu, incl, m - 1);
+            const int excl = incl - cnt;
+            sp -= m;
+            int e = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                int cand = e + step;
+                int ex = __shfl_sync(0xffffffffu, excl, cand & 31);
+                if (cand < m && ex <= lane) e = cand;
+            }
+            const unsigned ent_e = __shfl_sync(0xffffffffu, ent, e);
+            const int excl_e = __shfl_sync(0xffffffffu, excl, e);
+            const bool has = lane < T;
+            const unsigned cell = (ent_e >> 3) + (unsigned)(lane - excl_e);
+
+            bool open = false, acc = false, isleaf = false;
+            uint2 lk = make_uint2(0u, 0u);
+            if (has) {
+                const float4 tc = __ldg(test + cell);
+                lk = __ldg(link + cell);
+                const float dx = fmaxf(fmaxf(bx0 - tc.x, tc.x - bx1), 0.f);
+                const float dy = fmaxf(fmaxf(by0 - tc.y, tc.y - by1), 0.f);
+                const float dz = fmaxf(fmaxf(bz0 - tc.z, tc.z - bz1), 0.f);
+                const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                open = d2 < tc.w * tc.w;
+                acc = !open;
+                isleaf = (lk.y & LEAF_BIT) != 0u;
+            }
+            // Accepted cells -> body-cell ring.
+            const unsigned am = __ballot_sync(0xffffffffu, acc);
+            if (acc) {
+                const int s = (pc_head + pc_n + __popc(am & lt)) & (RING - 1);
+                const float4 mo = __ldg(mono + cell);
+                const float4 qa = __ldg(quadA + cell);
+                const float2 qb = __ldg(quadB + cell);
+                R.mono[s] = mo; R.qa[s] = qa; R.qb[s] = qb;
+            }
+            pc_n += __popc(am);
+            npc += __popc(am);
+            // Opened internal cells -> push child ranges.
+            const unsigned im = __ballot_sync(0xffffffffu, open && !isleaf);
+            const int np = __popc(im);
+            if (sp + np > stack_cap) {
+                overflow = true;
+            } else {
+                if (open && !isleaf) stk[sp + __popc(im & lt)] = (lk.x << 3) | ((lk.y - 1u) & 7u);
+                sp += np;
+            }
+            // Opened leaves -> body-body ring, 32 bodies at a time.
+            unsigned lm = __ballot_sync(0xffffffffu, open && isleaf);
+            while (lm) {
+                const int src = __ffs(lm) - 1;
+                lm &= lm - 1u;
+                const unsigned lb = __shfl_sync(0xffffffffu, lk.x, src);
+                const unsigned lc = __shfl_sync(0xffffffffu, lk.y, src) & ~LEAF_BIT;
+                npp += lc;
+                for (unsigned o = 0; o < lc; o += 32u) {
+                    const int k = (int)min(32u, lc - o);
+                    if (lane < k) R.pp[(pp_head + pp_n + lane) & (RING - 1)] = __ldg(pos4 + lb + o + lane);
+                    pp_n += k;
+                    if (pp_n >= 32) {
+                        __syncwarp();
+                        eval_pp(R, pp_head, 32, phase, nph, me.x, me.y, me.z, eps2, A);
+                        __syncwarp();
+                        pp_head = (pp_head + 32) & (RING - 1);
+                        pp_n -= 32;
+                    }
+                }
+            }
+            __syncwarp();
+            if (pc_n >= 32) {
+                eval_pc(R, pc_head, 32, phase, nph, me.x, me.y, me.z, eps2, A);
+                pc_head = (pc_head + 32) & (RING - 1);
+                pc_n -= 32;
+            }
+            __syncwarp();
+        }
+        // Remaining partial tiles (they do not wrap: head is 0 or 32, n < 32).
+        if (pc_n > 0) eval_pc(R, pc_head, pc_n, phase, nph, me.x, me.y, me.z, eps2, A);
+        if (pp_n > 0) eval_pp(R, pp_head, pp_n, phase, nph, me.x, me.y, me.z, eps2, A);
+        float ax = A.ax - A.cx, ay = A.ay - A.cy, az = A.az - A.cz, ph = A.ph - A.cp;
+        for (int o = slots; o < 32; o <<= 1) {
+            ax += __shfl_xor_sync(0xffffffffu, ax, o);
+            ay += __shfl_xor_sync(0xffffffffu, ay, o);
+            az += __shfl_xor_sync(0xffffffffu, az, o);
+            ph += __shfl_xor_sync(0xffffffffu, ph, o);
+        }
+        if (live && phase == 0) {
+            ph += me.w * rsqrtf(eps2);           // remove the self term -m/eps
+            acc4[bi] = make_float4(ax, ay, az, ph);
+            counts[bi] = make_uint2(npc, npp - 1u);
+        }
+        if (lane == 0) {
+            atomicAdd(&st->inter[0], (unsigned long long)npc * (unsigned long long)ng);
+            atomicAdd(&st->inter[1], (unsigned long long)(npp - 1u) * (unsigned long long)ng);
+            if (overflow) atomicOr(&st->status, ST_CAPACITY);
+            if (timeout) atomicOr(&st->status, ST_TIMEOUT);
+        }
+        __syncwarp();
+    }
+}
+
+size_t walk_smem_bytes(int warps, int stack_cap) {
+    return (size_t)warps * (sizeof(WarpRings) + (size_t)stack_cap * sizeof(unsigned));
+}
+
+cudaError_t launch_walk(Ctx &c, float eps) {
+    const int warps = c.walk_warps;
+    size_t smem = walk_smem_bytes(warps, c.list_capacity);
+    // Function attribute and occupancy are set up once per shape, before any
+    // stream capture of a step (the first step always runs eagerly).
+    static size_t attr_smem = 0;
+    static int occ_warps = 0, occ_per_sm = 0;
+    static size_t occ_smem = 0;
+    if (smem > attr_smem) {
+        cudaError_t e = cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_smem = smem;
+    }
+    if (occ_warps != warps || occ_smem != smem) {
+        int per = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk, warps * 32, smem);
+        if (e != cudaSuccess) return e;
+        occ_warps = warps; occ_smem = smem; occ_per_sm = per < 1 ? 1 : per;
+    }
+    const int per_sm = occ_per_sm;
+    k_walk<<<c.num_sms * per_sm, warps * 32, smem, c.stream>>>(
+        c.st, c.st, c.groups, c.pos4, c.test, c.cell_link, c.mono, c.quadA, c.quadB, eps,
+        c.list_capacity, c.max_spin, c.acc4, c.counts);
+    return cudaGetLastError();
+}
+
+}  // namespace bonsai

@@ -1,0 +1,60 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+declared in include/bonsai.h (no GPU needed; no compute calls)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bonsai.h")
+
+
+def declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bonsai_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1204_2280_gb300 import builder
+    return builder.build()
+
+
+def test_header_and_binding_agree():
+    import paper_1204_2280_gb300 as B
+    assert declared() == sorted(B.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    syms = {l.split()[-1] for l in out.splitlines() if l.strip()}
+    missing = [s for s in declared() if s not in syms]
+    assert not missing, missing
+    L = C.CDLL(libpath)
+    for s in declared():
+        assert hasattr(L, s)
+
+
+def test_invalid_arguments_rejected_without_gpu(libpath):
+    import paper_1204_2280_gb300 as B
+    L = B.lib()
+    assert L.bonsai_create(None, None, None) == -1
+    ctx = C.c_void_p()
+    bad = B.Config(ncrit=64)
+    assert L.bonsai_create(C.byref(ctx), C.byref(bad), None) == -1
+    assert b"ncrit" in L.bonsai_last_error(None)
+    assert L.bonsai_build(None) == -1
+    assert B.bonsai_version().startswith("bonsai-gb300")
+
+
+def test_create_without_gpu_fails_cleanly(libpath):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_1204_2280_gb300 as B
+    ctx = C.c_void_p()
+    rc = B.lib().bonsai_create(C.byref(ctx), None, None)
+    assert rc == -3 and not ctx.value

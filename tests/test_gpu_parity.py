@@ -1,0 +1,243 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Bars (paper Sect. 2 stages; tolerances from the accuracy requirements of the
+tree-code and FP32 arithmetic):
+* domain, Morton keys, sort permutation, tree topology and groups: bit-exact;
+* moments: M relative 1e-6; com within 4e-7 |com| + 2e-6 l (l the cell side);
+  Q within 1e-5 M l^2 per component;
+* forces vs the oracle tree at the same theta/eps: per-body relative error
+  <= 1e-5 for acceleration and potential, identical interaction counts, for
+  every body whose group took no opening decision within tau of the
+  threshold (tau = 2e-6 + 1e-6 r_open: FP32 and FP64 may decide those
+  differently); the share of such bodies is bounded and they still meet
+* forces vs the FP64 direct sum at theta = 0.75: median <= 1e-3, p99 <= 1e-2.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1204_2280_gb300 as B
+from paper_1204_2280_gb300 import workloads as W
+
+from gpu_common import edge_bodies, gpu_run, rel_err
+
+pytestmark = pytest.mark.gpu
+
+TAU_ABS, TAU_REL = 2e-6, 1e-6
+
+
+def check_keys_tree(res, pos, nleaf, ncrit):
+    mn, S = oracle.domain(pos)
+    k = oracle.keys(pos, mn, S)
+    perm = oracle.sort(k)
+    gmn, gS = res["domain"]
+    assert np.array_equal(gmn, mn) and gS == S
+    assert np.array_equal(res["keys"], k[perm])
+    assert np.array_equal(res["perm"], perm)
+    t = oracle.build_tree(k[perm], nleaf)
+    g = res["tree"]
+    assert g["body_begin"].shape[0] == t.ncells
+    for f in ("body_begin", "body_count", "child_begin", "nchild", "level"):
+        assert np.array_equal(g[f], getattr(t, f)), f
+    gb, gc = oracle.groups(t, ncrit)
+    assert np.array_equal(res["groups"][0], gb) and np.array_equal(res["groups"][1], gc)
+    return mn, S, k, perm, t
+
+
+@pytest.mark.parametrize("n", [1, 2, 17, 4099, 32768, 100003])
+def test_keys_sort_tree_bit_exact_plummer(n):
+    b = W.plummer(n, 0)
+    res = gpu_run(b.pos, b.mass, forces=False)
+    check_keys_tree(res, b.pos, 16, 32)
+
+
+@pytest.mark.parametrize("nleaf,ncrit", [(16, 32), (8, 16), (1, 1), (64, 8), (4, 32)])
+def test_keys_sort_tree_bit_exact_edge_cases(nleaf, ncrit):
+    b = edge_bodies(20000, 3)
+    res = gpu_run(b.pos, b.mass, forces=False, nleaf=nleaf, ncrit=ncrit)
+    check_keys_tree(res, b.pos, nleaf, ncrit)
+
+
+def test_host_buffers_path():
+    b = W.plummer(5000, 7)
+    res = gpu_run(b.pos, b.mass, b.vel, device_io=False)
+    check_keys_tree(res, b.pos, 16, 32)
+    tf = oracle.tree_forces(b.pos, b.mass, 0.75, 0.01, tau_abs=TAU_ABS, tau_rel=TAU_REL)
+    ok = ~tf.borderline
+    assert rel_err(res["acc"], tf.acc)[ok].max() <= 1e-5
+
+
+def test_moments_vs_oracle():
+    b = edge_bodies(32768, 1)
+    res = gpu_run(b.pos, b.mass, forces=False)
+    mn, S, k, perm, t = check_keys_tree(res, b.pos, 16, 32)
+    M, com, Q = oracle.moments(t, b.pos[perm], b.mass[perm])
+    mono, quad = res["mono"].astype(np.float64), res["quad"].astype(np.float64)
+    l = S / 2.0 ** t.level
+    assert np.all(np.abs(mono[:, 3] - M) <= 1e-6 * M)
+    dcom = np.linalg.norm(mono[:, :3] - com, axis=1)
+    assert np.all(dcom <= 4e-7 * np.linalg.norm(com, axis=1) + 2e-6 * l)
+    assert np.all(np.abs(quad - Q) <= 1e-5 * (M * l * l)[:, None])
+
+
+@pytest.mark.parametrize("theta", [0.5, 0.75, 1.0])
+def test_forces_vs_oracle_tree(theta):
+    b = W.plummer(32768, 0)
+    res = gpu_run(b.pos, b.mass, theta=theta, eps=0.01)
+    tf = oracle.tree_forces(b.pos, b.mass, theta, 0.01, 16, 32, TAU_ABS, TAU_REL)
+    ok = ~tf.borderline
+    assert ok.mean() > 0.9, ok.mean()
+    ea = rel_err(res["acc"], tf.acc)
+    ep = np.abs(res["pot"] - tf.pot) / np.abs(tf.pot)
+    assert ea[ok].max() <= 1e-5, (ea[ok].max(), np.argmax(np.where(ok, ea, 0)))
+    assert ep[ok].max() <= 1e-5
+    assert np.array_equal(res["n_pc"][ok], tf.n_pc[ok])
+    assert np.array_equal(res["n_pp"][ok], tf.n_pp[ok])
+    # totals of the whole walk agree with the per-body counts
+    assert res["tot"][0] == int(res["n_pc"].astype(np.int64).sum())
+    assert res["tot"][1] == int(res["n_pp"].astype(np.int64).sum())
+    # borderline bodies: within the approximation's own error of the oracle tree
+    assert ea.max() <= 3e-2
+
+
+def test_forces_vs_direct_sum_gates():
+    """Config: Plummer N=2^15, seed 0, eps=0.01, theta=0.75 (all bodies)."""
+    b = W.plummer(32768, 0)
+    res = gpu_run(b.pos, b.mass, theta=0.75, eps=0.01)
+    a_d, p_d = oracle.direct(b.pos, b.mass, 0.01)
+    e = rel_err(res["acc"], a_d)
+    assert np.median(e) <= 1e-3 and np.percentile(e, 99) <= 1e-2
+    ep = np.abs(res["pot"] - p_d) / np.abs(p_d)
+    assert np.median(ep) <= 1e-3 and np.percentile(ep, 99) <= 1e-2
+
+
+@pytest.mark.parametrize("nleaf,ncrit", [(8, 16), (1, 1), (64, 8), (16, 32)])
+def test_forces_edge_cases(nleaf, ncrit):
+    b = edge_bodies(8192, 5)
+    res = gpu_run(b.pos, b.mass, theta=0.75, eps=0.01, nleaf=nleaf, ncrit=ncrit)
+    tf = oracle.tree_forces(b.pos, b.mass, 0.75, 0.01, nleaf, ncrit, TAU_ABS, TAU_REL)
+    ok = ~tf.borderline
+    assert rel_err(res["acc"], tf.acc)[ok].max() <= 1e-5
+    assert (np.abs(res["pot"] - tf.pot) / np.abs(tf.pot))[ok].max() <= 1e-5
+    assert np.array_equal(res["n_pp"][ok], tf.n_pp[ok])
+
+
+def test_two_bodies_closed_form():
+    pos = np.array([[0.0, 0.0, 0.0], [0.75, -0.5, 0.25]], np.float32)
+    mass = np.array([0.25, 2.0], np.float32)
+    res = gpu_run(pos, mass, theta=0.75, eps=0.1)
+    d = pos[1].astype(np.float64) - pos[0]
+    r2 = d.dot(d) + 0.01
+    assert np.allclose(res["acc"][0], 2.0 * d / r2 ** 1.5, rtol=1e-6)
+    assert np.allclose(res["acc"][1], -0.25 * d / r2 ** 1.5, rtol=1e-6)
+    assert np.allclose(res["pot"], [-2.0 / np.sqrt(r2), -0.25 / np.sqrt(r2)], rtol=1e-6)
+
+
+def test_single_body():
+    res = gpu_run(np.array([[1.0, 2.0, 3.0]], np.float32), np.array([1.0], np.float32))
+    assert np.all(res["acc"] == 0) and abs(res["pot"][0]) < 1e-6
+
+
+def test_theta_small_equals_direct():
+    b = W.plummer(3000, 9)
+    res = gpu_run(b.pos, b.mass, theta=0.02, eps=0.01, list_capacity=8192)
+    a_d, p_d = oracle.direct(b.pos, b.mass, 0.01)
+    assert rel_err(res["acc"], a_d).max() <= 1e-5
+    assert np.all(res["n_pp"] == 2999)
+
+
+def test_kdk_step_vs_oracle():
+    """One force evaluation plus one leapfrog step dt = 1/64 (Plummer 2^15)."""
+    b = W.plummer(32768, 0)
+    dt, th, eps = 1.0 / 64, 0.75, 0.01
+    import torch
+    with B.Bonsai(B.Config()) as bz:
+        bz.set_bodies(b.pos, b.mass, b.vel).build().multipoles()
+        bz.forces(th, eps)
+        bz.step(dt)
+        x1 = np.zeros((32768, 3), np.float32)
+        v1 = np.zeros((32768, 3), np.float32)
+        B.bonsai_get_bodies(bz.ctx, x1, v1)
+        diag = B.bonsai_diagnostics(bz.ctx)
+        bz.sync()
+    tf0 = oracle.tree_forces(b.pos, b.mass, th, eps)
+    ox1, ov1, oa1, op1 = oracle.kdk_step(b.pos, b.vel, b.mass, tf0.acc, dt, th, eps)
+    assert np.allclose(x1, ox1, rtol=2e-7, atol=2e-7)
+    dv = np.linalg.norm(v1 - ov1, axis=1)
+    scale = 0.5 * dt * np.linalg.norm(oa1, axis=1)
+    assert np.median(dv / scale) <= 1e-4 and np.max(dv / (scale + np.linalg.norm(ov1, axis=1))) <= 1e-2
+    # FP64 diagnostics of the new state vs the oracle's (its own potential)
+    e = oracle.energy(x1, v1, b.mass, op1)
+    assert diag[0] == pytest.approx(e[0], rel=1e-9)
+    assert diag[1] == pytest.approx(e[1], rel=2e-5)
+    assert np.allclose(diag[3:6], e[3:6], atol=1e-9)
+    assert diag[6] == pytest.approx(1.0, rel=1e-6)
+
+
+def test_diagnostics_same_snapshot():
+    b = W.plummer(32768, 2)
+    with B.Bonsai(B.Config()) as bz:
+        bz.set_bodies(b.pos, b.mass, b.vel).build().multipoles()
+        pot = np.zeros(32768, np.float32)
+        bz.forces(0.75, 0.01, None, pot)
+        d = B.bonsai_diagnostics(bz.ctx)
+    e = oracle.energy(b.pos, b.vel, b.mass, pot.astype(np.float64))
+    assert d[0] == pytest.approx(e[0], rel=1e-12)
+    assert d[1] == pytest.approx(e[1], rel=1e-9)
+    assert d[2] == pytest.approx(e[2], rel=1e-9)
+    assert np.allclose(d[3:6], e[3:6], atol=1e-12) and d[7] == pytest.approx(e[7], abs=1e-12)
+
+
+def test_multi_step_graph_replay_matches_direct_launches():
+    """Steps replayed from the captured CUDA graph give bit-identical state to
+    steps launched one kernel at a time."""
+    b = W.plummer(20000, 4)
+    outs = []
+    for ug in (1, -1):
+        with B.Bonsai(B.Config(use_graph=ug)) as bz:
+            bz.set_bodies(b.pos, b.mass, b.vel)
+            B.bonsai_set_params(bz.ctx, 0.75, 0.01)
+            for _ in range(4):
+                bz.step(1.0 / 128)
+            x = np.zeros((20000, 3), np.float32)
+            v = np.zeros((20000, 3), np.float32)
+            B.bonsai_get_bodies(bz.ctx, x, v)
+            bz.sync()
+            outs.append((x, v))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_capacity_overflow_reports_error_and_recovers():
+    b = W.plummer(20000, 1)
+    with B.Bonsai(B.Config(list_capacity=64)) as bz:
+        bz.set_bodies(b.pos, b.mass).build().multipoles()
+        with pytest.raises(B.BonsaiError) as ei:
+            bz.forces(0.05, 0.01)
+            bz.sync()
+        assert ei.value.code == -4
+        bz.forces(0.75, 0.01)      # a normal walk on the same context still works
+        bz.sync()
+
+
+def test_bounded_wait_timeout_is_reported():
+    """With a one-poll bound on the sort's look-back, either a timeout is
+    reported (and later stages skip work), or the results are exact; the
+    context stays usable and a fresh one computes correctly."""
+    b = W.plummer(1 << 20, 6)
+    mn, S = oracle.domain(b.pos)
+    k = oracle.keys(b.pos, mn, S)
+    perm = oracle.sort(k)
+    with B.Bonsai(B.Config(max_spin=1)) as bz:
+        bz.set_bodies(b.pos, b.mass).build()
+        try:
+            bz.sync()
+            timed_out = False
+        except B.BonsaiError as e:
+            assert e.code == -5
+            timed_out = True
+        if not timed_out:
+            kk, pp = B.bonsai_get_keys(bz.ctx)
+            assert np.array_equal(pp, perm)
+    res = gpu_run(b.pos[:50000], b.mass[:50000], forces=False)
+    check_keys_tree(res, b.pos[:50000], 16, 32)
