@@ -40,7 +40,7 @@ SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
 KERNELS_PER_STEP = 19               # reset, kick+drift, keys, 8 sort passes, reorder,
                                     # 3 build, multipoles, open radius, walk, kick
-WALK_TRAFFIC_PER_LAUNCH = None      # dram bytes per walk launch from the committed ncu capture
+WALK_TRAFFIC_PER_LAUNCH = 34.5e6   # dram bytes per walk launch, profiles/k_walk_plummer_n2e20_v1.md
 
 
 def parse():

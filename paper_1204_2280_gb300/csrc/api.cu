@@ -21,6 +21,7 @@ struct bonsai_ctx {
 static thread_local std::string g_create_err;
 
 static int fail(bonsai_ctx *ctx, int code, const std::string &what, cudaError_t e = cudaSuccess) {
+    cudaGetLastError();   // a failed runtime call must not leak into the next launch check
     std::string s = what;
     if (e != cudaSuccess) {
         s += ": ";
@@ -105,10 +106,15 @@ cudaError_t pipeline_forces(Ctx &c, float theta, float eps) {
 }
 
 // One kick-drift-kick step; events between the stages give per-stage times.
+// During stream capture the events become event-record nodes of the graph
+// (cudaEventRecordExternal), so replays are timed too.
 cudaError_t pipeline_step(Ctx &c, float dt) {
     cudaError_t e;
-#define STAGE(i, call)                                                  \
-    if ((e = cudaEventRecord(c.ev[i], c.stream)) != cudaSuccess) return e; \
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(c.stream, &cs)) != cudaSuccess) return e;
+    const unsigned evf = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+#define STAGE(i, call)                                                                 \
+    if ((e = cudaEventRecordWithFlags(c.ev[i], c.stream, evf)) != cudaSuccess) return e; \
     if ((e = (call)) != cudaSuccess) return e;
     STAGE(0, launch_reset(c));
     if ((e = launch_kick_drift_bbox(c, dt)) != cudaSuccess) return e;
@@ -120,7 +126,7 @@ cudaError_t pipeline_step(Ctx &c, float dt) {
     STAGE(6, pipeline_forces(c, c.theta, c.eps));
     STAGE(7, launch_kick(c, dt));
 #undef STAGE
-    return cudaEventRecord(c.ev[8], c.stream);
+    return cudaEventRecordWithFlags(c.ev[8], c.stream, evf);
 }
 
 }  // namespace
