@@ -159,8 +159,28 @@ int bonsai_get_moments(bonsai_ctx *ctx, float *mono, float *quad);
 int bonsai_get_counts(bonsai_ctx *ctx, uint32_t *n_pc, uint32_t *n_pp,
                       unsigned long long tot[2]);
 
-/* Text of the last error of ctx (or of the last failed bonsai_create when
- * ctx is NULL).  Valid until the next call on the context. */
+/* Stable sort of n 63-bit keys that allocates nothing.  No counterpart in
+ * the paper: it exists for callers that cannot call cudaMalloc -- code being
+ * captured into a CUDA graph (allocation is illegal there), latency-critical
+ * loops (cudaMalloc/cudaFree may synchronise the device), or hosts whose own
+ * allocator already owns the device memory.  keys (n, read only), sorted_keys
+ * (n) and perm (n) are caller-owned DEVICE buffers on the current device;
+ * sorted_keys[i] = keys[perm[i]], equal keys in input order.  All scratch is
+ * one static device array (about 0.9 MiB, held by every GPU that loads the
+ * library until exit), so n is limited to 65536 (larger n: INVALID_ARG).
+ * The first call on a device looks up that array's device address and must
+ * come before any stream capture.  Every call reuses the same scratch:
+ * calls whose GPU work could overlap (other threads or streams) race and
+ * must be serialised by the caller.  Work is ordered on cuda_stream (NULL:
+ * the legacy default stream); the call synchronises that stream and returns
+ * BONSAI_ERR_TIMEOUT if a bounded device-side wait gave up.  Error text:
+ * bonsai_last_error(NULL). */
+int bonsai_sort_keys_static(const uint64_t *keys, uint64_t *sorted_keys,
+                            uint32_t *perm, long long n, void *cuda_stream);
+
+/* Text of the last error of ctx (or, for ctx == NULL, of the last failed
+ * bonsai_create or bonsai_sort_keys_static of this thread).  Valid until the
+ * next call on the context. */
 const char *bonsai_last_error(const bonsai_ctx *ctx);
 
 /* Library version string. */

@@ -29,7 +29,7 @@ EXPORTS = ["bonsai_create", "bonsai_destroy", "bonsai_set_bodies", "bonsai_build
            "bonsai_get_bodies", "bonsai_diagnostics", "bonsai_sync", "bonsai_get_sizes",
            "bonsai_get_domain", "bonsai_get_keys", "bonsai_get_tree", "bonsai_get_groups",
            "bonsai_get_moments", "bonsai_get_counts", "bonsai_last_error", "bonsai_version",
-           "bonsai_get_stage_times"]
+           "bonsai_get_stage_times", "bonsai_sort_keys_static"]
 
 STAGES = ["kick_drift_domain", "keys", "sort", "reorder", "build", "multipoles", "walk", "kick"]
 
@@ -82,6 +82,7 @@ def lib():
         L.bonsai_last_error.restype = C.c_char_p
         L.bonsai_version.restype = C.c_char_p
         L.bonsai_get_stage_times.argtypes = [p, p, i]
+        L.bonsai_sort_keys_static.argtypes = [p, p, p, ll, p]
         _lib = L
     return _lib
 
@@ -237,6 +238,16 @@ def bonsai_get_stage_times(ctx) -> np.ndarray:
     if rc < 0:
         _check(ctx, rc)
     return ms
+
+
+def bonsai_sort_keys_static(keys, sorted_keys, perm, stream=None):
+    """Sort n <= 65536 device keys without any device allocation (see the
+    C header); keys/sorted_keys: int64 CUDA tensors holding the 63-bit keys,
+    perm: int32 CUDA tensor."""
+    n = int(keys.shape[0])
+    s = None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    _check(None, lib().bonsai_sort_keys_static(keys.data_ptr(), sorted_keys.data_ptr(),
+                                               perm.data_ptr(), n, s))
 
 
 def bonsai_version() -> str:

@@ -20,6 +20,11 @@ struct bonsai_ctx {
 
 static thread_local std::string g_create_err;
 
+namespace bonsai {
+// Errors of calls without a context (bonsai_create, bonsai_sort_keys_static).
+void set_global_error(const char *msg) { g_create_err = msg; }
+}  // namespace bonsai
+
 static int fail(bonsai_ctx *ctx, int code, const std::string &what, cudaError_t e = cudaSuccess) {
     cudaGetLastError();   // a failed runtime call must not leak into the next launch check
     std::string s = what;

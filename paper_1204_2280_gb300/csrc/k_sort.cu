@@ -162,6 +162,7 @@ k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restric
 }
 
 constexpr size_t SORT_DYN_SMEM = (size_t)SORT_TILE * (sizeof(unsigned long long) + sizeof(uint32_t));
+extern const size_t SORT_DYN_SMEM_BYTES = SORT_DYN_SMEM;
 
 cudaError_t launch_sort(Ctx &c) {
     static bool attr_set = false;
