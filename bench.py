@@ -38,9 +38,11 @@ UNIT = "particles/s"
 FLOP_PC, FLOP_PP = 65, 23           # flops per body-cell / body-body interaction
 SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
-KERNELS_PER_STEP = 19               # reset, kick+drift, keys, 8 sort passes, reorder,
-                                    # 3 build, multipoles, open radius, walk, kick
-WALK_TRAFFIC_PER_LAUNCH = 34.5e6   # dram bytes per walk launch, profiles/k_walk_plummer_n2e20_v1.md
+def kernels_per_step(ncrit):
+    """reset, kick+drift, keys, 8 sort passes, reorder, 4 build, multipoles,
+    open radius, walk (two instantiations when groups may exceed 32), kick."""
+    return 20 + (1 if ncrit > 32 else 0)
+WALK_TRAFFIC_PER_LAUNCH = 86.2e6   # dram bytes of the walk stage (both launches), profiles/k_walk_plummer_n2e20.md
 
 
 def parse():
@@ -54,8 +56,9 @@ def parse():
     p.add_argument("--theta", type=float, default=0.75)
     p.add_argument("--eps", type=float, default=0.005)
     p.add_argument("--dt", type=float, default=1.0 / 128)
-    p.add_argument("--ncrit", type=int, default=32)
+    p.add_argument("--ncrit", type=int, default=64)
     p.add_argument("--nleaf", type=int, default=16)
+    p.add_argument("--walk-warps", type=int, default=4)
     p.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -66,7 +69,7 @@ def config(a, world):
     return {"workload": f"Plummer sphere N={a.n} (Henon units, seed {a.seed}), eps={a.eps}, "
                         f"theta={a.theta}, KDK leapfrog dt={a.dt:g}, full rebuild every step",
             "n": a.n, "theta": a.theta, "eps": a.eps, "dt": a.dt, "nleaf": a.nleaf,
-            "ncrit": a.ncrit, "l2": "flushed between timed steps (256 MiB write)",
+            "ncrit": a.ncrit, "walk_warps": a.walk_warps, "l2": "flushed between timed steps (256 MiB write)",
             "parallelism": f"replicas x{world}"}
 
 
@@ -208,7 +211,7 @@ def run_ours(a, rank, world, local_rank):
     torch.cuda.set_stream(stream)
     b = W.plummer(a.n, a.seed)
     n = b.n
-    bz = B.Bonsai(B.Config(nleaf=a.nleaf, ncrit=a.ncrit), stream=stream)
+    bz = B.Bonsai(B.Config(nleaf=a.nleaf, ncrit=a.ncrit, walk_warps=a.walk_warps), stream=stream)
     bz.set_bodies(torch.from_numpy(b.pos).to(dev), torch.from_numpy(b.mass).to(dev),
                   torch.from_numpy(b.vel).to(dev))
     bz.build().multipoles().forces(a.theta, a.eps)
@@ -296,7 +299,7 @@ def run_ours(a, rank, world, local_rank):
                          "flops_basis": f"{FLOP_PC} per body-cell + {FLOP_PP} per body-body interaction"},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": KERNELS_PER_STEP * a.steps,
+            "gpu_launches": kernels_per_step(a.ncrit) * a.steps,
             "clocks": clocks,
             "stages_ms_per_step": {s: float(v) / a.steps for s, v in zip(B.STAGES, stages)},
             "interactions_per_body": {"pc": sum(npc) / (n * a.steps), "pp": sum(npp) / (n * a.steps)},

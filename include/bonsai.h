@@ -51,7 +51,7 @@ typedef struct bonsai_ctx bonsai_ctx;
 /* Tuning knobs; a zero field selects the default shown. */
 typedef struct {
     int nleaf;            /* max bodies per leaf cell (16)                    */
-    int ncrit;            /* max bodies per walk group, 1..32 (32)            */
+    int ncrit;            /* max bodies per walk group, 1..64 (64)            */
     int walk_warps;       /* warps per walk thread block, 1..8 (4)            */
     int list_capacity;    /* walk stack entries per warp, 64..8192 (256)      */
     int use_graph;        /* -1: direct launches; else replay bonsai_step

@@ -77,7 +77,7 @@ cudaError_t alloc_bodies(Ctx &c, long long n) {
     a.take(c.blockcount, (size_t)NROWS * nbb, plan);
     a.take(c.cell_body, ccap, plan); a.take(c.cell_link, ccap, plan);
     a.take(c.cell_level, ccap, plan); a.take(c.cell_parent, ccap, plan);
-    a.take(c.cell_done, ccap, plan);
+    a.take(c.cell_done, ccap, plan); a.take(c.cell_cb, ccap, plan);
     a.take(c.mono, ccap, plan); a.take(c.quadA, ccap, plan); a.take(c.quadB, ccap, plan);
     a.take(c.test, ccap, plan); a.take(c.delta, ccap, plan);
     a.take(c.shadow, 10 * 585, plan);
@@ -159,10 +159,10 @@ int bonsai_create(bonsai_ctx **out, const bonsai_config *cfg, void *cuda_stream)
         if (cfg->max_spin) c.max_spin = cfg->max_spin;
         if (cfg->use_graph < 0) c.use_graph = 0;
     }
-    if (c.nleaf < 1 || c.nleaf > 64 || c.ncrit < 1 || c.ncrit > 32 || c.list_capacity < 64 ||
+    if (c.nleaf < 1 || c.nleaf > 64 || c.ncrit < 1 || c.ncrit > 64 || c.list_capacity < 64 ||
         c.list_capacity > 8192 || c.max_spin < 1 || c.walk_warps < 1 || c.walk_warps > 8) {
         int r = fail(nullptr, BONSAI_ERR_INVALID_ARG,
-                     "bonsai_create: need 1<=nleaf<=64, 1<=ncrit<=32, 64<=list_capacity<=8192, "
+                     "bonsai_create: need 1<=nleaf<=64, 1<=ncrit<=64, 64<=list_capacity<=8192, "
                      "1<=walk_warps<=8");
         delete ctx;
         return r;

@@ -45,16 +45,17 @@ struct DevState {
     unsigned sort_tile[SORT_PASSES];  // tile tickets per pass
     unsigned ncells, ngroups;
     unsigned row_total[NROWS];        // cells per level, groups
-    unsigned walk_next;               // group queue head
+    unsigned level_start[MAX_LEVEL + 2]; // first cell of each level; [22] = ncells
+    unsigned walk_next;               // group queue heads (groups <= 32 / 33..64 bodies)
+    unsigned walk_next2;
     unsigned status;
-    unsigned pad0;
     unsigned long long inter[2];      // n_pc, n_pp totals of the last walk
     double diag[8];
 };
 
 struct Ctx {
     // configuration
-    int nleaf = 16, ncrit = 32, walk_warps = 4, list_capacity = 256, use_graph = 1;
+    int nleaf = 16, ncrit = 64, walk_warps = 4, list_capacity = 256, use_graph = 1;
     long long max_spin = 1ll << 24;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -73,11 +74,10 @@ struct Ctx {
     uint32_t *vals = nullptr, *vals_alt = nullptr;   // vals ends as perm
     unsigned *tile_status = nullptr;                   // SORT_PASSES * ntiles * 256
     // build
-    uint32_t *binfo = nullptr;       // per body: lo | hi<<5 | has<<10 | ngrp<<16
     unsigned *blockcount = nullptr;  // NROWS * nbblocks
     uint2 *cell_body = nullptr, *cell_link = nullptr;
     uint8_t *cell_level = nullptr;
-    uint32_t *cell_parent = nullptr, *cell_done = nullptr;
+    uint32_t *cell_parent = nullptr, *cell_done = nullptr, *cell_cb = nullptr;
     float4 *mono = nullptr, *quadA = nullptr, *test = nullptr;
     float2 *quadB = nullptr;
     float *delta = nullptr;

@@ -23,7 +23,7 @@ __global__ void k_reset(DevState *st, int what) {
         if (t < SORT_PASSES) st->sort_tile[t] = 0;
     }
     if (what & 2) {                        // walk inputs
-        if (t == 0) { st->walk_next = 0; st->inter[0] = 0; st->inter[1] = 0; }
+        if (t == 0) { st->walk_next = 0; st->walk_next2 = 0; st->inter[0] = 0; st->inter[1] = 0; }
     }
     if (what & 4) {
         if (t < 8) st->diag[t] = 0.0;

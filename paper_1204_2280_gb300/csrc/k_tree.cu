@@ -68,53 +68,72 @@ __device__ __forceinline__ unsigned digit_at(unsigned long long k, int level) {
     return (unsigned)(k >> (3 * (MAX_LEVEL - level))) & 7u;
 }
 
-// Number of distinct level-(l+1) octants among sorted keys sk[b..e) that
-// share their level-l prefix.
-__device__ int count_children(const unsigned long long *__restrict__ sk, int b, int e, int l) {
-    unsigned d0 = digit_at(sk[b], l + 1), d1 = digit_at(sk[e - 1], l + 1);
-    int nch = 1, pos = b;
-    for (unsigned o = d0 + 1; o <= d1; o++) {
-        int lo = pos, hi = e;                 // first index with digit >= o
-        while (lo < hi) {
-            int mid = lo + ((hi - lo) >> 1);
-            if (digit_at(sk[mid], l + 1) < o) lo = mid + 1; else hi = mid;
-        }
-        if (lo < e && digit_at(sk[lo], l + 1) == o) nch++;
-        pos = lo;
-    }
-    return nch;
-}
-
 struct BodyCells {
     bool has;
     int lo, hi, ngrp, lg;   // lg: group level (>hi: oversize leaf cut in chunks)
 };
 
-// Per-body analysis shared by the count and write kernels.  s_k holds keys
-// [base - W, base + BUILD_THREADS + W); keys outside [0, n) are never read.
-__device__ BodyCells analyse_body(const unsigned long long *s_k, int W, int base, int t, int n,
-                                  int nleaf, int ncrit, const unsigned long long *__restrict__ sk) {
+// Shared memory of a build block: keys [base-W, base+B+W) and, for
+// j in [base-W, base+B), D(j) = cpl(k[j], k[j+nleaf]) and DG(j) with ncrit
+// (-1 where j+w is past the end).
+struct BuildShared {
+    unsigned long long *k;
+    int *D, *DG;
+    int W, base;
+    __device__ unsigned long long key(int j) const { return k[j - base + W]; }
+    __device__ int d(int j) const { return D[j - base + W]; }
+    __device__ int dg(int j) const { return DG[j - base + W]; }
+};
+
+__device__ BuildShared load_build_shared(void *smem, const unsigned long long *__restrict__ sk,
+                                         int n, int base, int nleaf, int ncrit) {
+    BuildShared b;
+    b.W = max(nleaf, ncrit);
+    b.base = base;
+    b.k = (unsigned long long *)smem;
+    b.D = (int *)(b.k + BUILD_THREADS + 2 * b.W);
+    b.DG = b.D + BUILD_THREADS + b.W;
+    for (int i = threadIdx.x; i < BUILD_THREADS + 2 * b.W; i += blockDim.x) {
+        int j = base - b.W + i;
+        b.k[i] = (j >= 0 && j < n) ? sk[j] : 0ull;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < BUILD_THREADS + b.W; i += blockDim.x) {
+        int j = base - b.W + i;
+        b.D[i] = (j >= 0 && j + nleaf < n) ? key_cpl(b.key(j), b.key(j + nleaf)) : -1;
+        b.DG[i] = (j >= 0 && j + ncrit < n) ? key_cpl(b.key(j), b.key(j + ncrit)) : -1;
+    }
+    __syncthreads();
+    return b;
+}
+
+size_t build_smem_bytes(int nleaf, int ncrit) {
+    int W = nleaf > ncrit ? nleaf : ncrit;
+    return (size_t)(BUILD_THREADS + 2 * W) * 8 + 2 * (size_t)(BUILD_THREADS + W) * 4;
+}
+
+// Which cells body t starts (levels lo..hi) and how many groups.
+__device__ BodyCells analyse_body(const BuildShared &b, int t, int n, int nleaf, int ncrit,
+                                  const unsigned long long *__restrict__ sk) {
     BodyCells r{false, 0, -1, 0, 0};
     if (t >= n) return r;
-    auto K = [&](int j) { return s_k[j - base + W]; };
-    int l0 = (t == 0) ? 0 : key_cpl(K(t - 1), K(t)) + 1;
+    int l0 = (t == 0) ? 0 : key_cpl(b.key(t - 1), b.key(t)) + 1;
     if (l0 > MAX_LEVEL) return r;
-    auto D = [&](int j, int w) { return (j >= 0 && j + w < n) ? key_cpl(K(j), K(j + w)) : -1; };
     if (l0 > 0) {
         int e = -1;
-        for (int j = max(0, t - nleaf); j <= t; j++) e = max(e, D(j, nleaf));
+        for (int j = max(0, t - nleaf); j <= t; j++) e = max(e, b.d(j));
         if (e < l0 - 1) return r;
     }
     r.has = true;
     r.lo = l0;
-    r.hi = max(l0, min(D(t, nleaf) + 1, MAX_LEVEL));
-    int lg = max(l0, D(t, ncrit) + 1);
+    r.hi = max(l0, min(b.d(t) + 1, MAX_LEVEL));
+    int lg = max(l0, b.dg(t) + 1);
     r.lg = lg;
     if (lg <= r.hi) {
         bool starts = (lg > l0) || l0 == 0;
         if (!starts) {
             int e = -1;
-            for (int j = max(0, t - ncrit); j <= t; j++) e = max(e, D(j, ncrit));
+            for (int j = max(0, t - ncrit); j <= t; j++) e = max(e, b.dg(j));
             starts = e >= l0 - 1;
         }
         r.ngrp = starts ? 1 : 0;
@@ -125,29 +144,23 @@ __device__ BodyCells analyse_body(const unsigned long long *s_k, int W, int base
     return r;
 }
 
-__device__ void load_key_window(unsigned long long *s_k, const unsigned long long *__restrict__ sk,
-                                int n, int base, int W) {
-    for (int i = threadIdx.x; i < BUILD_THREADS + 2 * W; i += blockDim.x) {
-        int j = base - W + i;
-        s_k[i] = (j >= 0 && j < n) ? sk[j] : 0ull;
-    }
+__device__ __forceinline__ bool has_level(const BodyCells &bc, int r) {
+    return bc.has && bc.lo <= r && r <= bc.hi;
 }
 
 // Pass 1: per block, the number of cells of each level and of groups.
 __global__ void __launch_bounds__(BUILD_THREADS)
 k_build_count(const unsigned long long *__restrict__ sk, int n, int nleaf, int ncrit,
               unsigned *blockcount, int nblocks, const DevState *__restrict__ st) {
-    extern __shared__ unsigned long long s_k[];
-    if (st->status & ST_TIMEOUT) return;        // keys not sorted: skip the build
+    extern __shared__ unsigned long long smem_u64[];
     __shared__ unsigned s_wc[NROWS][32];
-    const int W = max(nleaf, ncrit);
+    if (st->status & ST_TIMEOUT) return;        // keys not sorted: skip the build
     const int base = blockIdx.x * BUILD_THREADS, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    load_key_window(s_k, sk, n, base, W);
-    __syncthreads();
-    BodyCells bc = analyse_body(s_k, W, base, base + tid, n, nleaf, ncrit, sk);
+    BuildShared b = load_build_shared(smem_u64, sk, n, base, nleaf, ncrit);
+    BodyCells bc = analyse_body(b, base + tid, n, nleaf, ncrit, sk);
     for (int r = 0; r <= MAX_LEVEL; r++) {
-        unsigned b = __ballot_sync(0xffffffffu, bc.has && bc.lo <= r && r <= bc.hi);
-        if (lane == 0) s_wc[r][warp] = __popc(b);
+        unsigned m = __ballot_sync(0xffffffffu, has_level(bc, r));
+        if (lane == 0) s_wc[r][warp] = __popc(m);
     }
     int g = bc.ngrp;
 #pragma unroll
@@ -199,30 +212,34 @@ k_build_scan(unsigned *blockcount, int nblocks, DevState *st) {
     if (tid == 0) st->row_total[blockIdx.x] = s_carry;
 }
 
-// Pass 3: write every cell, its children links and parent pointers, and the
-// groups.
+// Pass 3: number every cell and write its first body, level and link.  For
+// each cell (level r, first body t) it also records cb = the number of
+// level-(r+1) cells that start before t, offset to level r+1's first index:
+// for an internal cell that is its first child, and the children of a cell
+// are the level-(r+1) cells between its cb and the next cell's cb.  Leaves
+// get their body count here (a short search); internal cells in pass 4.
 __global__ void __launch_bounds__(BUILD_THREADS)
 k_build_write(const unsigned long long *__restrict__ sk, int n, int nleaf, int ncrit,
               const unsigned *__restrict__ blockcount, int nblocks, long long ccap, DevState *st,
               uint2 *cell_body, uint2 *cell_link, uint8_t *cell_level, uint32_t *cell_parent,
-              uint32_t *cell_done, uint2 *groups) {
-    extern __shared__ unsigned long long s_k[];
+              uint32_t *cell_done, uint32_t *cell_cb, uint2 *groups) {
+    extern __shared__ unsigned long long smem_u64[];
     __shared__ unsigned s_wc[NROWS][32];
     __shared__ unsigned s_base[NROWS];
     __shared__ int s_ok;
-    const int W = max(nleaf, ncrit);
     const int base = blockIdx.x * BUILD_THREADS, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (st->status & ST_TIMEOUT) return;        // keys not sorted: skip the build
-    load_key_window(s_k, sk, n, base, W);
     if (tid == 0) {
         unsigned run = 0;
         for (int r = 0; r <= MAX_LEVEL; r++) {
             s_base[r] = run + blockcount[(size_t)r * nblocks + blockIdx.x];
+            if (blockIdx.x == 0) st->level_start[r] = run;
             run += st->row_total[r];
         }
         s_base[GROUP_ROW] = blockcount[(size_t)GROUP_ROW * nblocks + blockIdx.x];
         s_ok = (long long)run <= ccap;
         if (blockIdx.x == 0) {
+            st->level_start[MAX_LEVEL + 1] = run;
             st->ncells = run;
             st->ngroups = st->row_total[GROUP_ROW];
             if (!s_ok) atomicOr(&st->status, ST_CAPACITY);
@@ -230,14 +247,14 @@ k_build_write(const unsigned long long *__restrict__ sk, int n, int nleaf, int n
     }
     __syncthreads();
     if (!s_ok) return;
+    BuildShared b = load_build_shared(smem_u64, sk, n, base, nleaf, ncrit);
     const int t = base + tid;
-    BodyCells bc = analyse_body(s_k, W, base, t, n, nleaf, ncrit, sk);
+    BodyCells bc = analyse_body(b, t, n, nleaf, ncrit, sk);
     const unsigned lt = (1u << lane) - 1u;
 
-    // Warp-level counts per row, then exclusive prefix across warps.
     for (int r = 0; r <= MAX_LEVEL; r++) {
-        unsigned b = __ballot_sync(0xffffffffu, bc.has && bc.lo <= r && r <= bc.hi);
-        if (lane == 0) s_wc[r][warp] = __popc(b);
+        unsigned m = __ballot_sync(0xffffffffu, has_level(bc, r));
+        if (lane == 0) s_wc[r][warp] = __popc(m);
     }
     int gx = bc.ngrp;                            // inclusive warp scan of group counts
 #pragma unroll
@@ -248,7 +265,7 @@ k_build_write(const unsigned long long *__restrict__ sk, int n, int nleaf, int n
     if (lane == 31) s_wc[GROUP_ROW][warp] = (unsigned)gx;
     gx -= bc.ngrp;
     __syncthreads();
-    if (warp < NROWS) {
+    if (warp < NROWS) {                          // exclusive prefix across warps per row
         unsigned v = s_wc[warp][lane], x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -260,30 +277,26 @@ k_build_write(const unsigned long long *__restrict__ sk, int n, int nleaf, int n
     }
     __syncthreads();
 
-    // Cells of this body, level by level (warp-uniform loop for the ballots).
-    unsigned prev_c = 0;
-    int prev_nch = 0;
+    unsigned bcur = __ballot_sync(0xffffffffu, has_level(bc, 0));
     for (int r = 0; r <= MAX_LEVEL; r++) {
-        bool mine = bc.has && bc.lo <= r && r <= bc.hi;
-        unsigned b = __ballot_sync(0xffffffffu, mine);
-        if (!mine) continue;
-        unsigned c = s_base[r] + s_wc[r][warp] + __popc(b & lt);
-        if (r > bc.lo) {                         // link the parent made at r-1
-            cell_link[prev_c] = make_uint2(c, (unsigned)prev_nch);
-            for (int k = 0; k < prev_nch; k++) cell_parent[c + k] = prev_c;
+        const unsigned bnext = r < MAX_LEVEL ? __ballot_sync(0xffffffffu, has_level(bc, r + 1)) : 0u;
+        if (has_level(bc, r)) {
+            const unsigned c = s_base[r] + s_wc[r][warp] + __popc(bcur & lt);
+            const unsigned cb = r < MAX_LEVEL ? s_base[r + 1] + s_wc[r + 1][warp] + __popc(bnext & lt) : 0u;
+            cell_cb[c] = cb;
+            cell_level[c] = (uint8_t)r;
+            cell_done[c] = 0u;
+            if (r == 0) cell_parent[c] = 0xffffffffu;
+            if (r == bc.hi) {
+                int cnt = run_end(sk, n, t, r) - t;
+                cell_body[c] = make_uint2((unsigned)t, (unsigned)cnt);
+                cell_link[c] = make_uint2((unsigned)t, (unsigned)cnt | LEAF_BIT);
+            } else {
+                cell_body[c] = make_uint2((unsigned)t, 0u);
+                cell_link[c] = make_uint2(cb, 0u);
+            }
         }
-        int e = run_end(sk, n, t, r);
-        int cnt = e - t;
-        cell_body[c] = make_uint2((unsigned)t, (unsigned)cnt);
-        cell_level[c] = (uint8_t)r;
-        cell_done[c] = 0u;
-        if (r == 0) cell_parent[c] = 0xffffffffu;
-        if (r == bc.hi) {
-            cell_link[c] = make_uint2((unsigned)t, (unsigned)cnt | LEAF_BIT);
-        } else {
-            prev_nch = count_children(sk, t, e, r);
-        }
-        prev_c = c;
+        bcur = bnext;
     }
     // Groups in key order.
     if (bc.ngrp > 0) {
@@ -301,10 +314,39 @@ k_build_write(const unsigned long long *__restrict__ sk, int n, int nleaf, int n
     }
 }
 
+// Pass 4 (one thread per internal cell): child count from the cb of the next
+// cell of the same level, parent pointers of the children, and the body
+// count from the descent along last children to a leaf.
+__global__ void k_build_link(const DevState *__restrict__ st, const uint32_t *__restrict__ cell_cb,
+                             const uint8_t *__restrict__ cell_level, uint2 *cell_link,
+                             uint2 *cell_body, uint32_t *cell_parent) {
+    const unsigned c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= st->ncells || (st->status & ST_TIMEOUT)) return;
+    if (cell_link[c].y & LEAF_BIT) return;
+    auto nchild_of = [&](unsigned d, int l) {
+        unsigned next = (d + 1 < st->level_start[l + 1]) ? cell_cb[d + 1] : st->level_start[l + 2];
+        return next - cell_cb[d];
+    };
+    const int l = cell_level[c];
+    const unsigned cb = cell_cb[c];
+    const unsigned nch = nchild_of(c, l);
+    cell_link[c] = make_uint2(cb, nch);
+    for (unsigned k = 0; k < nch; k++) cell_parent[cb + k] = c;
+    unsigned d = cb + nch - 1;                   // last child, then its last child, ...
+    int ld = l + 1;
+    uint2 lk = cell_link[d];
+    for (int it = 0; it < MAX_LEVEL && !(lk.y & LEAF_BIT); it++) {   // at most 21 levels
+        d = cell_cb[d] + nchild_of(d, ld) - 1;
+        ld++;
+        lk = cell_link[d];
+    }
+    const unsigned t = cell_body[c].x;
+    cell_body[c].y = lk.x + (lk.y & ~LEAF_BIT) - t;
+}
+
 cudaError_t launch_build(Ctx &c) {
     int n = (int)c.n;
-    int W = c.nleaf > c.ncrit ? c.nleaf : c.ncrit;
-    size_t smem = (size_t)(BUILD_THREADS + 2 * W) * sizeof(unsigned long long);
+    size_t smem = build_smem_bytes(c.nleaf, c.ncrit);
     k_build_count<<<c.nbblocks, BUILD_THREADS, smem, c.stream>>>(c.keys, n, c.nleaf, c.ncrit,
                                                                  c.blockcount, c.nbblocks, c.st);
     cudaError_t e = cudaGetLastError();
@@ -314,7 +356,12 @@ cudaError_t launch_build(Ctx &c) {
     if (e != cudaSuccess) return e;
     k_build_write<<<c.nbblocks, BUILD_THREADS, smem, c.stream>>>(
         c.keys, n, c.nleaf, c.ncrit, c.blockcount, c.nbblocks, c.ccap, c.st, c.cell_body,
-        c.cell_link, c.cell_level, c.cell_parent, c.cell_done, c.groups);
+        c.cell_link, c.cell_level, c.cell_parent, c.cell_done, c.cell_cb, c.groups);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    unsigned grid = (unsigned)((c.ccap + 255) / 256);
+    k_build_link<<<grid, 256, 0, c.stream>>>(c.st, c.cell_cb, c.cell_level, c.cell_link, c.cell_body,
+                                             c.cell_parent);
     return cudaGetLastError();
 }
 

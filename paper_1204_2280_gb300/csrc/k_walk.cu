@@ -1,8 +1,8 @@
 // k_walk.cu -- the group-wise Barnes-Hut tree-traverse (paper Sect. 2,
 // "tree-traverse"; MAC after Barnes 1994 combined with the vector-machine
-// group walk of Barnes 1990).  This is the dominant kernel (>90% of a step).
+// group walk of Barnes 1990).  This is the dominant kernel (>80% of a step).
 //
-// One warp owns one group (<= 32 bodies that share an interaction list).  A
+// One warp owns one group (<= 64 bodies that share an interaction list).  A
 // persistent grid pulls groups from an atomic queue in key order.  Per warp:
 //  * a stack of child ranges (first child, count <= 8) in shared memory; each
 //    round pops up to 32 cells, one per lane, and tests them against the
@@ -13,9 +13,11 @@
 //    cells push their child range;
 //  * whenever a ring holds 32 sources the warp evaluates that tile: every
 //    lane streams the sources from shared memory (broadcast reads) with FP32
-//    FMAs.  A group of n bodies uses s = next_pow2(n) body slots; the 32/s
-//    lanes sharing a body split the tile's sources between them and are summed
-//    at the end, so small groups still keep all lanes busy;
+//    FMAs.  Groups of <= 32 bodies: a group of n bodies uses s = next_pow2(n)
+//    body slots and the 32/s lanes sharing a body split the tile's sources
+//    (summed at the end), so small groups still keep all lanes busy.  Groups
+//    of 33..64 bodies run in a second instantiation with two bodies per lane
+//    that share every source read;
 //  * each tile is summed in plain FP32 and added to the body's accumulators
 //    with Kahan compensation (one compensated add per tile and component).
 // Body-cell (monopole + traceless quadrupole, softened):
@@ -28,6 +30,10 @@
 namespace bonsai {
 
 constexpr int RING = 64;
+#ifndef WALK_UNROLL
+#define WALK_UNROLL 4            // unroll depth of the tile loops
+#endif
+constexpr int kWalkUnroll = WALK_UNROLL;
 
 struct WarpRings {
     float4 mono[RING];   // com xyz, M
@@ -48,51 +54,121 @@ struct Acc {
     float cx, cy, cz, cp;    // Kahan compensations
 };
 
-__device__ __forceinline__ void eval_pc(const WarpRings &R, int head, int cnt, int phase, int nph,
-                                        float x, float y, float z, float eps2, Acc &A) {
-    float px = 0.f, py = 0.f, pz = 0.f, pp = 0.f;
-    for (int k = phase; k < cnt; k += nph) {
-        const int s = head + k;
-        const float4 mo = R.mono[s];
-        const float4 qa = R.qa[s];
-        const float2 qb = R.qb[s];
-        const float dx = mo.x - x, dy = mo.y - y, dz = mo.z - z;
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-        const float rinv = rsqrtf(r2);
-        const float rinv2 = rinv * rinv;
-        const float mr = mo.w * rinv;
-        const float mr3 = mr * rinv2;
-        const float qx = fmaf(qa.w, dy, fmaf(qb.x, dz, qa.x * dx));
-        const float qy = fmaf(qa.w, dx, fmaf(qb.y, dz, qa.y * dy));
-        const float qz = fmaf(qb.x, dx, fmaf(qb.y, dy, qa.z * dz));
-        const float q = fmaf(dz, qz, fmaf(dy, qy, dx * qx));
-        const float rinv5 = rinv2 * rinv2 * rinv;
-        const float qr5 = q * rinv5;
-        pp -= fmaf(0.5f, qr5, mr);
-        const float sc = fmaf(2.5f * qr5, rinv2, mr3);
-        px = fmaf(sc, dx, px); px = fmaf(-rinv5, qx, px);
-        py = fmaf(sc, dy, py); py = fmaf(-rinv5, qy, py);
-        pz = fmaf(sc, dz, pz); pz = fmaf(-rinv5, qz, pz);
-    }
-    kahan_add(A.ax, A.cx, px); kahan_add(A.ay, A.cy, py);
-    kahan_add(A.az, A.cz, pz); kahan_add(A.ph, A.cp, pp);
+struct Part {
+    float x, y, z, p;
+};
+
+__device__ __forceinline__ void pc_one(const float4 mo, const float4 qa, const float2 qb, const float4 me,
+                                       float eps2, Part &P) {
+    const float dx = mo.x - me.x, dy = mo.y - me.y, dz = mo.z - me.z;
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+    const float rinv = rsqrtf(r2);
+    const float rinv2 = rinv * rinv;
+    const float mr = mo.w * rinv;
+    const float mr3 = mr * rinv2;
+    const float qx = fmaf(qa.w, dy, fmaf(qb.x, dz, qa.x * dx));
+    const float qy = fmaf(qa.w, dx, fmaf(qb.y, dz, qa.y * dy));
+    const float qz = fmaf(qb.x, dx, fmaf(qb.y, dy, qa.z * dz));
+    const float q = fmaf(dz, qz, fmaf(dy, qy, dx * qx));
+    const float rinv5 = rinv2 * rinv2 * rinv;
+    const float qr5 = q * rinv5;
+    P.p -= fmaf(0.5f, qr5, mr);
+    const float sc = fmaf(2.5f * qr5, rinv2, mr3);
+    P.x = fmaf(sc, dx, P.x); P.x = fmaf(-rinv5, qx, P.x);
+    P.y = fmaf(sc, dy, P.y); P.y = fmaf(-rinv5, qy, P.y);
+    P.z = fmaf(sc, dz, P.z); P.z = fmaf(-rinv5, qz, P.z);
 }
 
-__device__ __forceinline__ void eval_pp(const WarpRings &R, int head, int cnt, int phase, int nph,
-                                        float x, float y, float z, float eps2, Acc &A) {
-    float px = 0.f, py = 0.f, pz = 0.f, pp = 0.f;
-    for (int k = phase; k < cnt; k += nph) {
-        const float4 s = R.pp[head + k];
-        const float dx = s.x - x, dy = s.y - y, dz = s.z - z;
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-        const float rinv = rsqrtf(r2);
-        const float mr = s.w * rinv;
-        const float mr3 = mr * rinv * rinv;
-        pp -= mr;
-        px = fmaf(mr3, dx, px); py = fmaf(mr3, dy, py); pz = fmaf(mr3, dz, pz);
+__device__ __forceinline__ void pp_one(const float4 s, const float4 me, float eps2, Part &P) {
+    const float dx = s.x - me.x, dy = s.y - me.y, dz = s.z - me.z;
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+    const float rinv = rsqrtf(r2);
+    const float mr = s.w * rinv;
+    const float mr3 = mr * rinv * rinv;
+    P.p -= mr;
+    P.x = fmaf(mr3, dx, P.x); P.y = fmaf(mr3, dy, P.y); P.z = fmaf(mr3, dz, P.z);
+}
+
+template <int BPL>
+__device__ __forceinline__ void commit(const Part (&P)[BPL], Acc (&A)[BPL]) {
+#pragma unroll
+    for (int b = 0; b < BPL; b++) {
+        kahan_add(A[b].ax, A[b].cx, P[b].x); kahan_add(A[b].ay, A[b].cy, P[b].y);
+        kahan_add(A[b].az, A[b].cz, P[b].z); kahan_add(A[b].ph, A[b].cp, P[b].p);
     }
-    kahan_add(A.ax, A.cx, px); kahan_add(A.ay, A.cy, py);
-    kahan_add(A.az, A.cz, pz); kahan_add(A.ph, A.cp, pp);
+}
+
+// Tile evaluation.  NPH lanes share one body and split the tile's 32 sources
+// (lane phase p takes sources p, p+NPH, ...): the trip count 32/NPH and the
+// stride are compile-time constants, so the shared-memory reads use immediate
+// offsets and there is no per-interaction loop bookkeeping.  Each lane holds
+// BPL bodies that reuse every source read.  Partial tiles are padded with
+// massless sources far away, which add exactly zero.
+template <int NPH, int BPL>
+__device__ __forceinline__ void eval_pc(const WarpRings &R, int head, int phase,
+                                        const float4 (&me)[BPL], float eps2, Acc (&A)[BPL]) {
+    constexpr int T = 32 / NPH;
+    const float4 *mono = R.mono + head + phase;
+    const float4 *qa4 = R.qa + head + phase;
+    const float2 *qb2 = R.qb + head + phase;
+    Part P[BPL];
+#pragma unroll
+    for (int b = 0; b < BPL; b++) P[b] = Part{0.f, 0.f, 0.f, 0.f};
+#pragma unroll kWalkUnroll
+    for (int j = 0; j < T; j++) {
+        const float4 mo = mono[j * NPH];
+        const float4 qa = qa4[j * NPH];
+        const float2 qb = qb2[j * NPH];
+#pragma unroll
+        for (int b = 0; b < BPL; b++) pc_one(mo, qa, qb, me[b], eps2, P[b]);
+    }
+    commit<BPL>(P, A);
+}
+
+template <int NPH, int BPL>
+__device__ __forceinline__ void eval_pp(const WarpRings &R, int head, int phase,
+                                        const float4 (&me)[BPL], float eps2, Acc (&A)[BPL]) {
+    constexpr int T = 32 / NPH;
+    const float4 *src = R.pp + head + phase;
+    Part P[BPL];
+#pragma unroll
+    for (int b = 0; b < BPL; b++) P[b] = Part{0.f, 0.f, 0.f, 0.f};
+#pragma unroll kWalkUnroll
+    for (int j = 0; j < T; j++) {
+        const float4 s = src[j * NPH];
+#pragma unroll
+        for (int b = 0; b < BPL; b++) pp_one(s, me[b], eps2, P[b]);
+    }
+    commit<BPL>(P, A);
+}
+
+// Warp-uniform dispatch on log2(body slots); two bodies per lane always use
+// all 32 lanes as slots.
+template <int BPL>
+__device__ __forceinline__ void tile_pc(int lg, const WarpRings &R, int head, int phase,
+                                        const float4 (&me)[BPL], float eps2, Acc (&A)[BPL]) {
+    if (BPL == 2) { eval_pc<1, BPL>(R, head, phase, me, eps2, A); return; }
+    switch (lg) {
+        case 0: eval_pc<32, BPL>(R, head, phase, me, eps2, A); break;
+        case 1: eval_pc<16, BPL>(R, head, phase, me, eps2, A); break;
+        case 2: eval_pc<8, BPL>(R, head, phase, me, eps2, A); break;
+        case 3: eval_pc<4, BPL>(R, head, phase, me, eps2, A); break;
+        case 4: eval_pc<2, BPL>(R, head, phase, me, eps2, A); break;
+        default: eval_pc<1, BPL>(R, head, phase, me, eps2, A); break;
+    }
+}
+template <int BPL>
+__device__ __forceinline__ void tile_pp(int lg, const WarpRings &R, int head, int phase,
+                                        const float4 (&me)[BPL], float eps2, Acc (&A)[BPL]) {
+    if (BPL == 2) { eval_pp<1, BPL>(R, head, phase, me, eps2, A); return; }
+    switch (lg) {
+        case 0: eval_pp<32, BPL>(R, head, phase, me, eps2, A); break;
+        case 1: eval_pp<16, BPL>(R, head, phase, me, eps2, A); break;
+        case 2: eval_pp<8, BPL>(R, head, phase, me, eps2, A); break;
+        case 3: eval_pp<4, BPL>(R, head, phase, me, eps2, A); break;
+        case 4: eval_pp<2, BPL>(R, head, phase, me, eps2, A); break;
+        default: eval_pp<1, BPL>(R, head, phase, me, eps2, A); break;
+    }
 }
 
 __device__ __forceinline__ unsigned lanemask_lt_w() {
@@ -101,6 +177,8 @@ __device__ __forceinline__ unsigned lanemask_lt_w() {
     return m;
 }
 
+// BPL = 1 walks the groups of <= 32 bodies, BPL = 2 those of 33..64.
+template <int BPL>
 __global__ void __launch_bounds__(256)
 k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__ groups,
        const float4 *__restrict__ pos4, const float4 *__restrict__ test,
@@ -116,23 +194,36 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
     const unsigned ngroups = (stc->status & ST_TIMEOUT) ? 0u : stc->ngroups;
     const float eps2 = eps * eps;
     const unsigned lt = lanemask_lt_w();
+    unsigned *queue = BPL == 1 ? &st->walk_next : &st->walk_next2;
 
     while (true) {
         unsigned g = 0;
-        if (lane == 0) g = atomicAdd(&st->walk_next, 1u);
+        if (lane == 0) g = atomicAdd(queue, 1u);
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= ngroups) break;
         const uint2 gr = groups[g];
         const int gb = (int)gr.x, ng = (int)gr.y;
-        // body slots and source phases
-        const int lg = ng <= 1 ? 0 : 32 - __clz(ng - 1);      // log2(next_pow2(ng))
-        const int slots = 1 << lg, nph = 32 >> lg;
+        if ((BPL == 1) != (ng <= 32)) continue;      // the other instantiation's group
+        // Body slots and source phases.
+        const int lg = BPL == 2 ? 5 : (ng <= 1 ? 0 : 32 - __clz(ng - 1));   // log2(next_pow2)
+        const int slots = 1 << lg;
         const int bslot = lane & (slots - 1), phase = lane >> lg;
-        const bool live = bslot < ng;
-        const int bi = gb + (live ? bslot : 0);
-        const float4 me = pos4[bi];
-        float bx0 = live ? me.x : INFINITY, by0 = live ? me.y : INFINITY, bz0 = live ? me.z : INFINITY;
-        float bx1 = live ? me.x : -INFINITY, by1 = live ? me.y : -INFINITY, bz1 = live ? me.z : -INFINITY;
+        bool live[BPL];
+        int bi[BPL];
+        float4 me[BPL];
+        float bx0 = INFINITY, by0 = INFINITY, bz0 = INFINITY;
+        float bx1 = -INFINITY, by1 = -INFINITY, bz1 = -INFINITY;
+#pragma unroll
+        for (int b = 0; b < BPL; b++) {
+            const int slot = bslot + 32 * b;
+            live[b] = slot < ng;
+            bi[b] = gb + (live[b] ? slot : 0);
+            me[b] = pos4[bi[b]];
+            if (live[b]) {
+                bx0 = fminf(bx0, me[b].x); by0 = fminf(by0, me[b].y); bz0 = fminf(bz0, me[b].z);
+                bx1 = fmaxf(bx1, me[b].x); by1 = fmaxf(by1, me[b].y); bz1 = fmaxf(bz1, me[b].z);
+            }
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             bx0 = fminf(bx0, __shfl_xor_sync(0xffffffffu, bx0, o));
@@ -142,9 +233,11 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
             by1 = fmaxf(by1, __shfl_xor_sync(0xffffffffu, by1, o));
             bz1 = fmaxf(bz1, __shfl_xor_sync(0xffffffffu, bz1, o));
         }
-        Acc A = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        Acc A[BPL];
+#pragma unroll
+        for (int b = 0; b < BPL; b++) A[b] = Acc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         int sp = 1;
-        if (lane == 0) stk[0] = 0u << 3 | 0u;      // root range: cell 0, count 1
+        if (lane == 0) stk[0] = 0u;                  // root range: cell 0, count 1
         int pc_head = 0, pc_n = 0, pp_head = 0, pp_n = 0;
         unsigned npc = 0, npp = 0;
         bool overflow = false, timeout = false;
@@ -227,7 +320,7 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
                     pp_n += k;
                     if (pp_n >= 32) {
                         __syncwarp();
-                        eval_pp(R, pp_head, 32, phase, nph, me.x, me.y, me.z, eps2, A);
+                        tile_pp<BPL>(lg, R, pp_head, phase, me, eps2, A);
                         __syncwarp();
                         pp_head = (pp_head + 32) & (RING - 1);
                         pp_n -= 32;
@@ -236,26 +329,45 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
             }
             __syncwarp();
             if (pc_n >= 32) {
-                eval_pc(R, pc_head, 32, phase, nph, me.x, me.y, me.z, eps2, A);
+                tile_pc<BPL>(lg, R, pc_head, phase, me, eps2, A);
                 pc_head = (pc_head + 32) & (RING - 1);
                 pc_n -= 32;
             }
             __syncwarp();
         }
-        // Remaining partial tiles (they do not wrap: head is 0 or 32, n < 32).
-        if (pc_n > 0) eval_pc(R, pc_head, pc_n, phase, nph, me.x, me.y, me.z, eps2, A);
-        if (pp_n > 0) eval_pp(R, pp_head, pp_n, phase, nph, me.x, me.y, me.z, eps2, A);
-        float ax = A.ax - A.cx, ay = A.ay - A.cy, az = A.az - A.cz, ph = A.ph - A.cp;
-        for (int o = slots; o < 32; o <<= 1) {
-            ax += __shfl_xor_sync(0xffffffffu, ax, o);
-            ay += __shfl_xor_sync(0xffffffffu, ay, o);
-            az += __shfl_xor_sync(0xffffffffu, az, o);
-            ph += __shfl_xor_sync(0xffffffffu, ph, o);
+        // Remaining partial tiles (head is 0 or 32, n < 32): pad to 32 with
+        // massless sources far away, then evaluate as full tiles.
+        const float FAR = 1e18f;
+        if (pc_n > 0) {
+            const int s = pc_head + pc_n + lane;
+            if (lane < 32 - pc_n) {
+                R.mono[s] = make_float4(FAR, FAR, FAR, 0.f);
+                R.qa[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+                R.qb[s] = make_float2(0.f, 0.f);
+            }
+            __syncwarp();
+            tile_pc<BPL>(lg, R, pc_head, phase, me, eps2, A);
         }
-        if (live && phase == 0) {
-            ph += me.w * rsqrtf(eps2);           // remove the self term -m/eps
-            acc4[bi] = make_float4(ax, ay, az, ph);
-            counts[bi] = make_uint2(npc, npp - 1u);
+        if (pp_n > 0) {
+            if (lane < 32 - pp_n) R.pp[pp_head + pp_n + lane] = make_float4(FAR, FAR, FAR, 0.f);
+            __syncwarp();
+            tile_pp<BPL>(lg, R, pp_head, phase, me, eps2, A);
+        }
+#pragma unroll
+        for (int b = 0; b < BPL; b++) {
+            float ax = A[b].ax - A[b].cx, ay = A[b].ay - A[b].cy, az = A[b].az - A[b].cz,
+                  ph = A[b].ph - A[b].cp;
+            for (int o = slots; o < 32; o <<= 1) {
+                ax += __shfl_xor_sync(0xffffffffu, ax, o);
+                ay += __shfl_xor_sync(0xffffffffu, ay, o);
+                az += __shfl_xor_sync(0xffffffffu, az, o);
+                ph += __shfl_xor_sync(0xffffffffu, ph, o);
+            }
+            if (live[b] && phase == 0) {
+                ph += me[b].w * rsqrtf(eps2);    // remove the self term -m/eps
+                acc4[bi[b]] = make_float4(ax, ay, az, ph);
+                counts[bi[b]] = make_uint2(npc, npp - 1u);
+            }
         }
         if (lane == 0) {
             atomicAdd(&st->inter[0], (unsigned long long)npc * (unsigned long long)ng);
@@ -271,30 +383,35 @@ size_t walk_smem_bytes(int warps, int stack_cap) {
     return (size_t)warps * (sizeof(WarpRings) + (size_t)stack_cap * sizeof(unsigned));
 }
 
-cudaError_t launch_walk(Ctx &c, float eps) {
+// Function attribute and occupancy are set up once per shape, before any
+// stream capture of a step (the first step always runs eagerly).
+template <int BPL>
+static cudaError_t launch_walk_t(Ctx &c, float eps) {
     const int warps = c.walk_warps;
-    size_t smem = walk_smem_bytes(warps, c.list_capacity);
-    // Function attribute and occupancy are set up once per shape, before any
-    // stream capture of a step (the first step always runs eagerly).
-    static size_t attr_smem = 0;
+    const size_t smem = walk_smem_bytes(warps, c.list_capacity);
+    static size_t attr_smem = 0, occ_smem = 0;
     static int occ_warps = 0, occ_per_sm = 0;
-    static size_t occ_smem = 0;
     if (smem > attr_smem) {
-        cudaError_t e = cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_walk<BPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_smem = smem;
     }
     if (occ_warps != warps || occ_smem != smem) {
         int per = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk, warps * 32, smem);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk<BPL>, warps * 32, smem);
         if (e != cudaSuccess) return e;
         occ_warps = warps; occ_smem = smem; occ_per_sm = per < 1 ? 1 : per;
     }
-    const int per_sm = occ_per_sm;
-    k_walk<<<c.num_sms * per_sm, warps * 32, smem, c.stream>>>(
+    k_walk<BPL><<<c.num_sms * occ_per_sm, warps * 32, smem, c.stream>>>(
         c.st, c.st, c.groups, c.pos4, c.test, c.cell_link, c.mono, c.quadA, c.quadB, eps,
         c.list_capacity, c.max_spin, c.acc4, c.counts);
     return cudaGetLastError();
+}
+
+cudaError_t launch_walk(Ctx &c, float eps) {
+    cudaError_t e = launch_walk_t<1>(c, eps);
+    if (e != cudaSuccess || c.ncrit <= 32) return e;
+    return launch_walk_t<2>(c, eps);
 }
 
 }  // namespace bonsai

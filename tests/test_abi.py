@@ -43,7 +43,7 @@ def test_invalid_arguments_rejected_without_gpu(libpath):
     L = B.lib()
     assert L.bonsai_create(None, None, None) == -1
     ctx = C.c_void_p()
-    bad = B.Config(ncrit=64)
+    bad = B.Config(ncrit=65)
     assert L.bonsai_create(C.byref(ctx), C.byref(bad), None) == -1
     assert b"ncrit" in L.bonsai_last_error(None)
     assert L.bonsai_build(None) == -1
