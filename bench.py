@@ -62,6 +62,9 @@ def parse():
     p.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--no-ensemble", action="store_true")
+    p.add_argument("--ensemble-systems", type=int, default=64)
     return p.parse_args()
 
 
@@ -198,6 +201,49 @@ def run_reference(a, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_ensemble(a, dev, stream):
+    """Batched ensemble: independent Plummer spheres with N log-uniform in
+    [2^12, 2^18] (seeds 100..), eps = 0.01, theta = 0.75, all stepped together
+    (one sort, one build, one persistent walk, one CUDA graph per step)."""
+    import numpy as np
+    import torch
+    import paper_1204_2280_gb300 as B
+    from paper_1204_2280_gb300 import workloads as W
+    systems = W.ensemble(a.ensemble_systems, 100)
+    pos = np.concatenate([s.pos for s in systems])
+    vel = np.concatenate([s.vel for s in systems])
+    mass = np.concatenate([s.mass for s in systems])
+    off = np.cumsum([0] + [s.n for s in systems])
+    n = int(mass.shape[0])
+    theta, eps, dt = 0.75, 0.01, a.dt
+    bz = B.Bonsai(B.Config(), stream=stream)
+    bz.set_bodies(torch.from_numpy(pos).to(dev), torch.from_numpy(mass).to(dev), torch.from_numpy(vel).to(dev))
+    bz.set_systems(off)
+    nc, w, _ = B.bonsai_autotune(bz.ctx, theta, eps)
+    B.bonsai_set_params(bz.ctx, theta, eps)
+    for _ in range(max(3, a.warmup)):
+        bz.step(dt)
+    bz.sync()
+    ms = []
+    for _ in range(a.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bz.step(dt)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    stages = B.bonsai_get_stage_times(bz.ctx)
+    bz.sync()
+    bz.close()
+    t = sum(ms) / len(ms)
+    return {"systems": len(systems), "n_total": n, "n_min": int(min(s.n for s in systems)),
+            "n_max": int(max(s.n for s in systems)), "ms_per_step": t, "particles_per_s": n / (t / 1e3),
+            "ncrit": nc, "walk_warps": w, "theta": theta, "eps": eps,
+            "last_step_stages_ms": {k: float(v) for k, v in zip(B.STAGES, stages)},
+            "what": "all systems in one bonsai_step: one sort, one build, one persistent walk, one graph"}
+
+
 def run_ours(a, rank, world, local_rank):
     import numpy as np
     import torch
@@ -214,7 +260,10 @@ def run_ours(a, rank, world, local_rank):
     bz = B.Bonsai(B.Config(nleaf=a.nleaf, ncrit=a.ncrit, walk_warps=a.walk_warps), stream=stream)
     bz.set_bodies(torch.from_numpy(b.pos).to(dev), torch.from_numpy(b.mass).to(dev),
                   torch.from_numpy(b.vel).to(dev))
-    bz.build().multipoles().forces(a.theta, a.eps)
+    if not a.no_autotune:
+        a.ncrit, a.walk_warps, _ = B.bonsai_autotune(bz.ctx, a.theta, a.eps)
+    else:
+        bz.build().multipoles().forces(a.theta, a.eps)
     B.bonsai_set_params(bz.ctx, a.theta, a.eps)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     for _ in range(a.warmup):
@@ -281,6 +330,8 @@ def run_ours(a, rank, world, local_rank):
                "what": "set_bodies(host pos, mass, vel) + build + multipoles + forces(host acc, pot)"}
     bz.close()
 
+    ens = None if a.no_ensemble else run_ensemble(a, dev, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_oracle_sample(b, a.theta, a.eps, a.nleaf, a.ncrit, a.cpu_budget)
@@ -305,6 +356,7 @@ def run_ours(a, rank, world, local_rank):
             "interactions_per_body": {"pc": sum(npc) / (n * a.steps), "pp": sum(npp) / (n * a.steps)},
             "interactions_per_s": (sum(npc) + sum(npp)) / (walk_ms / 1e3),
             "wall_s_timed_loop": t_wall,
+            "ensemble": ens,
         }
         print(json.dumps(line), flush=True)
 

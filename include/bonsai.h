@@ -75,6 +75,16 @@ void bonsai_destroy(bonsai_ctx *ctx);
 int bonsai_set_bodies(bonsai_ctx *ctx, const float *pos, const float *mass,
                       const float *vel, long long n, int on_device);
 
+/* Batched ensemble: the n bodies of the last bonsai_set_bodies form nsys
+ * independent systems, system s holding bodies [offsets[s], offsets[s+1])
+ * (host array of nsys + 1 entries, offsets[0] = 0, offsets[nsys] = n, no
+ * empty system, 1 <= nsys <= 256).  Every stage then runs on all systems at
+ * once: per-system domain cubes and keys, one sort by (system, key), one tree
+ * build with one root per system, one multipole pass and one persistent walk
+ * over the groups of all systems.  Call right after bonsai_set_bodies
+ * (bonsai_set_bodies resets to a single system). */
+int bonsai_set_systems(bonsai_ctx *ctx, const long long *offsets, int nsys);
+
 /* Sect. 2 "sorting", "moving", "tree-construction": domain cube, 63-bit
  * Morton keys (21 bits per axis, x in the lowest bit of each triple), stable
  * LSD radix sort, body reorder, octree (cells with more than nleaf bodies
@@ -103,6 +113,15 @@ int bonsai_forces(bonsai_ctx *ctx, float theta, float eps, float *acc,
  * 0.01), then the drift, the full rebuild (keys, sort, reorder, build,
  * multipoles), the walk and the second kick.  No host synchronisation. */
 int bonsai_step(bonsai_ctx *ctx, float dt);
+
+/* Autotuner: times the walk of the current bodies (CUDA events, mean of two
+ * walks after one untimed) for every group size ncrit in {16, 32, 48, 64}
+ * and walk thread-block width in {2, 4, 8} warps, keeps the fastest pair in
+ * the context (rebuilding the tree and groups for it) and leaves forces at
+ * (theta, eps) computed.  Candidates that overflow the walk stack are
+ * skipped.  Any output pointer may be NULL. */
+int bonsai_autotune(bonsai_ctx *ctx, float theta, float eps, int *best_ncrit,
+                    int *best_warps, float *best_ms);
 
 /* Sets theta and eps for bonsai_step without computing forces. */
 int bonsai_set_params(bonsai_ctx *ctx, float theta, float eps);
@@ -134,8 +153,12 @@ int bonsai_get_stage_times(bonsai_ctx *ctx, float *ms, int n);
 int bonsai_get_sizes(bonsai_ctx *ctx, long long *n, long long *ncells,
                      long long *ngroups);
 
-/* Domain of the last build: mn[3] (per-axis float minimum) and side[1]. */
+/* Domain of the last build: mn[3] (per-axis float minimum) and side[1]
+ * (of system 0). */
 int bonsai_get_domain(bonsai_ctx *ctx, float mn[3], float side[1]);
+
+/* Domains of all systems: mn (nsys x 3), side (nsys). */
+int bonsai_get_domains(bonsai_ctx *ctx, float *mn, float *side);
 
 /* Sorted keys (N) and the sort permutation perm (N): sorted position i holds
  * caller body perm[i]. */

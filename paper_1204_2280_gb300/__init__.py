@@ -29,7 +29,8 @@ EXPORTS = ["bonsai_create", "bonsai_destroy", "bonsai_set_bodies", "bonsai_build
            "bonsai_get_bodies", "bonsai_diagnostics", "bonsai_sync", "bonsai_get_sizes",
            "bonsai_get_domain", "bonsai_get_keys", "bonsai_get_tree", "bonsai_get_groups",
            "bonsai_get_moments", "bonsai_get_counts", "bonsai_last_error", "bonsai_version",
-           "bonsai_get_stage_times", "bonsai_sort_keys_static"]
+           "bonsai_get_stage_times", "bonsai_sort_keys_static", "bonsai_set_systems",
+           "bonsai_get_domains", "bonsai_autotune"]
 
 STAGES = ["kick_drift_domain", "keys", "sort", "reorder", "build", "multipoles", "walk", "kick"]
 
@@ -83,6 +84,9 @@ def lib():
         L.bonsai_version.restype = C.c_char_p
         L.bonsai_get_stage_times.argtypes = [p, p, i]
         L.bonsai_sort_keys_static.argtypes = [p, p, p, ll, p]
+        L.bonsai_set_systems.argtypes = [p, p, i]
+        L.bonsai_get_domains.argtypes = [p, p, p]
+        L.bonsai_autotune.argtypes = [p, f, f, p, p, p]
         _lib = L
     return _lib
 
@@ -143,6 +147,12 @@ def bonsai_set_bodies(ctx, pos, mass, vel=None):
     _check(ctx, lib().bonsai_set_bodies(ctx, pp, mp, vp, n, _same_side(d0, d1, d2)))
 
 
+def bonsai_set_systems(ctx, offsets):
+    """offsets: nsys + 1 body offsets (first body of each system, then n)."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    _check(ctx, lib().bonsai_set_systems(ctx, off.ctypes.data, int(off.shape[0]) - 1))
+
+
 def bonsai_build(ctx):
     _check(ctx, lib().bonsai_build(ctx))
 
@@ -158,6 +168,14 @@ def bonsai_forces(ctx, theta: float, eps: float, acc=None, pot=None):
 
 def bonsai_step(ctx, dt: float):
     _check(ctx, lib().bonsai_step(ctx, dt))
+
+
+def bonsai_autotune(ctx, theta: float, eps: float):
+    """Pick (ncrit, warps per walk block) by timing the walk; returns
+    (ncrit, warps, ms per walk)."""
+    nc, w, ms = C.c_int(), C.c_int(), C.c_float()
+    _check(ctx, lib().bonsai_autotune(ctx, theta, eps, C.byref(nc), C.byref(w), C.byref(ms)))
+    return nc.value, w.value, ms.value
 
 
 def bonsai_set_params(ctx, theta: float, eps: float):
@@ -190,6 +208,13 @@ def bonsai_get_domain(ctx):
     side = np.zeros(1, np.float32)
     _check(ctx, lib().bonsai_get_domain(ctx, mn.ctypes.data, side.ctypes.data))
     return mn, float(side[0])
+
+
+def bonsai_get_domains(ctx, nsys: int):
+    mn = np.zeros((nsys, 3), np.float32)
+    side = np.zeros(nsys, np.float32)
+    _check(ctx, lib().bonsai_get_domains(ctx, mn.ctypes.data, side.ctypes.data))
+    return mn, side
 
 
 def bonsai_get_keys(ctx):
@@ -281,6 +306,10 @@ class Bonsai:
 
     def set_bodies(self, pos, mass, vel=None):
         bonsai_set_bodies(self.ctx, pos, mass, vel)
+        return self
+
+    def set_systems(self, offsets):
+        bonsai_set_systems(self.ctx, offsets)
         return self
 
     def build(self):

@@ -70,17 +70,17 @@ cudaError_t alloc_bodies(Ctx &c, long long n) {
     Arena a;
     a.take(c.pos4, n, plan); a.take(c.vel4, n, plan); a.take(c.acc4, n, plan);
     a.take(c.pos4_alt, n, plan); a.take(c.vel4_alt, n, plan);
-    a.take(c.id, n, plan); a.take(c.id_alt, n, plan);
+    a.take(c.id, n, plan); a.take(c.id_alt, n, plan); a.take(c.sysid, n, plan);
     a.take(c.keys, n, plan); a.take(c.keys_alt, n, plan);
     a.take(c.vals, n, plan); a.take(c.vals_alt, n, plan);
-    a.take(c.tile_status, (size_t)SORT_PASSES * ntiles * 256, plan);
+    a.take(c.tile_status, (size_t)(SORT_PASSES + 1) * ntiles * 256, plan);
     a.take(c.blockcount, (size_t)NROWS * nbb, plan);
     a.take(c.cell_body, ccap, plan); a.take(c.cell_link, ccap, plan);
     a.take(c.cell_level, ccap, plan); a.take(c.cell_parent, ccap, plan);
     a.take(c.cell_done, ccap, plan); a.take(c.cell_cb, ccap, plan);
     a.take(c.mono, ccap, plan); a.take(c.quadA, ccap, plan); a.take(c.quadB, ccap, plan);
     a.take(c.test, ccap, plan); a.take(c.delta, ccap, plan);
-    a.take(c.shadow, 10 * 585, plan);
+    a.take(c.shadow, 10 * (size_t)(ccap < 585 * MAX_SYSTEMS ? ccap : 585 * MAX_SYSTEMS), plan);
     a.take(c.groups, n, plan); a.take(c.counts, n, plan);
     a.take(c.stage, 7 * (size_t)n, plan);
     char *base = nullptr;
@@ -219,12 +219,44 @@ int bonsai_set_bodies(bonsai_ctx *ctx, const float *pos, const float *mass, cons
         p = s; m = s + 3 * n; v = vel ? s + 4 * n : nullptr;
     }
     CK(launch_pack(c, p, m, v));
-    if (!on_device) CK(cudaStreamSynchronize(c.stream));
+    // One system holding every body until bonsai_set_systems says otherwise.
+    c.nsys = 1;
+    unsigned off1[2] = {0u, (unsigned)n};
+    CK(cudaMemcpyAsync(c.st->sys_off, off1, sizeof(off1), cudaMemcpyHostToDevice, c.stream));
+    CK(cudaMemsetAsync(c.sysid, 0, (size_t)n, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
     // The state now lives in the pre-sort (*_alt) arrays; nothing derived
     // from earlier bodies stays valid.
     c.have_bodies = true;
     c.built = c.moments_ready = c.have_acc = false;
     c.err.clear();
+    return BONSAI_OK;
+}
+
+int bonsai_set_systems(bonsai_ctx *ctx, const long long *offsets, int nsys) {
+    if (!ctx) return BONSAI_ERR_INVALID_ARG;
+    Ctx &c = ctx->c;
+    if (!c.have_bodies) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_set_systems: no bodies");
+    if (!offsets || nsys < 1 || nsys > MAX_SYSTEMS)
+        return fail(ctx, BONSAI_ERR_INVALID_ARG, "bonsai_set_systems: need offsets and 1 <= nsys <= 256");
+    std::vector<unsigned> off(nsys + 1);
+    if (offsets[0] != 0 || offsets[nsys] != c.n)
+        return fail(ctx, BONSAI_ERR_INVALID_ARG, "bonsai_set_systems: offsets must run from 0 to n");
+    for (int s = 0; s <= nsys; s++) {
+        if (s > 0 && offsets[s] <= offsets[s - 1])
+            return fail(ctx, BONSAI_ERR_INVALID_ARG, "bonsai_set_systems: every system needs at least one body");
+        off[s] = (unsigned)offsets[s];
+    }
+    if (c.built || c.have_acc)
+        return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_set_systems: call it right after bonsai_set_bodies");
+    if (c.step_graph) { cudaGraphExecDestroy(c.step_graph); c.step_graph = nullptr; }
+    c.graph_n = -1;
+    c.nsys = nsys;
+    CK(cudaMemcpyAsync(c.st->sys_off, off.data(), sizeof(unsigned) * (nsys + 1), cudaMemcpyHostToDevice,
+                       c.stream));
+    CK(launch_fill_sysid(c));
+    CK(cudaStreamSynchronize(c.stream));
+    c.built = c.moments_ready = c.have_acc = false;
     return BONSAI_OK;
 }
 
@@ -351,6 +383,66 @@ int bonsai_get_stage_times(bonsai_ctx *ctx, float *ms, int n) {
     return k;
 }
 
+int bonsai_autotune(bonsai_ctx *ctx, float theta, float eps, int *best_ncrit, int *best_warps,
+                    float *best_ms) {
+    if (!ctx) return BONSAI_ERR_INVALID_ARG;
+    Ctx &c = ctx->c;
+    int r = check_theta_eps(ctx, theta, eps);
+    if (r) return r;
+    if (!c.have_bodies) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_autotune: no bodies");
+    static const int ncrits[] = {16, 32, 48, 64};
+    static const int warps[] = {2, 4, 8};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bn = c.ncrit, bw = c.walk_warps;
+    cudaError_t e = cudaSuccess;
+    for (int nc : ncrits) {
+        c.ncrit = nc;
+        if ((r = bonsai_build(ctx)) || (r = bonsai_multipoles(ctx))) break;
+        for (int w : warps) {
+            c.walk_warps = w;
+            // one untimed walk, then the mean of two timed ones
+            if ((e = launch_reset(c)) != cudaSuccess || (e = pipeline_forces(c, theta, eps)) != cudaSuccess) break;
+            if ((e = cudaEventRecord(e0, c.stream)) != cudaSuccess) break;
+            for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {
+                e = launch_reset(c);
+                if (e == cudaSuccess) e = pipeline_forces(c, theta, eps);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(e1, c.stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) break;
+            unsigned status = 0;
+            if ((e = cudaMemcpy(&status, &c.st->status, sizeof(unsigned), cudaMemcpyDeviceToHost)) != cudaSuccess)
+                break;
+            if (status) {                     // e.g. stack overflow: not a valid choice
+                if ((e = cudaMemset(&c.st->status, 0, sizeof(unsigned))) != cudaSuccess) break;
+                continue;
+            }
+            if (ms / 2 < best) { best = ms / 2; bn = nc; bw = w; }
+        }
+        if (e != cudaSuccess) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r) return r;
+    if (e != cudaSuccess) return fail(ctx, BONSAI_ERR_CUDA, "bonsai_autotune", e);
+    c.ncrit = bn;
+    c.walk_warps = bw;
+    if (c.step_graph) { cudaGraphExecDestroy(c.step_graph); c.step_graph = nullptr; }
+    c.graph_n = -1;
+    if ((r = bonsai_build(ctx)) || (r = bonsai_multipoles(ctx)) ||
+        (r = bonsai_forces(ctx, theta, eps, nullptr, nullptr, 1)))
+        return r;
+    if (best_ncrit) *best_ncrit = bn;
+    if (best_warps) *best_warps = bw;
+    if (best_ms) *best_ms = best;
+    return BONSAI_OK;
+}
+
 int bonsai_get_bodies(bonsai_ctx *ctx, float *pos, float *vel, int on_device) {
     if (!ctx) return BONSAI_ERR_INVALID_ARG;
     Ctx &c = ctx->c;
@@ -416,12 +508,18 @@ int bonsai_get_sizes(bonsai_ctx *ctx, long long *n, long long *ncells, long long
 }
 
 int bonsai_get_domain(bonsai_ctx *ctx, float mn[3], float side[1]) {
+    return bonsai_get_domains(ctx, mn, side);
+}
+
+int bonsai_get_domains(bonsai_ctx *ctx, float *mn, float *side) {
     if (!ctx || !mn || !side) return BONSAI_ERR_INVALID_ARG;
-    if (!ctx->c.built) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_get_domain: not built");
+    if (!ctx->c.built) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_get_domains: not built");
     int r = read_state(ctx);
     if (r) return r;
-    for (int d = 0; d < 3; d++) mn[d] = ctx->c.st_host->mn[d];
-    side[0] = ctx->c.st_host->side;
+    for (int s = 0; s < ctx->c.nsys; s++) {
+        for (int d = 0; d < 3; d++) mn[3 * s + d] = ctx->c.st_host->mn[3 * s + d];
+        side[s] = ctx->c.st_host->side[s];
+    }
     return BONSAI_OK;
 }
 

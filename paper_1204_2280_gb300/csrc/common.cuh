@@ -30,6 +30,7 @@ constexpr int SORT_THREADS = 256;
 constexpr int SORT_ITEMS = 16;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;   // 4096 keys per tile
 constexpr int SORT_PASSES = 8;                         // 8-bit digits, 63-bit keys
+constexpr int MAX_SYSTEMS = 256;                       // ensemble: one more pass on the system id
 constexpr int BUILD_THREADS = 1024;                    // bodies per build block
 
 // Device status bits (ORed by kernels, read and cleared by bonsai_sync).
@@ -38,11 +39,13 @@ constexpr unsigned ST_TIMEOUT = 2u;
 constexpr unsigned ST_NAN = 4u;
 
 struct DevState {
-    int dom[6];                       // orderable-int min xyz, max xyz
-    float mn[3];                      // domain corner (written by keys block 0)
-    float side;                       // domain side S
-    unsigned hist[SORT_PASSES * 256]; // digit histograms of the keys
-    unsigned sort_tile[SORT_PASSES];  // tile tickets per pass
+    int dom[6 * MAX_SYSTEMS];         // per system: orderable-int min xyz, max xyz
+    float mn[3 * MAX_SYSTEMS];        // per system: domain corner
+    float side[MAX_SYSTEMS];          // per system: domain side S
+    float scale[MAX_SYSTEMS];         // per system: 2^21 / S
+    unsigned sys_off[MAX_SYSTEMS + 1];    // first body of each system (+ n)
+    unsigned hist[(SORT_PASSES + 1) * 256]; // digit histograms (+ system sizes)
+    unsigned sort_tile[SORT_PASSES + 1];    // tile tickets per pass
     unsigned ncells, ngroups;
     unsigned row_total[NROWS];        // cells per level, groups
     unsigned level_start[MAX_LEVEL + 2]; // first cell of each level; [22] = ncells
@@ -64,15 +67,17 @@ struct Ctx {
     // sizes
     long long n = 0, ncap = 0, ccap = 0;
     int ntiles = 0, nbblocks = 0;     // sort tiles, build blocks
+    int nsys = 1;                     // independent systems (contiguous body segments)
 
     // body arrays
     float4 *pos4 = nullptr, *vel4 = nullptr, *acc4 = nullptr;
     float4 *pos4_alt = nullptr, *vel4_alt = nullptr;
     uint32_t *id = nullptr, *id_alt = nullptr;
+    uint8_t *sysid = nullptr;         // system of each body position (same before/after sorting)
     // sort
     unsigned long long *keys = nullptr, *keys_alt = nullptr;
     uint32_t *vals = nullptr, *vals_alt = nullptr;   // vals ends as perm
-    unsigned *tile_status = nullptr;                   // SORT_PASSES * ntiles * 256
+    unsigned *tile_status = nullptr;                   // (SORT_PASSES + 1) * ntiles * 256
     // build
     unsigned *blockcount = nullptr;  // NROWS * nbblocks
     uint2 *cell_body = nullptr, *cell_link = nullptr;
@@ -80,7 +85,7 @@ struct Ctx {
     uint32_t *cell_parent = nullptr, *cell_done = nullptr, *cell_cb = nullptr;
     float4 *mono = nullptr, *quadA = nullptr, *test = nullptr;
     float2 *quadB = nullptr;
-    float *delta = nullptr;
+    float2 *delta = nullptr;         // per cell: (|com - centre|, side l)
     double *shadow = nullptr;        // FP64 moments of the top levels (10 per cell)
     uint2 *groups = nullptr;
     uint2 *counts = nullptr;         // per body (n_pc, n_pp), sorted order
@@ -122,12 +127,19 @@ __device__ __forceinline__ int key_cpl(unsigned long long a, unsigned long long 
     return MAX_LEVEL - p / 3 - 1;
 }
 
+// Shared levels of two bodies that may belong to different systems (-1: none).
+__device__ __forceinline__ int body_cpl(unsigned long long a, unsigned long long b, uint8_t sa, uint8_t sb) {
+    return sa == sb ? key_cpl(a, b) : -1;
+}
+
 __device__ __forceinline__ unsigned long long key_prefix(unsigned long long k, int level) {
     return level == 0 ? 0ull : (k >> (3 * (MAX_LEVEL - level)));
 }
 
 // ---- launchers (host) ------------------------------------------------------
 cudaError_t launch_reset(Ctx &c);
+cudaError_t launch_domains(Ctx &c);
+cudaError_t launch_fill_sysid(Ctx &c);
 cudaError_t launch_pack(Ctx &c, const float *pos, const float *mass, const float *vel);
 cudaError_t launch_bbox(Ctx &c);
 cudaError_t launch_kick_drift_bbox(Ctx &c, float dt);

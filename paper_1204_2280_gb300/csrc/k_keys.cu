@@ -15,12 +15,16 @@
 namespace bonsai {
 
 // ---------------------------------------------------------------------------
-__global__ void k_reset(DevState *st, int what) {
+__global__ void k_reset(DevState *st, int what, int nsys) {
     int t = threadIdx.x;
     if (what & 1) {                        // build inputs
-        if (t < 3) { st->dom[t] = 0x7fffffff; st->dom[3 + t] = (int)0x80000000; }
-        for (int i = t; i < SORT_PASSES * 256; i += blockDim.x) st->hist[i] = 0;
-        if (t < SORT_PASSES) st->sort_tile[t] = 0;
+        for (int i = t; i < 3 * nsys; i += blockDim.x) {
+            int sys = i / 3, d = i % 3;
+            st->dom[6 * sys + d] = 0x7fffffff;
+            st->dom[6 * sys + 3 + d] = (int)0x80000000;
+        }
+        for (int i = t; i < (SORT_PASSES + 1) * 256; i += blockDim.x) st->hist[i] = 0;
+        if (t < SORT_PASSES + 1) st->sort_tile[t] = 0;
     }
     if (what & 2) {                        // walk inputs
         if (t == 0) { st->walk_next = 0; st->walk_next2 = 0; st->inter[0] = 0; st->inter[1] = 0; }
@@ -31,7 +35,25 @@ __global__ void k_reset(DevState *st, int what) {
 }
 
 cudaError_t launch_reset(Ctx &c) {
-    k_reset<<<1, 256, 0, c.stream>>>(c.st, 7);
+    k_reset<<<1, 256, 0, c.stream>>>(c.st, 7, c.nsys);
+    return cudaGetLastError();
+}
+
+// System id of every body position from the segment offsets.
+__global__ void k_fill_sysid(const DevState *__restrict__ st, int nsys, int n, uint8_t *sysid) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = nsys - 1;               // last system with sys_off <= i
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (st->sys_off[mid] <= (unsigned)i) lo = mid; else hi = mid - 1;
+    }
+    sysid[i] = (uint8_t)lo;
+}
+
+cudaError_t launch_fill_sysid(Ctx &c) {
+    int n = (int)c.n;
+    k_fill_sysid<<<(n + 255) / 256, 256, 0, c.stream>>>(c.st, c.nsys, n, c.sysid);
     return cudaGetLastError();
 }
 
@@ -60,12 +82,47 @@ cudaError_t launch_pack(Ctx &c, const float *pos, const float *mass, const float
 }
 
 // ---------------------------------------------------------------------------
-// Block min/max of three floats -> one atomic per component per block.
-__device__ __forceinline__ void bbox_accumulate(float x, float y, float z, bool valid,
+// Per-system min/max of the positions.  Systems are contiguous runs of body
+// positions, so a block almost always lies inside one system: then a block
+// reduction and six atomics; warps that straddle a boundary fall back to
+// warp reductions per uniform warp or per-lane atomics.
+__device__ __forceinline__ void dom_atomics(DevState *st, int sys, const float (&v)[6]) {
+    for (int d = 0; d < 3; d++) {
+        atomicMin(&st->dom[6 * sys + d], f2ord(v[d]));
+        atomicMax(&st->dom[6 * sys + 3 + d], f2ord(v[3 + d]));
+    }
+}
+
+__device__ __forceinline__ void bbox_accumulate(float x, float y, float z, bool valid, int sys,
                                                 DevState *st) {
     __shared__ float red[6][32];
+    __shared__ int s_sys[2];
+    if (threadIdx.x == 0) { s_sys[0] = 1 << 30; s_sys[1] = -1; }
+    __syncthreads();
+    if (valid) { atomicMin(&s_sys[0], sys); atomicMax(&s_sys[1], sys); }
+    __syncthreads();
+    const bool uniform_block = s_sys[0] == s_sys[1];
     float v[6] = {x, y, z, x, y, z};
     if (!valid) { v[0] = v[1] = v[2] = INFINITY; v[3] = v[4] = v[5] = -INFINITY; }
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (!uniform_block) {
+        if (s_sys[1] < 0) return;            // no valid body in the block
+        const int s0 = __shfl_sync(0xffffffffu, valid ? sys : -1, 0);
+        const bool wu = __all_sync(0xffffffffu, !valid || sys == s0) && s0 >= 0;
+        if (!wu) {
+            if (valid) dom_atomics(st, sys, v);
+            return;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                v[d] = fminf(v[d], __shfl_xor_sync(0xffffffffu, v[d], o));
+                v[3 + d] = fmaxf(v[3 + d], __shfl_xor_sync(0xffffffffu, v[3 + d], o));
+            }
+        if (l == 0) dom_atomics(st, s0, v);
+        return;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
@@ -74,35 +131,33 @@ __device__ __forceinline__ void bbox_accumulate(float x, float y, float z, bool 
             v[3 + d] = fmaxf(v[3 + d], __shfl_xor_sync(0xffffffffu, v[3 + d], o));
         }
     }
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
     if (l == 0)
         for (int d = 0; d < 6; d++) red[d][w] = v[d];
     __syncthreads();
     if (w == 0) {
+        float r[6];
         for (int d = 0; d < 6; d++) {
-            float r = l < nw ? red[d][l] : (d < 3 ? INFINITY : -INFINITY);
+            r[d] = l < nw ? red[d][l] : (d < 3 ? INFINITY : -INFINITY);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                float s = __shfl_xor_sync(0xffffffffu, r, o);
-                r = d < 3 ? fminf(r, s) : fmaxf(r, s);
-            }
-            if (l == 0) {
-                if (d < 3) atomicMin(&st->dom[d], f2ord(r));
-                else atomicMax(&st->dom[d], f2ord(r));
+                float q = __shfl_xor_sync(0xffffffffu, r[d], o);
+                r[d] = d < 3 ? fminf(r[d], q) : fmaxf(r[d], q);
             }
         }
+        if (l == 0) dom_atomics(st, s_sys[0], r);
     }
 }
 
-__global__ void k_bbox(const float4 *__restrict__ p, int n, DevState *st) {
+__global__ void k_bbox(const float4 *__restrict__ p, const uint8_t *__restrict__ sysid, int n,
+                       DevState *st) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float4 q = i < n ? p[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    bbox_accumulate(q.x, q.y, q.z, i < n, st);
+    bbox_accumulate(q.x, q.y, q.z, i < n, i < n ? sysid[i] : 0, st);
 }
 
 cudaError_t launch_bbox(Ctx &c) {
     int n = (int)c.n;
-    k_bbox<<<(n + 255) / 256, 256, 0, c.stream>>>(c.pos4_alt, n, c.st);
+    k_bbox<<<(n + 255) / 256, 256, 0, c.stream>>>(c.pos4_alt, c.sysid, n, c.st);
     return cudaGetLastError();
 }
 
@@ -110,8 +165,8 @@ cudaError_t launch_bbox(Ctx &c) {
 // v' = v + a dt/2, x' = x + v' dt (written to the pre-sort arrays).
 __global__ void k_kick_drift_bbox(const float4 *__restrict__ pos, const float4 *__restrict__ vel,
                                   const float4 *__restrict__ acc, const uint32_t *__restrict__ id,
-                                  int n, float dt, float4 *pos_o, float4 *vel_o, uint32_t *id_o,
-                                  DevState *st) {
+                                  const uint8_t *__restrict__ sysid, int n, float dt, float4 *pos_o,
+                                  float4 *vel_o, uint32_t *id_o, DevState *st) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
     if (i < n) {
@@ -123,13 +178,13 @@ __global__ void k_kick_drift_bbox(const float4 *__restrict__ pos, const float4 *
         if (!(isfinite(x.x) && isfinite(x.y) && isfinite(x.z))) atomicOr(&st->status, ST_NAN);
         pos_o[i] = x; vel_o[i] = v; id_o[i] = id[i];
     }
-    bbox_accumulate(x.x, x.y, x.z, i < n, st);
+    bbox_accumulate(x.x, x.y, x.z, i < n, i < n ? sysid[i] : 0, st);
 }
 
 cudaError_t launch_kick_drift_bbox(Ctx &c, float dt) {
     int n = (int)c.n;
-    k_kick_drift_bbox<<<(n + 255) / 256, 256, 0, c.stream>>>(c.pos4, c.vel4, c.acc4, c.id, n, dt,
-                                                             c.pos4_alt, c.vel4_alt, c.id_alt, c.st);
+    k_kick_drift_bbox<<<(n + 255) / 256, 256, 0, c.stream>>>(c.pos4, c.vel4, c.acc4, c.id, c.sysid, n,
+                                                             dt, c.pos4_alt, c.vel4_alt, c.id_alt, c.st);
     return cudaGetLastError();
 }
 
@@ -155,36 +210,50 @@ __device__ __forceinline__ unsigned long long spread3(unsigned v) {
     return x;
 }
 
+// Domain of every system from its bounding box, and the histogram of the
+// extra radix pass on the system id (the system sizes).
+__global__ void k_domains(DevState *st, int nsys) {
+    for (int sys = threadIdx.x; sys < MAX_SYSTEMS; sys += blockDim.x) {
+        if (sys < nsys) {
+            float S = 0x1p-64f;
+            for (int d = 0; d < 3; d++) {
+                float lo = ord2f(st->dom[6 * sys + d]), hi = ord2f(st->dom[6 * sys + 3 + d]);
+                st->mn[3 * sys + d] = lo;
+                S = fmaxf(S, pow2_above_diff(hi, lo));
+            }
+            int ex;
+            frexpf(S, &ex);                // S = 2^(ex-1)
+            st->side[sys] = S;
+            st->scale[sys] = ldexpf(1.f, KEY_BITS_PER_AXIS - (ex - 1));
+            st->hist[SORT_PASSES * 256 + sys] = st->sys_off[sys + 1] - st->sys_off[sys];
+        } else {
+            st->hist[SORT_PASSES * 256 + sys] = 0u;
+        }
+    }
+}
+
+cudaError_t launch_domains(Ctx &c) {
+    k_domains<<<1, 256, 0, c.stream>>>(c.st, c.nsys);
+    return cudaGetLastError();
+}
+
 constexpr int KEYS_THREADS = 256;
 constexpr int KEYS_ITEMS = 8;
 
-// Keys of all bodies plus the 8 digit histograms of the radix sort; also
-// clears the pass-0 tile status of the sort.
+// Keys of all bodies (each quantised in its own system's cube) plus the 8
+// digit histograms of the radix sort; also clears the pass-0 tile status of
+// the sort.
 __global__ void __launch_bounds__(KEYS_THREADS)
-k_keys(const float4 *__restrict__ p, int n, DevState *st, unsigned long long *keys,
-       unsigned *status0, int nstatus) {
+k_keys(const float4 *__restrict__ p, const uint8_t *__restrict__ sysid, int n, int nsys,
+       DevState *st, unsigned long long *keys, unsigned *status0, int nstatus) {
     __shared__ unsigned h[SORT_PASSES * 256];
-    __shared__ float s_mn[3], s_scale;
+    __shared__ float4 s_dom[MAX_SYSTEMS];   // mn xyz, scale
     for (int i = threadIdx.x; i < SORT_PASSES * 256; i += blockDim.x) h[i] = 0;
+    for (int i = threadIdx.x; i < nsys; i += blockDim.x)
+        s_dom[i] = make_float4(st->mn[3 * i], st->mn[3 * i + 1], st->mn[3 * i + 2], st->scale[i]);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nstatus; i += gridDim.x * blockDim.x)
         status0[i] = 0;
-    if (threadIdx.x == 0) {
-        float S = 0x1p-64f;
-        for (int d = 0; d < 3; d++) {
-            float lo = ord2f(st->dom[d]), hi = ord2f(st->dom[3 + d]);
-            s_mn[d] = lo;
-            S = fmaxf(S, pow2_above_diff(hi, lo));
-        }
-        int ex;
-        frexpf(S, &ex);                    // S = 2^(ex-1)
-        s_scale = ldexpf(1.f, KEY_BITS_PER_AXIS - (ex - 1));
-        if (blockIdx.x == 0) {
-            st->mn[0] = s_mn[0]; st->mn[1] = s_mn[1]; st->mn[2] = s_mn[2];
-            st->side = S;
-        }
-    }
     __syncthreads();
-    const float mx = s_mn[0], my = s_mn[1], mz = s_mn[2], sc = s_scale;
     const unsigned qmax = (1u << KEY_BITS_PER_AXIS) - 1u;
     int base = blockIdx.x * KEYS_THREADS * KEYS_ITEMS + threadIdx.x;
 #pragma unroll
@@ -192,9 +261,10 @@ k_keys(const float4 *__restrict__ p, int n, DevState *st, unsigned long long *ke
         int i = base + k * KEYS_THREADS;
         if (i < n) {
             float4 q = p[i];
-            unsigned qx = min((unsigned)(__fsub_rd(q.x, mx) * sc), qmax);
-            unsigned qy = min((unsigned)(__fsub_rd(q.y, my) * sc), qmax);
-            unsigned qz = min((unsigned)(__fsub_rd(q.z, mz) * sc), qmax);
+            const float4 dm = s_dom[sysid[i]];
+            unsigned qx = min((unsigned)(__fsub_rd(q.x, dm.x) * dm.w), qmax);
+            unsigned qy = min((unsigned)(__fsub_rd(q.y, dm.y) * dm.w), qmax);
+            unsigned qz = min((unsigned)(__fsub_rd(q.z, dm.z) * dm.w), qmax);
             unsigned long long key = spread3(qx) | (spread3(qy) << 1) | (spread3(qz) << 2);
             keys[i] = key;
 #pragma unroll
@@ -210,7 +280,12 @@ k_keys(const float4 *__restrict__ p, int n, DevState *st, unsigned long long *ke
 cudaError_t launch_keys(Ctx &c) {
     int n = (int)c.n;
     int per = KEYS_THREADS * KEYS_ITEMS;
-    k_keys<<<(n + per - 1) / per, KEYS_THREADS, 0, c.stream>>>(c.pos4_alt, n, c.st, c.keys,
+    cudaError_t e = launch_domains(c);
+    if (e != cudaSuccess) return e;
+    // With several systems the sort takes one more pass and so starts from
+    // the alternate buffer, to end in c.keys.
+    unsigned long long *out = c.nsys > 1 ? c.keys_alt : c.keys;
+    k_keys<<<(n + per - 1) / per, KEYS_THREADS, 0, c.stream>>>(c.pos4_alt, c.sysid, n, c.nsys, c.st, out,
                                                               c.tile_status, c.ntiles * 256);
     return cudaGetLastError();
 }

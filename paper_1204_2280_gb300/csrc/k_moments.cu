@@ -25,15 +25,17 @@ __device__ __forceinline__ unsigned compact3(unsigned long long x) {
     return (unsigned)x;
 }
 
-// |com - geometric centre| of a cell at `level` whose first body has key k.
-__device__ float cell_delta(unsigned long long k, int level, float3 com, const DevState *st) {
+// (|com - geometric centre|, side) of a cell at `level` of system `sys`
+// whose first body has key k.
+__device__ float2 cell_delta(unsigned long long k, int level, int sys, float3 com, const DevState *st) {
     unsigned long long pre = key_prefix(k, level);
-    float l = ldexpf(st->side, -level);
-    float cx = fmaf((float)compact3(pre) + 0.5f, l, st->mn[0]);
-    float cy = fmaf((float)compact3(pre >> 1) + 0.5f, l, st->mn[1]);
-    float cz = fmaf((float)compact3(pre >> 2) + 0.5f, l, st->mn[2]);
+    float l = ldexpf(st->side[sys], -level);
+    const float *mn = st->mn + 3 * sys;
+    float cx = fmaf((float)compact3(pre) + 0.5f, l, mn[0]);
+    float cy = fmaf((float)compact3(pre >> 1) + 0.5f, l, mn[1]);
+    float cz = fmaf((float)compact3(pre >> 2) + 0.5f, l, mn[2]);
     float dx = com.x - cx, dy = com.y - cy, dz = com.z - cz;
-    return sqrtf(dx * dx + dy * dy + dz * dz);
+    return make_float2(sqrtf(dx * dx + dy * dy + dz * dz), l);
 }
 
 struct Mom32 { float M, x, y, z, q[6]; };
@@ -49,7 +51,8 @@ k_multipoles(const DevState *__restrict__ stc, DevState *st, const uint2 *__rest
              const uint2 *__restrict__ cell_link, const uint8_t *__restrict__ cell_level,
              const uint32_t *__restrict__ cell_parent, uint32_t *cell_done,
              const float4 *__restrict__ pos4, const unsigned long long *__restrict__ sk,
-             float4 *mono, float4 *qa, float2 *qb, float *delta, double *shadow) {
+             const uint8_t *__restrict__ sysid, float4 *mono, float4 *qa, float2 *qb, float2 *delta,
+             double *shadow) {
     unsigned c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= stc->ncells || (stc->status & ST_TIMEOUT)) return;
     uint2 link = cell_link[c];
@@ -82,15 +85,16 @@ k_multipoles(const DevState *__restrict__ stc, DevState *st, const uint2 *__rest
     }
     int lev = cell_level[c];
     store32(c, m, mono, qa, qb);
-    delta[c] = cell_delta(sk[b], lev, make_float3(m.x, m.y, m.z), stc);
+    delta[c] = cell_delta(sk[b], lev, sysid[b], make_float3(m.x, m.y, m.z), stc);
     if (lev < FP64_LEVELS) {
         double *s = shadow + 10 * (size_t)c;
         s[0] = m.M; s[1] = m.x; s[2] = m.y; s[3] = m.z;
         for (int k = 0; k < 6; k++) s[4 + k] = m.q[k];
     }
 
-    // Up the tree while this thread is the last child to finish.
-    while (c != 0) {
+    // Up the tree while this thread is the last child to finish (roots are
+    // the level-0 cells, one per system).
+    while (lev != 0) {
         unsigned p = cell_parent[c];
         __threadfence();
         unsigned nch = __ldcg(&cell_link[p].y);
@@ -98,7 +102,8 @@ k_multipoles(const DevState *__restrict__ stc, DevState *st, const uint2 *__rest
         __threadfence();
         c = p;
         unsigned cb = __ldcg(&cell_link[c].x);
-        int lv = cell_level[c];
+        const int lv = cell_level[c];
+        lev = lv;
         if (lv < FP64_LEVELS) {
             double dM = 0, c0x = 0, c0y = 0, c0z = 0, ax = 0, ay = 0, az = 0;
             double ch[8][10];
@@ -169,34 +174,32 @@ k_multipoles(const DevState *__restrict__ stc, DevState *st, const uint2 *__rest
         }
         store32(c, m, mono, qa, qb);
         unsigned b0 = __ldcg(&cell_body[c].x);
-        delta[c] = cell_delta(sk[b0], lv, make_float3(m.x, m.y, m.z), stc);
+        delta[c] = cell_delta(sk[b0], lv, sysid[b0], make_float3(m.x, m.y, m.z), stc);
     }
 }
 
 cudaError_t launch_multipoles(Ctx &c) {
     unsigned grid = (unsigned)((c.ccap + 255) / 256);
     k_multipoles<<<grid, 256, 0, c.stream>>>(c.st, c.st, c.cell_body, c.cell_link, c.cell_level,
-                                             c.cell_parent, c.cell_done, c.pos4, c.keys, c.mono,
-                                             c.quadA, c.quadB, c.delta, c.shadow);
+                                             c.cell_parent, c.cell_done, c.pos4, c.keys, c.sysid,
+                                             c.mono, c.quadA, c.quadB, c.delta, c.shadow);
     return cudaGetLastError();
 }
 
 // test[c] = (com, l/theta + delta), l = S / 2^level: the opening radius of
 // the Barnes (1994) criterion as read here.
 __global__ void k_open_radius(const DevState *__restrict__ st, const float4 *__restrict__ mono,
-                              const float *__restrict__ delta, const uint8_t *__restrict__ level,
-                              float inv_theta, float4 *test) {
+                              const float2 *__restrict__ delta, float inv_theta, float4 *test) {
     unsigned c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= st->ncells) return;
     float4 m = mono[c];
-    float l = ldexpf(st->side, -(int)level[c]);
-    test[c] = make_float4(m.x, m.y, m.z, fmaf(l, inv_theta, delta[c]));
+    float2 dl = delta[c];
+    test[c] = make_float4(m.x, m.y, m.z, fmaf(dl.y, inv_theta, dl.x));
 }
 
 cudaError_t launch_open_radius(Ctx &c, float theta) {
     unsigned grid = (unsigned)((c.ccap + 255) / 256);
-    k_open_radius<<<grid, 256, 0, c.stream>>>(c.st, c.mono, c.delta, c.cell_level, 1.0f / theta,
-                                              c.test);
+    k_open_radius<<<grid, 256, 0, c.stream>>>(c.st, c.mono, c.delta, 1.0f / theta, c.test);
     return cudaGetLastError();
 }
 

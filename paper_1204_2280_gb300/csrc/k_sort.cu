@@ -58,7 +58,8 @@ __global__ void __launch_bounds__(SORT_THREADS, 2)
 k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restrict__ vin,
            unsigned long long *__restrict__ kout, uint32_t *__restrict__ vout, int n, int shift,
            const unsigned *__restrict__ ghist, unsigned *status, unsigned *status_next,
-           unsigned *ticket, int ntiles, DevState *st, long long max_spin) {
+           unsigned *ticket, int ntiles, DevState *st, long long max_spin,
+           const uint8_t *__restrict__ dsrc) {
     extern __shared__ unsigned long long s_keys[];                 // SORT_TILE keys
     uint32_t *s_vals = (uint32_t *)(s_keys + SORT_TILE);          // SORT_TILE values
     __shared__ unsigned s_whist[SORT_THREADS / 32][256];
@@ -85,11 +86,17 @@ k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restric
         k[it] = ok ? kin[idx] : ~0ull;
         v[it] = vin ? (ok ? vin[idx] : 0u) : (uint32_t)idx;
     }
+    // Digit of each item: a byte of the key, or (dsrc) the byte dsrc[value],
+    // the system id of the body's pre-sort position.
+    unsigned char dg[SORT_ITEMS];
+#pragma unroll
+    for (int it = 0; it < SORT_ITEMS; it++)
+        dg[it] = dsrc ? (wbase + it * 32 + lane < n ? dsrc[v[it]] : 0) : (unsigned char)((k[it] >> shift) & 0xffu);
     const unsigned lt = lanemask_lt();
 #pragma unroll
     for (int it = 0; it < SORT_ITEMS; it++) {
         int idx = wbase + it * 32 + lane;
-        unsigned d = idx < n ? (unsigned)((k[it] >> shift) & 0xffu) : 256u;
+        unsigned d = idx < n ? (unsigned)dg[it] : 256u;
         unsigned peers = __match_any_sync(0xffffffffu, d);
         unsigned below = __popc(peers & lt);
         unsigned basec = d < 256u ? s_whist[warp][d] : 0u;
@@ -144,7 +151,7 @@ k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restric
     for (int it = 0; it < SORT_ITEMS; it++) {
         int idx = wbase + it * 32 + lane;
         if (idx < n) {
-            unsigned dd = (unsigned)((k[it] >> shift) & 0xffu);
+            unsigned dd = dg[it];
             unsigned pos = s_dstart[dd] + s_whist[warp][dd] + rk[it];
             s_keys[pos] = k[it];
             s_vals[pos] = v[it];
@@ -154,7 +161,7 @@ k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restric
     const int nvalid = min(SORT_TILE, n - tile * SORT_TILE);
     for (int p = tid; p < nvalid; p += SORT_THREADS) {
         unsigned long long key = s_keys[p];
-        unsigned dd = (unsigned)((key >> shift) & 0xffu);
+        unsigned dd = dsrc ? (unsigned)dsrc[s_vals[p]] : (unsigned)((key >> shift) & 0xffu);
         unsigned g = s_goff[dd] + ((unsigned)p - s_dstart[dd]);
         kout[g] = key;
         vout[g] = s_vals[p];
@@ -164,6 +171,10 @@ k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restric
 constexpr size_t SORT_DYN_SMEM = (size_t)SORT_TILE * (sizeof(unsigned long long) + sizeof(uint32_t));
 extern const size_t SORT_DYN_SMEM_BYTES = SORT_DYN_SMEM;
 
+// 8 passes over the key bytes; with several systems a 9th stable pass on the
+// system id groups the bodies by system (key order inside each).  Buffers
+// alternate so that the result always lands in c.keys / c.vals (the key
+// kernel writes to c.keys_alt when there are 9 passes).
 cudaError_t launch_sort(Ctx &c) {
     static bool attr_set = false;
     if (!attr_set) {
@@ -172,16 +183,19 @@ cudaError_t launch_sort(Ctx &c) {
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    int n = (int)c.n;
+    const int n = (int)c.n;
+    const int npass = SORT_PASSES + (c.nsys > 1 ? 1 : 0);
+    const int start = npass & 1;
     unsigned long long *kb[2] = {c.keys, c.keys_alt};
     uint32_t *vb[2] = {c.vals, c.vals_alt};
-    size_t plane = (size_t)c.ntiles * 256;
-    for (int p = 0; p < SORT_PASSES; p++) {
+    const size_t plane = (size_t)c.ntiles * 256;
+    for (int p = 0; p < npass; p++) {
+        const int src = (p + start) & 1, dst = src ^ 1;
         k_onesweep<<<c.ntiles, SORT_THREADS, SORT_DYN_SMEM, c.stream>>>(
-            kb[p & 1], p == 0 ? nullptr : vb[p & 1], kb[(p + 1) & 1], vb[(p + 1) & 1], n, 8 * p,
-            c.st->hist + 256 * p, c.tile_status + plane * p,
-            p + 1 < SORT_PASSES ? c.tile_status + plane * (p + 1) : nullptr, c.st->sort_tile + p,
-            c.ntiles, c.st, c.max_spin);
+            kb[src], p == 0 ? nullptr : vb[src], kb[dst], vb[dst], n, p < SORT_PASSES ? 8 * p : 0,
+            c.st->hist + 256 * p,
+            c.tile_status + plane * p, p + 1 < npass ? c.tile_status + plane * (p + 1) : nullptr,
+            c.st->sort_tile + p, c.ntiles, c.st, c.max_spin, p == SORT_PASSES ? c.sysid : nullptr);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -43,8 +43,8 @@ cudaError_t launch_reorder(Ctx &c) {
     return cudaGetLastError();
 }
 
-// First index > t whose level-`level` key prefix differs from k[t] (or n):
-// galloping then bisection.
+// First index > t whose level-`level` key prefix differs from k[t], or n
+// (the end of t's system): galloping then bisection.
 __device__ int run_end(const unsigned long long *__restrict__ sk, int n, int t, int level) {
     if (level == 0) return n;
     int sh = 3 * (MAX_LEVEL - level);
@@ -79,29 +79,39 @@ struct BodyCells {
 struct BuildShared {
     unsigned long long *k;
     int *D, *DG;
+    uint8_t *sy;
     int W, base;
     __device__ unsigned long long key(int j) const { return k[j - base + W]; }
+    __device__ uint8_t sys(int j) const { return sy[j - base + W]; }
+    __device__ int cpl(int a, int b) const { return body_cpl(key(a), key(b), sys(a), sys(b)); }
     __device__ int d(int j) const { return D[j - base + W]; }
     __device__ int dg(int j) const { return DG[j - base + W]; }
 };
 
+// Keys and system ids of [base-W, base+B+W); D and DG of [base-W, base+B).
+// Bodies of different systems share no level (cpl -1), so each system gets
+// its own root on level 0.
 __device__ BuildShared load_build_shared(void *smem, const unsigned long long *__restrict__ sk,
-                                         int n, int base, int nleaf, int ncrit) {
+                                         const uint8_t *__restrict__ sysid, int n, int base,
+                                         int nleaf, int ncrit) {
     BuildShared b;
     b.W = max(nleaf, ncrit);
     b.base = base;
     b.k = (unsigned long long *)smem;
     b.D = (int *)(b.k + BUILD_THREADS + 2 * b.W);
     b.DG = b.D + BUILD_THREADS + b.W;
+    b.sy = (uint8_t *)(b.DG + BUILD_THREADS + b.W);
     for (int i = threadIdx.x; i < BUILD_THREADS + 2 * b.W; i += blockDim.x) {
         int j = base - b.W + i;
-        b.k[i] = (j >= 0 && j < n) ? sk[j] : 0ull;
+        const bool in = j >= 0 && j < n;
+        b.k[i] = in ? sk[j] : 0ull;
+        b.sy[i] = in ? sysid[j] : 0;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < BUILD_THREADS + b.W; i += blockDim.x) {
         int j = base - b.W + i;
-        b.D[i] = (j >= 0 && j + nleaf < n) ? key_cpl(b.key(j), b.key(j + nleaf)) : -1;
-        b.DG[i] = (j >= 0 && j + ncrit < n) ? key_cpl(b.key(j), b.key(j + ncrit)) : -1;
+        b.D[i] = (j >= 0 && j + nleaf < n) ? b.cpl(j, j + nleaf) : -1;
+        b.DG[i] = (j >= 0 && j + ncrit < n) ? b.cpl(j, j + ncrit) : -1;
     }
     __syncthreads();
     return b;
@@ -109,15 +119,17 @@ __device__ BuildShared load_build_shared(void *smem, const unsigned long long *_
 
 size_t build_smem_bytes(int nleaf, int ncrit) {
     int W = nleaf > ncrit ? nleaf : ncrit;
-    return (size_t)(BUILD_THREADS + 2 * W) * 8 + 2 * (size_t)(BUILD_THREADS + W) * 4;
+    return (size_t)(BUILD_THREADS + 2 * W) * 8 + 2 * (size_t)(BUILD_THREADS + W) * 4 +
+           (size_t)(BUILD_THREADS + 2 * W);
 }
 
-// Which cells body t starts (levels lo..hi) and how many groups.
+// Which cells body t starts (levels lo..hi) and how many groups; send is the
+// end of t's system.
 __device__ BodyCells analyse_body(const BuildShared &b, int t, int n, int nleaf, int ncrit,
-                                  const unsigned long long *__restrict__ sk) {
+                                  const unsigned long long *__restrict__ sk, int send) {
     BodyCells r{false, 0, -1, 0, 0};
     if (t >= n) return r;
-    int l0 = (t == 0) ? 0 : key_cpl(b.key(t - 1), b.key(t)) + 1;
+    int l0 = (t == 0) ? 0 : b.cpl(t - 1, t) + 1;
     if (l0 > MAX_LEVEL) return r;
     if (l0 > 0) {
         int e = -1;
@@ -138,10 +150,15 @@ __device__ BodyCells analyse_body(const BuildShared &b, int t, int n, int nleaf,
         }
         r.ngrp = starts ? 1 : 0;
     } else {
-        int cnt = run_end(sk, n, t, r.hi) - t;
+        int cnt = run_end(sk, send, t, r.hi) - t;
         r.ngrp = (cnt + ncrit - 1) / ncrit;
     }
     return r;
+}
+
+__device__ __forceinline__ int system_end(const DevState *__restrict__ st, const uint8_t *__restrict__ sysid,
+                                          int t, int n) {
+    return t < n ? (int)st->sys_off[sysid[t] + 1] : n;
 }
 
 __device__ __forceinline__ bool has_level(const BodyCells &bc, int r) {
@@ -150,14 +167,15 @@ __device__ __forceinline__ bool has_level(const BodyCells &bc, int r) {
 
 // Pass 1: per block, the number of cells of each level and of groups.
 __global__ void __launch_bounds__(BUILD_THREADS)
-k_build_count(const unsigned long long *__restrict__ sk, int n, int nleaf, int ncrit,
-              unsigned *blockcount, int nblocks, const DevState *__restrict__ st) {
+k_build_count(const unsigned long long *__restrict__ sk, const uint8_t *__restrict__ sysid, int n,
+              int nleaf, int ncrit, unsigned *blockcount, int nblocks, const DevState *__restrict__ st) {
     extern __shared__ unsigned long long smem_u64[];
     __shared__ unsigned s_wc[NROWS][32];
     if (st->status & ST_TIMEOUT) return;        // keys not sorted: skip the build
     const int base = blockIdx.x * BUILD_THREADS, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    BuildShared b = load_build_shared(smem_u64, sk, n, base, nleaf, ncrit);
-    BodyCells bc = analyse_body(b, base + tid, n, nleaf, ncrit, sk);
+    BuildShared b = load_build_shared(smem_u64, sk, sysid, n, base, nleaf, ncrit);
+    const int t = base + tid;
+    BodyCells bc = analyse_body(b, t, n, nleaf, ncrit, sk, system_end(st, sysid, t, n));
     for (int r = 0; r <= MAX_LEVEL; r++) {
         unsigned m = __ballot_sync(0xffffffffu, has_level(bc, r));
         if (lane == 0) s_wc[r][warp] = __popc(m);
@@ -219,8 +237,9 @@ k_build_scan(unsigned *blockcount, int nblocks, DevState *st) {
 // are the level-(r+1) cells between its cb and the next cell's cb.  Leaves
 // get their body count here (a short search); internal cells in pass 4.
 __global__ void __launch_bounds__(BUILD_THREADS)
-k_build_write(const unsigned long long *__restrict__ sk, int n, int nleaf, int ncrit,
-              const unsigned *__restrict__ blockcount, int nblocks, long long ccap, DevState *st,
+k_build_write(const unsigned long long *__restrict__ sk, const uint8_t *__restrict__ sysid, int n,
+              int nleaf, int ncrit, const unsigned *__restrict__ blockcount, int nblocks, long long ccap,
+              DevState *st,
               uint2 *cell_body, uint2 *cell_link, uint8_t *cell_level, uint32_t *cell_parent,
               uint32_t *cell_done, uint32_t *cell_cb, uint2 *groups) {
     extern __shared__ unsigned long long smem_u64[];
@@ -247,9 +266,10 @@ k_build_write(const unsigned long long *__restrict__ sk, int n, int nleaf, int n
     }
     __syncthreads();
     if (!s_ok) return;
-    BuildShared b = load_build_shared(smem_u64, sk, n, base, nleaf, ncrit);
+    BuildShared b = load_build_shared(smem_u64, sk, sysid, n, base, nleaf, ncrit);
     const int t = base + tid;
-    BodyCells bc = analyse_body(b, t, n, nleaf, ncrit, sk);
+    const int send = system_end(st, sysid, t, n);
+    BodyCells bc = analyse_body(b, t, n, nleaf, ncrit, sk, send);
     const unsigned lt = (1u << lane) - 1u;
 
     for (int r = 0; r <= MAX_LEVEL; r++) {
@@ -288,7 +308,7 @@ k_build_write(const unsigned long long *__restrict__ sk, int n, int nleaf, int n
             cell_done[c] = 0u;
             if (r == 0) cell_parent[c] = 0xffffffffu;
             if (r == bc.hi) {
-                int cnt = run_end(sk, n, t, r) - t;
+                int cnt = run_end(sk, send, t, r) - t;
                 cell_body[c] = make_uint2((unsigned)t, (unsigned)cnt);
                 cell_link[c] = make_uint2((unsigned)t, (unsigned)cnt | LEAF_BIT);
             } else {
@@ -302,10 +322,10 @@ k_build_write(const unsigned long long *__restrict__ sk, int n, int nleaf, int n
     if (bc.ngrp > 0) {
         unsigned g = s_base[GROUP_ROW] + s_wc[GROUP_ROW][warp] + (unsigned)gx;
         if (bc.lg <= bc.hi) {
-            int e = run_end(sk, n, t, bc.lg);
+            int e = run_end(sk, send, t, bc.lg);
             groups[g] = make_uint2((unsigned)t, (unsigned)(e - t));
         } else {
-            int e = run_end(sk, n, t, bc.hi);
+            int e = run_end(sk, send, t, bc.hi);
             for (int k = 0; k < bc.ngrp; k++) {
                 int b0 = t + k * ncrit;
                 groups[g + k] = make_uint2((unsigned)b0, (unsigned)min(ncrit, e - b0));
@@ -347,7 +367,7 @@ __global__ void k_build_link(const DevState *__restrict__ st, const uint32_t *__
 cudaError_t launch_build(Ctx &c) {
     int n = (int)c.n;
     size_t smem = build_smem_bytes(c.nleaf, c.ncrit);
-    k_build_count<<<c.nbblocks, BUILD_THREADS, smem, c.stream>>>(c.keys, n, c.nleaf, c.ncrit,
+    k_build_count<<<c.nbblocks, BUILD_THREADS, smem, c.stream>>>(c.keys, c.sysid, n, c.nleaf, c.ncrit,
                                                                  c.blockcount, c.nbblocks, c.st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -355,7 +375,7 @@ cudaError_t launch_build(Ctx &c) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_build_write<<<c.nbblocks, BUILD_THREADS, smem, c.stream>>>(
-        c.keys, n, c.nleaf, c.ncrit, c.blockcount, c.nbblocks, c.ccap, c.st, c.cell_body,
+        c.keys, c.sysid, n, c.nleaf, c.ncrit, c.blockcount, c.nbblocks, c.ccap, c.st, c.cell_body,
         c.cell_link, c.cell_level, c.cell_parent, c.cell_done, c.cell_cb, c.groups);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -3,7 +3,8 @@
 // group walk of Barnes 1990).  This is the dominant kernel (>80% of a step).
 //
 // One warp owns one group (<= 64 bodies that share an interaction list).  A
-// persistent grid pulls groups from an atomic queue in key order.  Per warp:
+// persistent grid pulls groups from one atomic queue in key order -- for an
+// ensemble, the groups of all systems, each walked from its own root.  Per warp:
 //  * a stack of child ranges (first child, count <= 8) in shared memory; each
 //    round pops up to 32 cells, one per lane, and tests them against the
 //    group's bounding box: a cell is opened when the squared distance from its
@@ -183,8 +184,9 @@ __global__ void __launch_bounds__(256)
 k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__ groups,
        const float4 *__restrict__ pos4, const float4 *__restrict__ test,
        const uint2 *__restrict__ link, const float4 *__restrict__ mono,
-       const float4 *__restrict__ quadA, const float2 *__restrict__ quadB, float eps,
-       int stack_cap, long long max_rounds, float4 *acc4, uint2 *counts) {
+       const float4 *__restrict__ quadA, const float2 *__restrict__ quadB,
+       const uint8_t *__restrict__ sysid, float eps, int stack_cap, long long max_rounds,
+       float4 *acc4, uint2 *counts) {
     extern __shared__ float4 smem4[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const size_t warp_bytes = sizeof(WarpRings) + (size_t)stack_cap * sizeof(unsigned);
@@ -237,7 +239,9 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
 #pragma unroll
         for (int b = 0; b < BPL; b++) A[b] = Acc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         int sp = 1;
-        if (lane == 0) stk[0] = 0u;                  // root range: cell 0, count 1
+        // Root of the group's system: the level-0 cells are the system roots in
+        // system order, so system s's root is cell s (range of one cell).
+        if (lane == 0) stk[0] = (unsigned)sysid[gb] << 3;
         int pc_head = 0, pc_n = 0, pp_head = 0, pp_n = 0;
         unsigned npc = 0, npp = 0;
         bool overflow = false, timeout = false;
@@ -403,7 +407,7 @@ static cudaError_t launch_walk_t(Ctx &c, float eps) {
         occ_warps = warps; occ_smem = smem; occ_per_sm = per < 1 ? 1 : per;
     }
     k_walk<BPL><<<c.num_sms * occ_per_sm, warps * 32, smem, c.stream>>>(
-        c.st, c.st, c.groups, c.pos4, c.test, c.cell_link, c.mono, c.quadA, c.quadB, eps,
+        c.st, c.st, c.groups, c.pos4, c.test, c.cell_link, c.mono, c.quadA, c.quadB, c.sysid, eps,
         c.list_capacity, c.max_spin, c.acc4, c.counts);
     return cudaGetLastError();
 }

@@ -25,7 +25,7 @@ __global__ void k_onesweep(const unsigned long long *__restrict__ kin, const uin
                            unsigned long long *__restrict__ kout, uint32_t *__restrict__ vout, int n,
                            int shift, const unsigned *__restrict__ ghist, unsigned *status,
                            unsigned *status_next, unsigned *ticket, int ntiles, DevState *st,
-                           long long max_spin);
+                           long long max_spin, const uint8_t *__restrict__ dsrc);
 extern const size_t SORT_DYN_SMEM_BYTES;
 
 constexpr int STATIC_SORT_MAX_N = 1 << 16;                       // 65536 keys
@@ -134,7 +134,7 @@ extern "C" int bonsai_sort_keys_static(const uint64_t *keys, uint64_t *sorted_ke
         k_onesweep<<<ntiles, SORT_THREADS, SORT_DYN_SMEM_BYTES, st>>>(
             kin, vin, kb[1 - (p & 1)], vb[1 - (p & 1)], nn, 8 * p, s->st.hist + 256 * p,
             s->tile_status + plane * p, p + 1 < SORT_PASSES ? s->tile_status + plane * (p + 1) : nullptr,
-            s->st.sort_tile + p, ntiles, &s->st, 1ll << 24);
+            s->st.sort_tile + p, ntiles, &s->st, 1ll << 24, nullptr);
     }
     if (cudaGetLastError() != cudaSuccess)
         return set_err(BONSAI_ERR_CUDA, "bonsai_sort_keys_static: kernel launch failed");

@@ -1,0 +1,43 @@
+"""The autotuner picks a (group size, walk block width) pair by timing the
+walk; the tuned context must compute exactly what a context configured with
+that pair by hand computes (the block width never changes the arithmetic)."""
+import numpy as np
+import pytest
+
+import paper_1204_2280_gb300 as B
+from paper_1204_2280_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def forces(bz, n):
+    acc = np.zeros((n, 3), np.float32)
+    pot = np.zeros(n, np.float32)
+    bz.forces(0.75, 0.01, acc, pot)
+    return acc, pot
+
+
+def test_autotune_result_is_consistent():
+    b = W.plummer(1 << 15, 3)
+    with B.Bonsai(B.Config()) as bz:
+        bz.set_bodies(b.pos, b.mass, b.vel)
+        nc, w, ms = B.bonsai_autotune(bz.ctx, 0.75, 0.01)
+        assert nc in (16, 32, 48, 64) and w in (2, 4, 8) and ms > 0
+        a1, p1 = forces(bz, b.n)
+        bz.step(1.0 / 64)
+        bz.sync()
+    with B.Bonsai(B.Config(ncrit=nc, walk_warps=w)) as bz:
+        bz.set_bodies(b.pos, b.mass, b.vel).build().multipoles()
+        a2, p2 = forces(bz, b.n)
+    assert np.array_equal(a1, a2) and np.array_equal(p1, p2)
+
+
+@pytest.mark.parametrize("w", [1, 2, 8])
+def test_walk_block_width_does_not_change_results(w):
+    b = W.plummer(20000, 4)
+    out = []
+    for ww in (4, w):
+        with B.Bonsai(B.Config(ncrit=64, walk_warps=ww)) as bz:
+            bz.set_bodies(b.pos, b.mass).build().multipoles()
+            out.append(forces(bz, b.n))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
