@@ -65,6 +65,10 @@ def parse():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-ensemble", action="store_true")
     p.add_argument("--ensemble-systems", type=int, default=64)
+    p.add_argument("--no-learned", action="store_true")
+    p.add_argument("--learned-n", type=int, default=1 << 22)
+    p.add_argument("--learned-plummer", type=int, default=8, help="Plummer training snapshots")
+    p.add_argument("--learned-merger", type=int, default=8, help="merger training snapshots")
     return p.parse_args()
 
 
@@ -244,6 +248,135 @@ def run_ensemble(a, dev, stream):
             "what": "all systems in one bonsai_step: one sort, one build, one persistent walk, one graph"}
 
 
+def run_learned(a, dev, stream):
+    """Plain vs learned at equal 99th-percentile force error.
+
+    Workload: Plummer sphere N = 2^22 (seed 4) and a two-Plummer merger
+    (2 x 2^21, centres +-2 on x, relative speed 0.5), eps = 0.002.  The
+    network (12 -> 64 -> 64 -> 3) is trained here, on the GPU, on theta = 1
+    walk features vs direct-sum labels from rotated Plummer spheres (seeds
+    1000..) and snapshots of a merger stepped at theta = 0.5.  Errors are the
+    judge's: p99 of |a - a_direct| / |a_direct| over 4096 bodies sampled
+    every N/4096 in key order.  theta* is the plain opening angle whose p99
+    equals the learned one (bisection).  Step throughputs are full
+    bonsai_step calls (sort ... walk, kicks) timed with CUDA events, L2
+    flushed between steps."""
+    import numpy as np
+    import torch
+    import paper_1204_2280_gb300 as B
+    from paper_1204_2280_gb300 import learned as L
+    from paper_1204_2280_gb300 import workloads as W
+    n, eps, dt = a.learned_n, 0.002, 1.0 / 256
+    t0 = time.perf_counter()
+    plummers = L.snapshots(n, range(1000, 1000 + a.learned_plummer), rotations=1)
+    mergers = L.evolved(W.merger(n, 40), steps=16 * a.learned_merger, every=16, theta=0.5, eps=eps)
+    X, Y = L.training_set(plummers, theta=1.0, eps=eps, per_snapshot=4096, ncrit=64)
+    Xm, Ym = L.training_set(mergers, theta=1.0, eps=eps, per_snapshot=4096, ncrit=64, seed=500)
+    X, Y = np.concatenate([X, Xm]), np.concatenate([Y, Ym])
+    t1 = time.perf_counter()
+    net, losses = L.train(X, Y, epochs=40, batch=4096, lr=2e-3, wd=1e-4, seed=0)
+    t2 = time.perf_counter()
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    bz = B.Bonsai(B.Config(ncrit=64), stream=stream)
+
+    def load(b):
+        bz.set_bodies(torch.from_numpy(b.pos).to(dev), torch.from_numpy(b.mass).to(dev),
+                      torch.from_numpy(b.vel).to(dev))
+        bz.build().multipoles()
+
+    def p99_plain(theta):
+        bz.forces(theta, eps)
+        return B.bonsai_judge(bz.ctx, eps)
+
+    def p99_learned():
+        B.bonsai_set_learned(bz.ctx, net, 1.0, 0.5, 1e30)
+        B.bonsai_forces_learned(bz.ctx, eps)
+        p = B.bonsai_get_judge(bz.ctx)[0]
+        B.bonsai_set_learned(bz.ctx, None)
+        return p
+
+    def errors(b):
+        load(b)
+        Xh, Yh, _ = B.bonsai_learn_samples(bz.ctx, 1.0, eps, 4096, 99)
+        ysig = net.get_params()[1][-1]
+        mse = (float(np.mean(Yh.astype(np.float64) ** 2)),
+               float(np.mean((Yh - ysig * net.predict(Xh)).astype(np.float64) ** 2)))
+        return {"theta_1.0": p99_plain(1.0), "theta_1.0_mlp": p99_learned(), "theta_0.5": p99_plain(0.5),
+                "theta_0.75": p99_plain(0.75), "mse_residual_heldout": {"theta_1.0": mse[0], "theta_1.0_mlp": mse[1]}}
+
+    held = W.plummer(n, 4)
+    merger = W.merger(n, 41)
+    err = {"merger": errors(merger), "plummer": errors(held)}
+    target = err["plummer"]["theta_1.0_mlp"]
+    lo, hi = 0.3, 1.15                      # plain p99 grows with theta
+    if p99_plain(hi) <= target:
+        lo = hi
+    else:
+        for _ in range(14):
+            mid = 0.5 * (lo + hi)
+            if p99_plain(mid) <= target:
+                lo = mid
+            else:
+                hi = mid
+    theta_star = lo
+    p_star = p99_plain(theta_star)
+
+    def timed(setup, steps=5, warm=3):
+        load(held)
+        setup()
+        for _ in range(warm):
+            bz.step(dt)
+        bz.sync()
+        ms, fell = [], 0
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bz.step(dt)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            fell += int(B.bonsai_get_judge(bz.ctx)[1])
+        B.bonsai_set_learned(bz.ctx, None)
+        bz.sync()
+        t = sum(ms) / len(ms)
+        return {"ms_per_step": t, "particles_per_s": n / (t / 1e3), "fallback_steps": fell, "steps": steps}
+
+    def plain(theta):
+        return lambda: B.bonsai_set_params(bz.ctx, theta, eps)
+
+    def learned(budget, every):
+        def f():
+            B.bonsai_set_params(bz.ctx, 1.0, eps)
+            B.bonsai_set_learned(bz.ctx, net, 1.0, 0.5, budget)
+            B.bonsai_set_judge_interval(bz.ctx, every)
+        return f
+
+    runs = {"plain_theta_0.5": timed(plain(0.5)),
+            "plain_theta_star": timed(plain(theta_star)),
+            "plain_theta_1.0": timed(plain(1.0)),
+            "learned_judged_every_step": timed(learned(1e30, 1)),
+            "learned_unjudged": timed(learned(1e30, 0)),
+            "learned_budget_p99_theta_0.5": timed(learned(err["plummer"]["theta_0.5"], 1))}
+    bz.close()
+    lj, ps = runs["learned_judged_every_step"], runs["plain_theta_star"]
+    return {
+        "workload": f"Plummer N={n} seed 4 and merger 2x{n // 2} (seed 41), eps={eps}, dt={dt:g}",
+        "network": "12 -> 64 -> 64 -> 3, BF16 tensor cores, FP32 accumulate, rotation-equivariant frame",
+        "train": {"samples": int(X.shape[0]), "plummer_snapshots": a.learned_plummer,
+                  "merger_snapshots": a.learned_merger, "epochs": 40, "loss_first": float(losses[0]),
+                  "loss_last": float(losses[-1]), "data_s": t1 - t0, "train_s": t2 - t1},
+        "p99": err,
+        "equal_p99": {"p99": target, "plain_theta": theta_star, "plain_p99": p_star,
+                      "plain_particles_per_s": ps["particles_per_s"],
+                      "learned_particles_per_s": lj["particles_per_s"],
+                      "learned_over_plain": lj["particles_per_s"] / ps["particles_per_s"]},
+        "steps": runs,
+    }
+
+
 def run_ours(a, rank, world, local_rank):
     import numpy as np
     import torch
@@ -331,6 +464,7 @@ def run_ours(a, rank, world, local_rank):
     bz.close()
 
     ens = None if a.no_ensemble else run_ensemble(a, dev, stream)
+    lrn = None if a.no_learned else run_learned(a, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -357,6 +491,7 @@ def run_ours(a, rank, world, local_rank):
             "interactions_per_s": (sum(npc) + sum(npp)) / (walk_ms / 1e3),
             "wall_s_timed_loop": t_wall,
             "ensemble": ens,
+            "learned": lrn,
         }
         print(json.dumps(line), flush=True)
 

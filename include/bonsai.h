@@ -201,6 +201,89 @@ int bonsai_get_counts(bonsai_ctx *ctx, uint32_t *n_pc, uint32_t *n_pp,
 int bonsai_sort_keys_static(const uint64_t *keys, uint64_t *sorted_keys,
                             uint32_t *perm, long long n, void *cuda_stream);
 
+/* ---- learned far-field correction (spec extension of Sect. 2) ----
+ * A per-body MLP 12 -> 64 -> 64 -> 3 (ReLU; BF16 weights, inputs and hidden
+ * activations, FP32 accumulation; inference on the tensor cores) predicts
+ * the residual r = (a_direct - a_tree) / |a_tree| of the coarse-theta walk
+ * as coefficients along a body-local frame (e0 = a_tree/|a_tree|, e1 = the
+ * part of the body's offset o from its group box's centre orthogonal to e0,
+ * e2 = e0 x e1), from 12 rotation-invariant quantities the walk produces:
+ * log|a_tree|, log(-phi_tree), log(1 + accepted cells) in the level bins
+ * 0-3, 4-6, 7-9, 10-21, log(1 + body-body interactions), log(n_G / (e_G^3 +
+ * eps^3)), log((d_G + eps)/eps), |o| / (d_G / 2), cos(o, a_tree), log n_G
+ * (e_G / d_G the largest extent / diagonal of the group's box).  Parameters:
+ * 5187 floats, rows W[out][in]: W1 64x12, b1 64, W2 64x64, b2 64, W3 3x64,
+ * b3 3; normalisation: mu[12], sigma[12], ysig (inputs (x-mu)/sigma, the net
+ * predicts r / ysig).  Feature rows X are n x 12 raw (unnormalised) inputs,
+ * targets Y n x 3 frame coefficients of r. */
+typedef struct bonsai_mlp bonsai_mlp;
+
+/* New MLP on the current device: He-normal weights from `seed`, zero
+ * biases, identity normalisation. */
+int bonsai_mlp_create(bonsai_mlp **out, unsigned long long seed);
+void bonsai_mlp_destroy(bonsai_mlp *m);
+const char *bonsai_mlp_last_error(const bonsai_mlp *m);
+
+/* Host copies in/out of the 5187 parameters and 25 normalisation values
+ * (either pointer may be NULL). */
+int bonsai_mlp_set_params(bonsai_mlp *m, const float *params, const float *norm);
+int bonsai_mlp_get_params(bonsai_mlp *m, float *params, float *norm);
+
+/* Normalisation from a training set: per-feature mean and standard
+ * deviation of X, RMS of Y. */
+int bonsai_mlp_fit_norm(bonsai_mlp *m, const float *X, const float *Y, long long n, int on_device);
+
+/* Raw network outputs (r / ysig) of n feature rows, on the tensor cores. */
+int bonsai_mlp_predict(bonsai_mlp *m, const float *X, float *Y, long long n, int on_device);
+
+/* Gradient (5187, host) and value (host) of the loss mean((net(X) -
+ * Y/ysig)^2) over the n rows and 3 outputs; forward and backward on the GPU. */
+int bonsai_mlp_grad(bonsai_mlp *m, const float *X, const float *Y, long long n, int on_device, float *grad,
+                    float *loss);
+
+/* AdamW training (beta 0.9/0.999, decoupled weight decay wd on the weight
+ * matrices) for `epochs` passes over the n rows in shuffled batches of
+ * `batch`; fits the normalisation first if it was never set.  loss_per_epoch
+ * (host, may be NULL) receives the mean batch loss of each epoch. */
+int bonsai_mlp_train(bonsai_mlp *m, const float *X, const float *Y, long long n, int on_device, int epochs,
+                     int batch, float lr, float wd, unsigned long long seed, float *loss_per_epoch);
+
+/* Training samples from a built context (after bonsai_multipoles): walk at
+ * theta with features, direct sum at ntar <= 4096 distinct bodies drawn with
+ * `seed`; X (ntar x 12) features, Y (ntar x 3) targets r, ids (ntar, may be
+ * NULL) the caller indices of the sampled bodies.  Leaves the theta-walk
+ * forces in the context. */
+int bonsai_learn_samples(bonsai_ctx *ctx, float theta, float eps, int ntar, unsigned long long seed,
+                         float *X, float *Y, uint32_t *ids, int on_device);
+
+/* Judge of the current accelerations: direct sum (FP32, Kahan, FP64
+ * reduction) at min(n, 4096) bodies spaced evenly in key order and the 99th
+ * percentile (numpy's linear interpolation) of |a - a_direct| / |a_direct|. */
+int bonsai_judge(bonsai_ctx *ctx, float eps, float *p99);
+
+/* Use the learned correction in bonsai_step and bonsai_forces_learned: walk
+ * at theta_coarse with features, add the MLP's correction, judge it; if the
+ * judge's p99 exceeds p99_budget, redo the walk at theta_fine (decided on the
+ * device, no host synchronisation).  m must stay alive while in use; NULL
+ * turns the correction off. */
+int bonsai_set_learned(bonsai_ctx *ctx, const bonsai_mlp *m, float theta_coarse, float theta_fine,
+                       float p99_budget);
+
+/* Judge only every `every`-th learned evaluation (bonsai_step or
+ * bonsai_forces_learned), counted from this call; the p99 and the fallback
+ * decision of a judged evaluation hold until the next judged one.  every = 1
+ * (the default) judges each evaluation; every = 0 never judges and never falls
+ * back.  Resets the count and the fallback flag.  BONSAI_ERR_INVALID_ARG for
+ * every < 0. */
+int bonsai_set_judge_interval(bonsai_ctx *ctx, int every);
+
+/* One learned force evaluation (requires bonsai_set_learned and
+ * bonsai_multipoles); outputs as in bonsai_forces. */
+int bonsai_forces_learned(bonsai_ctx *ctx, float eps, float *acc, float *pot, int on_device);
+
+/* The last learned evaluation's judge p99 and whether it fell back. */
+int bonsai_get_judge(bonsai_ctx *ctx, float *p99, int *fell_back);
+
 /* Text of the last error of ctx (or, for ctx == NULL, of the last failed
  * bonsai_create or bonsai_sort_keys_static of this thread).  Valid until the
  * next call on the context. */

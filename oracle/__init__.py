@@ -60,7 +60,7 @@ def lib():
             L.oracle_moments.argtypes = [i64, p, p, p, p, p, p, p]
             L.oracle_open_radius.argtypes = [i64, p, p, p, p, d, p, d, p]
             L.oracle_walk.argtypes = [i64, p, p, i64, p, p, p, p, p, p, p, p, i64, p, p,
-                                      d, d, d, p, p, p, p, p]
+                                      d, d, d, p, p, p, p, p, p, p]
             L.oracle_direct.argtypes = [p, p, i64, p, i64, d, p, p]
             L.oracle_energy.argtypes = [p, p, p, p, i64, p]
             L.oracle_pc_eval.argtypes = [p, p, d, p, d, p, p]
@@ -183,7 +183,7 @@ def cell_cube(tree: Tree, skeys, mn, S):
 
 
 def walk(spos, smass, tree: Tree, M, com, Q, r_open, gbeg, gcnt, eps: float,
-         tau_abs: float = 0.0, tau_rel: float = 0.0):
+         tau_abs: float = 0.0, tau_rel: float = 0.0, bins: bool = False):
     spos, smass = _f32(spos), _f32(smass)
     n = spos.shape[0]
     acc = np.zeros((n, 3))
@@ -191,14 +191,18 @@ def walk(spos, smass, tree: Tree, M, com, Q, r_open, gbeg, gcnt, eps: float,
     npc = np.zeros(n, np.int32)
     npp = np.zeros(n, np.int32)
     flag = np.zeros(n, np.int8)
+    nb = np.zeros((n, 4), np.int32) if bins else None
     rc = lib().oracle_walk(n, _ptr(spos), _ptr(smass), tree.ncells, _ptr(tree.body_begin),
                            _ptr(tree.body_count), _ptr(tree.child_begin), _ptr(tree.nchild),
                            _ptr(np.ascontiguousarray(M)), _ptr(np.ascontiguousarray(com)),
                            _ptr(np.ascontiguousarray(Q)), _ptr(np.ascontiguousarray(r_open)),
                            gbeg.shape[0], _ptr(gbeg), _ptr(gcnt), float(eps), float(tau_abs),
-                           float(tau_rel), _ptr(acc), _ptr(pot), _ptr(npc), _ptr(npp), _ptr(flag))
+                           float(tau_rel), _ptr(acc), _ptr(pot), _ptr(npc), _ptr(npp), _ptr(flag),
+                           _ptr(tree.level) if bins else None, _ptr(nb) if bins else None)
     if rc:
         raise ValueError("oracle_walk: a body's own leaf was accepted (theta too large)")
+    if bins:
+        return acc, pot, npc, npp, flag, nb
     return acc, pot, npc, npp, flag
 
 
@@ -252,6 +256,8 @@ class TreeForces:
     n_pc: np.ndarray          # caller order
     n_pp: np.ndarray
     borderline: np.ndarray    # caller order, bool
+    npc_bins: np.ndarray      # caller order (n, 4): accepted cells per level bin
+    group_of: np.ndarray      # caller order: index of the body's group
 
 
 def tree_forces(pos, mass, theta: float, eps: float, nleaf: int = 16, ncrit: int = 32,
@@ -267,15 +273,17 @@ def tree_forces(pos, mass, theta: float, eps: float, nleaf: int = 16, ncrit: int
     gb, gc = groups(tree, ncrit)
     M, com, Q = moments(tree, spos, smass)
     ro = open_radius(tree, skeys, mn, S, com, theta)
-    acc_s, pot_s, npc_s, npp_s, flag_s = walk(spos, smass, tree, M, com, Q, ro, gb, gc, eps,
-                                              tau_abs, tau_rel)
+    acc_s, pot_s, npc_s, npp_s, flag_s, nb_s = walk(spos, smass, tree, M, com, Q, ro, gb, gc, eps,
+                                                    tau_abs, tau_rel, bins=True)
     n = pos.shape[0]
     acc = np.zeros((n, 3)); acc[perm] = acc_s
     pot = np.zeros(n); pot[perm] = pot_s
     npc = np.zeros(n, np.int32); npc[perm] = npc_s
     npp = np.zeros(n, np.int32); npp[perm] = npp_s
     fl = np.zeros(n, bool); fl[perm] = flag_s.astype(bool)
-    return TreeForces(mn, S, k, perm, tree, gb, gc, M, com, Q, ro, acc, pot, npc, npp, fl)
+    nb = np.zeros((n, 4), np.int32); nb[perm] = nb_s
+    gid = np.zeros(n, np.int64); gid[perm] = np.repeat(np.arange(gb.shape[0]), gc)
+    return TreeForces(mn, S, k, perm, tree, gb, gc, M, com, Q, ro, acc, pot, npc, npp, fl, nb, gid)
 
 
 def kdk_step(pos, vel, mass, acc0, dt: float, theta: float, eps: float, nleaf: int = 16,

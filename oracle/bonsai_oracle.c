@@ -375,7 +375,8 @@ int oracle_open_radius(int64_t ncells, const int32_t *body_begin,
  * Outputs per body (sorted order): acc[3], pot, n_pc, n_pp (self excluded).
  * A group is flagged borderline (flag[body] = 1 for its bodies) when some
  * tested cell had |dist - r_open| <= tau_abs + tau_rel * r_open, i.e. a
- * single-precision implementation may take the other decision there. */
+ * single-precision implementation may take the other decision there.
+ * npc_bins (may be NULL, needs level): accepted cells per level bin. */
 int oracle_walk(int64_t n, const float *spos, const float *smass,
                 int64_t ncells, const int32_t *body_begin,
                 const int32_t *body_count, const int32_t *child_begin,
@@ -383,7 +384,8 @@ int oracle_walk(int64_t n, const float *spos, const float *smass,
                 const double *Q, const double *r_open, int64_t ngroups,
                 const int32_t *g_begin, const int32_t *g_count, double eps,
                 double tau_abs, double tau_rel, double *acc, double *pot,
-                int32_t *n_pc, int32_t *n_pp, int8_t *flag)
+                int32_t *n_pc, int32_t *n_pp, int8_t *flag,
+                const int32_t *level, int32_t *npc_bins)
 {
     (void)n; (void)ncells;
     double eps2 = eps * eps;
@@ -440,6 +442,14 @@ int oracle_walk(int64_t n, const float *spos, const float *smass,
                     acc_cells[na++] = c;
                 }
             }
+            /* Accepted cells by level bin (0-3, 4-6, 7-9, 10-21): an input of
+             * the learned correction. */
+            int32_t bins[4] = {0, 0, 0, 0};
+            if (npc_bins)
+                for (int64_t k = 0; k < na; k++) {
+                    int32_t lv = level[acc_cells[k]];
+                    bins[lv <= 3 ? 0 : lv <= 6 ? 1 : lv <= 9 ? 2 : 3]++;
+                }
             /* 2. Evaluate for every body of the group. */
             int32_t npp_group = 0;
             for (int64_t k = 0; k < nl; k++) npp_group += body_count[open_leaves[k]];
@@ -464,6 +474,8 @@ int oracle_walk(int64_t n, const float *spos, const float *smass,
                 n_pc[i] = (int32_t)na;
                 n_pp[i] = npp_group - self_seen;
                 flag[i] = (int8_t)border;
+                if (npc_bins)
+                    for (int b = 0; b < 4; b++) npc_bins[4 * i + b] = bins[b];
                 if (self_seen != 1) {
                     #pragma omp atomic write
                     err = 1;

@@ -30,7 +30,15 @@ EXPORTS = ["bonsai_create", "bonsai_destroy", "bonsai_set_bodies", "bonsai_build
            "bonsai_get_domain", "bonsai_get_keys", "bonsai_get_tree", "bonsai_get_groups",
            "bonsai_get_moments", "bonsai_get_counts", "bonsai_last_error", "bonsai_version",
            "bonsai_get_stage_times", "bonsai_sort_keys_static", "bonsai_set_systems",
-           "bonsai_get_domains", "bonsai_autotune"]
+           "bonsai_get_domains", "bonsai_autotune", "bonsai_mlp_create", "bonsai_mlp_destroy",
+           "bonsai_mlp_last_error", "bonsai_mlp_set_params", "bonsai_mlp_get_params",
+           "bonsai_mlp_fit_norm", "bonsai_mlp_predict", "bonsai_mlp_grad", "bonsai_mlp_train",
+           "bonsai_learn_samples", "bonsai_judge", "bonsai_set_learned", "bonsai_forces_learned",
+           "bonsai_get_judge", "bonsai_set_judge_interval"]
+
+MLP_IN, MLP_H, MLP_OUT = 12, 64, 3
+MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_OUT * MLP_H + MLP_OUT
+MLP_NNORM = 2 * MLP_IN + 1
 
 STAGES = ["kick_drift_domain", "keys", "sort", "reorder", "build", "multipoles", "walk", "kick"]
 
@@ -87,6 +95,24 @@ def lib():
         L.bonsai_set_systems.argtypes = [p, p, i]
         L.bonsai_get_domains.argtypes = [p, p, p]
         L.bonsai_autotune.argtypes = [p, f, f, p, p, p]
+        u64 = C.c_ulonglong
+        L.bonsai_mlp_create.argtypes = [C.POINTER(p), u64]
+        L.bonsai_mlp_destroy.argtypes = [p]
+        L.bonsai_mlp_destroy.restype = None
+        L.bonsai_mlp_last_error.argtypes = [p]
+        L.bonsai_mlp_last_error.restype = C.c_char_p
+        L.bonsai_mlp_set_params.argtypes = [p, p, p]
+        L.bonsai_mlp_get_params.argtypes = [p, p, p]
+        L.bonsai_mlp_fit_norm.argtypes = [p, p, p, ll, i]
+        L.bonsai_mlp_predict.argtypes = [p, p, p, ll, i]
+        L.bonsai_mlp_grad.argtypes = [p, p, p, ll, i, p, p]
+        L.bonsai_mlp_train.argtypes = [p, p, p, ll, i, i, i, f, f, u64, p]
+        L.bonsai_learn_samples.argtypes = [p, f, f, i, u64, p, p, p, i]
+        L.bonsai_judge.argtypes = [p, f, p]
+        L.bonsai_set_learned.argtypes = [p, p, f, f, f]
+        L.bonsai_forces_learned.argtypes = [p, f, p, p, i]
+        L.bonsai_get_judge.argtypes = [p, p, p]
+        L.bonsai_set_judge_interval.argtypes = [p, i]
         _lib = L
     return _lib
 
@@ -277,6 +303,109 @@ def bonsai_sort_keys_static(keys, sorted_keys, perm, stream=None):
 
 def bonsai_version() -> str:
     return lib().bonsai_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# Learned far-field correction
+# ---------------------------------------------------------------------------
+
+def _mcheck(m, rc):
+    if rc != BONSAI_OK:
+        msg = lib().bonsai_mlp_last_error(m)
+        raise BonsaiError(rc, msg.decode() if msg else "")
+
+
+class MLP:
+    """Owning wrapper of a bonsai_mlp."""
+
+    def __init__(self, seed: int = 0):
+        self.m = C.c_void_p()
+        _check(None, lib().bonsai_mlp_create(C.byref(self.m), seed))
+
+    def close(self):
+        if self.m:
+            lib().bonsai_mlp_destroy(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params=None, norm=None):
+        pp = None if params is None else np.ascontiguousarray(params, np.float32)
+        nn = None if norm is None else np.ascontiguousarray(norm, np.float32)
+        _mcheck(self.m, lib().bonsai_mlp_set_params(self.m, None if pp is None else pp.ctypes.data,
+                                                     None if nn is None else nn.ctypes.data))
+
+    def get_params(self):
+        pp = np.zeros(MLP_NPARAM, np.float32)
+        nn = np.zeros(MLP_NNORM, np.float32)
+        _mcheck(self.m, lib().bonsai_mlp_get_params(self.m, pp.ctypes.data, nn.ctypes.data))
+        return pp, nn
+
+    def fit_norm(self, X, Y):
+        (xp, d0), (yp, d1) = _buf(X, np.float32), _buf(Y, np.float32)
+        _mcheck(self.m, lib().bonsai_mlp_fit_norm(self.m, xp, yp, int(X.shape[0]), _same_side(d0, d1)))
+
+    def predict(self, X, Y=None):
+        if Y is None:
+            Y = np.zeros((X.shape[0], MLP_OUT), np.float32)
+        (xp, d0), (yp, d1) = _buf(X, np.float32), _buf(Y, np.float32)
+        _mcheck(self.m, lib().bonsai_mlp_predict(self.m, xp, yp, int(X.shape[0]), _same_side(d0, d1)))
+        return Y
+
+    def grad(self, X, Y):
+        g = np.zeros(MLP_NPARAM, np.float32)
+        loss = C.c_float()
+        (xp, d0), (yp, d1) = _buf(X, np.float32), _buf(Y, np.float32)
+        _mcheck(self.m, lib().bonsai_mlp_grad(self.m, xp, yp, int(X.shape[0]), _same_side(d0, d1),
+                                              g.ctypes.data, C.byref(loss)))
+        return g, loss.value
+
+    def train(self, X, Y, epochs=10, batch=8192, lr=1e-3, wd=1e-4, seed=0):
+        losses = np.zeros(epochs, np.float32)
+        (xp, d0), (yp, d1) = _buf(X, np.float32), _buf(Y, np.float32)
+        _mcheck(self.m, lib().bonsai_mlp_train(self.m, xp, yp, int(X.shape[0]), _same_side(d0, d1), epochs,
+                                               batch, lr, wd, seed, losses.ctypes.data))
+        return losses
+
+
+def bonsai_learn_samples(ctx, theta: float, eps: float, ntar: int, seed: int):
+    """Features X, targets Y and caller ids of ntar sampled bodies."""
+    X = np.zeros((ntar, MLP_IN), np.float32)
+    Y = np.zeros((ntar, MLP_OUT), np.float32)
+    ids = np.zeros(ntar, np.uint32)
+    _check(ctx, lib().bonsai_learn_samples(ctx, theta, eps, ntar, seed, X.ctypes.data, Y.ctypes.data,
+                                           ids.ctypes.data, 0))
+    return X, Y, ids
+
+
+def bonsai_judge(ctx, eps: float) -> float:
+    v = C.c_float()
+    _check(ctx, lib().bonsai_judge(ctx, eps, C.byref(v)))
+    return v.value
+
+
+def bonsai_set_learned(ctx, mlp, theta_coarse=1.0, theta_fine=0.5, p99_budget=0.0):
+    _check(ctx, lib().bonsai_set_learned(ctx, None if mlp is None else mlp.m, theta_coarse, theta_fine,
+                                         p99_budget))
+
+
+def bonsai_forces_learned(ctx, eps: float, acc=None, pot=None):
+    (ap, d0), (pp, d1) = _buf(acc, np.float32), _buf(pot, np.float32)
+    _check(ctx, lib().bonsai_forces_learned(ctx, eps, ap, pp, _same_side(d0, d1)))
+
+
+def bonsai_set_judge_interval(ctx, every: int):
+    _check(ctx, lib().bonsai_set_judge_interval(ctx, int(every)))
+
+
+def bonsai_get_judge(ctx):
+    v, f = C.c_float(), C.c_int()
+    _check(ctx, lib().bonsai_get_judge(ctx, C.byref(v), C.byref(f)))
+    return v.value, bool(f.value)
 
 
 class Bonsai:

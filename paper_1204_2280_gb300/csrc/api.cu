@@ -14,10 +14,6 @@
 
 using namespace bonsai;
 
-struct bonsai_ctx {
-    Ctx c;
-};
-
 static thread_local std::string g_create_err;
 
 namespace bonsai {
@@ -81,8 +77,10 @@ cudaError_t alloc_bodies(Ctx &c, long long n) {
     a.take(c.mono, ccap, plan); a.take(c.quadA, ccap, plan); a.take(c.quadB, ccap, plan);
     a.take(c.test, ccap, plan); a.take(c.delta, ccap, plan);
     a.take(c.shadow, 10 * (size_t)(ccap < 585 * MAX_SYSTEMS ? ccap : 585 * MAX_SYSTEMS), plan);
-    a.take(c.groups, n, plan); a.take(c.counts, n, plan);
+    a.take(c.groups, n, plan); a.take(c.counts, n, plan); a.take(c.feat, FEAT_STRIDE * (size_t)n, plan);
     a.take(c.stage, 7 * (size_t)n, plan);
+    a.take(c.judge_targets, JUDGE_MAX, plan); a.take(c.judge_direct, JUDGE_MAX, plan);
+    a.take(c.judge_partial, (size_t)JUDGE_SPLIT * JUDGE_MAX, plan);
     char *base = nullptr;
     cudaError_t e = cudaMalloc(&base, a.off);
     if (e != cudaSuccess) return e;
@@ -91,6 +89,7 @@ cudaError_t alloc_bodies(Ctx &c, long long n) {
     c.ntiles = (int)ntiles;
     c.nbblocks = (int)nbb;
     c.ccap = ccap;
+    c.judge_n = 0;
     return cudaMemsetAsync(base, 0, a.off, c.stream);
 }
 
@@ -128,7 +127,7 @@ cudaError_t pipeline_step(Ctx &c, float dt) {
     STAGE(3, launch_reorder(c));
     STAGE(4, launch_build(c));
     STAGE(5, launch_multipoles(c));
-    STAGE(6, pipeline_forces(c, c.theta, c.eps));
+    STAGE(6, c.mlp_P ? pipeline_learned_forces(c, c.eps) : pipeline_forces(c, c.theta, c.eps));
     STAGE(7, launch_kick(c, dt));
 #undef STAGE
     return cudaEventRecordWithFlags(c.ev[8], c.stream, evf);

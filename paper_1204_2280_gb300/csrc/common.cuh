@@ -31,6 +31,12 @@ constexpr int SORT_ITEMS = 16;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;   // 4096 keys per tile
 constexpr int SORT_PASSES = 8;                         // 8-bit digits, 63-bit keys
 constexpr int MAX_SYSTEMS = 256;                       // ensemble: one more pass on the system id
+constexpr int MLP_IN = 12, MLP_H = 64, MLP_OUT = 3;    // learned correction 12 -> 64 -> 64 -> 3
+constexpr int MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_OUT * MLP_H + MLP_OUT;
+constexpr int MLP_NNORM = 2 * MLP_IN + 1;              // mu[12], sigma[12], ysig
+constexpr int FEAT_STRIDE = 12;                        // walk features per body
+constexpr int JUDGE_MAX = 4096;                        // sampled bodies of the direct-sum judge
+constexpr int JUDGE_SPLIT = 32;                        // source splits of the judge's direct sum
 constexpr int BUILD_THREADS = 1024;                    // bodies per build block
 
 // Device status bits (ORed by kernels, read and cleared by bonsai_sync).
@@ -54,6 +60,10 @@ struct DevState {
     unsigned status;
     unsigned long long inter[2];      // n_pc, n_pp totals of the last walk
     double diag[8];
+    float judge_p99;                  // learned path: p99 relative error at the judge's samples
+    unsigned fallback;                // 1: the judge asked for the fine-theta walk
+    unsigned judge_tick;              // learned evaluations since the interval was set
+    unsigned judge_on;                // 1: this evaluation is judged
 };
 
 struct Ctx {
@@ -89,6 +99,7 @@ struct Ctx {
     double *shadow = nullptr;        // FP64 moments of the top levels (10 per cell)
     uint2 *groups = nullptr;
     uint2 *counts = nullptr;         // per body (n_pc, n_pp), sorted order
+    float *feat = nullptr;           // per body FEAT_STRIDE walk features (learned correction), sorted order
     // staging for host transfers and caller-order outputs
     float *stage = nullptr;          // 7 floats per body
     DevState *st = nullptr;          // device
@@ -103,6 +114,16 @@ struct Ctx {
     bool timed_step = false;
     float graph_dt = 0.f, graph_theta = 0.f, graph_eps = 0.f;
     long long graph_n = -1;
+
+    // learned far-field correction (bonsai_set_learned): weights, thetas,
+    // judge budget, and the judge's sample and scratch
+    const float *mlp_P = nullptr, *mlp_norm = nullptr;
+    float theta_coarse = 1.0f, theta_fine = 0.5f, p99_budget = 0.f;
+    int judge_every = 1;                 // judge every k-th learned evaluation, 0: never
+    uint32_t *judge_targets = nullptr;   // JUDGE_MAX sorted positions
+    float4 *judge_partial = nullptr;     // JUDGE_SPLIT x JUDGE_MAX
+    float4 *judge_direct = nullptr;      // JUDGE_MAX
+    int judge_n = 0;                     // targets in use
 
     std::string err;
 };
@@ -148,8 +169,21 @@ cudaError_t launch_sort(Ctx &c);
 cudaError_t launch_reorder(Ctx &c);
 cudaError_t launch_build(Ctx &c);
 cudaError_t launch_multipoles(Ctx &c);
-cudaError_t launch_open_radius(Ctx &c, float theta);
-cudaError_t launch_walk(Ctx &c, float eps);
+cudaError_t launch_open_radius(Ctx &c, float theta, const unsigned *gate = nullptr);
+cudaError_t launch_walk(Ctx &c, float eps, bool features = false, const unsigned *gate = nullptr);
+cudaError_t launch_direct(Ctx &c, const uint32_t *targets, int ntar, float eps, float4 *partial, int nsplit,
+                          float4 *out, const unsigned *gate = nullptr);
+cudaError_t launch_judge(Ctx &c, const uint32_t *targets, int ntar, const float4 *direct, float budget,
+                         const unsigned *gate = nullptr);
+cudaError_t launch_mlp_infer(Ctx &c, const float *P, const float *norm);
+cudaError_t launch_mlp_rows(cudaStream_t s, const float *P, const float *norm, const float *X, float *Y, int n);
+cudaError_t launch_mlp_grad(cudaStream_t s, const float *P, const float *norm, const float *X, const float *Y,
+                            const uint32_t *idx, int bsz, float *grad, float *loss);
+cudaError_t launch_adamw(cudaStream_t s, float *P, const float *grad, float *m, float *v, float lr, float wd,
+                         int step);
+cudaError_t launch_gather_features(Ctx &c, const uint32_t *targets, int ntar, float *X, uint32_t *ids);
+cudaError_t launch_labels(Ctx &c, const uint32_t *targets, int ntar, const float4 *direct, float *Y);
+cudaError_t launch_feature_stats(cudaStream_t s, const float *X, const float *Y, int n, float *norm);
 cudaError_t launch_kick(Ctx &c, float dt);
 cudaError_t launch_scatter_forces(Ctx &c, float *acc, float *pot);
 cudaError_t launch_scatter_bodies(Ctx &c, float *pos, float *vel);
@@ -158,4 +192,12 @@ cudaError_t launch_diag(Ctx &c);
 cudaError_t launch_tree_export(Ctx &c, int32_t *bb, int32_t *bc, int32_t *cb, int32_t *nc, int32_t *lv);
 cudaError_t launch_moments_export(Ctx &c, float *mono, float *quad);
 
+cudaError_t launch_judge_targets(Ctx &c);
+cudaError_t launch_gated_walk_reset(Ctx &c);
+cudaError_t pipeline_learned_forces(Ctx &c, float eps);
+
 }  // namespace bonsai
+
+struct bonsai_ctx {
+    bonsai::Ctx c;
+};

@@ -1,0 +1,137 @@
+// k_judge.cu -- direct summation on a sample of bodies: the labels of the
+// learned correction and the per-step judge of its error (paper Sect. 1: the
+// O(N^2) method is the exact reference the tree approximates).
+//
+// For T target bodies (sorted positions) the softened acceleration and
+// potential from all N bodies: sources are streamed through shared memory in
+// tiles, each tile summed in FP32 and added with Kahan compensation; the
+// source range is split over blocks and the partial sums are added in FP64.
+// The judge then ranks the relative errors of the current accelerations at
+// the targets and compares their 99th percentile with a budget.
+#include "common.cuh"
+
+namespace bonsai {
+
+constexpr int DS_THREADS = 128;        // targets per block
+constexpr int DS_TILE = 256;           // sources per shared tile
+
+__device__ __forceinline__ void kadd(float &s, float &c, float v) {
+    float y = __fsub_rn(v, c);
+    float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+// Partial sums of split blockIdx.y over sources [chunk*y, chunk*(y+1)).
+// A non-null gate that reads 0 skips the work (all kernels of this file).
+__global__ void __launch_bounds__(DS_THREADS)
+k_direct_partial(const float4 *__restrict__ pos4, int n, const uint32_t *__restrict__ targets, int ntar,
+                 float eps2, int chunk, float4 *partial, const unsigned *__restrict__ gate) {
+    if (gate && *gate == 0u) return;
+    __shared__ float4 tile[DS_TILE];
+    const int k = blockIdx.x * DS_THREADS + threadIdx.x;
+    const bool live = k < ntar;
+    const float4 me = live ? pos4[targets[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float ax = 0.f, ay = 0.f, az = 0.f, ph = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, cp = 0.f;
+    const int s0 = blockIdx.y * chunk, s1 = min(n, s0 + chunk);
+    for (int b = s0; b < s1; b += DS_TILE) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < DS_TILE; i += DS_THREADS)
+            tile[i] = b + i < s1 ? pos4[b + i] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
+        __syncthreads();
+        float px = 0.f, py = 0.f, pz = 0.f, pp = 0.f;
+#pragma unroll 8
+        for (int j = 0; j < DS_TILE; j++) {
+            const float4 s = tile[j];
+            const float dx = s.x - me.x, dy = s.y - me.y, dz = s.z - me.z;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+            const float rinv = rsqrtf(r2);
+            const float mr = s.w * rinv;
+            const float mr3 = mr * rinv * rinv;
+            pp -= mr;
+            px = fmaf(mr3, dx, px); py = fmaf(mr3, dy, py); pz = fmaf(mr3, dz, pz);
+        }
+        kadd(ax, cx, px); kadd(ay, cy, py); kadd(az, cz, pz); kadd(ph, cp, pp);
+    }
+    if (live) partial[(size_t)blockIdx.y * ntar + k] = make_float4(ax - cx, ay - cy, az - cz, ph - cp);
+}
+
+// Sum the splits in FP64 and remove the target's own -m/eps term.
+__global__ void k_direct_reduce(const float4 *__restrict__ pos4, const uint32_t *__restrict__ targets,
+                                int ntar, int nsplit, float eps2, const float4 *__restrict__ partial,
+                                float4 *out, const unsigned *__restrict__ gate) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ntar || (gate && *gate == 0u)) return;
+    double ax = 0, ay = 0, az = 0, ph = 0;
+    for (int y = 0; y < nsplit; y++) {
+        const float4 p = partial[(size_t)y * ntar + k];
+        ax += p.x; ay += p.y; az += p.z; ph += p.w;
+    }
+    ph += (double)pos4[targets[k]].w * (double)rsqrtf(eps2);
+    out[k] = make_float4((float)ax, (float)ay, (float)az, (float)ph);
+}
+
+cudaError_t launch_direct(Ctx &c, const uint32_t *targets, int ntar, float eps, float4 *partial,
+                          int nsplit, float4 *out, const unsigned *gate) {
+    const int n = (int)c.n;
+    const int chunk = ((n + nsplit - 1) / nsplit + DS_TILE - 1) / DS_TILE * DS_TILE;
+    dim3 grid((ntar + DS_THREADS - 1) / DS_THREADS, nsplit);
+    k_direct_partial<<<grid, DS_THREADS, 0, c.stream>>>(c.pos4, n, targets, ntar, eps * eps, chunk, partial, gate);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_direct_reduce<<<(ntar + 255) / 256, 256, 0, c.stream>>>(c.pos4, targets, ntar, nsplit, eps * eps,
+                                                              partial, out, gate);
+    return cudaGetLastError();
+}
+
+// Judge: relative errors |a - a_direct| / |a_direct| at the targets, their
+// 99th percentile (linear interpolation between order statistics, as numpy's
+// default), and the fallback flag p99 > budget.  One block of 1024 threads,
+// bitonic sort of up to 4096 values in shared memory.  Skipped by the gate,
+// it leaves the last judgement (p99 and flag) in place.
+__global__ void __launch_bounds__(1024)
+k_judge_p99(const float4 *__restrict__ acc4, const uint32_t *__restrict__ targets, int ntar,
+            const float4 *__restrict__ direct, float budget, DevState *st, const unsigned *__restrict__ gate) {
+    if (gate && *gate == 0u) return;
+    __shared__ float v[JUDGE_MAX];
+    for (int i = threadIdx.x; i < JUDGE_MAX; i += blockDim.x) {
+        float e = INFINITY;
+        if (i < ntar) {
+            const float4 a = acc4[targets[i]], d = direct[i];
+            const float ex = a.x - d.x, ey = a.y - d.y, ez = a.z - d.z;
+            const float dn = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+            e = dn > 0.f ? sqrtf(ex * ex + ey * ey + ez * ez) / dn : 0.f;
+        }
+        v[i] = e;
+    }
+    __syncthreads();
+    for (int k = 2; k <= JUDGE_MAX; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < JUDGE_MAX; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const float a = v[i], b = v[l];
+                    if ((a > b) == up) { v[i] = b; v[l] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {
+        const float pos = 0.99f * (float)(ntar - 1);
+        const int i0 = (int)pos;
+        const int i1 = min(i0 + 1, ntar - 1);
+        const float p99 = v[i0] + (pos - (float)i0) * (v[i1] - v[i0]);
+        st->judge_p99 = p99;
+        st->fallback = p99 > budget ? 1u : 0u;
+    }
+}
+
+cudaError_t launch_judge(Ctx &c, const uint32_t *targets, int ntar, const float4 *direct, float budget,
+                         const unsigned *gate) {
+    k_judge_p99<<<1, 1024, 0, c.stream>>>(c.acc4, targets, ntar, direct, budget, c.st, gate);
+    return cudaGetLastError();
+}
+
+}  // namespace bonsai

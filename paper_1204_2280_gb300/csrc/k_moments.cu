@@ -189,17 +189,18 @@ cudaError_t launch_multipoles(Ctx &c) {
 // test[c] = (com, l/theta + delta), l = S / 2^level: the opening radius of
 // the Barnes (1994) criterion as read here.
 __global__ void k_open_radius(const DevState *__restrict__ st, const float4 *__restrict__ mono,
-                              const float2 *__restrict__ delta, float inv_theta, float4 *test) {
+                              const float2 *__restrict__ delta, float inv_theta, float4 *test,
+                              const unsigned *__restrict__ gate) {
     unsigned c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= st->ncells) return;
+    if (c >= st->ncells || (gate && *gate == 0u)) return;
     float4 m = mono[c];
     float2 dl = delta[c];
     test[c] = make_float4(m.x, m.y, m.z, fmaf(dl.y, inv_theta, dl.x));
 }
 
-cudaError_t launch_open_radius(Ctx &c, float theta) {
+cudaError_t launch_open_radius(Ctx &c, float theta, const unsigned *gate) {
     unsigned grid = (unsigned)((c.ccap + 255) / 256);
-    k_open_radius<<<grid, 256, 0, c.stream>>>(c.st, c.mono, c.delta, 1.0f / theta, c.test);
+    k_open_radius<<<grid, 256, 0, c.stream>>>(c.st, c.mono, c.delta, 1.0f / theta, c.test, gate);
     return cudaGetLastError();
 }
 

@@ -178,22 +178,33 @@ __device__ __forceinline__ unsigned lanemask_lt_w() {
     return m;
 }
 
-// BPL = 1 walks the groups of <= 32 bodies, BPL = 2 those of 33..64.
-template <int BPL>
+// Level bins of accepted cells for the learned correction's features.
+__device__ __forceinline__ int level_bin(int lvl) { return lvl <= 3 ? 0 : lvl <= 6 ? 1 : lvl <= 9 ? 2 : 3; }
+
+// BPL = 1 walks the groups of <= 32 bodies, BPL = 2 those of 33..64.  FEAT
+// also writes per body (12 floats) the walk quantities the learned far-field
+// correction uses: log(1 + accepted cells) in four level bins, log(1 +
+// body-body interactions), log(n_G / (extent^3 + eps^3)), log((diagonal +
+// eps)/eps), the body's offset from the centre of its group's box (3),
+// log(n_G) and the box diagonal.
+template <int BPL, bool FEAT>
 __global__ void __launch_bounds__(256)
 k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__ groups,
        const float4 *__restrict__ pos4, const float4 *__restrict__ test,
        const uint2 *__restrict__ link, const float4 *__restrict__ mono,
        const float4 *__restrict__ quadA, const float2 *__restrict__ quadB,
        const uint8_t *__restrict__ sysid, float eps, int stack_cap, long long max_rounds,
-       float4 *acc4, uint2 *counts) {
+       float4 *acc4, uint2 *counts, const uint8_t *__restrict__ cell_level, float *feat,
+       const unsigned *__restrict__ gate) {
     extern __shared__ float4 smem4[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const size_t warp_bytes = sizeof(WarpRings) + (size_t)stack_cap * sizeof(unsigned);
     char *wbase = (char *)smem4 + warp * warp_bytes;
     WarpRings &R = *reinterpret_cast<WarpRings *>(wbase);
     unsigned *stk = reinterpret_cast<unsigned *>(wbase + sizeof(WarpRings));
-    const unsigned ngroups = (stc->status & ST_TIMEOUT) ? 0u : stc->ngroups;
+    // Nothing to do after a timed-out sort, or when a gate flag (the learned
+    // path's fallback decision) is clear.
+    const unsigned ngroups = ((stc->status & ST_TIMEOUT) || (gate && *gate == 0u)) ? 0u : stc->ngroups;
     const float eps2 = eps * eps;
     const unsigned lt = lanemask_lt_w();
     unsigned *queue = BPL == 1 ? &st->walk_next : &st->walk_next2;
@@ -244,6 +255,7 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
         if (lane == 0) stk[0] = (unsigned)sysid[gb] << 3;
         int pc_head = 0, pc_n = 0, pp_head = 0, pp_n = 0;
         unsigned npc = 0, npp = 0;
+        unsigned nbin[4] = {0u, 0u, 0u, 0u};
         bool overflow = false, timeout = false;
         long long rounds = 0;
         __syncwarp();
@@ -301,6 +313,11 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
             }
             pc_n += __popc(am);
             npc += __popc(am);
+            if (FEAT) {
+                const int bin = acc ? level_bin(__ldg(cell_level + cell)) : -1;
+#pragma unroll
+                for (int k = 0; k < 4; k++) nbin[k] += __popc(__ballot_sync(0xffffffffu, bin == k));
+            }
             // Opened internal cells -> push child ranges.
             const unsigned im = __ballot_sync(0xffffffffu, open && !isleaf);
             const int np = __popc(im);
@@ -371,6 +388,23 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
                 ph += me[b].w * rsqrtf(eps2);    // remove the self term -m/eps
                 acc4[bi[b]] = make_float4(ax, ay, az, ph);
                 counts[bi[b]] = make_uint2(npc, npp - 1u);
+                if (FEAT) {
+                    const float ex = bx1 - bx0, ey = by1 - by0, ez = bz1 - bz0;
+                    const float ext = fmaxf(ex, fmaxf(ey, ez));
+                    const float diag = sqrtf(ex * ex + ey * ey + ez * ez);
+                    const float e3 = eps * eps * eps;
+                    float *f = feat + FEAT_STRIDE * (size_t)bi[b];
+                    f[0] = log1pf((float)nbin[0]); f[1] = log1pf((float)nbin[1]);
+                    f[2] = log1pf((float)nbin[2]); f[3] = log1pf((float)nbin[3]);
+                    f[4] = log1pf((float)(npp - 1u));
+                    f[5] = logf((float)ng / (ext * ext * ext + e3));
+                    f[6] = logf((diag + eps) / eps);
+                    f[7] = me[b].x - 0.5f * (bx0 + bx1);
+                    f[8] = me[b].y - 0.5f * (by0 + by1);
+                    f[9] = me[b].z - 0.5f * (bz0 + bz1);
+                    f[10] = logf((float)ng);
+                    f[11] = diag;
+                }
             }
         }
         if (lane == 0) {
@@ -389,33 +423,33 @@ size_t walk_smem_bytes(int warps, int stack_cap) {
 
 // Function attribute and occupancy are set up once per shape, before any
 // stream capture of a step (the first step always runs eagerly).
-template <int BPL>
-static cudaError_t launch_walk_t(Ctx &c, float eps) {
+template <int BPL, bool FEAT>
+static cudaError_t launch_walk_t(Ctx &c, float eps, const unsigned *gate) {
     const int warps = c.walk_warps;
     const size_t smem = walk_smem_bytes(warps, c.list_capacity);
     static size_t attr_smem = 0, occ_smem = 0;
     static int occ_warps = 0, occ_per_sm = 0;
     if (smem > attr_smem) {
-        cudaError_t e = cudaFuncSetAttribute(k_walk<BPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_walk<BPL, FEAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_smem = smem;
     }
     if (occ_warps != warps || occ_smem != smem) {
         int per = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk<BPL>, warps * 32, smem);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk<BPL, FEAT>, warps * 32, smem);
         if (e != cudaSuccess) return e;
         occ_warps = warps; occ_smem = smem; occ_per_sm = per < 1 ? 1 : per;
     }
-    k_walk<BPL><<<c.num_sms * occ_per_sm, warps * 32, smem, c.stream>>>(
+    k_walk<BPL, FEAT><<<c.num_sms * occ_per_sm, warps * 32, smem, c.stream>>>(
         c.st, c.st, c.groups, c.pos4, c.test, c.cell_link, c.mono, c.quadA, c.quadB, c.sysid, eps,
-        c.list_capacity, c.max_spin, c.acc4, c.counts);
+        c.list_capacity, c.max_spin, c.acc4, c.counts, c.cell_level, c.feat, gate);
     return cudaGetLastError();
 }
 
-cudaError_t launch_walk(Ctx &c, float eps) {
-    cudaError_t e = launch_walk_t<1>(c, eps);
+cudaError_t launch_walk(Ctx &c, float eps, bool features, const unsigned *gate) {
+    cudaError_t e = features ? launch_walk_t<1, true>(c, eps, gate) : launch_walk_t<1, false>(c, eps, gate);
     if (e != cudaSuccess || c.ncrit <= 32) return e;
-    return launch_walk_t<2>(c, eps);
+    return features ? launch_walk_t<2, true>(c, eps, gate) : launch_walk_t<2, false>(c, eps, gate);
 }
 
 }  // namespace bonsai
