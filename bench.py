@@ -42,7 +42,7 @@ def kernels_per_step(ncrit):
     """reset, kick+drift, keys, 8 sort passes, reorder, 4 build, multipoles,
     open radius, walk (two instantiations when groups may exceed 32), kick."""
     return 20 + (1 if ncrit > 32 else 0)
-WALK_TRAFFIC_PER_LAUNCH = 86.2e6   # dram bytes of the walk stage (both launches), profiles/k_walk_plummer_n2e20.md
+WALK_TRAFFIC_PER_LAUNCH = None     # dram bytes of the walk stage (both launches) from an ncu capture of the current kernel
 
 
 def parse():
@@ -69,6 +69,8 @@ def parse():
     p.add_argument("--learned-n", type=int, default=1 << 22)
     p.add_argument("--learned-plummer", type=int, default=8, help="Plummer training snapshots")
     p.add_argument("--learned-merger", type=int, default=8, help="merger training snapshots")
+    p.add_argument("--sweep", action="store_true",
+                   help="per-stage scaling sweep instead of the bench line: one JSON line per (N, theta)")
     return p.parse_args()
 
 
@@ -377,6 +379,103 @@ def run_learned(a, dev, stream):
     }
 
 
+# Algorithmic bytes per body of the memory-bound stages (what the stage must
+# read and write once), and per cell / group where the stage writes cells.
+STAGE_BYTES = {
+    "kick_drift_domain": "pos, vel, acc, id read (52 B); pos, vel, id written (36 B)",
+    "keys": "pos read (16 B); key written (8 B)",
+    "sort": "8 passes: pass 0 reads keys (8 B), later passes keys + values (12 B); each writes 12 B",
+    "reorder": "perm, pos, vel, id read (40 B); pos, vel, id written (36 B)",
+    "build": "sorted keys read (8 B/body); 16 B per cell and 8 B per group written",
+    "multipoles": "pos read (16 B/body); 44 B per cell written (com, M, Q, r_open)",
+    "kick": "vel, acc read (32 B); vel written (16 B)",
+}
+
+
+def stage_bytes(n, ncells, ngroups):
+    return {"kick_drift_domain": 88 * n, "keys": 24 * n, "sort": (20 + 7 * 24) * n,
+            "reorder": 76 * n, "build": 8 * n + 16 * ncells + 8 * ngroups,
+            "multipoles": 16 * n + 44 * ncells, "kick": 48 * n}
+
+
+def run_sweep(a, dev, stream):
+    """Scaling sweep: Plummer spheres N = 2^15 .. 2^20 at theta = 0.75
+    (interactions per body vs N), then N = 2^22 (seed 2) and 2^24 (seed 3)
+    at theta in {0.5, 0.75, 1.0}; eps = 0.002, 5 KDK steps of dt = 1/256
+    after 2 untimed ones.  Per stage: device ms per step and algorithmic
+    GB/s against the measured copy bandwidth; walk FP32 rate against the
+    FP32 peak; FP64 energy drift over the timed steps; p99 force error of the
+    first evaluation at 4096 stratified bodies (the library's direct sum)."""
+    import numpy as np
+    import torch
+    import paper_1204_2280_gb300 as B
+    from paper_1204_2280_gb300 import workloads as W
+    import ctypes as C
+    hbm = measured_hbm_gbs()
+    eps, dt, steps = 0.002, 1.0 / 256, 5
+    cases = [(1 << k, 1, (0.75,)) for k in range(15, 21)]
+    cases += [(1 << 22, 2, (0.5, 0.75, 1.0)), (1 << 24, 3, (0.5, 0.75, 1.0))]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    tot = (C.c_ulonglong * 2)()
+    for n, seed, thetas in cases:
+        b = W.plummer(n, seed)
+        for theta in thetas:
+            bz = B.Bonsai(B.Config(nleaf=16, ncrit=64, walk_warps=8), stream=stream)
+            bz.set_bodies(torch.from_numpy(b.pos).to(dev), torch.from_numpy(b.mass).to(dev),
+                          torch.from_numpy(b.vel).to(dev))
+            bz.build().multipoles().forces(theta, eps)
+            p99 = B.bonsai_judge(bz.ctx, eps)
+            d0 = B.bonsai_diagnostics(bz.ctx)
+            for _ in range(2):
+                bz.step(dt)
+            bz.sync()
+            ms, st, npc, npp = [], [], 0, 0
+            for _ in range(steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                bz.step(dt)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                st.append(B.bonsai_get_stage_times(bz.ctx))
+                B._check(bz.ctx, B.lib().bonsai_get_counts(bz.ctx, None, None, tot))
+                npc += int(tot[0]); npp += int(tot[1])
+            d1 = B.bonsai_diagnostics(bz.ctx)
+            _, ncells, ngroups = B.bonsai_get_sizes(bz.ctx)
+            bz.sync()
+            bz.close()
+            stage = dict(zip(B.STAGES, (np.array(st).sum(0) / steps).tolist()))
+            sb = stage_bytes(n, ncells, ngroups)
+            walk_s = stage["walk"] / 1e3
+            tflops = (FLOP_PC * npc + FLOP_PP * npp) / steps / walk_s / 1e12
+            t = sum(ms) / steps
+            print(json.dumps({
+                "mode": "sweep", "n": n, "seed": seed, "theta": theta, "eps": eps, "dt": dt,
+                "steps": steps, "ms_per_step": t, "particles_per_s": n / (t / 1e3),
+                "stage_ms": stage,
+                "stage_gbs": {k: sb[k] / (stage[k] / 1e3) / 1e9 for k in sb if stage[k] > 0},
+                "stage_hbm_frac": {k: sb[k] / (stage[k] / 1e3) / 1e9 / hbm for k in sb if stage[k] > 0},
+                "sort_reorder_build_hbm_frac": sum(sb[k] for k in ("sort", "reorder", "build")) /
+                    (sum(stage[k] for k in ("sort", "reorder", "build")) / 1e3) / 1e9 / hbm,
+                "walk_tflops": tflops, "walk_fp32_frac": tflops / FP32_PEAK_TFLOPS,
+                "interactions_per_body": {"pc": npc / (steps * n), "pp": npp / (steps * n)},
+                "interactions_per_s": (npc + npp) / steps / walk_s,
+                "ncells": ncells, "ngroups": ngroups,
+                "p99_acc_err_t0": p99,
+                "energy_drift": (d1[2] - d0[2]) / abs(d0[2]),
+                "hbm_peak_gbs": hbm, "fp32_peak_tflops": FP32_PEAK_TFLOPS}), flush=True)
+
+
+def measured_hbm_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
+
+
 def run_ours(a, rank, world, local_rank):
     import numpy as np
     import torch
@@ -503,6 +602,13 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if a.impl == "reference":
         run_reference(a, rank, world)
+        return
+    if a.sweep:
+        import torch
+        torch.cuda.set_device(local_rank)
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        run_sweep(a, torch.device("cuda", local_rank), stream)
         return
     if world > 1:
         import torch

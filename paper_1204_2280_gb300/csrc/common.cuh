@@ -26,8 +26,11 @@ constexpr int GROUP_ROW = MAX_LEVEL + 1;
 constexpr uint32_t LEAF_BIT = 0x80000000u;
 constexpr int FP64_LEVELS = 4;                   // levels 0..3 combine in FP64
 
-constexpr int SORT_THREADS = 256;
-constexpr int SORT_ITEMS = 16;
+#ifndef SORT_THREADS_CFG
+#define SORT_THREADS_CFG 256
+#endif
+constexpr int SORT_THREADS = SORT_THREADS_CFG;          // >= 256: thread d owns digit d
+constexpr int SORT_ITEMS = 4096 / SORT_THREADS;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;   // 4096 keys per tile
 constexpr int SORT_PASSES = 8;                         // 8-bit digits, 63-bit keys
 constexpr int MAX_SYSTEMS = 256;                       // ensemble: one more pass on the system id

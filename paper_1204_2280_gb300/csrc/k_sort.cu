@@ -6,8 +6,9 @@
 // the digit histograms of all passes come from the key kernel, so a pass
 // reads every key/value once and writes it once (24 B per body per pass):
 //   1. a tile of 4096 keys is taken in ticket order (atomic counter), loaded
-//      warp-striped and ranked per warp with match_any (stable: item order,
-//      then lane order, then warp order);
+//      warp-striped and ranked per warp: peers with equal digits by ballots,
+//      counts by shared-memory atomics (stable: item order, then lane order,
+//      then warp order);
 //   2. per digit the tile count is published and the prefix over earlier
 //      tiles found by decoupled look-back (bounded spin; on timeout a status
 //      bit is set and the kernel continues, so it always terminates);
@@ -16,6 +17,10 @@
 #include "common.cuh"
 
 namespace bonsai {
+
+#ifndef SORT_MIN_BLOCKS
+#define SORT_MIN_BLOCKS 2         // resident onesweep blocks per SM the register budget allows
+#endif
 
 constexpr unsigned FLAG_AGG = 1u << 30;
 constexpr unsigned FLAG_INC = 2u << 30;
@@ -36,8 +41,8 @@ __device__ __forceinline__ void st_volatile(unsigned *p, unsigned v) {
     asm volatile("st.volatile.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Exclusive scan over the 256 threads of a block (one value per thread).
-__device__ __forceinline__ unsigned block_excl_scan256(unsigned v, unsigned *s_warp) {
+// Exclusive scan over the threads of a block (one value per thread).
+__device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned *s_warp) {
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned x = v;
 #pragma unroll
@@ -54,7 +59,7 @@ __device__ __forceinline__ unsigned block_excl_scan256(unsigned v, unsigned *s_w
     return off + x - v;
 }
 
-__global__ void __launch_bounds__(SORT_THREADS, 2)
+__global__ void __launch_bounds__(SORT_THREADS, SORT_MIN_BLOCKS)
 k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restrict__ vin,
            unsigned long long *__restrict__ kout, uint32_t *__restrict__ vout, int n, int shift,
            const unsigned *__restrict__ ghist, unsigned *status, unsigned *status_next,
@@ -92,58 +97,76 @@ k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restric
 #pragma unroll
     for (int it = 0; it < SORT_ITEMS; it++)
         dg[it] = dsrc ? (wbase + it * 32 + lane < n ? dsrc[v[it]] : 0) : (unsigned char)((k[it] >> shift) & 0xffu);
+    // Rank within the warp: peers with the same digit by 8 ballots; the
+    // lowest peer adds the peer count to the warp's digit counter with a
+    // shared-memory atomic that returns the count before it.  A warp's
+    // atomics execute in program order, so item order (then lane order) is
+    // kept: stable.  All atomics are issued before the first result is used.
     const unsigned lt = lanemask_lt();
+    unsigned pe[SORT_ITEMS], old[SORT_ITEMS];
 #pragma unroll
     for (int it = 0; it < SORT_ITEMS; it++) {
-        int idx = wbase + it * 32 + lane;
-        unsigned d = idx < n ? (unsigned)dg[it] : 256u;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        unsigned below = __popc(peers & lt);
-        unsigned basec = d < 256u ? s_whist[warp][d] : 0u;
-        rk[it] = (unsigned short)(basec + below);
-        __syncwarp();
-        if (d < 256u && below == 0u) s_whist[warp][d] = basec + __popc(peers);
-        __syncwarp();
+        const int idx = wbase + it * 32 + lane;
+        const unsigned d = idx < n ? (unsigned)dg[it] : 256u;
+        unsigned peers = __ballot_sync(0xffffffffu, d < 256u);
+        if (d >= 256u) peers = ~peers;
+#pragma unroll
+        for (int bit = 0; bit < 8; bit++) {
+            const bool on = (d >> bit) & 1u;
+            const unsigned bm = __ballot_sync(0xffffffffu, on);
+            peers &= on ? bm : ~bm;
+        }
+        pe[it] = peers;
+        old[it] = (d < 256u && (peers & lt) == 0u) ? atomicAdd(&s_whist[warp][d], (unsigned)__popc(peers)) : 0u;
+    }
+#pragma unroll
+    for (int it = 0; it < SORT_ITEMS; it++) {
+        const unsigned base = __shfl_sync(0xffffffffu, old[it], __ffs(pe[it]) - 1);
+        rk[it] = (unsigned short)(base + __popc(pe[it] & lt));
     }
     __syncthreads();
 
-    // Thread d owns digit d: exclusive prefix over warps, tile count.
+    // Thread d < 256 owns digit d: exclusive prefix over warps, tile count.
     const unsigned d = (unsigned)tid;
+    const bool owner = tid < 256;
     unsigned run = 0;
+    if (owner) {
 #pragma unroll
-    for (int w = 0; w < SORT_THREADS / 32; w++) {
-        unsigned c = s_whist[w][d];
-        s_whist[w][d] = run;
-        run += c;
+        for (int w = 0; w < SORT_THREADS / 32; w++) {
+            unsigned c = s_whist[w][d];
+            s_whist[w][d] = run;
+            run += c;
+        }
     }
     const unsigned tcount = run;
-    unsigned dstart = block_excl_scan256(tcount, s_warp);
-    unsigned gbase = block_excl_scan256(ghist[d], s_warp);
-    s_dstart[d] = dstart;
-
-    // Decoupled look-back over earlier tiles for digit d.
-    unsigned *my = status + (size_t)tile * 256 + d;
-    unsigned prefix = 0;
-    if (tile == 0) {
-        st_volatile(my, FLAG_INC | tcount);
-    } else {
-        st_volatile(my, FLAG_AGG | tcount);
-        int j = tile - 1;
-        long long spins = 0;
-        while (j >= 0) {
-            unsigned s = ld_volatile(status + (size_t)j * 256 + d);
-            unsigned f = s & ~VAL_MASK;
-            if (f == 0u) {
-                if (++spins > max_spin) { atomicOr(&st->status, ST_TIMEOUT); break; }
-                continue;
+    unsigned dstart = block_excl_scan(tcount, s_warp);
+    unsigned gbase = block_excl_scan(owner ? ghist[d] : 0u, s_warp);
+    if (owner) {
+        s_dstart[d] = dstart;
+        // Decoupled look-back over earlier tiles for digit d.
+        unsigned *my = status + (size_t)tile * 256 + d;
+        unsigned prefix = 0;
+        if (tile == 0) {
+            st_volatile(my, FLAG_INC | tcount);
+        } else {
+            st_volatile(my, FLAG_AGG | tcount);
+            int j = tile - 1;
+            long long spins = 0;
+            while (j >= 0) {
+                unsigned s = ld_volatile(status + (size_t)j * 256 + d);
+                unsigned f = s & ~VAL_MASK;
+                if (f == 0u) {
+                    if (++spins > max_spin) { atomicOr(&st->status, ST_TIMEOUT); break; }
+                    continue;
+                }
+                prefix += s & VAL_MASK;
+                if (f == FLAG_INC) break;
+                j--;
             }
-            prefix += s & VAL_MASK;
-            if (f == FLAG_INC) break;
-            j--;
+            st_volatile(my, FLAG_INC | ((prefix + tcount) & VAL_MASK));
         }
-        st_volatile(my, FLAG_INC | ((prefix + tcount) & VAL_MASK));
+        s_goff[d] = gbase + prefix;
     }
-    s_goff[d] = gbase + prefix;
     __syncthreads();
 
     // Reorder the tile by digit in shared memory.

@@ -78,15 +78,21 @@ struct BodyCells {
 // (-1 where j+w is past the end).
 struct BuildShared {
     unsigned long long *k;
-    int *D, *DG;
+    int *D, *DG, *TD, *TG;   // TD/TG: maxima of D/DG over [j, j + HD/HG)
     uint8_t *sy;
-    int W, base;
+    int W, base, nleaf, ncrit, HD, HG;
     __device__ unsigned long long key(int j) const { return k[j - base + W]; }
     __device__ uint8_t sys(int j) const { return sy[j - base + W]; }
     __device__ int cpl(int a, int b) const { return body_cpl(key(a), key(b), sys(a), sys(b)); }
     __device__ int d(int j) const { return D[j - base + W]; }
     __device__ int dg(int j) const { return DG[j - base + W]; }
+    // max D(j) over j in [t - nleaf, t] and max DG(j) over [t - ncrit, t]
+    // (two overlapping power-of-two windows each)
+    __device__ int dmax(int t) const { return max(TD[t - nleaf - base + W], TD[t - HD + 1 - base + W]); }
+    __device__ int dgmax(int t) const { return max(TG[t - ncrit - base + W], TG[t - HG + 1 - base + W]); }
 };
+
+__device__ __forceinline__ int pow2_floor(int x) { return 1 << (31 - __clz(x)); }
 
 // Keys and system ids of [base-W, base+B+W); D and DG of [base-W, base+B).
 // Bodies of different systems share no level (cpl -1), so each system gets
@@ -97,10 +103,17 @@ __device__ BuildShared load_build_shared(void *smem, const unsigned long long *_
     BuildShared b;
     b.W = max(nleaf, ncrit);
     b.base = base;
+    b.nleaf = nleaf;
+    b.ncrit = ncrit;
+    b.HD = pow2_floor(nleaf + 1);
+    b.HG = pow2_floor(ncrit + 1);
+    const int m = BUILD_THREADS + b.W;
     b.k = (unsigned long long *)smem;
     b.D = (int *)(b.k + BUILD_THREADS + 2 * b.W);
-    b.DG = b.D + BUILD_THREADS + b.W;
-    b.sy = (uint8_t *)(b.DG + BUILD_THREADS + b.W);
+    b.DG = b.D + m;
+    b.TD = b.DG + m;
+    b.TG = b.TD + m;
+    b.sy = (uint8_t *)(b.TG + m);
     for (int i = threadIdx.x; i < BUILD_THREADS + 2 * b.W; i += blockDim.x) {
         int j = base - b.W + i;
         const bool in = j >= 0 && j < n;
@@ -108,18 +121,80 @@ __device__ BuildShared load_build_shared(void *smem, const unsigned long long *_
         b.sy[i] = in ? sysid[j] : 0;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < BUILD_THREADS + b.W; i += blockDim.x) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
         int j = base - b.W + i;
-        b.D[i] = (j >= 0 && j + nleaf < n) ? b.cpl(j, j + nleaf) : -1;
-        b.DG[i] = (j >= 0 && j + ncrit < n) ? b.cpl(j, j + ncrit) : -1;
+        b.D[i] = b.TD[i] = (j >= 0 && j + nleaf < n) ? b.cpl(j, j + nleaf) : -1;
+        b.DG[i] = b.TG[i] = (j >= 0 && j + ncrit < n) ? b.cpl(j, j + ncrit) : -1;
     }
     __syncthreads();
+    // Doubling: after the step with width h, T[i] = max over [i, i + 2h).
+    // Entries whose window runs past the array keep a truncated maximum;
+    // dmax/dgmax never read them.
+    for (int h = 1; 2 * h <= b.HG; h <<= 1) {
+        int nd[2], ng[2];
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            const int i = threadIdx.x + r * BUILD_THREADS;
+            nd[r] = ng[r] = 0;
+            if (i < m) {
+                nd[r] = (2 * h <= b.HD && i + h < m) ? max(b.TD[i], b.TD[i + h]) : b.TD[i];
+                ng[r] = i + h < m ? max(b.TG[i], b.TG[i + h]) : b.TG[i];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            const int i = threadIdx.x + r * BUILD_THREADS;
+            if (i < m) { b.TD[i] = nd[r]; b.TG[i] = ng[r]; }
+        }
+        __syncthreads();
+    }
+    for (int h = b.HG; 2 * h <= b.HD; h <<= 1) {      // nleaf > ncrit: finish TD
+        int nd[2];
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            const int i = threadIdx.x + r * BUILD_THREADS;
+            nd[r] = (i < m && i + h < m) ? max(b.TD[i], b.TD[i + h]) : (i < m ? b.TD[i] : 0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            const int i = threadIdx.x + r * BUILD_THREADS;
+            if (i < m) b.TD[i] = nd[r];
+        }
+        __syncthreads();
+    }
     return b;
+}
+
+// run_end for a body t of the block, from the keys held in shared memory
+// (indices below lim = min(send, base + BUILD_THREADS + W)); falls back to
+// the global search only when the run reaches the end of that window.
+// Leaf and group runs (<= nleaf, <= ncrit bodies) always end inside it.
+__device__ int run_end_win(const BuildShared &b, const unsigned long long *__restrict__ sk, int send, int t,
+                           int level) {
+    if (level == 0) return send;
+    const int sh = 3 * (MAX_LEVEL - level);
+    const unsigned long long pre = b.key(t) >> sh;
+    const int lim = min(send, b.base + BUILD_THREADS + b.W);
+    const int last = lim - 1;
+    if ((b.key(last) >> sh) == pre) return lim == send ? send : run_end(sk, send, last, level);
+    int lo = t, hi = last, step = 1;          // key(lo) in the run, key(hi) not
+    while (t + step < hi) {
+        if ((b.key(t + step) >> sh) != pre) { hi = t + step; break; }
+        lo = t + step;
+        step <<= 1;
+    }
+    while (hi - lo > 1) {
+        const int mid = lo + ((hi - lo) >> 1);
+        if ((b.key(mid) >> sh) == pre) lo = mid; else hi = mid;
+    }
+    return hi;
 }
 
 size_t build_smem_bytes(int nleaf, int ncrit) {
     int W = nleaf > ncrit ? nleaf : ncrit;
-    return (size_t)(BUILD_THREADS + 2 * W) * 8 + 2 * (size_t)(BUILD_THREADS + W) * 4 +
+    return (size_t)(BUILD_THREADS + 2 * W) * 8 + 4 * (size_t)(BUILD_THREADS + W) * 4 +
            (size_t)(BUILD_THREADS + 2 * W);
 }
 
@@ -131,26 +206,17 @@ __device__ BodyCells analyse_body(const BuildShared &b, int t, int n, int nleaf,
     if (t >= n) return r;
     int l0 = (t == 0) ? 0 : b.cpl(t - 1, t) + 1;
     if (l0 > MAX_LEVEL) return r;
-    if (l0 > 0) {
-        int e = -1;
-        for (int j = max(0, t - nleaf); j <= t; j++) e = max(e, b.d(j));
-        if (e < l0 - 1) return r;
-    }
+    if (l0 > 0 && b.dmax(t) < l0 - 1) return r;
     r.has = true;
     r.lo = l0;
     r.hi = max(l0, min(b.d(t) + 1, MAX_LEVEL));
     int lg = max(l0, b.dg(t) + 1);
     r.lg = lg;
     if (lg <= r.hi) {
-        bool starts = (lg > l0) || l0 == 0;
-        if (!starts) {
-            int e = -1;
-            for (int j = max(0, t - ncrit); j <= t; j++) e = max(e, b.dg(j));
-            starts = e >= l0 - 1;
-        }
+        const bool starts = (lg > l0) || l0 == 0 || b.dgmax(t) >= l0 - 1;
         r.ngrp = starts ? 1 : 0;
     } else {
-        int cnt = run_end(sk, send, t, r.hi) - t;
+        int cnt = run_end_win(b, sk, send, t, r.hi) - t;
         r.ngrp = (cnt + ncrit - 1) / ncrit;
     }
     return r;
@@ -165,6 +231,14 @@ __device__ __forceinline__ bool has_level(const BodyCells &bc, int r) {
     return bc.has && bc.lo <= r && r <= bc.hi;
 }
 
+// The levels on which any body of the warp starts a cell: [rlo, rhi]
+// (empty, rlo > rhi, when none does).  Warp-uniform.
+__device__ __forceinline__ void warp_level_range(const BodyCells &bc, int &rlo, int &rhi) {
+    rlo = (int)__reduce_min_sync(0xffffffffu, bc.has ? (unsigned)bc.lo : (unsigned)(MAX_LEVEL + 1));
+    rhi = (int)__reduce_max_sync(0xffffffffu, bc.has ? (unsigned)bc.hi : 0u);
+    if (rlo > MAX_LEVEL) rhi = -1;
+}
+
 // Pass 1: per block, the number of cells of each level and of groups.
 __global__ void __launch_bounds__(BUILD_THREADS)
 k_build_count(const unsigned long long *__restrict__ sk, const uint8_t *__restrict__ sysid, int n,
@@ -176,8 +250,10 @@ k_build_count(const unsigned long long *__restrict__ sk, const uint8_t *__restri
     BuildShared b = load_build_shared(smem_u64, sk, sysid, n, base, nleaf, ncrit);
     const int t = base + tid;
     BodyCells bc = analyse_body(b, t, n, nleaf, ncrit, sk, system_end(st, sysid, t, n));
+    int rlo, rhi;
+    warp_level_range(bc, rlo, rhi);
     for (int r = 0; r <= MAX_LEVEL; r++) {
-        unsigned m = __ballot_sync(0xffffffffu, has_level(bc, r));
+        unsigned m = (r >= rlo && r <= rhi) ? __ballot_sync(0xffffffffu, has_level(bc, r)) : 0u;
         if (lane == 0) s_wc[r][warp] = __popc(m);
     }
     int g = bc.ngrp;
@@ -248,20 +324,29 @@ k_build_write(const unsigned long long *__restrict__ sk, const uint8_t *__restri
     __shared__ int s_ok;
     const int base = blockIdx.x * BUILD_THREADS, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (st->status & ST_TIMEOUT) return;        // keys not sorted: skip the build
-    if (tid == 0) {
-        unsigned run = 0;
-        for (int r = 0; r <= MAX_LEVEL; r++) {
-            s_base[r] = run + blockcount[(size_t)r * nblocks + blockIdx.x];
-            if (blockIdx.x == 0) st->level_start[r] = run;
-            run += st->row_total[r];
+    if (warp == 0) {                             // level offsets: one lane per row
+        const bool lvl = lane <= MAX_LEVEL;
+        const unsigned tot = lane < NROWS ? st->row_total[lane] : 0u;
+        const unsigned bcnt = lane < NROWS ? blockcount[(size_t)lane * nblocks + blockIdx.x] : 0u;
+        unsigned x = lvl ? tot : 0u;             // inclusive scan of the level totals
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        s_base[GROUP_ROW] = blockcount[(size_t)GROUP_ROW * nblocks + blockIdx.x];
-        s_ok = (long long)run <= ccap;
-        if (blockIdx.x == 0) {
-            st->level_start[MAX_LEVEL + 1] = run;
-            st->ncells = run;
-            st->ngroups = st->row_total[GROUP_ROW];
-            if (!s_ok) atomicOr(&st->status, ST_CAPACITY);
+        const unsigned run = __shfl_sync(0xffffffffu, x, MAX_LEVEL);   // all cells
+        const unsigned excl = x - (lvl ? tot : 0u);
+        if (lvl) s_base[lane] = excl + bcnt;
+        if (lane == GROUP_ROW) s_base[GROUP_ROW] = bcnt;
+        if (lvl && blockIdx.x == 0) st->level_start[lane] = excl;
+        if (lane == 0) {
+            s_ok = (long long)run <= ccap;
+            if (blockIdx.x == 0) {
+                st->level_start[MAX_LEVEL + 1] = run;
+                st->ncells = run;
+                st->ngroups = st->row_total[GROUP_ROW];
+                if (!s_ok) atomicOr(&st->status, ST_CAPACITY);
+            }
         }
     }
     __syncthreads();
@@ -271,9 +356,11 @@ k_build_write(const unsigned long long *__restrict__ sk, const uint8_t *__restri
     const int send = system_end(st, sysid, t, n);
     BodyCells bc = analyse_body(b, t, n, nleaf, ncrit, sk, send);
     const unsigned lt = (1u << lane) - 1u;
+    int rlo, rhi;
+    warp_level_range(bc, rlo, rhi);
 
     for (int r = 0; r <= MAX_LEVEL; r++) {
-        unsigned m = __ballot_sync(0xffffffffu, has_level(bc, r));
+        unsigned m = (r >= rlo && r <= rhi) ? __ballot_sync(0xffffffffu, has_level(bc, r)) : 0u;
         if (lane == 0) s_wc[r][warp] = __popc(m);
     }
     int gx = bc.ngrp;                            // inclusive warp scan of group counts
@@ -297,8 +384,8 @@ k_build_write(const unsigned long long *__restrict__ sk, const uint8_t *__restri
     }
     __syncthreads();
 
-    unsigned bcur = __ballot_sync(0xffffffffu, has_level(bc, 0));
-    for (int r = 0; r <= MAX_LEVEL; r++) {
+    unsigned bcur = rlo <= rhi ? __ballot_sync(0xffffffffu, has_level(bc, rlo)) : 0u;
+    for (int r = rlo; r <= rhi; r++) {
         const unsigned bnext = r < MAX_LEVEL ? __ballot_sync(0xffffffffu, has_level(bc, r + 1)) : 0u;
         if (has_level(bc, r)) {
             const unsigned c = s_base[r] + s_wc[r][warp] + __popc(bcur & lt);
@@ -308,7 +395,7 @@ k_build_write(const unsigned long long *__restrict__ sk, const uint8_t *__restri
             cell_done[c] = 0u;
             if (r == 0) cell_parent[c] = 0xffffffffu;
             if (r == bc.hi) {
-                int cnt = run_end(sk, send, t, r) - t;
+                int cnt = run_end_win(b, sk, send, t, r) - t;
                 cell_body[c] = make_uint2((unsigned)t, (unsigned)cnt);
                 cell_link[c] = make_uint2((unsigned)t, (unsigned)cnt | LEAF_BIT);
             } else {
@@ -322,10 +409,10 @@ k_build_write(const unsigned long long *__restrict__ sk, const uint8_t *__restri
     if (bc.ngrp > 0) {
         unsigned g = s_base[GROUP_ROW] + s_wc[GROUP_ROW][warp] + (unsigned)gx;
         if (bc.lg <= bc.hi) {
-            int e = run_end(sk, send, t, bc.lg);
+            int e = run_end_win(b, sk, send, t, bc.lg);
             groups[g] = make_uint2((unsigned)t, (unsigned)(e - t));
         } else {
-            int e = run_end(sk, send, t, bc.hi);
+            int e = run_end_win(b, sk, send, t, bc.hi);
             for (int k = 0; k < bc.ngrp; k++) {
                 int b0 = t + k * ncrit;
                 groups[g + k] = make_uint2((unsigned)b0, (unsigned)min(ncrit, e - b0));

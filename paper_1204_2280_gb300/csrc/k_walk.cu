@@ -13,12 +13,14 @@
 //    memory; the bodies of opened leaves into a second ring; opened internal
 //    cells push their child range;
 //  * whenever a ring holds 32 sources the warp evaluates that tile: every
-//    lane streams the sources from shared memory (broadcast reads) with FP32
-//    FMAs.  Groups of <= 32 bodies: a group of n bodies uses s = next_pow2(n)
-//    body slots and the 32/s lanes sharing a body split the tile's sources
-//    (summed at the end), so small groups still keep all lanes busy.  Groups
-//    of 33..64 bodies run in a second instantiation with two bodies per lane
-//    that share every source read;
+//    lane streams the sources from shared memory (broadcast reads) two at a
+//    time through the packed FP32x2 instructions (add/mul/fma .f32x2, one
+//    issue slot for two operations).  Groups of <= 32 bodies: a group of n
+//    bodies uses s = max(2, next_pow2(n)) body slots and the 32/s lanes
+//    sharing a body split the tile's 16 source pairs (summed at the end), so
+//    small groups still keep all lanes busy.  Groups of 33..64 bodies run in a
+//    second instantiation with two bodies per lane that share every source
+//    read;
 //  * each tile is summed in plain FP32 and added to the body's accumulators
 //    with Kahan compensation (one compensated add per tile and component).
 // Body-cell (monopole + traceless quadrupole, softened):
@@ -30,18 +32,42 @@
 
 namespace bonsai {
 
-constexpr int RING = 64;
+constexpr int RING = 64;          // sources per ring
+constexpr int RPAIR = RING / 2;   // source pairs per ring
 #ifndef WALK_UNROLL
-#define WALK_UNROLL 4            // unroll depth of the tile loops
+#define WALK_UNROLL 4             // unroll depth of the tile loops
 #endif
 constexpr int kWalkUnroll = WALK_UNROLL;
 
+// Rings in source-pair layout: pair k holds sources 2k (low half) and 2k+1
+// (high half) of two components per float4, so one 16-byte shared load
+// yields two packed (even, odd) operand pairs for the FP32x2 instructions.
+// Quadrupoles are staged negated, which turns every subtraction of the
+// body-cell formula into an addition (negation is exact).
 struct WarpRings {
-    float4 mono[RING];   // com xyz, M
-    float4 qa[RING];     // Qxx Qyy Qzz Qxy
-    float2 qb[RING];     // Qxz Qyz
-    float4 pp[RING];     // x y z m
+    float4 c0[RPAIR];   // x x' y y'
+    float4 c1[RPAIR];   // z z' M M'
+    float4 c2[RPAIR];   // -Qxx -Qxx' -Qyy -Qyy'
+    float4 c3[RPAIR];   // -Qzz -Qzz' -Qxy -Qxy'
+    float4 c4[RPAIR];   // -Qxz -Qxz' -Qyz -Qyz'
+    float4 b0[RPAIR];   // body sources: x x' y y'
+    float4 b1[RPAIR];   //               z z' m m'
 };
+
+__device__ __forceinline__ void put_cell(WarpRings &R, int s, const float4 mo, const float4 qa, const float2 qb) {
+    const int k = s >> 1, h = s & 1;
+    float *c0 = reinterpret_cast<float *>(&R.c0[k]) + h, *c1 = reinterpret_cast<float *>(&R.c1[k]) + h;
+    float *c2 = reinterpret_cast<float *>(&R.c2[k]) + h, *c3 = reinterpret_cast<float *>(&R.c3[k]) + h;
+    float *c4 = reinterpret_cast<float *>(&R.c4[k]) + h;
+    c0[0] = mo.x; c0[2] = mo.y; c1[0] = mo.z; c1[2] = mo.w;
+    c2[0] = -qa.x; c2[2] = -qa.y; c3[0] = -qa.z; c3[2] = -qa.w; c4[0] = -qb.x; c4[2] = -qb.y;
+}
+
+__device__ __forceinline__ void put_body(WarpRings &R, int s, const float4 p) {
+    const int k = s >> 1, h = s & 1;
+    float *b0 = reinterpret_cast<float *>(&R.b0[k]) + h, *b1 = reinterpret_cast<float *>(&R.b1[k]) + h;
+    b0[0] = p.x; b0[2] = p.y; b1[0] = p.z; b1[2] = p.w;
+}
 
 __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
     float y = __fsub_rn(v, c);
@@ -55,120 +81,153 @@ struct Acc {
     float cx, cy, cz, cp;    // Kahan compensations
 };
 
-struct Part {
-    float x, y, z, p;
+// Per-tile partial sums of one body: (even sources, odd sources) pairs; the
+// potential is summed with the opposite sign (mr + q/(2 r^5) > 0 terms).
+struct Part2 {
+    float2 x, y, z, p;
 };
 
-__device__ __forceinline__ void pc_one(const float4 mo, const float4 qa, const float2 qb, const float4 me,
-                                       float eps2, Part &P) {
-    const float dx = mo.x - me.x, dy = mo.y - me.y, dz = mo.z - me.z;
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-    const float rinv = rsqrtf(r2);
-    const float rinv2 = rinv * rinv;
-    const float mr = mo.w * rinv;
-    const float mr3 = mr * rinv2;
-    const float qx = fmaf(qa.w, dy, fmaf(qb.x, dz, qa.x * dx));
-    const float qy = fmaf(qa.w, dx, fmaf(qb.y, dz, qa.y * dy));
-    const float qz = fmaf(qb.x, dx, fmaf(qb.y, dy, qa.z * dz));
-    const float q = fmaf(dz, qz, fmaf(dy, qy, dx * qx));
-    const float rinv5 = rinv2 * rinv2 * rinv;
-    const float qr5 = q * rinv5;
-    P.p -= fmaf(0.5f, qr5, mr);
-    const float sc = fmaf(2.5f * qr5, rinv2, mr3);
-    P.x = fmaf(sc, dx, P.x); P.x = fmaf(-rinv5, qx, P.x);
-    P.y = fmaf(sc, dy, P.y); P.y = fmaf(-rinv5, qy, P.y);
-    P.z = fmaf(sc, dz, P.z); P.z = fmaf(-rinv5, qz, P.z);
+// The body as packed operands: negated coordinates in both halves.
+struct Me2 {
+    float2 nx, ny, nz;
+};
+
+__device__ __forceinline__ Me2 me2_of(const float4 me) {
+    return Me2{make_float2(-me.x, -me.x), make_float2(-me.y, -me.y), make_float2(-me.z, -me.z)};
 }
 
-__device__ __forceinline__ void pp_one(const float4 s, const float4 me, float eps2, Part &P) {
-    const float dx = s.x - me.x, dy = s.y - me.y, dz = s.z - me.z;
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-    const float rinv = rsqrtf(r2);
-    const float mr = s.w * rinv;
-    const float mr3 = mr * rinv * rinv;
-    P.p -= mr;
-    P.x = fmaf(mr3, dx, P.x); P.y = fmaf(mr3, dy, P.y); P.z = fmaf(mr3, dz, P.z);
+// Two body-cell interactions (sources 2k, 2k+1) of one body, element-wise
+// the same FP32 operations as the scalar formula:
+//   d = com - x, r^2 = |d|^2 + eps^2, q = d.Q.d,
+//   phi -= M/r + q/(2 r^5),  a += (M/r^3 + 5q/(2 r^7)) d - Q d / r^5,
+// with -Q staged, so q and Q d arrive negated.
+__device__ __forceinline__ void pc_two(const float4 v0, const float4 v1, const float4 v2, const float4 v3,
+                                       const float4 v4, const Me2 &m, const float2 eps2, Part2 &P) {
+    const float2 dx = __fadd2_rn(make_float2(v0.x, v0.y), m.nx);
+    const float2 dy = __fadd2_rn(make_float2(v0.z, v0.w), m.ny);
+    const float2 dz = __fadd2_rn(make_float2(v1.x, v1.y), m.nz);
+    const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, eps2)));
+    const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 rinv2 = __fmul2_rn(rinv, rinv);
+    const float2 mr = __fmul2_rn(make_float2(v1.z, v1.w), rinv);
+    const float2 mr3 = __fmul2_rn(mr, rinv2);
+    const float2 nqxx = make_float2(v2.x, v2.y), nqyy = make_float2(v2.z, v2.w);
+    const float2 nqzz = make_float2(v3.x, v3.y), nqxy = make_float2(v3.z, v3.w);
+    const float2 nqxz = make_float2(v4.x, v4.y), nqyz = make_float2(v4.z, v4.w);
+    const float2 qx = __ffma2_rn(nqxy, dy, __ffma2_rn(nqxz, dz, __fmul2_rn(nqxx, dx)));   // -(Q d)
+    const float2 qy = __ffma2_rn(nqxy, dx, __ffma2_rn(nqyz, dz, __fmul2_rn(nqyy, dy)));
+    const float2 qz = __ffma2_rn(nqxz, dx, __ffma2_rn(nqyz, dy, __fmul2_rn(nqzz, dz)));
+    const float2 q = __ffma2_rn(dz, qz, __ffma2_rn(dy, qy, __fmul2_rn(dx, qx)));          // -q
+    const float2 rinv5 = __fmul2_rn(__fmul2_rn(rinv2, rinv2), rinv);
+    const float2 qr5 = __fmul2_rn(q, rinv5);                                               // -q / r^5
+    P.p = __fadd2_rn(P.p, __ffma2_rn(make_float2(-0.5f, -0.5f), qr5, mr));
+    const float2 sc = __ffma2_rn(__fmul2_rn(make_float2(-2.5f, -2.5f), qr5), rinv2, mr3);
+    P.x = __ffma2_rn(rinv5, qx, __ffma2_rn(sc, dx, P.x));
+    P.y = __ffma2_rn(rinv5, qy, __ffma2_rn(sc, dy, P.y));
+    P.z = __ffma2_rn(rinv5, qz, __ffma2_rn(sc, dz, P.z));
+}
+
+// Two body-body interactions: a += m d / r^3, phi -= m / r.
+__device__ __forceinline__ void pp_two(const float4 v0, const float4 v1, const Me2 &m, const float2 eps2,
+                                       Part2 &P) {
+    const float2 dx = __fadd2_rn(make_float2(v0.x, v0.y), m.nx);
+    const float2 dy = __fadd2_rn(make_float2(v0.z, v0.w), m.ny);
+    const float2 dz = __fadd2_rn(make_float2(v1.x, v1.y), m.nz);
+    const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, eps2)));
+    const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 mr = __fmul2_rn(make_float2(v1.z, v1.w), rinv);
+    const float2 mr3 = __fmul2_rn(__fmul2_rn(mr, rinv), rinv);
+    P.p = __fadd2_rn(P.p, mr);
+    P.x = __ffma2_rn(mr3, dx, P.x);
+    P.y = __ffma2_rn(mr3, dy, P.y);
+    P.z = __ffma2_rn(mr3, dz, P.z);
 }
 
 template <int BPL>
-__device__ __forceinline__ void commit(const Part (&P)[BPL], Acc (&A)[BPL]) {
+__device__ __forceinline__ void commit(const Part2 (&P)[BPL], Acc (&A)[BPL]) {
 #pragma unroll
     for (int b = 0; b < BPL; b++) {
-        kahan_add(A[b].ax, A[b].cx, P[b].x); kahan_add(A[b].ay, A[b].cy, P[b].y);
-        kahan_add(A[b].az, A[b].cz, P[b].z); kahan_add(A[b].ph, A[b].cp, P[b].p);
+        kahan_add(A[b].ax, A[b].cx, __fadd_rn(P[b].x.x, P[b].x.y));
+        kahan_add(A[b].ay, A[b].cy, __fadd_rn(P[b].y.x, P[b].y.y));
+        kahan_add(A[b].az, A[b].cz, __fadd_rn(P[b].z.x, P[b].z.y));
+        kahan_add(A[b].ph, A[b].cp, -__fadd_rn(P[b].p.x, P[b].p.y));
     }
 }
 
-// Tile evaluation.  NPH lanes share one body and split the tile's 32 sources
-// (lane phase p takes sources p, p+NPH, ...): the trip count 32/NPH and the
-// stride are compile-time constants, so the shared-memory reads use immediate
-// offsets and there is no per-interaction loop bookkeeping.  Each lane holds
-// BPL bodies that reuse every source read.  Partial tiles are padded with
-// massless sources far away, which add exactly zero.
+// Tile evaluation.  NPH lanes share one body and split the tile's 16 source
+// pairs (lane phase p takes pairs p, p+NPH, ...): the trip count 16/NPH and
+// the stride are compile-time constants, so the shared-memory reads use
+// immediate offsets and there is no per-interaction loop bookkeeping.  Each
+// lane holds BPL bodies that reuse every source read.  Partial tiles are
+// padded with massless sources far away, which add exactly zero.
 template <int NPH, int BPL>
-__device__ __forceinline__ void eval_pc(const WarpRings &R, int head, int phase,
-                                        const float4 (&me)[BPL], float eps2, Acc (&A)[BPL]) {
-    constexpr int T = 32 / NPH;
-    const float4 *mono = R.mono + head + phase;
-    const float4 *qa4 = R.qa + head + phase;
-    const float2 *qb2 = R.qb + head + phase;
-    Part P[BPL];
+__device__ __forceinline__ void eval_pc(const WarpRings &R, int hp, int phase, const float4 (&me)[BPL],
+                                        const float2 eps2, Acc (&A)[BPL]) {
+    constexpr int T = 16 / NPH;
+    const int k0 = hp + phase;
+    Me2 m[BPL];
+    Part2 P[BPL];
 #pragma unroll
-    for (int b = 0; b < BPL; b++) P[b] = Part{0.f, 0.f, 0.f, 0.f};
+    for (int b = 0; b < BPL; b++) {
+        m[b] = me2_of(me[b]);
+        P[b] = Part2{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    }
 #pragma unroll kWalkUnroll
     for (int j = 0; j < T; j++) {
-        const float4 mo = mono[j * NPH];
-        const float4 qa = qa4[j * NPH];
-        const float2 qb = qb2[j * NPH];
+        const int k = k0 + j * NPH;
+        const float4 v0 = R.c0[k], v1 = R.c1[k], v2 = R.c2[k], v3 = R.c3[k], v4 = R.c4[k];
 #pragma unroll
-        for (int b = 0; b < BPL; b++) pc_one(mo, qa, qb, me[b], eps2, P[b]);
+        for (int b = 0; b < BPL; b++) pc_two(v0, v1, v2, v3, v4, m[b], eps2, P[b]);
     }
     commit<BPL>(P, A);
 }
 
 template <int NPH, int BPL>
-__device__ __forceinline__ void eval_pp(const WarpRings &R, int head, int phase,
-                                        const float4 (&me)[BPL], float eps2, Acc (&A)[BPL]) {
-    constexpr int T = 32 / NPH;
-    const float4 *src = R.pp + head + phase;
-    Part P[BPL];
+__device__ __forceinline__ void eval_pp(const WarpRings &R, int hp, int phase, const float4 (&me)[BPL],
+                                        const float2 eps2, Acc (&A)[BPL]) {
+    constexpr int T = 16 / NPH;
+    const int k0 = hp + phase;
+    Me2 m[BPL];
+    Part2 P[BPL];
 #pragma unroll
-    for (int b = 0; b < BPL; b++) P[b] = Part{0.f, 0.f, 0.f, 0.f};
+    for (int b = 0; b < BPL; b++) {
+        m[b] = me2_of(me[b]);
+        P[b] = Part2{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    }
 #pragma unroll kWalkUnroll
     for (int j = 0; j < T; j++) {
-        const float4 s = src[j * NPH];
+        const int k = k0 + j * NPH;
+        const float4 v0 = R.b0[k], v1 = R.b1[k];
 #pragma unroll
-        for (int b = 0; b < BPL; b++) pp_one(s, me[b], eps2, P[b]);
+        for (int b = 0; b < BPL; b++) pp_two(v0, v1, m[b], eps2, P[b]);
     }
     commit<BPL>(P, A);
 }
 
-// Warp-uniform dispatch on log2(body slots); two bodies per lane always use
-// all 32 lanes as slots.
+// Warp-uniform dispatch on log2(body slots) (>= 1: at most 16 phases share
+// the 16 source pairs); two bodies per lane always use all 32 lanes as slots.
 template <int BPL>
-__device__ __forceinline__ void tile_pc(int lg, const WarpRings &R, int head, int phase,
-                                        const float4 (&me)[BPL], float eps2, Acc (&A)[BPL]) {
-    if (BPL == 2) { eval_pc<1, BPL>(R, head, phase, me, eps2, A); return; }
+__device__ __forceinline__ void tile_pc(int lg, const WarpRings &R, int hp, int phase, const float4 (&me)[BPL],
+                                        const float2 eps2, Acc (&A)[BPL]) {
+    if (BPL == 2) { eval_pc<1, BPL>(R, hp, phase, me, eps2, A); return; }
     switch (lg) {
-        case 0: eval_pc<32, BPL>(R, head, phase, me, eps2, A); break;
-        case 1: eval_pc<16, BPL>(R, head, phase, me, eps2, A); break;
-        case 2: eval_pc<8, BPL>(R, head, phase, me, eps2, A); break;
-        case 3: eval_pc<4, BPL>(R, head, phase, me, eps2, A); break;
-        case 4: eval_pc<2, BPL>(R, head, phase, me, eps2, A); break;
-        default: eval_pc<1, BPL>(R, head, phase, me, eps2, A); break;
+        case 1: eval_pc<16, BPL>(R, hp, phase, me, eps2, A); break;
+        case 2: eval_pc<8, BPL>(R, hp, phase, me, eps2, A); break;
+        case 3: eval_pc<4, BPL>(R, hp, phase, me, eps2, A); break;
+        case 4: eval_pc<2, BPL>(R, hp, phase, me, eps2, A); break;
+        default: eval_pc<1, BPL>(R, hp, phase, me, eps2, A); break;
     }
 }
 template <int BPL>
-__device__ __forceinline__ void tile_pp(int lg, const WarpRings &R, int head, int phase,
-                                        const float4 (&me)[BPL], float eps2, Acc (&A)[BPL]) {
-    if (BPL == 2) { eval_pp<1, BPL>(R, head, phase, me, eps2, A); return; }
+__device__ __forceinline__ void tile_pp(int lg, const WarpRings &R, int hp, int phase, const float4 (&me)[BPL],
+                                        const float2 eps2, Acc (&A)[BPL]) {
+    if (BPL == 2) { eval_pp<1, BPL>(R, hp, phase, me, eps2, A); return; }
     switch (lg) {
-        case 0: eval_pp<32, BPL>(R, head, phase, me, eps2, A); break;
-        case 1: eval_pp<16, BPL>(R, head, phase, me, eps2, A); break;
-        case 2: eval_pp<8, BPL>(R, head, phase, me, eps2, A); break;
-        case 3: eval_pp<4, BPL>(R, head, phase, me, eps2, A); break;
-        case 4: eval_pp<2, BPL>(R, head, phase, me, eps2, A); break;
-        default: eval_pp<1, BPL>(R, head, phase, me, eps2, A); break;
+        case 1: eval_pp<16, BPL>(R, hp, phase, me, eps2, A); break;
+        case 2: eval_pp<8, BPL>(R, hp, phase, me, eps2, A); break;
+        case 3: eval_pp<4, BPL>(R, hp, phase, me, eps2, A); break;
+        case 4: eval_pp<2, BPL>(R, hp, phase, me, eps2, A); break;
+        default: eval_pp<1, BPL>(R, hp, phase, me, eps2, A); break;
     }
 }
 
@@ -187,8 +246,14 @@ __device__ __forceinline__ int level_bin(int lvl) { return lvl <= 3 ? 0 : lvl <=
 // body-body interactions), log(n_G / (extent^3 + eps^3)), log((diagonal +
 // eps)/eps), the body's offset from the centre of its group's box (3),
 // log(n_G) and the box diagonal.
+#ifndef WALK_MIN_BLOCKS1
+#define WALK_MIN_BLOCKS1 0          // 0: the compiler picks the register budget
+#endif
+#ifndef WALK_MIN_BLOCKS2
+#define WALK_MIN_BLOCKS2 0
+#endif
 template <int BPL, bool FEAT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, BPL == 1 ? WALK_MIN_BLOCKS1 : WALK_MIN_BLOCKS2)
 k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__ groups,
        const float4 *__restrict__ pos4, const float4 *__restrict__ test,
        const uint2 *__restrict__ link, const float4 *__restrict__ mono,
@@ -206,6 +271,7 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
     // path's fallback decision) is clear.
     const unsigned ngroups = ((stc->status & ST_TIMEOUT) || (gate && *gate == 0u)) ? 0u : stc->ngroups;
     const float eps2 = eps * eps;
+    const float2 eps2x2 = make_float2(eps2, eps2);
     const unsigned lt = lanemask_lt_w();
     unsigned *queue = BPL == 1 ? &st->walk_next : &st->walk_next2;
 
@@ -218,7 +284,7 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
         const int gb = (int)gr.x, ng = (int)gr.y;
         if ((BPL == 1) != (ng <= 32)) continue;      // the other instantiation's group
         // Body slots and source phases.
-        const int lg = BPL == 2 ? 5 : (ng <= 1 ? 0 : 32 - __clz(ng - 1));   // log2(next_pow2)
+        const int lg = BPL == 2 ? 5 : (ng <= 2 ? 1 : 32 - __clz(ng - 1));   // log2(next_pow2), >= 1
         const int slots = 1 << lg;
         const int bslot = lane & (slots - 1), phase = lane >> lg;
         bool live[BPL];
@@ -306,10 +372,7 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
             const unsigned am = __ballot_sync(0xffffffffu, acc);
             if (acc) {
                 const int s = (pc_head + pc_n + __popc(am & lt)) & (RING - 1);
-                const float4 mo = __ldg(mono + cell);
-                const float4 qa = __ldg(quadA + cell);
-                const float2 qb = __ldg(quadB + cell);
-                R.mono[s] = mo; R.qa[s] = qa; R.qb[s] = qb;
+                put_cell(R, s, __ldg(mono + cell), __ldg(quadA + cell), __ldg(quadB + cell));
             }
             pc_n += __popc(am);
             npc += __popc(am);
@@ -337,11 +400,11 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
                 npp += lc;
                 for (unsigned o = 0; o < lc; o += 32u) {
                     const int k = (int)min(32u, lc - o);
-                    if (lane < k) R.pp[(pp_head + pp_n + lane) & (RING - 1)] = __ldg(pos4 + lb + o + lane);
+                    if (lane < k) put_body(R, (pp_head + pp_n + lane) & (RING - 1), __ldg(pos4 + lb + o + lane));
                     pp_n += k;
                     if (pp_n >= 32) {
                         __syncwarp();
-                        tile_pp<BPL>(lg, R, pp_head, phase, me, eps2, A);
+                        tile_pp<BPL>(lg, R, pp_head >> 1, phase, me, eps2x2, A);
                         __syncwarp();
                         pp_head = (pp_head + 32) & (RING - 1);
                         pp_n -= 32;
@@ -350,7 +413,7 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
             }
             __syncwarp();
             if (pc_n >= 32) {
-                tile_pc<BPL>(lg, R, pc_head, phase, me, eps2, A);
+                tile_pc<BPL>(lg, R, pc_head >> 1, phase, me, eps2x2, A);
                 pc_head = (pc_head + 32) & (RING - 1);
                 pc_n -= 32;
             }
@@ -361,18 +424,15 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
         const float FAR = 1e18f;
         if (pc_n > 0) {
             const int s = pc_head + pc_n + lane;
-            if (lane < 32 - pc_n) {
-                R.mono[s] = make_float4(FAR, FAR, FAR, 0.f);
-                R.qa[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-                R.qb[s] = make_float2(0.f, 0.f);
-            }
+            if (lane < 32 - pc_n)
+                put_cell(R, s, make_float4(FAR, FAR, FAR, 0.f), make_float4(0.f, 0.f, 0.f, 0.f), make_float2(0.f, 0.f));
             __syncwarp();
-            tile_pc<BPL>(lg, R, pc_head, phase, me, eps2, A);
+            tile_pc<BPL>(lg, R, pc_head >> 1, phase, me, eps2x2, A);
         }
         if (pp_n > 0) {
-            if (lane < 32 - pp_n) R.pp[pp_head + pp_n + lane] = make_float4(FAR, FAR, FAR, 0.f);
+            if (lane < 32 - pp_n) put_body(R, pp_head + pp_n + lane, make_float4(FAR, FAR, FAR, 0.f));
             __syncwarp();
-            tile_pp<BPL>(lg, R, pp_head, phase, me, eps2, A);
+            tile_pp<BPL>(lg, R, pp_head >> 1, phase, me, eps2x2, A);
         }
 #pragma unroll
         for (int b = 0; b < BPL; b++) {

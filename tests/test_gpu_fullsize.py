@@ -1,0 +1,161 @@
+"""GPU parity at full workload sizes, in the configuration bench.py times
+(nleaf 16, ncrit 64, 4 or 8 warps per walk block), on outputs the oracle can
+compute one by one:
+
+* N = 2^20 (seed 1, eps = 0.005, theta = 0.75): keys, permutation, tree and
+  groups bit-exact over all bodies; forces vs the oracle tree walked for a
+  random sample of 512 groups (<= 1e-5 relative, identical interaction
+  counts, outside borderline groups); the walk block width does not change a
+  single bit; acceleration and potential vs the FP64 direct sum at 4096
+  sampled bodies: median <= 1e-3, p99 <= 1e-2.
+* N = 2^22 (seed 2, eps = 0.002), theta in {0.5, 0.75, 1.0}: the same
+  sampled-group check at each theta, the direct-sum gates at theta = 0.75 and
+  p99 growing with theta.
+* N = 2^24 (seed 3, eps = 0.002, theta = 0.75): keys and permutation
+  bit-exact, direct-sum gates at 2048 sampled bodies."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1204_2280_gb300 as B
+from paper_1204_2280_gb300 import workloads as W
+
+from gpu_common import rel_err
+
+pytestmark = pytest.mark.gpu
+
+TAU_ABS, TAU_REL = 2e-6, 1e-6
+
+
+def gpu_forces(b, theta, eps, warps=4, tree=True):
+    import torch
+    out = {}
+    with B.Bonsai(B.Config(nleaf=16, ncrit=64, walk_warps=warps)) as bz:
+        bz.set_bodies(torch.from_numpy(b.pos).cuda(), torch.from_numpy(b.mass).cuda())
+        bz.build()
+        out["domain"] = B.bonsai_get_domain(bz.ctx)
+        out["keys"], out["perm"] = B.bonsai_get_keys(bz.ctx)
+        if tree:
+            out["tree"] = B.bonsai_get_tree(bz.ctx)
+            out["groups"] = B.bonsai_get_groups(bz.ctx)
+        bz.multipoles()
+        out["acc"], out["pot"] = {}, {}
+        for th in np.atleast_1d(theta):
+            acc = torch.zeros((b.n, 3), dtype=torch.float32, device="cuda")
+            pot = torch.zeros(b.n, dtype=torch.float32, device="cuda")
+            bz.forces(float(th), eps, acc, pot)
+            torch.cuda.synchronize()
+            out["acc"][float(th)], out["pot"][float(th)] = acc.cpu().numpy(), pot.cpu().numpy()
+            out.setdefault("counts", {})[float(th)] = B.bonsai_get_counts(bz.ctx)[:2]
+        B.bonsai_sync(bz.ctx)
+    return out
+
+
+def oracle_setup(b, nleaf=16, ncrit=64):
+    mn, S = oracle.domain(b.pos)
+    k = oracle.keys(b.pos, mn, S)
+    perm = oracle.sort(k)
+    t = oracle.build_tree(k[perm], nleaf)
+    gb, gc = oracle.groups(t, ncrit)
+    M, com, Q = oracle.moments(t, b.pos[perm], b.mass[perm])
+    return dict(mn=mn, S=S, k=k, perm=perm, tree=t, gb=gb, gc=gc, M=M, com=com, Q=Q)
+
+
+def check_structure(res, o):
+    gmn, gS = res["domain"]
+    assert np.array_equal(gmn, o["mn"]) and gS == o["S"]
+    assert np.array_equal(res["keys"], o["k"][o["perm"]])
+    assert np.array_equal(res["perm"], o["perm"])
+    if "tree" in res:
+        for f in ("body_begin", "body_count", "child_begin", "nchild", "level"):
+            assert np.array_equal(res["tree"][f], getattr(o["tree"], f)), f
+        assert np.array_equal(res["groups"][0], o["gb"]) and np.array_equal(res["groups"][1], o["gc"])
+
+
+def check_sampled_groups(b, o, res_acc, res_pot, counts, theta, eps, ngroups, seed):
+    """The oracle walks a random sample of groups; bodies of those groups
+    are compared (positions in sorted order)."""
+    perm, t = o["perm"], o["tree"]
+    ro = oracle.open_radius(t, o["k"][perm], o["mn"], o["S"], o["com"], theta)
+    rng = np.random.default_rng(seed)
+    sel = np.sort(rng.choice(o["gb"].shape[0], ngroups, replace=False))
+    spos, smass = b.pos[perm], b.mass[perm]
+    acc, pot, npc, npp, flag = oracle.walk(spos, smass, t, o["M"], o["com"], o["Q"], ro,
+                                           o["gb"][sel], o["gc"][sel], eps, TAU_ABS, TAU_REL)
+    idx = np.concatenate([np.arange(s, s + c) for s, c in zip(o["gb"][sel], o["gc"][sel])])
+    ok = flag[idx] == 0
+    assert ok.mean() > 0.9, ok.mean()
+    ga, gp = res_acc[perm[idx]], res_pot[perm[idx]]
+    ea = rel_err(ga, acc[idx])
+    ep = np.abs(gp - pot[idx]) / np.abs(pot[idx])
+    assert ea[ok].max() <= 1e-5, ea[ok].max()
+    assert ep[ok].max() <= 1e-5, ep[ok].max()
+    assert np.array_equal(counts[0][perm[idx]][ok], npc[idx][ok])
+    assert np.array_equal(counts[1][perm[idx]][ok], npp[idx][ok])
+    assert ea.max() <= 3e-2
+
+
+def direct_errors(b, acc, pot, eps, nsample, seed, ref=None):
+    """Relative errors at sampled bodies vs the FP64 direct sum; ref caches
+    (idx, a_direct, phi_direct) between calls on the same bodies."""
+    if ref is None or not ref:
+        idx = W.sample_indices(b.n, nsample, seed)
+        a_d, p_d = oracle.direct(b.pos, b.mass, eps, idx)
+        if ref is not None:
+            ref.extend([idx, a_d, p_d])
+    else:
+        idx, a_d, p_d = ref
+    ea = rel_err(acc[idx], a_d)
+    ep = np.abs(pot[idx] - p_d) / np.abs(p_d)
+    return ea, ep
+
+
+def test_bench_workload_n2e20():
+    b = W.plummer(1 << 20, 1)
+    eps, theta = 0.005, 0.75
+    res = gpu_forces(b, theta, eps, warps=4)
+    res8 = gpu_forces(b, theta, eps, warps=8, tree=False)
+    assert np.array_equal(res["acc"][theta], res8["acc"][theta])
+    assert np.array_equal(res["pot"][theta], res8["pot"][theta])
+    o = oracle_setup(b)
+    check_structure(res, o)
+    check_sampled_groups(b, o, res["acc"][theta], res["pot"][theta], res["counts"][theta], theta, eps, 512, 11)
+    ea, ep = direct_errors(b, res["acc"][theta], res["pot"][theta], eps, 4096, 12)
+    print(f"N=2^20 theta=0.75: acc median {np.median(ea):.3e} p99 {np.percentile(ea, 99):.3e}")
+    assert np.median(ea) <= 1e-3 and np.percentile(ea, 99) <= 1e-2
+    assert np.median(ep) <= 1e-3 and np.percentile(ep, 99) <= 1e-2
+
+
+def test_theta_sweep_n2e22():
+    b = W.plummer(1 << 22, 2)
+    eps, thetas = 0.002, (0.5, 0.75, 1.0)
+    res = gpu_forces(b, thetas, eps, warps=8)
+    o = oracle_setup(b)
+    check_structure(res, o)
+    p99, ref = [], []
+    for k, th in enumerate(thetas):
+        check_sampled_groups(b, o, res["acc"][th], res["pot"][th], res["counts"][th], th, eps, 256, 20 + k)
+        ea, ep = direct_errors(b, res["acc"][th], res["pot"][th], eps, 4096, 30, ref)
+        p99.append(np.percentile(ea, 99))
+        print(f"N=2^22 theta={th}: acc median {np.median(ea):.3e} p99 {p99[-1]:.3e}")
+        if th == 0.75:
+            assert np.median(ea) <= 1e-3 and p99[-1] <= 1e-2
+            assert np.median(ep) <= 1e-3 and np.percentile(ep, 99) <= 1e-2
+    assert p99[0] < p99[1] < p99[2]
+
+
+def test_keys_and_direct_gates_n2e24():
+    b = W.plummer(1 << 24, 3)
+    eps, theta = 0.002, 0.75
+    res = gpu_forces(b, theta, eps, warps=8, tree=False)
+    mn, S = oracle.domain(b.pos)
+    k = oracle.keys(b.pos, mn, S)
+    perm = oracle.sort(k)
+    gmn, gS = res["domain"]
+    assert np.array_equal(gmn, mn) and gS == S
+    assert np.array_equal(res["perm"], perm)
+    assert np.array_equal(res["keys"], k[perm])
+    ea, ep = direct_errors(b, res["acc"][theta], res["pot"][theta], eps, 2048, 40)
+    print(f"N=2^24 theta=0.75: acc median {np.median(ea):.3e} p99 {np.percentile(ea, 99):.3e}")
+    assert np.median(ea) <= 1e-3 and np.percentile(ea, 99) <= 1e-2
+    assert np.median(ep) <= 1e-3 and np.percentile(ep, 99) <= 1e-2
