@@ -29,8 +29,11 @@ constexpr int FP64_LEVELS = 4;                   // levels 0..3 combine in FP64
 #ifndef SORT_THREADS_CFG
 #define SORT_THREADS_CFG 256
 #endif
+#ifndef SORT_ITEMS_CFG
+#define SORT_ITEMS_CFG 16
+#endif
 constexpr int SORT_THREADS = SORT_THREADS_CFG;          // >= 256: thread d owns digit d
-constexpr int SORT_ITEMS = 4096 / SORT_THREADS;
+constexpr int SORT_ITEMS = SORT_ITEMS_CFG;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;   // 4096 keys per tile
 constexpr int SORT_PASSES = 8;                         // 8-bit digits, 63-bit keys
 constexpr int MAX_SYSTEMS = 256;                       // ensemble: one more pass on the system id

@@ -14,13 +14,13 @@
 //                                          bodies iff l <= D(t)
 // A cell (level l, first body t) exists iff the run at level l-1 containing t
 // has more than nleaf bodies.  For l > l0(t) that run also starts at t; for
-// l = l0(t) it does iff some window [j, j+nleaf] around t stays inside it:
-//   E(t) = max_{t-nleaf <= j <= t} D(j) >= l0(t) - 1.
-// So body t starts exactly the cells of levels lo..hi with lo = l0(t) (if
-// E(t)) and hi = max(lo, min(D(t)+1, 21)); the one at hi is a leaf.  Groups
-// (cells with <= ncrit bodies whose parent has more) follow the same way with
-// ncrit in place of nleaf.  Three launches: count per block and level, scan
-// per level, write cells.
+// l = l0(t) its length is read from per-level bit masks of run starts over a
+// 64-body halo (a longer run is split in any case).  So body t starts exactly
+// the cells of levels lo..hi with lo = l0(t) (if that parent run is split)
+// and hi = max(lo, min(D(t)+1, 21)); the one at hi is a leaf.  Groups (cells
+// with <= ncrit bodies whose parent has more) follow the same way with ncrit
+// in place of nleaf.  Four launches: count per block and level, scan per
+// level, write cells, link children and internal body counts.
 #include "common.cuh"
 
 namespace bonsai {
@@ -73,129 +73,92 @@ struct BodyCells {
     int lo, hi, ngrp, lg;   // lg: group level (>hi: oversize leaf cut in chunks)
 };
 
-// Shared memory of a build block: keys [base-W, base+B+W) and, for
-// j in [base-W, base+B), D(j) = cpl(k[j], k[j+nleaf]) and DG(j) with ncrit
-// (-1 where j+w is past the end).
+// Shared memory of a build block.  The block's bodies are [base, base+B);
+// a halo of BW = 64 bodies on each side gives the extended range
+// [base-BW, base+B+BW) of BCH chunks of 32 positions, plus one key below it.
+//   M[l * BCH + c], bit i: position 32c + i of the extended range is the
+//   first body of a level-l key-prefix run (l0 <= l; every position outside
+//   [1, n) and every first body of a system counts as one).
+// Any run that matters here (<= 64 bodies around a body of the block) is
+// then answered by bit operations on at most five mask words per query.
+constexpr int BW = 64;
+constexpr int BCH = (BUILD_THREADS + 2 * BW) / 32;
+
 struct BuildShared {
-    unsigned long long *k;
-    int *D, *DG, *TD, *TG;   // TD/TG: maxima of D/DG over [j, j + HD/HG)
-    uint8_t *sy;
-    int W, base, nleaf, ncrit, HD, HG;
-    __device__ unsigned long long key(int j) const { return k[j - base + W]; }
-    __device__ uint8_t sys(int j) const { return sy[j - base + W]; }
+    unsigned long long *k;   // keys of [base-BW-1, base+B+BW)
+    uint8_t *sy;             // system ids, same range
+    unsigned *M;             // run-start masks, (MAX_LEVEL + 1) x BCH
+    int base;
+    __device__ unsigned long long key(int j) const { return k[j - base + BW + 1]; }
+    __device__ uint8_t sys(int j) const { return sy[j - base + BW + 1]; }
     __device__ int cpl(int a, int b) const { return body_cpl(key(a), key(b), sys(a), sys(b)); }
-    __device__ int d(int j) const { return D[j - base + W]; }
-    __device__ int dg(int j) const { return DG[j - base + W]; }
-    // max D(j) over j in [t - nleaf, t] and max DG(j) over [t - ncrit, t]
-    // (two overlapping power-of-two windows each)
-    __device__ int dmax(int t) const { return max(TD[t - nleaf - base + W], TD[t - HD + 1 - base + W]); }
-    __device__ int dgmax(int t) const { return max(TG[t - ncrit - base + W], TG[t - HG + 1 - base + W]); }
+
+    // First body s <= t and end e > t of the level-l run holding body t of
+    // the block, as extended-range positions; -4096 / 1 << 20 when farther
+    // than the two neighbouring chunks (then the run exceeds 64 bodies).
+    __device__ void run_of(int t, int l, int &s, int &e) const {
+        const int q = t - base + BW, c = q >> 5, i = q & 31;
+        const unsigned *Ml = M + l * BCH;
+        const unsigned a0 = Ml[c] & (0xffffffffu >> (31 - i));
+        const unsigned a1 = Ml[c - 1], a2 = Ml[c - 2];
+        s = a0 ? (c << 5) + 31 - __clz(a0)
+               : a1 ? ((c - 1) << 5) + 31 - __clz(a1) : a2 ? ((c - 2) << 5) + 31 - __clz(a2) : -4096;
+        const unsigned b0 = i == 31 ? 0u : (Ml[c] & (0xffffffffu << (i + 1)));
+        const unsigned b1 = Ml[c + 1], b2 = Ml[c + 2];
+        e = b0 ? (c << 5) + __ffs(b0) - 1
+               : b1 ? ((c + 1) << 5) + __ffs(b1) - 1 : b2 ? ((c + 2) << 5) + __ffs(b2) - 1 : 1 << 20;
+    }
+    // Whether the level-l run holding t has more than w (<= 64) bodies.
+    __device__ bool run_longer(int t, int l, int w) const {
+        int s, e;
+        run_of(t, l, s, e);
+        return e - s > w;
+    }
+    // End (exclusive) of the level-l run starting at t: from the masks when
+    // within the halo, else by the global search.
+    __device__ int run_end_at(const unsigned long long *__restrict__ sk, int send, int t, int l) const {
+        if (l == 0) return send;
+        int s, e;
+        run_of(t, l, s, e);
+        return e < (1 << 20) ? min(send, base - BW + e) : run_end(sk, send, t, l);
+    }
 };
 
-__device__ __forceinline__ int pow2_floor(int x) { return 1 << (31 - __clz(x)); }
-
-// Keys and system ids of [base-W, base+B+W); D and DG of [base-W, base+B).
-// Bodies of different systems share no level (cpl -1), so each system gets
-// its own root on level 0.
+// Keys and system ids of the extended range, then the run-start masks: one
+// chunk per warp and pass, 22 ballots, lane l keeps level l's mask.
 __device__ BuildShared load_build_shared(void *smem, const unsigned long long *__restrict__ sk,
-                                         const uint8_t *__restrict__ sysid, int n, int base,
-                                         int nleaf, int ncrit) {
+                                         const uint8_t *__restrict__ sysid, int n, int base) {
     BuildShared b;
-    b.W = max(nleaf, ncrit);
     b.base = base;
-    b.nleaf = nleaf;
-    b.ncrit = ncrit;
-    b.HD = pow2_floor(nleaf + 1);
-    b.HG = pow2_floor(ncrit + 1);
-    const int m = BUILD_THREADS + b.W;
+    constexpr int NK = BUILD_THREADS + 2 * BW + 1;
     b.k = (unsigned long long *)smem;
-    b.D = (int *)(b.k + BUILD_THREADS + 2 * b.W);
-    b.DG = b.D + m;
-    b.TD = b.DG + m;
-    b.TG = b.TD + m;
-    b.sy = (uint8_t *)(b.TG + m);
-    for (int i = threadIdx.x; i < BUILD_THREADS + 2 * b.W; i += blockDim.x) {
-        int j = base - b.W + i;
+    b.M = (unsigned *)(b.k + NK);
+    b.sy = (uint8_t *)(b.M + (MAX_LEVEL + 1) * BCH);
+    for (int i = threadIdx.x; i < NK; i += blockDim.x) {
+        const int j = base - BW - 1 + i;
         const bool in = j >= 0 && j < n;
         b.k[i] = in ? sk[j] : 0ull;
         b.sy[i] = in ? sysid[j] : 0;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        int j = base - b.W + i;
-        b.D[i] = b.TD[i] = (j >= 0 && j + nleaf < n) ? b.cpl(j, j + nleaf) : -1;
-        b.DG[i] = b.TG[i] = (j >= 0 && j + ncrit < n) ? b.cpl(j, j + ncrit) : -1;
+    const int lane = threadIdx.x & 31;
+    for (int c = threadIdx.x >> 5; c < BCH; c += BUILD_THREADS / 32) {
+        const int j = base - BW + (c << 5) + lane;
+        const int l0 = (j > 0 && j < n) ? b.cpl(j - 1, j) + 1 : 0;
+        unsigned mine = 0u;
+#pragma unroll
+        for (int l = 0; l <= MAX_LEVEL; l++) {
+            const unsigned m = __ballot_sync(0xffffffffu, l0 <= l);
+            if (lane == l) mine = m;
+        }
+        if (lane <= MAX_LEVEL) b.M[lane * BCH + c] = mine;
     }
     __syncthreads();
-    // Doubling: after the step with width h, T[i] = max over [i, i + 2h).
-    // Entries whose window runs past the array keep a truncated maximum;
-    // dmax/dgmax never read them.
-    for (int h = 1; 2 * h <= b.HG; h <<= 1) {
-        int nd[2], ng[2];
-#pragma unroll
-        for (int r = 0; r < 2; r++) {
-            const int i = threadIdx.x + r * BUILD_THREADS;
-            nd[r] = ng[r] = 0;
-            if (i < m) {
-                nd[r] = (2 * h <= b.HD && i + h < m) ? max(b.TD[i], b.TD[i + h]) : b.TD[i];
-                ng[r] = i + h < m ? max(b.TG[i], b.TG[i + h]) : b.TG[i];
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < 2; r++) {
-            const int i = threadIdx.x + r * BUILD_THREADS;
-            if (i < m) { b.TD[i] = nd[r]; b.TG[i] = ng[r]; }
-        }
-        __syncthreads();
-    }
-    for (int h = b.HG; 2 * h <= b.HD; h <<= 1) {      // nleaf > ncrit: finish TD
-        int nd[2];
-#pragma unroll
-        for (int r = 0; r < 2; r++) {
-            const int i = threadIdx.x + r * BUILD_THREADS;
-            nd[r] = (i < m && i + h < m) ? max(b.TD[i], b.TD[i + h]) : (i < m ? b.TD[i] : 0);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < 2; r++) {
-            const int i = threadIdx.x + r * BUILD_THREADS;
-            if (i < m) b.TD[i] = nd[r];
-        }
-        __syncthreads();
-    }
     return b;
 }
 
-// run_end for a body t of the block, from the keys held in shared memory
-// (indices below lim = min(send, base + BUILD_THREADS + W)); falls back to
-// the global search only when the run reaches the end of that window.
-// Leaf and group runs (<= nleaf, <= ncrit bodies) always end inside it.
-__device__ int run_end_win(const BuildShared &b, const unsigned long long *__restrict__ sk, int send, int t,
-                           int level) {
-    if (level == 0) return send;
-    const int sh = 3 * (MAX_LEVEL - level);
-    const unsigned long long pre = b.key(t) >> sh;
-    const int lim = min(send, b.base + BUILD_THREADS + b.W);
-    const int last = lim - 1;
-    if ((b.key(last) >> sh) == pre) return lim == send ? send : run_end(sk, send, last, level);
-    int lo = t, hi = last, step = 1;          // key(lo) in the run, key(hi) not
-    while (t + step < hi) {
-        if ((b.key(t + step) >> sh) != pre) { hi = t + step; break; }
-        lo = t + step;
-        step <<= 1;
-    }
-    while (hi - lo > 1) {
-        const int mid = lo + ((hi - lo) >> 1);
-        if ((b.key(mid) >> sh) == pre) lo = mid; else hi = mid;
-    }
-    return hi;
-}
-
-size_t build_smem_bytes(int nleaf, int ncrit) {
-    int W = nleaf > ncrit ? nleaf : ncrit;
-    return (size_t)(BUILD_THREADS + 2 * W) * 8 + 4 * (size_t)(BUILD_THREADS + W) * 4 +
-           (size_t)(BUILD_THREADS + 2 * W);
+size_t build_smem_bytes(int, int) {
+    return (size_t)(BUILD_THREADS + 2 * BW + 1) * 9 + (size_t)(MAX_LEVEL + 1) * BCH * 4;
 }
 
 // Which cells body t starts (levels lo..hi) and how many groups; send is the
@@ -204,19 +167,21 @@ __device__ BodyCells analyse_body(const BuildShared &b, int t, int n, int nleaf,
                                   const unsigned long long *__restrict__ sk, int send) {
     BodyCells r{false, 0, -1, 0, 0};
     if (t >= n) return r;
-    int l0 = (t == 0) ? 0 : b.cpl(t - 1, t) + 1;
+    const int l0 = t == 0 ? 0 : b.cpl(t - 1, t) + 1;
     if (l0 > MAX_LEVEL) return r;
-    if (l0 > 0 && b.dmax(t) < l0 - 1) return r;
+    if (l0 > 0 && !b.run_longer(t, l0 - 1, nleaf)) return r;     // parent not split
     r.has = true;
     r.lo = l0;
-    r.hi = max(l0, min(b.d(t) + 1, MAX_LEVEL));
-    int lg = max(l0, b.dg(t) + 1);
+    const int D = t + nleaf < n ? b.cpl(t, t + nleaf) : -1;
+    r.hi = max(l0, min(D + 1, MAX_LEVEL));
+    const int DG = t + ncrit < n ? b.cpl(t, t + ncrit) : -1;
+    const int lg = max(l0, DG + 1);
     r.lg = lg;
     if (lg <= r.hi) {
-        const bool starts = (lg > l0) || l0 == 0 || b.dgmax(t) >= l0 - 1;
+        const bool starts = (lg > l0) || l0 == 0 || b.run_longer(t, l0 - 1, ncrit);
         r.ngrp = starts ? 1 : 0;
     } else {
-        int cnt = run_end_win(b, sk, send, t, r.hi) - t;
+        const int cnt = b.run_end_at(sk, send, t, r.hi) - t;
         r.ngrp = (cnt + ncrit - 1) / ncrit;
     }
     return r;
@@ -247,7 +212,7 @@ k_build_count(const unsigned long long *__restrict__ sk, const uint8_t *__restri
     __shared__ unsigned s_wc[NROWS][32];
     if (st->status & ST_TIMEOUT) return;        // keys not sorted: skip the build
     const int base = blockIdx.x * BUILD_THREADS, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    BuildShared b = load_build_shared(smem_u64, sk, sysid, n, base, nleaf, ncrit);
+    BuildShared b = load_build_shared(smem_u64, sk, sysid, n, base);
     const int t = base + tid;
     BodyCells bc = analyse_body(b, t, n, nleaf, ncrit, sk, system_end(st, sysid, t, n));
     int rlo, rhi;
@@ -312,7 +277,10 @@ k_build_scan(unsigned *blockcount, int nblocks, DevState *st) {
 // for an internal cell that is its first child, and the children of a cell
 // are the level-(r+1) cells between its cb and the next cell's cb.  Leaves
 // get their body count here (a short search); internal cells in pass 4.
-__global__ void __launch_bounds__(BUILD_THREADS)
+#ifndef BUILD_WRITE_MIN_BLOCKS
+#define BUILD_WRITE_MIN_BLOCKS 2        // two 1024-thread blocks per SM (32 registers)
+#endif
+__global__ void __launch_bounds__(BUILD_THREADS, BUILD_WRITE_MIN_BLOCKS)
 k_build_write(const unsigned long long *__restrict__ sk, const uint8_t *__restrict__ sysid, int n,
               int nleaf, int ncrit, const unsigned *__restrict__ blockcount, int nblocks, long long ccap,
               DevState *st,
@@ -351,7 +319,7 @@ k_build_write(const unsigned long long *__restrict__ sk, const uint8_t *__restri
     }
     __syncthreads();
     if (!s_ok) return;
-    BuildShared b = load_build_shared(smem_u64, sk, sysid, n, base, nleaf, ncrit);
+    BuildShared b = load_build_shared(smem_u64, sk, sysid, n, base);
     const int t = base + tid;
     const int send = system_end(st, sysid, t, n);
     BodyCells bc = analyse_body(b, t, n, nleaf, ncrit, sk, send);
@@ -395,7 +363,7 @@ k_build_write(const unsigned long long *__restrict__ sk, const uint8_t *__restri
             cell_done[c] = 0u;
             if (r == 0) cell_parent[c] = 0xffffffffu;
             if (r == bc.hi) {
-                int cnt = run_end_win(b, sk, send, t, r) - t;
+                int cnt = b.run_end_at(sk, send, t, r) - t;
                 cell_body[c] = make_uint2((unsigned)t, (unsigned)cnt);
                 cell_link[c] = make_uint2((unsigned)t, (unsigned)cnt | LEAF_BIT);
             } else {
@@ -409,10 +377,10 @@ k_build_write(const unsigned long long *__restrict__ sk, const uint8_t *__restri
     if (bc.ngrp > 0) {
         unsigned g = s_base[GROUP_ROW] + s_wc[GROUP_ROW][warp] + (unsigned)gx;
         if (bc.lg <= bc.hi) {
-            int e = run_end_win(b, sk, send, t, bc.lg);
+            int e = b.run_end_at(sk, send, t, bc.lg);
             groups[g] = make_uint2((unsigned)t, (unsigned)(e - t));
         } else {
-            int e = run_end_win(b, sk, send, t, bc.hi);
+            int e = b.run_end_at(sk, send, t, bc.hi);
             for (int k = 0; k < bc.ngrp; k++) {
                 int b0 = t + k * ncrit;
                 groups[g + k] = make_uint2((unsigned)b0, (unsigned)min(ncrit, e - b0));
