@@ -39,10 +39,11 @@ FLOP_PC, FLOP_PP = 65, 23           # flops per body-cell / body-body interactio
 SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
 def kernels_per_step(ncrit):
-    """reset, kick+drift, keys, 8 sort passes, reorder, 4 build, multipoles,
-    open radius, walk (two instantiations when groups may exceed 32), kick."""
-    return 20 + (1 if ncrit > 32 else 0)
-WALK_TRAFFIC_PER_LAUNCH = None     # dram bytes of the walk stage (both launches) from an ncu capture of the current kernel
+    """reset, kick+drift+bbox, domains, keys, 8 sort passes, reorder, 4 build,
+    multipoles, open radius, walk (two instantiations when groups may exceed
+    32 bodies), kick."""
+    return 21 + (1 if ncrit > 32 else 0)
+WALK_TRAFFIC_PER_LAUNCH = 69.48e6  # dram bytes of the walk stage (both launches), profiles/k_walk_plummer_n2e20.md
 
 
 def parse():
