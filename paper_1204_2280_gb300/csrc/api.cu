@@ -177,6 +177,9 @@ int bonsai_create(bonsai_ctx **out, const bonsai_config *cfg, void *cuda_stream)
     if (e == cudaSuccess) e = cudaMallocHost(&c.st_host, sizeof(DevState));
     if (e == cudaSuccess) e = cudaMemsetAsync(c.st, 0, sizeof(DevState), c.stream);
     for (int i = 0; i <= Ctx::NSTAGE && e == cudaSuccess; i++) e = cudaEventCreate(&c.ev[i]);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         int r = fail(nullptr, BONSAI_ERR_CUDA, "bonsai_create", e);
         bonsai_destroy(ctx);
@@ -195,6 +198,9 @@ void bonsai_destroy(bonsai_ctx *ctx) {
     if (c.st_host) cudaFreeHost(c.st_host);
     for (int i = 0; i <= Ctx::NSTAGE; i++)
         if (c.ev[i]) cudaEventDestroy(c.ev[i]);
+    if (c.side) { cudaStreamSynchronize(c.side); cudaStreamDestroy(c.side); }
+    if (c.ev_fork) cudaEventDestroy(c.ev_fork);
+    if (c.ev_join) cudaEventDestroy(c.ev_join);
     if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
     delete ctx;
 }

@@ -7,8 +7,8 @@
 //   keys  u64[N] + sort ping-pong buffers, perm u32[N]
 //   cells (capacity C): body uint2 (begin, count), link uint2 (internal:
 //     child_begin, nchild; leaf: begin, count | LEAF_BIT), level u8,
-//     parent u32, done u32, mono float4 (com, M), quadA float4 (xx yy zz xy),
-//     quadB float2 (xz yz), test float4 (com, r_open), delta float
+//     parent u32, done u32, mono float4 (com, M), quadA float4 (-Q: xx yy zz xy),
+//     quadB float2 (-Q: xz yz), test float4 (com, r_open), delta float
 //   groups (capacity N): uint2 (begin, count)
 #pragma once
 #include <cuda_runtime.h>
@@ -61,8 +61,8 @@ struct DevState {
     unsigned ncells, ngroups;
     unsigned row_total[NROWS];        // cells per level, groups
     unsigned level_start[MAX_LEVEL + 2]; // first cell of each level; [22] = ncells
-    unsigned walk_next;               // group queue heads (groups <= 32 / 33..64 bodies)
-    unsigned walk_next2;
+    unsigned walk_next;               // group queue heads of the walk instantiations with
+    unsigned walk_next2;              // one and two bodies per lane
     unsigned status;
     unsigned long long inter[2];      // n_pc, n_pp totals of the last walk
     double diag[8];
@@ -78,6 +78,8 @@ struct Ctx {
     long long max_spin = 1ll << 24;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t side = nullptr;                     // forked from stream for concurrent walk launches
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = 0, num_sms = 0;
 
     // sizes

@@ -131,7 +131,7 @@ __global__ void k_moments_export(const DevState *__restrict__ st, const float4 *
     float2 d = qb[c];
     m[4 * (size_t)c] = a.x; m[4 * (size_t)c + 1] = a.y; m[4 * (size_t)c + 2] = a.z; m[4 * (size_t)c + 3] = a.w;
     float *o = q + 6 * (size_t)c;
-    o[0] = b.x; o[1] = b.y; o[2] = b.z; o[3] = b.w; o[4] = d.x; o[5] = d.y;
+    o[0] = -b.x; o[1] = -b.y; o[2] = -b.z; o[3] = -b.w; o[4] = -d.x; o[5] = -d.y;   // stored as -Q
 }
 
 cudaError_t launch_moments_export(Ctx &c, float *mono, float *quad) {

@@ -40,10 +40,12 @@ __device__ float2 cell_delta(unsigned long long k, int level, int sys, float3 co
 
 struct Mom32 { float M, x, y, z, q[6]; };
 
+// The quadrupole arrays hold -Q (negation is exact): the walk consumes it in
+// that form, parents and the export negate it back.
 __device__ __forceinline__ void store32(int c, const Mom32 &m, float4 *mono, float4 *qa, float2 *qb) {
     mono[c] = make_float4(m.x, m.y, m.z, m.M);
-    qa[c] = make_float4(m.q[0], m.q[1], m.q[2], m.q[3]);
-    qb[c] = make_float2(m.q[4], m.q[5]);
+    qa[c] = make_float4(-m.q[0], -m.q[1], -m.q[2], -m.q[3]);
+    qb[c] = make_float2(-m.q[4], -m.q[5]);
 }
 
 __global__ void __launch_bounds__(256)
@@ -115,8 +117,8 @@ k_multipoles(const DevState *__restrict__ stc, DevState *st, const uint2 *__rest
                     float4 mo = __ldcg(mono + cc), a = __ldcg(qa + cc);
                     float2 q2 = __ldcg(qb + cc);
                     ch[k][0] = mo.w; ch[k][1] = mo.x; ch[k][2] = mo.y; ch[k][3] = mo.z;
-                    ch[k][4] = a.x; ch[k][5] = a.y; ch[k][6] = a.z; ch[k][7] = a.w;
-                    ch[k][8] = q2.x; ch[k][9] = q2.y;
+                    ch[k][4] = -a.x; ch[k][5] = -a.y; ch[k][6] = -a.z; ch[k][7] = -a.w;
+                    ch[k][8] = -q2.x; ch[k][9] = -q2.y;
                 }
             }
             c0x = ch[0][1]; c0y = ch[0][2]; c0z = ch[0][3];
@@ -164,12 +166,12 @@ k_multipoles(const DevState *__restrict__ stc, DevState *st, const uint2 *__rest
                 float2 q2 = __ldcg(qb + cb + k);
                 float dx = mo.x - m.x, dy = mo.y - m.y, dz = mo.z - m.z;
                 float d2 = dx * dx + dy * dy + dz * dz;
-                m.q[0] += a.x + mo.w * (3.f * dx * dx - d2);
-                m.q[1] += a.y + mo.w * (3.f * dy * dy - d2);
-                m.q[2] += a.z + mo.w * (3.f * dz * dz - d2);
-                m.q[3] += a.w + mo.w * (3.f * dx * dy);
-                m.q[4] += q2.x + mo.w * (3.f * dx * dz);
-                m.q[5] += q2.y + mo.w * (3.f * dy * dz);
+                m.q[0] += -a.x + mo.w * (3.f * dx * dx - d2);
+                m.q[1] += -a.y + mo.w * (3.f * dy * dy - d2);
+                m.q[2] += -a.z + mo.w * (3.f * dz * dz - d2);
+                m.q[3] += -a.w + mo.w * (3.f * dx * dy);
+                m.q[4] += -q2.x + mo.w * (3.f * dx * dz);
+                m.q[5] += -q2.y + mo.w * (3.f * dy * dz);
             }
         }
         store32(c, m, mono, qa, qb);

@@ -25,7 +25,7 @@
 //    with Kahan compensation (one compensated add per tile and component).
 // Body-cell (monopole + traceless quadrupole, softened):
 //   d = com - x, r^2 = |d|^2 + eps^2, q = d.Q.d
-//   phi -= M/r + q/(2 r^5),  a += (M/r^3 + 5q/(2 r^7)) d - Q d / r^5
+//   phi -= M/r + q/(2 r^5),  a += ((M/r + 5q/(2 r^5)) / r^2) d - Q d / r^5
 // Body-body: a += m d / r^3, phi -= m / r.  The body's own term has d = 0
 // (zero force); its potential -m/eps is removed after the walk.
 #include "common.cuh"
@@ -42,8 +42,8 @@ constexpr int kWalkUnroll = WALK_UNROLL;
 // Rings in source-pair layout: pair k holds sources 2k (low half) and 2k+1
 // (high half) of two components per float4, so one 16-byte shared load
 // yields two packed (even, odd) operand pairs for the FP32x2 instructions.
-// Quadrupoles are staged negated, which turns every subtraction of the
-// body-cell formula into an addition (negation is exact).
+// Quadrupoles arrive negated from the cell arrays, which turns every
+// subtraction of the body-cell formula into an addition.
 struct WarpRings {
     float4 c0[RPAIR];   // x x' y y'
     float4 c1[RPAIR];   // z z' M M'
@@ -54,13 +54,14 @@ struct WarpRings {
     float4 b1[RPAIR];   //               z z' m m'
 };
 
+// qa, qb: -Q as stored in the cell arrays.
 __device__ __forceinline__ void put_cell(WarpRings &R, int s, const float4 mo, const float4 qa, const float2 qb) {
     const int k = s >> 1, h = s & 1;
     float *c0 = reinterpret_cast<float *>(&R.c0[k]) + h, *c1 = reinterpret_cast<float *>(&R.c1[k]) + h;
     float *c2 = reinterpret_cast<float *>(&R.c2[k]) + h, *c3 = reinterpret_cast<float *>(&R.c3[k]) + h;
     float *c4 = reinterpret_cast<float *>(&R.c4[k]) + h;
     c0[0] = mo.x; c0[2] = mo.y; c1[0] = mo.z; c1[2] = mo.w;
-    c2[0] = -qa.x; c2[2] = -qa.y; c3[0] = -qa.z; c3[2] = -qa.w; c4[0] = -qb.x; c4[2] = -qb.y;
+    c2[0] = qa.x; c2[2] = qa.y; c3[0] = qa.z; c3[2] = qa.w; c4[0] = qb.x; c4[2] = qb.y;
 }
 
 __device__ __forceinline__ void put_body(WarpRings &R, int s, const float4 p) {
@@ -96,11 +97,10 @@ __device__ __forceinline__ Me2 me2_of(const float4 me) {
     return Me2{make_float2(-me.x, -me.x), make_float2(-me.y, -me.y), make_float2(-me.z, -me.z)};
 }
 
-// Two body-cell interactions (sources 2k, 2k+1) of one body, element-wise
-// the same FP32 operations as the scalar formula:
+// Two body-cell interactions (sources 2k, 2k+1) of one body:
 //   d = com - x, r^2 = |d|^2 + eps^2, q = d.Q.d,
-//   phi -= M/r + q/(2 r^5),  a += (M/r^3 + 5q/(2 r^7)) d - Q d / r^5,
-// with -Q staged, so q and Q d arrive negated.
+//   phi -= M/r + q/(2 r^5),  a += ((M/r + 5q/(2 r^5)) / r^2) d - Q d / r^5,
+// with -Q staged, so q and Q d arrive negated (33 FP32 operations each).
 __device__ __forceinline__ void pc_two(const float4 v0, const float4 v1, const float4 v2, const float4 v3,
                                        const float4 v4, const Me2 &m, const float2 eps2, Part2 &P) {
     const float2 dx = __fadd2_rn(make_float2(v0.x, v0.y), m.nx);
@@ -110,7 +110,6 @@ __device__ __forceinline__ void pc_two(const float4 v0, const float4 v1, const f
     const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
     const float2 rinv2 = __fmul2_rn(rinv, rinv);
     const float2 mr = __fmul2_rn(make_float2(v1.z, v1.w), rinv);
-    const float2 mr3 = __fmul2_rn(mr, rinv2);
     const float2 nqxx = make_float2(v2.x, v2.y), nqyy = make_float2(v2.z, v2.w);
     const float2 nqzz = make_float2(v3.x, v3.y), nqxy = make_float2(v3.z, v3.w);
     const float2 nqxz = make_float2(v4.x, v4.y), nqyz = make_float2(v4.z, v4.w);
@@ -121,7 +120,7 @@ __device__ __forceinline__ void pc_two(const float4 v0, const float4 v1, const f
     const float2 rinv5 = __fmul2_rn(__fmul2_rn(rinv2, rinv2), rinv);
     const float2 qr5 = __fmul2_rn(q, rinv5);                                               // -q / r^5
     P.p = __fadd2_rn(P.p, __ffma2_rn(make_float2(-0.5f, -0.5f), qr5, mr));
-    const float2 sc = __ffma2_rn(__fmul2_rn(make_float2(-2.5f, -2.5f), qr5), rinv2, mr3);
+    const float2 sc = __fmul2_rn(__ffma2_rn(make_float2(-2.5f, -2.5f), qr5, mr), rinv2);   // (M/r + 5q/(2r^5)) / r^2
     P.x = __ffma2_rn(rinv5, qx, __ffma2_rn(sc, dx, P.x));
     P.y = __ffma2_rn(rinv5, qy, __ffma2_rn(sc, dy, P.y));
     P.z = __ffma2_rn(rinv5, qz, __ffma2_rn(sc, dz, P.z));
@@ -143,6 +142,8 @@ __device__ __forceinline__ void pp_two(const float4 v0, const float4 v1, const M
     P.z = __ffma2_rn(mr3, dz, P.z);
 }
 
+// Adds a tile's partial sums to the compensated accumulators (one Kahan add
+// per component).
 template <int BPL>
 __device__ __forceinline__ void commit(const Part2 (&P)[BPL], Acc (&A)[BPL]) {
 #pragma unroll
@@ -181,7 +182,6 @@ __device__ __forceinline__ void eval_pc(const WarpRings &R, int hp, int phase, c
     }
     commit<BPL>(P, A);
 }
-
 template <int NPH, int BPL>
 __device__ __forceinline__ void eval_pp(const WarpRings &R, int hp, int phase, const float4 (&me)[BPL],
                                         const float2 eps2, Acc (&A)[BPL]) {
@@ -204,30 +204,47 @@ __device__ __forceinline__ void eval_pp(const WarpRings &R, int hp, int phase, c
     commit<BPL>(P, A);
 }
 
-// Warp-uniform dispatch on log2(body slots) (>= 1: at most 16 phases share
-// the 16 source pairs); two bodies per lane always use all 32 lanes as slots.
+// Which instantiation walks a group of ng bodies: one body per lane up to
+// 32 bodies, two beyond.
+__host__ __device__ constexpr int walk_bpl(int ng) { return ng <= 32 ? 1 : 2; }
+
+// log2 of the body slots of a group: one body per lane, next power of two
+// (>= 2: at most 16 phases share the 16 source pairs); two bodies, 32.
+template <int BPL>
+__device__ __forceinline__ int walk_lg(int ng) {
+    if (BPL == 2) return 5;
+    return ng <= 2 ? 1 : 32 - __clz(ng - 1);
+}
+
+// Warp-uniform dispatch on log2(body slots).
 template <int BPL>
 __device__ __forceinline__ void tile_pc(int lg, const WarpRings &R, int hp, int phase, const float4 (&me)[BPL],
                                         const float2 eps2, Acc (&A)[BPL]) {
-    if (BPL == 2) { eval_pc<1, BPL>(R, hp, phase, me, eps2, A); return; }
-    switch (lg) {
-        case 1: eval_pc<16, BPL>(R, hp, phase, me, eps2, A); break;
-        case 2: eval_pc<8, BPL>(R, hp, phase, me, eps2, A); break;
-        case 3: eval_pc<4, BPL>(R, hp, phase, me, eps2, A); break;
-        case 4: eval_pc<2, BPL>(R, hp, phase, me, eps2, A); break;
-        default: eval_pc<1, BPL>(R, hp, phase, me, eps2, A); break;
+    if constexpr (BPL == 2) {
+        eval_pc<1, 2>(R, hp, phase, me, eps2, A);
+    } else {
+        switch (lg) {
+            case 1: eval_pc<16, 1>(R, hp, phase, me, eps2, A); break;
+            case 2: eval_pc<8, 1>(R, hp, phase, me, eps2, A); break;
+            case 3: eval_pc<4, 1>(R, hp, phase, me, eps2, A); break;
+            case 4: eval_pc<2, 1>(R, hp, phase, me, eps2, A); break;
+            default: eval_pc<1, 1>(R, hp, phase, me, eps2, A); break;
+        }
     }
 }
 template <int BPL>
 __device__ __forceinline__ void tile_pp(int lg, const WarpRings &R, int hp, int phase, const float4 (&me)[BPL],
                                         const float2 eps2, Acc (&A)[BPL]) {
-    if (BPL == 2) { eval_pp<1, BPL>(R, hp, phase, me, eps2, A); return; }
-    switch (lg) {
-        case 1: eval_pp<16, BPL>(R, hp, phase, me, eps2, A); break;
-        case 2: eval_pp<8, BPL>(R, hp, phase, me, eps2, A); break;
-        case 3: eval_pp<4, BPL>(R, hp, phase, me, eps2, A); break;
-        case 4: eval_pp<2, BPL>(R, hp, phase, me, eps2, A); break;
-        default: eval_pp<1, BPL>(R, hp, phase, me, eps2, A); break;
+    if constexpr (BPL == 2) {
+        eval_pp<1, 2>(R, hp, phase, me, eps2, A);
+    } else {
+        switch (lg) {
+            case 1: eval_pp<16, 1>(R, hp, phase, me, eps2, A); break;
+            case 2: eval_pp<8, 1>(R, hp, phase, me, eps2, A); break;
+            case 3: eval_pp<4, 1>(R, hp, phase, me, eps2, A); break;
+            case 4: eval_pp<2, 1>(R, hp, phase, me, eps2, A); break;
+            default: eval_pp<1, 1>(R, hp, phase, me, eps2, A); break;
+        }
     }
 }
 
@@ -240,7 +257,7 @@ __device__ __forceinline__ unsigned lanemask_lt_w() {
 // Level bins of accepted cells for the learned correction's features.
 __device__ __forceinline__ int level_bin(int lvl) { return lvl <= 3 ? 0 : lvl <= 6 ? 1 : lvl <= 9 ? 2 : 3; }
 
-// BPL = 1 walks the groups of <= 32 bodies, BPL = 2 those of 33..64.  FEAT
+// BPL: bodies per lane (walk_bpl picks the groups of each).  FEAT
 // also writes per body (12 floats) the walk quantities the learned far-field
 // correction uses: log(1 + accepted cells) in four level bins, log(1 +
 // body-body interactions), log(n_G / (extent^3 + eps^3)), log((diagonal +
@@ -258,7 +275,7 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
        const float4 *__restrict__ pos4, const float4 *__restrict__ test,
        const uint2 *__restrict__ link, const float4 *__restrict__ mono,
        const float4 *__restrict__ quadA, const float2 *__restrict__ quadB,
-       const uint8_t *__restrict__ sysid, float eps, int stack_cap, long long max_rounds,
+       const uint8_t *__restrict__ sysid, float eps, int stack_cap, unsigned max_rounds,
        float4 *acc4, uint2 *counts, const uint8_t *__restrict__ cell_level, float *feat,
        const unsigned *__restrict__ gate) {
     extern __shared__ float4 smem4[];
@@ -282,9 +299,9 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
         if (g >= ngroups) break;
         const uint2 gr = groups[g];
         const int gb = (int)gr.x, ng = (int)gr.y;
-        if ((BPL == 1) != (ng <= 32)) continue;      // the other instantiation's group
+        if (walk_bpl(ng) != BPL) continue;          // another instantiation's group
         // Body slots and source phases.
-        const int lg = BPL == 2 ? 5 : (ng <= 2 ? 1 : 32 - __clz(ng - 1));   // log2(next_pow2), >= 1
+        const int lg = walk_lg<BPL>(ng);
         const int slots = 1 << lg;
         const int bslot = lane & (slots - 1), phase = lane >> lg;
         bool live[BPL];
@@ -294,7 +311,7 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
         float bx1 = -INFINITY, by1 = -INFINITY, bz1 = -INFINITY;
 #pragma unroll
         for (int b = 0; b < BPL; b++) {
-            const int slot = bslot + 32 * b;
+            const int slot = bslot + slots * b;
             live[b] = slot < ng;
             bi[b] = gb + (live[b] ? slot : 0);
             me[b] = pos4[bi[b]];
@@ -323,7 +340,7 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
         unsigned npc = 0, npp = 0;
         unsigned nbin[4] = {0u, 0u, 0u, 0u};
         bool overflow = false, timeout = false;
-        long long rounds = 0;
+        unsigned rounds = 0;
         __syncwarp();
 
         while (sp > 0) {
@@ -343,13 +360,10 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
             const int T = __shfl_sync(0xffffffffu, incl, m - 1);
             const int excl = incl - cnt;
             sp -= m;
-            int e = 0;
-#pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                int cand = e + step;
-                int ex = __shfl_sync(0xffffffffu, excl, cand & 31);
-                if (cand < m && ex <= lane) e = cand;
-            }
+            // The popped entry that covers output lane: bit excl of every taken
+            // entry marks where its cells start (all distinct, < 32).
+            const unsigned starts = __reduce_or_sync(0xffffffffu, ((take >> lane) & 1u) ? (1u << excl) : 0u);
+            const int e = __popc(starts & (0xffffffffu >> (31 - lane))) - 1;
             const unsigned ent_e = __shfl_sync(0xffffffffu, ent, e);
             const int excl_e = __shfl_sync(0xffffffffu, excl, e);
             const bool has = lane < T;
@@ -484,7 +498,7 @@ size_t walk_smem_bytes(int warps, int stack_cap) {
 // Function attribute and occupancy are set up once per shape, before any
 // stream capture of a step (the first step always runs eagerly).
 template <int BPL, bool FEAT>
-static cudaError_t launch_walk_t(Ctx &c, float eps, const unsigned *gate) {
+static cudaError_t launch_walk_t(Ctx &c, float eps, const unsigned *gate, cudaStream_t stream) {
     const int warps = c.walk_warps;
     const size_t smem = walk_smem_bytes(warps, c.list_capacity);
     static size_t attr_smem = 0, occ_smem = 0;
@@ -500,16 +514,30 @@ static cudaError_t launch_walk_t(Ctx &c, float eps, const unsigned *gate) {
         if (e != cudaSuccess) return e;
         occ_warps = warps; occ_smem = smem; occ_per_sm = per < 1 ? 1 : per;
     }
-    k_walk<BPL, FEAT><<<c.num_sms * occ_per_sm, warps * 32, smem, c.stream>>>(
+    k_walk<BPL, FEAT><<<c.num_sms * occ_per_sm, warps * 32, smem, stream>>>(
         c.st, c.st, c.groups, c.pos4, c.test, c.cell_link, c.mono, c.quadA, c.quadB, c.sysid, eps,
-        c.list_capacity, c.max_spin, c.acc4, c.counts, c.cell_level, c.feat, gate);
+        c.list_capacity, (unsigned)(c.max_spin < 0xffffffffll ? c.max_spin : 0xffffffffll), c.acc4, c.counts,
+        c.cell_level, c.feat, gate);
     return cudaGetLastError();
 }
 
+// One persistent launch per instantiation that can receive groups (group
+// sizes are at most ncrit; oversize leaves are cut into chunks of ncrit).
+// With both, the two-body launch runs on a side stream forked from and
+// joined back into the context's stream (event edges inside a captured
+// step), so the tail of each launch overlaps the other's work.
 cudaError_t launch_walk(Ctx &c, float eps, bool features, const unsigned *gate) {
-    cudaError_t e = features ? launch_walk_t<1, true>(c, eps, gate) : launch_walk_t<1, false>(c, eps, gate);
-    if (e != cudaSuccess || c.ncrit <= 32) return e;
-    return features ? launch_walk_t<2, true>(c, eps, gate) : launch_walk_t<2, false>(c, eps, gate);
+    if (c.ncrit <= 32)
+        return features ? launch_walk_t<1, true>(c, eps, gate, c.stream) : launch_walk_t<1, false>(c, eps, gate, c.stream);
+    cudaError_t e = cudaEventRecord(c.ev_fork, c.stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c.side, c.ev_fork, 0);
+    if (e == cudaSuccess)
+        e = features ? launch_walk_t<2, true>(c, eps, gate, c.side) : launch_walk_t<2, false>(c, eps, gate, c.side);
+    if (e == cudaSuccess)
+        e = features ? launch_walk_t<1, true>(c, eps, gate, c.stream) : launch_walk_t<1, false>(c, eps, gate, c.stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c.ev_join, c.side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c.stream, c.ev_join, 0);
+    return e;
 }
 
 }  // namespace bonsai
