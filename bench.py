@@ -43,7 +43,7 @@ def kernels_per_step(ncrit):
     multipoles, open radius, walk (two instantiations when groups may exceed
     32 bodies), kick."""
     return 21 + (1 if ncrit > 32 else 0)
-WALK_TRAFFIC_PER_LAUNCH = 69.48e6  # dram bytes of the walk stage (both launches), profiles/k_walk_plummer_n2e20.md
+WALK_TRAFFIC_PER_LAUNCH = 67.15e6  # dram bytes of the walk stage (both launches), profiles/k_walk_plummer_n2e20.md
 
 
 def parse():
