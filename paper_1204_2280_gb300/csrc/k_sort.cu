@@ -150,18 +150,28 @@ k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restric
             st_volatile(my, FLAG_INC | tcount);
         } else {
             st_volatile(my, FLAG_AGG | tcount);
+            // Look back LB tiles per round trip (independent loads), then
+            // consume them in order: aggregates are added, an inclusive
+            // prefix ends the look-back, an unpublished tile is polled again.
+            constexpr int LB = 4;
             int j = tile - 1;
             long long spins = 0;
-            while (j >= 0) {
-                unsigned s = ld_volatile(status + (size_t)j * 256 + d);
-                unsigned f = s & ~VAL_MASK;
-                if (f == 0u) {
-                    if (++spins > max_spin) { atomicOr(&st->status, ST_TIMEOUT); break; }
-                    continue;
+            bool found = false;
+            while (!found) {
+                unsigned sv[LB];
+#pragma unroll
+                for (int q = 0; q < LB; q++)
+                    sv[q] = j - q >= 0 ? ld_volatile(status + (size_t)(j - q) * 256 + d) : FLAG_INC;
+                int q = 0;
+                for (; q < LB; q++) {
+                    const unsigned f = sv[q] & ~VAL_MASK;
+                    if (f == 0u) break;
+                    prefix += sv[q] & VAL_MASK;
+                    if (f == FLAG_INC) { found = true; break; }
                 }
-                prefix += s & VAL_MASK;
-                if (f == FLAG_INC) break;
-                j--;
+                if (found) break;
+                if (q == 0 && ++spins > max_spin) { atomicOr(&st->status, ST_TIMEOUT); break; }
+                j -= q;
             }
             st_volatile(my, FLAG_INC | ((prefix + tcount) & VAL_MASK));
         }
