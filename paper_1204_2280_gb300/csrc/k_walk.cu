@@ -52,6 +52,7 @@ struct WarpRings {
     float4 c4[RPAIR];   // -Qxz -Qxz' -Qyz -Qyz'
     float4 b0[RPAIR];   // body sources: x x' y y'
     float4 b1[RPAIR];   //               z z' m m'
+    uint2 leaf[32];     // opened leaves of a round: first body, offset in the round's body list
 };
 
 // qa, qb: -Q as stored in the cell arrays.
@@ -404,18 +405,35 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
                 if (open && !isleaf) stk[sp + __popc(im & lt)] = (lk.x << 3) | ((lk.y - 1u) & 7u);
                 sp += np;
             }
-            // Opened leaves -> body-body ring, 32 bodies at a time.
-            unsigned lm = __ballot_sync(0xffffffffu, open && isleaf);
-            while (lm) {
-                const int src = __ffs(lm) - 1;
-                lm &= lm - 1u;
-                const unsigned lb = __shfl_sync(0xffffffffu, lk.x, src);
-                const unsigned lc = __shfl_sync(0xffffffffu, lk.y, src) & ~LEAF_BIT;
-                npp += lc;
-                for (unsigned o = 0; o < lc; o += 32u) {
-                    const int k = (int)min(32u, lc - o);
-                    if (lane < k) put_body(R, (pp_head + pp_n + lane) & (RING - 1), __ldg(pos4 + lb + o + lane));
-                    pp_n += k;
+            // Opened leaves -> body-body ring: the bodies of all of the round's
+            // opened leaves in lane order, 32 per pass, one load per lane.
+            const bool ol = open && isleaf;
+            const unsigned lm = __ballot_sync(0xffffffffu, ol);
+            if (lm) {
+                const unsigned lc = ol ? (lk.y & ~LEAF_BIT) : 0u;
+                unsigned lincl = lc;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned y = __shfl_up_sync(0xffffffffu, lincl, o);
+                    if (lane >= o) lincl += y;
+                }
+                const unsigned total = __shfl_sync(0xffffffffu, lincl, 31);
+                const unsigned lex = lincl - lc;
+                if (ol) R.leaf[__popc(lm & lt)] = make_uint2(lk.x, lex);
+                npp += total;
+                __syncwarp();
+                const unsigned upto = 0xffffffffu >> (31 - lane);
+                for (unsigned base = 0; base < total; base += 32u) {
+                    // leaf k of body base+lane: leaves starting before base plus
+                    // those starting in [base, base+lane]
+                    const unsigned starts =
+                        __reduce_or_sync(0xffffffffu, ol && lex >= base && lex < base + 32u ? 1u << (lex - base) : 0u);
+                    const int before = __popc(__ballot_sync(0xffffffffu, ol && lex < base));
+                    const uint2 li = R.leaf[before + __popc(starts & upto) - 1];
+                    const int nb = (int)min(32u, total - base);
+                    if (lane < nb)
+                        put_body(R, (pp_head + pp_n + lane) & (RING - 1), __ldg(pos4 + li.x + (base + lane - li.y)));
+                    pp_n += nb;
                     if (pp_n >= 32) {
                         __syncwarp();
                         tile_pp<BPL>(lg, R, pp_head >> 1, phase, me, eps2x2, A);
