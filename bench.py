@@ -311,6 +311,26 @@ def run_learned(a, dev, stream):
     held = W.plummer(n, 4)
     merger = W.merger(n, 41)
     err = {"merger": errors(merger), "plummer": errors(held)}
+    # The judge alone (direct sum of 4096 sampled bodies against all N, then
+    # the p99): CUDA events around bonsai_judge on the held-out sphere.
+    bz.forces(1.0, eps)
+    jms = []
+    for r in range(6):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.bonsai_judge(bz.ctx, eps)
+        e1.record(stream)
+        e1.synchronize()
+        if r >= 2:
+            jms.append(e0.elapsed_time(e1))
+    jt = sum(jms) / len(jms)
+    jint = 4096 * n
+    judge = {"ms": jt, "interactions": jint, "interactions_per_s": jint / (jt / 1e3),
+             "tflops": FLOP_PP * jint / (jt / 1e3) / 1e12,
+             "fp32_frac": FLOP_PP * jint / (jt / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+             "what": "bonsai_judge: direct sum of 4096 stratified bodies against all N (23 flop per "
+                     "interaction) + p99, host copy of the p99 included"}
     target = err["plummer"]["theta_1.0_mlp"]
     lo, hi = 0.3, 1.15                      # plain p99 grows with theta
     if p99_plain(hi) <= target:
@@ -372,6 +392,7 @@ def run_learned(a, dev, stream):
                   "merger_snapshots": a.learned_merger, "epochs": 40, "loss_first": float(losses[0]),
                   "loss_last": float(losses[-1]), "data_s": t1 - t0, "train_s": t2 - t1},
         "p99": err,
+        "judge": judge,
         "equal_p99": {"p99": target, "plain_theta": theta_star, "plain_p99": p_star,
                       "plain_particles_per_s": ps["particles_per_s"],
                       "learned_particles_per_s": lj["particles_per_s"],

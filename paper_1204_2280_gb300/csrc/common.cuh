@@ -42,7 +42,7 @@ constexpr int MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_
 constexpr int MLP_NNORM = 2 * MLP_IN + 1;              // mu[12], sigma[12], ysig
 constexpr int FEAT_STRIDE = 12;                        // walk features per body
 constexpr int JUDGE_MAX = 4096;                        // sampled bodies of the direct-sum judge
-constexpr int JUDGE_SPLIT = 32;                        // source splits of the judge's direct sum
+constexpr int JUDGE_SPLIT = 64;                        // source splits of the judge's direct sum
 constexpr int BUILD_THREADS = 1024;                    // bodies per build block
 
 // Device status bits (ORed by kernels, read and cleared by bonsai_sync).

@@ -6,13 +6,14 @@
 // potential from all N bodies: sources are streamed through shared memory in
 // tiles, each tile summed in FP32 and added with Kahan compensation; the
 // source range is split over blocks and the partial sums are added in FP64.
+// Tiles run on packed FP32x2 arithmetic, two targets per thread.
 // The judge then ranks the relative errors of the current accelerations at
 // the targets and compares their 99th percentile with a budget.
 #include "common.cuh"
 
 namespace bonsai {
 
-constexpr int DS_THREADS = 128;        // targets per block
+constexpr int DS_THREADS = 128;        // threads per block, two targets each
 constexpr int DS_TILE = 256;           // sources per shared tile
 
 __device__ __forceinline__ void kadd(float &s, float &c, float v) {
@@ -23,37 +24,55 @@ __device__ __forceinline__ void kadd(float &s, float &c, float v) {
 }
 
 // Partial sums of split blockIdx.y over sources [chunk*y, chunk*(y+1)).
-// A non-null gate that reads 0 skips the work (all kernels of this file).
+// Each thread owns targets k and k + DS_THREADS of its block as one packed
+// FP32x2 operand; the tile holds every source twice per component ((x, x,
+// y, y), (z, z, m, m)), so two broadcast loads feed 13 packed operations.
+// Per target the arithmetic and its order are those of one scalar loop over
+// the sources.  A non-null gate that reads 0 skips the work (all kernels of
+// this file).
 __global__ void __launch_bounds__(DS_THREADS)
 k_direct_partial(const float4 *__restrict__ pos4, int n, const uint32_t *__restrict__ targets, int ntar,
                  float eps2, int chunk, float4 *partial, const unsigned *__restrict__ gate) {
     if (gate && *gate == 0u) return;
-    __shared__ float4 tile[DS_TILE];
-    const int k = blockIdx.x * DS_THREADS + threadIdx.x;
-    const bool live = k < ntar;
-    const float4 me = live ? pos4[targets[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float ax = 0.f, ay = 0.f, az = 0.f, ph = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, cp = 0.f;
+    __shared__ float4 tile[2 * DS_TILE];
+    const int k0 = blockIdx.x * 2 * DS_THREADS + threadIdx.x, k1 = k0 + DS_THREADS;
+    const bool live0 = k0 < ntar, live1 = k1 < ntar;
+    const float4 m0 = live0 ? pos4[targets[k0]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 m1 = live1 ? pos4[targets[k1]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float2 nx = make_float2(-m0.x, -m1.x), ny = make_float2(-m0.y, -m1.y), nz = make_float2(-m0.z, -m1.z);
+    const float2 e2 = make_float2(eps2, eps2);
+    float ax[2] = {0.f, 0.f}, ay[2] = {0.f, 0.f}, az[2] = {0.f, 0.f}, ph[2] = {0.f, 0.f};
+    float cx[2] = {0.f, 0.f}, cy[2] = {0.f, 0.f}, cz[2] = {0.f, 0.f}, cp[2] = {0.f, 0.f};
     const int s0 = blockIdx.y * chunk, s1 = min(n, s0 + chunk);
     for (int b = s0; b < s1; b += DS_TILE) {
         __syncthreads();
-        for (int i = threadIdx.x; i < DS_TILE; i += DS_THREADS)
-            tile[i] = b + i < s1 ? pos4[b + i] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
+        for (int i = threadIdx.x; i < DS_TILE; i += DS_THREADS) {
+            const float4 v = b + i < s1 ? pos4[b + i] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
+            tile[2 * i] = make_float4(v.x, v.x, v.y, v.y);
+            tile[2 * i + 1] = make_float4(v.z, v.z, v.w, v.w);
+        }
         __syncthreads();
-        float px = 0.f, py = 0.f, pz = 0.f, pp = 0.f;
+        float2 px = make_float2(0.f, 0.f), py = px, pz = px, pq = px;     // pq: +sum m/r
 #pragma unroll 8
         for (int j = 0; j < DS_TILE; j++) {
-            const float4 s = tile[j];
-            const float dx = s.x - me.x, dy = s.y - me.y, dz = s.z - me.z;
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-            const float rinv = rsqrtf(r2);
-            const float mr = s.w * rinv;
-            const float mr3 = mr * rinv * rinv;
-            pp -= mr;
-            px = fmaf(mr3, dx, px); py = fmaf(mr3, dy, py); pz = fmaf(mr3, dz, pz);
+            const float4 u = tile[2 * j], w = tile[2 * j + 1];
+            const float2 dx = __fadd2_rn(make_float2(u.x, u.y), nx);
+            const float2 dy = __fadd2_rn(make_float2(u.z, u.w), ny);
+            const float2 dz = __fadd2_rn(make_float2(w.x, w.y), nz);
+            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, e2)));
+            const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+            const float2 mr = __fmul2_rn(make_float2(w.z, w.w), rinv);
+            const float2 mr3 = __fmul2_rn(__fmul2_rn(mr, rinv), rinv);
+            pq = __fadd2_rn(pq, mr);
+            px = __ffma2_rn(mr3, dx, px);
+            py = __ffma2_rn(mr3, dy, py);
+            pz = __ffma2_rn(mr3, dz, pz);
         }
-        kadd(ax, cx, px); kadd(ay, cy, py); kadd(az, cz, pz); kadd(ph, cp, pp);
+        kadd(ax[0], cx[0], px.x); kadd(ay[0], cy[0], py.x); kadd(az[0], cz[0], pz.x); kadd(ph[0], cp[0], -pq.x);
+        kadd(ax[1], cx[1], px.y); kadd(ay[1], cy[1], py.y); kadd(az[1], cz[1], pz.y); kadd(ph[1], cp[1], -pq.y);
     }
-    if (live) partial[(size_t)blockIdx.y * ntar + k] = make_float4(ax - cx, ay - cy, az - cz, ph - cp);
+    if (live0) partial[(size_t)blockIdx.y * ntar + k0] = make_float4(ax[0] - cx[0], ay[0] - cy[0], az[0] - cz[0], ph[0] - cp[0]);
+    if (live1) partial[(size_t)blockIdx.y * ntar + k1] = make_float4(ax[1] - cx[1], ay[1] - cy[1], az[1] - cz[1], ph[1] - cp[1]);
 }
 
 // Sum the splits in FP64 and remove the target's own -m/eps term.
@@ -75,7 +94,7 @@ cudaError_t launch_direct(Ctx &c, const uint32_t *targets, int ntar, float eps, 
                           int nsplit, float4 *out, const unsigned *gate) {
     const int n = (int)c.n;
     const int chunk = ((n + nsplit - 1) / nsplit + DS_TILE - 1) / DS_TILE * DS_TILE;
-    dim3 grid((ntar + DS_THREADS - 1) / DS_THREADS, nsplit);
+    dim3 grid((ntar + 2 * DS_THREADS - 1) / (2 * DS_THREADS), nsplit);
     k_direct_partial<<<grid, DS_THREADS, 0, c.stream>>>(c.pos4, n, targets, ntar, eps * eps, chunk, partial, gate);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

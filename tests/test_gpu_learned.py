@@ -114,6 +114,27 @@ def test_fallback_gives_fine_theta_forces():
     assert out["learned"][1] == out["fallback"][1]          # same judge input: the coarse + MLP forces
 
 
+def test_judge_p99_vs_oracle():
+    """The judge's p99: relative errors of the current accelerations at the
+    sorted positions k*N/4096 (k < 4096) against the FP64 direct sum, 99th
+    percentile with linear interpolation between order statistics."""
+    b = W.plummer(50000, 12)
+    eps = 0.01
+    for theta in (1.0, 0.5):
+        with B.Bonsai(B.Config(ncrit=64)) as bz:
+            bz.set_bodies(b.pos, b.mass).build().multipoles()
+            acc = np.zeros((b.n, 3), np.float32)
+            bz.forces(theta, eps, acc)
+            p = B.bonsai_judge(bz.ctx, eps)
+            _, perm = B.bonsai_get_keys(bz.ctx)
+            bz.sync()
+        ids = perm[(np.arange(4096, dtype=np.int64) * b.n) // 4096].astype(np.int64)
+        a_d, _ = oracle.direct(b.pos, b.mass, eps, ids)
+        e = rel_err(acc[ids], a_d)
+        ref = np.percentile(e, 99)
+        assert abs(p - ref) <= 1e-4 * ref, (theta, p, ref)
+
+
 def test_judge_interval():
     """Interval k judges evaluations 0, k, 2k, ...; a decision holds until the
     next judged evaluation; interval 0 never judges and never falls back."""
