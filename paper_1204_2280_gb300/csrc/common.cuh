@@ -43,7 +43,10 @@ constexpr int MLP_NNORM = 2 * MLP_IN + 1;              // mu[12], sigma[12], ysi
 constexpr int FEAT_STRIDE = 12;                        // walk features per body
 constexpr int JUDGE_MAX = 4096;                        // sampled bodies of the direct-sum judge
 constexpr int JUDGE_SPLIT = 64;                        // source splits of the judge's direct sum
-constexpr int BUILD_THREADS = 1024;                    // bodies per build block
+#ifndef BUILD_THREADS_CFG
+#define BUILD_THREADS_CFG 1024
+#endif
+constexpr int BUILD_THREADS = BUILD_THREADS_CFG;       // bodies per build block (multiple of 32, <= 1024)
 
 // Device status bits (ORed by kernels, read and cleared by bonsai_sync).
 constexpr unsigned ST_CAPACITY = 1u;

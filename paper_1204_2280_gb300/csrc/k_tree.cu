@@ -217,8 +217,9 @@ k_build_count(const unsigned long long *__restrict__ sk, const uint8_t *__restri
     BodyCells bc = analyse_body(b, t, n, nleaf, ncrit, sk, system_end(st, sysid, t, n));
     int rlo, rhi;
     warp_level_range(bc, rlo, rhi);
-    for (int r = 0; r <= MAX_LEVEL; r++) {
-        unsigned m = (r >= rlo && r <= rhi) ? __ballot_sync(0xffffffffu, has_level(bc, r)) : 0u;
+    if (lane <= MAX_LEVEL && (lane < rlo || lane > rhi)) s_wc[lane][warp] = 0u;
+    for (int r = rlo; r <= rhi; r++) {
+        const unsigned m = __ballot_sync(0xffffffffu, has_level(bc, r));
         if (lane == 0) s_wc[r][warp] = __popc(m);
     }
     int g = bc.ngrp;
@@ -228,6 +229,7 @@ k_build_count(const unsigned long long *__restrict__ sk, const uint8_t *__restri
     __syncthreads();
     if (tid < NROWS) {
         unsigned s = 0;
+#pragma unroll 8
         for (int w = 0; w < BUILD_THREADS / 32; w++) s += s_wc[tid][w];
         blockcount[(size_t)tid * nblocks + blockIdx.x] = s;
     }
@@ -327,8 +329,9 @@ k_build_write(const unsigned long long *__restrict__ sk, const uint8_t *__restri
     int rlo, rhi;
     warp_level_range(bc, rlo, rhi);
 
-    for (int r = 0; r <= MAX_LEVEL; r++) {
-        unsigned m = (r >= rlo && r <= rhi) ? __ballot_sync(0xffffffffu, has_level(bc, r)) : 0u;
+    if (lane <= MAX_LEVEL && (lane < rlo || lane > rhi)) s_wc[lane][warp] = 0u;
+    for (int r = rlo; r <= rhi; r++) {
+        const unsigned m = __ballot_sync(0xffffffffu, has_level(bc, r));
         if (lane == 0) s_wc[r][warp] = __popc(m);
     }
     int gx = bc.ngrp;                            // inclusive warp scan of group counts
@@ -340,15 +343,16 @@ k_build_write(const unsigned long long *__restrict__ sk, const uint8_t *__restri
     if (lane == 31) s_wc[GROUP_ROW][warp] = (unsigned)gx;
     gx -= bc.ngrp;
     __syncthreads();
-    if (warp < NROWS) {                          // exclusive prefix across warps per row
-        unsigned v = s_wc[warp][lane], x = v;
+    constexpr int NW = BUILD_THREADS / 32;
+    for (int row = warp; row < NROWS; row += NW) {   // exclusive prefix across warps per row
+        unsigned v = lane < NW ? s_wc[row][lane] : 0u, x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             unsigned y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
         __syncwarp();
-        s_wc[warp][lane] = x - v;
+        if (lane < NW) s_wc[row][lane] = x - v;
     }
     __syncthreads();
 
