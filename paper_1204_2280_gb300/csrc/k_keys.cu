@@ -181,8 +181,66 @@ __global__ void k_kick_drift_bbox(const float4 *__restrict__ pos, const float4 *
     bbox_accumulate(x.x, x.y, x.z, i < n, i < n ? sysid[i] : 0, st);
 }
 
+// One system: grid-stride loop, running min/max per thread, one block
+// reduction and six atomics per block (no per-body system bookkeeping).
+__device__ __forceinline__ void block_bbox_atomics(float (&v)[6], DevState *st) {
+    __shared__ float red[6][8];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            v[d] = fminf(v[d], __shfl_xor_sync(0xffffffffu, v[d], o));
+            v[3 + d] = fmaxf(v[3 + d], __shfl_xor_sync(0xffffffffu, v[3 + d], o));
+        }
+    if (l == 0)
+#pragma unroll
+        for (int d = 0; d < 6; d++) red[d][w] = v[d];
+    __syncthreads();
+    if (w == 0) {
+        float r[6];
+#pragma unroll
+        for (int d = 0; d < 6; d++) {
+            r[d] = l < 8 ? red[d][l] : (d < 3 ? INFINITY : -INFINITY);
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+                const float q = __shfl_xor_sync(0xffffffffu, r[d], o);
+                r[d] = d < 3 ? fminf(r[d], q) : fmaxf(r[d], q);
+            }
+        }
+        if (l == 0) dom_atomics(st, 0, r);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_kick_drift_bbox1(const float4 *__restrict__ pos, const float4 *__restrict__ vel, const float4 *__restrict__ acc,
+                   const uint32_t *__restrict__ id, int n, float dt, float4 *pos_o, float4 *vel_o, uint32_t *id_o,
+                   DevState *st) {
+    float v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    bool bad = false;
+    const float h = 0.5f * dt;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float4 u = vel[i], x = pos[i];
+        const float4 a = acc[i];
+        u.x = fmaf(a.x, h, u.x); u.y = fmaf(a.y, h, u.y); u.z = fmaf(a.z, h, u.z);
+        x.x = fmaf(u.x, dt, x.x); x.y = fmaf(u.y, dt, x.y); x.z = fmaf(u.z, dt, x.z);
+        bad |= !(isfinite(x.x) && isfinite(x.y) && isfinite(x.z));
+        pos_o[i] = x; vel_o[i] = u; id_o[i] = id[i];
+        v[0] = fminf(v[0], x.x); v[1] = fminf(v[1], x.y); v[2] = fminf(v[2], x.z);
+        v[3] = fmaxf(v[3], x.x); v[4] = fmaxf(v[4], x.y); v[5] = fmaxf(v[5], x.z);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&st->status, ST_NAN);
+    block_bbox_atomics(v, st);
+}
+
 cudaError_t launch_kick_drift_bbox(Ctx &c, float dt) {
     int n = (int)c.n;
+    if (c.nsys == 1) {
+        const int grid = min((n + 255) / 256, c.num_sms * 8);
+        k_kick_drift_bbox1<<<grid, 256, 0, c.stream>>>(c.pos4, c.vel4, c.acc4, c.id, n, dt, c.pos4_alt,
+                                                        c.vel4_alt, c.id_alt, c.st);
+        return cudaGetLastError();
+    }
     k_kick_drift_bbox<<<(n + 255) / 256, 256, 0, c.stream>>>(c.pos4, c.vel4, c.acc4, c.id, c.sysid, n,
                                                              dt, c.pos4_alt, c.vel4_alt, c.id_alt, c.st);
     return cudaGetLastError();
