@@ -60,31 +60,32 @@ k_multipoles(const DevState *__restrict__ stc, DevState *st, const uint2 *__rest
     uint2 link = cell_link[c];
     if (!(link.y & LEAF_BIT)) return;
 
-    // Leaf from its bodies.
+    // Leaf from its bodies in one pass: mass, first and second moments of
+    // the offsets u = x - x0 from the first body; then with c = s/M the
+    // central moments C = S - s c^T and Q = 3C - tr(C) I.  The offsets are
+    // at most the cell size, so nothing cancels beyond FP32 rounding.
     unsigned b = link.x, cnt = link.y & ~LEAF_BIT;
     float4 x0 = pos4[b];
     float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+    float sxx = 0.f, syy = 0.f, szz = 0.f, sxy = 0.f, sxz = 0.f, syz = 0.f;
     for (unsigned j = b; j < b + cnt; j++) {
-        float4 p = pos4[j];
+        const float4 p = pos4[j];
+        const float ux = p.x - x0.x, uy = p.y - x0.y, uz = p.z - x0.z;
+        const float wx = p.w * ux, wy = p.w * uy, wz = p.w * uz;
         M += p.w;
-        sx = fmaf(p.w, p.x - x0.x, sx); sy = fmaf(p.w, p.y - x0.y, sy); sz = fmaf(p.w, p.z - x0.z, sz);
+        sx += wx; sy += wy; sz += wz;
+        sxx = fmaf(wx, ux, sxx); syy = fmaf(wy, uy, syy); szz = fmaf(wz, uz, szz);
+        sxy = fmaf(wx, uy, sxy); sxz = fmaf(wx, uz, sxz); syz = fmaf(wy, uz, syz);
     }
     Mom32 m;
     m.M = M;
-    float inv = M > 0.f ? 1.f / M : 0.f;
-    m.x = x0.x + sx * inv; m.y = x0.y + sy * inv; m.z = x0.z + sz * inv;
-    for (int k = 0; k < 6; k++) m.q[k] = 0.f;
-    for (unsigned j = b; j < b + cnt; j++) {
-        float4 p = pos4[j];
-        float yx = p.x - m.x, yy = p.y - m.y, yz = p.z - m.z;
-        float r2 = yx * yx + yy * yy + yz * yz;
-        m.q[0] += p.w * (3.f * yx * yx - r2);
-        m.q[1] += p.w * (3.f * yy * yy - r2);
-        m.q[2] += p.w * (3.f * yz * yz - r2);
-        m.q[3] += p.w * (3.f * yx * yy);
-        m.q[4] += p.w * (3.f * yx * yz);
-        m.q[5] += p.w * (3.f * yy * yz);
-    }
+    const float inv = M > 0.f ? 1.f / M : 0.f;
+    const float cx = sx * inv, cy = sy * inv, cz = sz * inv;
+    m.x = x0.x + cx; m.y = x0.y + cy; m.z = x0.z + cz;
+    const float Cxx = fmaf(-sx, cx, sxx), Cyy = fmaf(-sy, cy, syy), Czz = fmaf(-sz, cz, szz);
+    const float tr = Cxx + Cyy + Czz;
+    m.q[0] = 3.f * Cxx - tr; m.q[1] = 3.f * Cyy - tr; m.q[2] = 3.f * Czz - tr;
+    m.q[3] = 3.f * fmaf(-sx, cy, sxy); m.q[4] = 3.f * fmaf(-sx, cz, sxz); m.q[5] = 3.f * fmaf(-sy, cz, syz);
     int lev = cell_level[c];
     store32(c, m, mono, qa, qb);
     delta[c] = cell_delta(sk[b], lev, sysid[b], make_float3(m.x, m.y, m.z), stc);
