@@ -208,47 +208,61 @@ def run_reference(a, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_ensemble(a, dev, stream):
+def run_ensemble(a, dev, stream, rank=0, world=1):
     """Batched ensemble: independent Plummer spheres with N log-uniform in
     [2^12, 2^18] (seeds 100..), eps = 0.01, theta = 0.75, all stepped together
-    (one sort, one build, one persistent walk, one CUDA graph per step)."""
+    (one sort, one build, one persistent walk, one CUDA graph per step).
+    Under torchrun each rank steps a contiguous slice of the systems
+    (balanced by N log N, no collective in the data path); the job's time is
+    the maximum over ranks and its bodies the sum."""
     import numpy as np
     import torch
     import paper_1204_2280_gb300 as B
+    from paper_1204_2280_gb300 import dist as D
     from paper_1204_2280_gb300 import workloads as W
-    systems = W.ensemble(a.ensemble_systems, 100)
-    pos = np.concatenate([s.pos for s in systems])
-    vel = np.concatenate([s.vel for s in systems])
-    mass = np.concatenate([s.mass for s in systems])
-    off = np.cumsum([0] + [s.n for s in systems])
-    n = int(mass.shape[0])
+    everything = W.ensemble(a.ensemble_systems, 100)
+    lo, hi = D.shard_systems([s.n for s in everything], world, rank)
+    systems = everything[lo:hi]
     theta, eps, dt = 0.75, 0.01, a.dt
-    bz = B.Bonsai(B.Config(), stream=stream)
-    bz.set_bodies(torch.from_numpy(pos).to(dev), torch.from_numpy(mass).to(dev), torch.from_numpy(vel).to(dev))
-    bz.set_systems(off)
-    nc, w, _ = B.bonsai_autotune(bz.ctx, theta, eps)
-    B.bonsai_set_params(bz.ctx, theta, eps)
-    for _ in range(max(3, a.warmup)):
-        bz.step(dt)
-    bz.sync()
-    ms = []
-    for _ in range(a.steps):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        bz.step(dt)
-        e1.record(stream)
-        e1.synchronize()
-        ms.append(e0.elapsed_time(e1))
-    stages = B.bonsai_get_stage_times(bz.ctx)
-    bz.sync()
-    bz.close()
-    t = sum(ms) / len(ms)
-    return {"systems": len(systems), "n_total": n, "n_min": int(min(s.n for s in systems)),
-            "n_max": int(max(s.n for s in systems)), "ms_per_step": t, "particles_per_s": n / (t / 1e3),
+    ms, nc, w, stages, n = [], None, None, [0.0] * len(B.STAGES), 0
+    if systems:
+        pos = np.concatenate([s.pos for s in systems])
+        vel = np.concatenate([s.vel for s in systems])
+        mass = np.concatenate([s.mass for s in systems])
+        off = np.cumsum([0] + [s.n for s in systems])
+        n = int(mass.shape[0])
+        bz = B.Bonsai(B.Config(), stream=stream)
+        bz.set_bodies(torch.from_numpy(pos).to(dev), torch.from_numpy(mass).to(dev), torch.from_numpy(vel).to(dev))
+        bz.set_systems(off)
+        nc, w, _ = B.bonsai_autotune(bz.ctx, theta, eps)
+        B.bonsai_set_params(bz.ctx, theta, eps)
+        for _ in range(max(3, a.warmup)):
+            bz.step(dt)
+        bz.sync()
+    if world > 1:
+        torch.distributed.barrier()
+    if systems:
+        for _ in range(a.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bz.step(dt)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        stages = B.bonsai_get_stage_times(bz.ctx)
+        bz.sync()
+        bz.close()
+    total_ms, bodies = D.combine(sum(ms), float(n * a.steps))
+    t = total_ms / a.steps
+    return {"systems": len(everything), "n_total": int(sum(s.n for s in everything)),
+            "n_min": int(min(s.n for s in everything)), "n_max": int(max(s.n for s in everything)),
+            "ms_per_step": t, "particles_per_s": bodies / (total_ms / 1e3),
+            "ranks": world, "systems_rank0": [lo, hi] if rank == 0 else None,
             "ncrit": nc, "walk_warps": w, "theta": theta, "eps": eps,
-            "last_step_stages_ms": {k: float(v) for k, v in zip(B.STAGES, stages)},
-            "what": "all systems in one bonsai_step: one sort, one build, one persistent walk, one graph"}
+            "last_step_stages_ms_rank0": {k: float(v) for k, v in zip(B.STAGES, stages)},
+            "scaling": "strong (the 64 systems split over the ranks)",
+            "what": "all systems of a rank in one bonsai_step: one sort, one build, one persistent walk, one graph"}
 
 
 def run_learned(a, dev, stream):
@@ -554,10 +568,8 @@ def run_ours(a, rank, world, local_rank):
     clocks = sampler.stop()
     bz.sync()
     total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    from paper_1204_2280_gb300 import dist as D
+    total_ms, _ = D.combine(total_ms, float(n * a.steps))
     value = world * n * a.steps / (total_ms / 1e3)
     stages = np.array(stage_ms).sum(0)
     walk_ms = float(stages[B.STAGES.index("walk")])
@@ -584,7 +596,7 @@ def run_ours(a, rank, world, local_rank):
                "what": "set_bodies(host pos, mass, vel) + build + multipoles + forces(host acc, pot)"}
     bz.close()
 
-    ens = None if a.no_ensemble else run_ensemble(a, dev, stream)
+    ens = None if a.no_ensemble else run_ensemble(a, dev, stream, rank, world)
     lrn = None if a.no_learned else run_learned(a, dev, stream)
 
     cpu = None
