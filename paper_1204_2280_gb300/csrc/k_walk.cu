@@ -55,21 +55,30 @@ struct WarpRings {
     uint2 leaf[32];     // opened leaves of a round: first body, offset in the round's body list
 };
 
+// Staging into pair layout: component array i of a ring or tile starts at
+// base + i * STRIDE float4s; source s goes to pair s/2, half s%2.
 // qa, qb: -Q as stored in the cell arrays.
-__device__ __forceinline__ void put_cell(WarpRings &R, int s, const float4 mo, const float4 qa, const float2 qb) {
-    const int k = s >> 1, h = s & 1;
-    float *c0 = reinterpret_cast<float *>(&R.c0[k]) + h, *c1 = reinterpret_cast<float *>(&R.c1[k]) + h;
-    float *c2 = reinterpret_cast<float *>(&R.c2[k]) + h, *c3 = reinterpret_cast<float *>(&R.c3[k]) + h;
-    float *c4 = reinterpret_cast<float *>(&R.c4[k]) + h;
-    c0[0] = mo.x; c0[2] = mo.y; c1[0] = mo.z; c1[2] = mo.w;
-    c2[0] = qa.x; c2[2] = qa.y; c3[0] = qa.z; c3[2] = qa.w; c4[0] = qb.x; c4[2] = qb.y;
+template <int STRIDE>
+__device__ __forceinline__ void put_cell_at(float4 *base, int s, const float4 mo, const float4 qa, const float2 qb) {
+    float *f = reinterpret_cast<float *>(base + (s >> 1)) + (s & 1);
+    constexpr int C = 4 * STRIDE;               // floats between component arrays
+    f[0] = mo.x; f[2] = mo.y; f[C] = mo.z; f[C + 2] = mo.w;
+    f[2 * C] = qa.x; f[2 * C + 2] = qa.y; f[3 * C] = qa.z; f[3 * C + 2] = qa.w;
+    f[4 * C] = qb.x; f[4 * C + 2] = qb.y;
 }
 
-__device__ __forceinline__ void put_body(WarpRings &R, int s, const float4 p) {
-    const int k = s >> 1, h = s & 1;
-    float *b0 = reinterpret_cast<float *>(&R.b0[k]) + h, *b1 = reinterpret_cast<float *>(&R.b1[k]) + h;
-    b0[0] = p.x; b0[2] = p.y; b1[0] = p.z; b1[2] = p.w;
+template <int STRIDE>
+__device__ __forceinline__ void put_body_at(float4 *base, int s, const float4 p) {
+    float *f = reinterpret_cast<float *>(base + (s >> 1)) + (s & 1);
+    constexpr int C = 4 * STRIDE;
+    f[0] = p.x; f[2] = p.y; f[C] = p.z; f[C + 2] = p.w;
 }
+
+__device__ __forceinline__ void put_cell(WarpRings &R, int s, const float4 mo, const float4 qa, const float2 qb) {
+    put_cell_at<RPAIR>(R.c0, s, mo, qa, qb);
+}
+
+__device__ __forceinline__ void put_body(WarpRings &R, int s, const float4 p) { put_body_at<RPAIR>(R.b0, s, p); }
 
 __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
     float y = __fsub_rn(v, c);
@@ -162,11 +171,11 @@ __device__ __forceinline__ void commit(const Part2 (&P)[BPL], Acc (&A)[BPL]) {
 // immediate offsets and there is no per-interaction loop bookkeeping.  Each
 // lane holds BPL bodies that reuse every source read.  Partial tiles are
 // padded with massless sources far away, which add exactly zero.
-template <int NPH, int BPL>
-__device__ __forceinline__ void eval_pc(const WarpRings &R, int hp, int phase, const float4 (&me)[BPL],
+template <int NPH, int BPL, int STRIDE>
+__device__ __forceinline__ void eval_pc(const float4 *__restrict__ base, int phase, const float4 (&me)[BPL],
                                         const float2 eps2, Acc (&A)[BPL]) {
     constexpr int T = 16 / NPH;
-    const int k0 = hp + phase;
+    const int k0 = phase;
     Me2 m[BPL];
     Part2 P[BPL];
 #pragma unroll
@@ -177,17 +186,18 @@ __device__ __forceinline__ void eval_pc(const WarpRings &R, int hp, int phase, c
 #pragma unroll kWalkUnroll
     for (int j = 0; j < T; j++) {
         const int k = k0 + j * NPH;
-        const float4 v0 = R.c0[k], v1 = R.c1[k], v2 = R.c2[k], v3 = R.c3[k], v4 = R.c4[k];
+        const float4 v0 = base[k], v1 = base[STRIDE + k], v2 = base[2 * STRIDE + k],
+                     v3 = base[3 * STRIDE + k], v4 = base[4 * STRIDE + k];
 #pragma unroll
         for (int b = 0; b < BPL; b++) pc_two(v0, v1, v2, v3, v4, m[b], eps2, P[b]);
     }
     commit<BPL>(P, A);
 }
-template <int NPH, int BPL>
-__device__ __forceinline__ void eval_pp(const WarpRings &R, int hp, int phase, const float4 (&me)[BPL],
+template <int NPH, int BPL, int STRIDE>
+__device__ __forceinline__ void eval_pp(const float4 *__restrict__ base, int phase, const float4 (&me)[BPL],
                                         const float2 eps2, Acc (&A)[BPL]) {
     constexpr int T = 16 / NPH;
-    const int k0 = hp + phase;
+    const int k0 = phase;
     Me2 m[BPL];
     Part2 P[BPL];
 #pragma unroll
@@ -198,7 +208,7 @@ __device__ __forceinline__ void eval_pp(const WarpRings &R, int hp, int phase, c
 #pragma unroll kWalkUnroll
     for (int j = 0; j < T; j++) {
         const int k = k0 + j * NPH;
-        const float4 v0 = R.b0[k], v1 = R.b1[k];
+        const float4 v0 = base[k], v1 = base[STRIDE + k];
 #pragma unroll
         for (int b = 0; b < BPL; b++) pp_two(v0, v1, m[b], eps2, P[b]);
     }
@@ -218,33 +228,33 @@ __device__ __forceinline__ int walk_lg(int ng) {
 }
 
 // Warp-uniform dispatch on log2(body slots).
-template <int BPL>
-__device__ __forceinline__ void tile_pc(int lg, const WarpRings &R, int hp, int phase, const float4 (&me)[BPL],
+template <int BPL, int STRIDE>
+__device__ __forceinline__ void tile_pc(int lg, const float4 *__restrict__ base, int phase, const float4 (&me)[BPL],
                                         const float2 eps2, Acc (&A)[BPL]) {
     if constexpr (BPL == 2) {
-        eval_pc<1, 2>(R, hp, phase, me, eps2, A);
+        eval_pc<1, 2, STRIDE>(base, phase, me, eps2, A);
     } else {
         switch (lg) {
-            case 1: eval_pc<16, 1>(R, hp, phase, me, eps2, A); break;
-            case 2: eval_pc<8, 1>(R, hp, phase, me, eps2, A); break;
-            case 3: eval_pc<4, 1>(R, hp, phase, me, eps2, A); break;
-            case 4: eval_pc<2, 1>(R, hp, phase, me, eps2, A); break;
-            default: eval_pc<1, 1>(R, hp, phase, me, eps2, A); break;
+            case 1: eval_pc<16, 1, STRIDE>(base, phase, me, eps2, A); break;
+            case 2: eval_pc<8, 1, STRIDE>(base, phase, me, eps2, A); break;
+            case 3: eval_pc<4, 1, STRIDE>(base, phase, me, eps2, A); break;
+            case 4: eval_pc<2, 1, STRIDE>(base, phase, me, eps2, A); break;
+            default: eval_pc<1, 1, STRIDE>(base, phase, me, eps2, A); break;
         }
     }
 }
-template <int BPL>
-__device__ __forceinline__ void tile_pp(int lg, const WarpRings &R, int hp, int phase, const float4 (&me)[BPL],
+template <int BPL, int STRIDE>
+__device__ __forceinline__ void tile_pp(int lg, const float4 *__restrict__ base, int phase, const float4 (&me)[BPL],
                                         const float2 eps2, Acc (&A)[BPL]) {
     if constexpr (BPL == 2) {
-        eval_pp<1, 2>(R, hp, phase, me, eps2, A);
+        eval_pp<1, 2, STRIDE>(base, phase, me, eps2, A);
     } else {
         switch (lg) {
-            case 1: eval_pp<16, 1>(R, hp, phase, me, eps2, A); break;
-            case 2: eval_pp<8, 1>(R, hp, phase, me, eps2, A); break;
-            case 3: eval_pp<4, 1>(R, hp, phase, me, eps2, A); break;
-            case 4: eval_pp<2, 1>(R, hp, phase, me, eps2, A); break;
-            default: eval_pp<1, 1>(R, hp, phase, me, eps2, A); break;
+            case 1: eval_pp<16, 1, STRIDE>(base, phase, me, eps2, A); break;
+            case 2: eval_pp<8, 1, STRIDE>(base, phase, me, eps2, A); break;
+            case 3: eval_pp<4, 1, STRIDE>(base, phase, me, eps2, A); break;
+            case 4: eval_pp<2, 1, STRIDE>(base, phase, me, eps2, A); break;
+            default: eval_pp<1, 1, STRIDE>(base, phase, me, eps2, A); break;
         }
     }
 }
@@ -257,6 +267,33 @@ __device__ __forceinline__ unsigned lanemask_lt_w() {
 
 // Level bins of accepted cells for the learned correction's features.
 __device__ __forceinline__ int level_bin(int lvl) { return lvl <= 3 ? 0 : lvl <= 6 ? 1 : lvl <= 9 ? 2 : 3; }
+
+// Pops up to 32 cells (whole child ranges from the top of the stack), one
+// per lane: warp scan of the entries' child counts; the entry of each output
+// lane from one reduction of the entries' start offsets (bit excl of every
+// taken entry; all distinct, < 32).  Warp-uniform; requires sp > 0.
+__device__ __forceinline__ void walk_pop(const unsigned *stk, int &sp, int lane, unsigned &cell, bool &has) {
+    const int avail = min(sp, 32);
+    const unsigned ent = lane < avail ? stk[sp - 1 - lane] : 0u;
+    const int cnt = lane < avail ? (int)(ent & 7u) + 1 : 0;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const unsigned take = __ballot_sync(0xffffffffu, lane < avail && incl <= 32);
+    const int m = __popc(take);
+    const int T = __shfl_sync(0xffffffffu, incl, m - 1);
+    const int excl = incl - cnt;
+    sp -= m;
+    const unsigned starts = __reduce_or_sync(0xffffffffu, ((take >> lane) & 1u) ? (1u << excl) : 0u);
+    const int e = __popc(starts & (0xffffffffu >> (31 - lane))) - 1;
+    const unsigned ent_e = __shfl_sync(0xffffffffu, ent, e);
+    const int excl_e = __shfl_sync(0xffffffffu, excl, e);
+    has = lane < T;
+    cell = (ent_e >> 3) + (unsigned)(lane - excl_e);
+}
 
 // BPL: bodies per lane (walk_bpl picks the groups of each).  FEAT
 // also writes per body (12 floats) the walk quantities the learned far-field
@@ -346,29 +383,9 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
 
         while (sp > 0) {
             if (++rounds > max_rounds) { timeout = true; break; }   // bounded traversal
-            // Pop up to 32 cells from the top ranges.
-            const int avail = min(sp, 32);
-            const unsigned ent = lane < avail ? stk[sp - 1 - lane] : 0u;
-            const int cnt = lane < avail ? (int)(ent & 7u) + 1 : 0;
-            int incl = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            const unsigned take = __ballot_sync(0xffffffffu, lane < avail && incl <= 32);
-            const int m = __popc(take);
-            const int T = __shfl_sync(0xffffffffu, incl, m - 1);
-            const int excl = incl - cnt;
-            sp -= m;
-            // The popped entry that covers output lane: bit excl of every taken
-            // entry marks where its cells start (all distinct, < 32).
-            const unsigned starts = __reduce_or_sync(0xffffffffu, ((take >> lane) & 1u) ? (1u << excl) : 0u);
-            const int e = __popc(starts & (0xffffffffu >> (31 - lane))) - 1;
-            const unsigned ent_e = __shfl_sync(0xffffffffu, ent, e);
-            const int excl_e = __shfl_sync(0xffffffffu, excl, e);
-            const bool has = lane < T;
-            const unsigned cell = (ent_e >> 3) + (unsigned)(lane - excl_e);
+            unsigned cell;
+            bool has;
+            walk_pop(stk, sp, lane, cell, has);
 
             bool open = false, acc = false, isleaf = false;
             uint2 lk = make_uint2(0u, 0u);
@@ -436,7 +453,7 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
                     pp_n += nb;
                     if (pp_n >= 32) {
                         __syncwarp();
-                        tile_pp<BPL>(lg, R, pp_head >> 1, phase, me, eps2x2, A);
+                        tile_pp<BPL, RPAIR>(lg, R.b0 + (pp_head >> 1), phase, me, eps2x2, A);
                         __syncwarp();
                         pp_head = (pp_head + 32) & (RING - 1);
                         pp_n -= 32;
@@ -445,7 +462,7 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
             }
             __syncwarp();
             if (pc_n >= 32) {
-                tile_pc<BPL>(lg, R, pc_head >> 1, phase, me, eps2x2, A);
+                tile_pc<BPL, RPAIR>(lg, R.c0 + (pc_head >> 1), phase, me, eps2x2, A);
                 pc_head = (pc_head + 32) & (RING - 1);
                 pc_n -= 32;
             }
@@ -459,12 +476,12 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
             if (lane < 32 - pc_n)
                 put_cell(R, s, make_float4(FAR, FAR, FAR, 0.f), make_float4(0.f, 0.f, 0.f, 0.f), make_float2(0.f, 0.f));
             __syncwarp();
-            tile_pc<BPL>(lg, R, pc_head >> 1, phase, me, eps2x2, A);
+            tile_pc<BPL, RPAIR>(lg, R.c0 + (pc_head >> 1), phase, me, eps2x2, A);
         }
         if (pp_n > 0) {
             if (lane < 32 - pp_n) put_body(R, pp_head + pp_n + lane, make_float4(FAR, FAR, FAR, 0.f));
             __syncwarp();
-            tile_pp<BPL>(lg, R, pp_head >> 1, phase, me, eps2x2, A);
+            tile_pp<BPL, RPAIR>(lg, R.b0 + (pp_head >> 1), phase, me, eps2x2, A);
         }
 #pragma unroll
         for (int b = 0; b < BPL; b++) {
@@ -517,6 +534,7 @@ size_t walk_smem_bytes(int warps, int stack_cap) {
 // stream capture of a step (the first step always runs eagerly).
 template <int BPL, bool FEAT>
 static cudaError_t launch_walk_t(Ctx &c, float eps, const unsigned *gate, cudaStream_t stream) {
+    const unsigned polls = (unsigned)(c.max_spin < 0xffffffffll ? c.max_spin : 0xffffffffll);
     const int warps = c.walk_warps;
     const size_t smem = walk_smem_bytes(warps, c.list_capacity);
     static size_t attr_smem = 0, occ_smem = 0;
@@ -534,8 +552,7 @@ static cudaError_t launch_walk_t(Ctx &c, float eps, const unsigned *gate, cudaSt
     }
     k_walk<BPL, FEAT><<<c.num_sms * occ_per_sm, warps * 32, smem, stream>>>(
         c.st, c.st, c.groups, c.pos4, c.test, c.cell_link, c.mono, c.quadA, c.quadB, c.sysid, eps,
-        c.list_capacity, (unsigned)(c.max_spin < 0xffffffffll ? c.max_spin : 0xffffffffll), c.acc4, c.counts,
-        c.cell_level, c.feat, gate);
+        c.list_capacity, polls, c.acc4, c.counts, c.cell_level, c.feat, gate);
     return cudaGetLastError();
 }
 
