@@ -14,9 +14,14 @@ the walk kernel's algorithmic FP32 rate against the FP32 peak of 152 SMs x
 128 lanes x 2 flop x 2070 MHz; `cpu_baseline` = the FP64 oracle tree-code on
 a bounded sample of the same workload on the host cores.
 
-`--impl reference` times the FP64 oracle (the reference arm of this build) on
-the host cores instead.  Under torchrun each rank is an independent replica
-(no collective in the data path).
+The line also carries the batched ensemble (64 spheres, one pipeline per
+step; sharded over the ranks under torchrun) and the plain-vs-learned
+comparison at equal 99th-percentile force error on the N = 2^22 workload.
+`--sweep` prints per-stage scaling lines instead of the bench line.
+
+`--impl reference` times the FP64 oracle on the host cores instead (the
+reference arm: the method's paper publishes no code to run).  Under torchrun
+each rank is an independent replica (no collective in the data path).
 """
 from __future__ import annotations
 
