@@ -48,15 +48,13 @@ __device__ __forceinline__ void store32(int c, const Mom32 &m, float4 *mono, flo
     qb[c] = make_float2(-m.q[4], -m.q[5]);
 }
 
-__global__ void __launch_bounds__(256)
-k_multipoles(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__ cell_body,
-             const uint2 *__restrict__ cell_link, const uint8_t *__restrict__ cell_level,
-             const uint32_t *__restrict__ cell_parent, uint32_t *cell_done,
-             const float4 *__restrict__ pos4, const unsigned long long *__restrict__ sk,
-             const uint8_t *__restrict__ sysid, float4 *mono, float4 *qa, float2 *qb, float2 *delta,
-             double *shadow) {
-    unsigned c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= stc->ncells || (stc->status & ST_TIMEOUT)) return;
+__device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__restrict__ stc, DevState *st,
+                                               const uint2 *__restrict__ cell_body, const uint2 *__restrict__ cell_link,
+                                               const uint8_t *__restrict__ cell_level,
+                                               const uint32_t *__restrict__ cell_parent, uint32_t *cell_done,
+                                               const float4 *__restrict__ pos4, const unsigned long long *__restrict__ sk,
+                                               const uint8_t *__restrict__ sysid, float4 *mono, float4 *qa, float2 *qb,
+                                               float2 *delta, double *shadow) {
     uint2 link = cell_link[c];
     if (!(link.y & LEAF_BIT)) return;
 
@@ -181,8 +179,25 @@ k_multipoles(const DevState *__restrict__ stc, DevState *st, const uint2 *__rest
     }
 }
 
+// One thread per cell (leaves do the work): leaf moments from the bodies,
+// then up the tree while it is the last child to arrive.  A thread per cell
+// of the capacity keeps many climbs in flight; a grid-stride loop that
+// serialises them per thread measured twice as slow.
+__global__ void __launch_bounds__(256)
+k_multipoles(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__ cell_body,
+             const uint2 *__restrict__ cell_link, const uint8_t *__restrict__ cell_level,
+             const uint32_t *__restrict__ cell_parent, uint32_t *cell_done,
+             const float4 *__restrict__ pos4, const unsigned long long *__restrict__ sk,
+             const uint8_t *__restrict__ sysid, float4 *mono, float4 *qa, float2 *qb, float2 *delta,
+             double *shadow) {
+    const unsigned c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= stc->ncells || (stc->status & ST_TIMEOUT)) return;
+    multipole_cell(c, stc, st, cell_body, cell_link, cell_level, cell_parent, cell_done, pos4, sk, sysid, mono, qa, qb,
+                   delta, shadow);
+}
+
 cudaError_t launch_multipoles(Ctx &c) {
-    unsigned grid = (unsigned)((c.ccap + 255) / 256);
+    const unsigned grid = (unsigned)((c.ccap + 255) / 256);
     k_multipoles<<<grid, 256, 0, c.stream>>>(c.st, c.st, c.cell_body, c.cell_link, c.cell_level,
                                              c.cell_parent, c.cell_done, c.pos4, c.keys, c.sysid,
                                              c.mono, c.quadA, c.quadB, c.delta, c.shadow);
@@ -194,15 +209,17 @@ cudaError_t launch_multipoles(Ctx &c) {
 __global__ void k_open_radius(const DevState *__restrict__ st, const float4 *__restrict__ mono,
                               const float2 *__restrict__ delta, float inv_theta, float4 *test,
                               const unsigned *__restrict__ gate) {
-    unsigned c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= st->ncells || (gate && *gate == 0u)) return;
-    float4 m = mono[c];
-    float2 dl = delta[c];
-    test[c] = make_float4(m.x, m.y, m.z, fmaf(dl.y, inv_theta, dl.x));
+    if (gate && *gate == 0u) return;
+    const unsigned nc = st->ncells;
+    for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        const float4 m = mono[c];
+        const float2 dl = delta[c];
+        test[c] = make_float4(m.x, m.y, m.z, fmaf(dl.y, inv_theta, dl.x));
+    }
 }
 
 cudaError_t launch_open_radius(Ctx &c, float theta, const unsigned *gate) {
-    unsigned grid = (unsigned)((c.ccap + 255) / 256);
+    const unsigned grid = (unsigned)min((c.ccap + 255) / 256, (long long)c.num_sms * 8);
     k_open_radius<<<grid, 256, 0, c.stream>>>(c.st, c.mono, c.delta, 1.0f / theta, c.test, gate);
     return cudaGetLastError();
 }

@@ -393,14 +393,11 @@ k_build_write(const unsigned long long *__restrict__ sk, const uint8_t *__restri
     }
 }
 
-// Pass 4 (one thread per internal cell): child count from the cb of the next
-// cell of the same level, parent pointers of the children, and the body
-// count from the descent along last children to a leaf.
-__global__ void k_build_link(const DevState *__restrict__ st, const uint32_t *__restrict__ cell_cb,
-                             const uint8_t *__restrict__ cell_level, uint2 *cell_link,
-                             uint2 *cell_body, uint32_t *cell_parent) {
-    const unsigned c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= st->ncells || (st->status & ST_TIMEOUT)) return;
+// Child count, children's parent and body count of internal cell c.
+__device__ __forceinline__ void link_cell(unsigned c, const DevState *__restrict__ st,
+                                               const uint32_t *__restrict__ cell_cb,
+                                               const uint8_t *__restrict__ cell_level, uint2 *cell_link,
+                                               uint2 *cell_body, uint32_t *cell_parent) {
     if (cell_link[c].y & LEAF_BIT) return;
     auto nchild_of = [&](unsigned d, int l) {
         unsigned next = (d + 1 < st->level_start[l + 1]) ? cell_cb[d + 1] : st->level_start[l + 2];
@@ -423,6 +420,18 @@ __global__ void k_build_link(const DevState *__restrict__ st, const uint32_t *__
     cell_body[c].y = lk.x + (lk.y & ~LEAF_BIT) - t;
 }
 
+// Pass 4 (grid-stride over the cells, internal cells only): child count from the cb of the next
+// cell of the same level, parent pointers of the children, and the body
+// count from the descent along last children to a leaf.
+__global__ void k_build_link(const DevState *__restrict__ st, const uint32_t *__restrict__ cell_cb,
+                             const uint8_t *__restrict__ cell_level, uint2 *cell_link,
+                             uint2 *cell_body, uint32_t *cell_parent) {
+    if (st->status & ST_TIMEOUT) return;
+    const unsigned ncells = st->ncells;
+    for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x)
+        link_cell(c, st, cell_cb, cell_level, cell_link, cell_body, cell_parent);
+}
+
 cudaError_t launch_build(Ctx &c) {
     int n = (int)c.n;
     size_t smem = build_smem_bytes(c.nleaf, c.ncrit);
@@ -438,7 +447,7 @@ cudaError_t launch_build(Ctx &c) {
         c.cell_link, c.cell_level, c.cell_parent, c.cell_done, c.cell_cb, c.groups);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    unsigned grid = (unsigned)((c.ccap + 255) / 256);
+    const unsigned grid = (unsigned)min((c.ccap + 255) / 256, (long long)c.num_sms * 8);
     k_build_link<<<grid, 256, 0, c.stream>>>(c.st, c.cell_cb, c.cell_level, c.cell_link, c.cell_body,
                                              c.cell_parent);
     return cudaGetLastError();
