@@ -55,7 +55,7 @@ def lib():
             L.oracle_sort.argtypes = [p, i64, p]
             L.oracle_build.argtypes = [p, i64, C.c_int, i64, p, p, p, p, p, p]
             L.oracle_build.restype = i64
-            L.oracle_groups.argtypes = [i64, p, p, p, p, C.c_int, i64, p, p]
+            L.oracle_groups.argtypes = [i64, p, p, p, p, C.c_int, C.c_int, i64, p, p]
             L.oracle_groups.restype = i64
             L.oracle_moments.argtypes = [i64, p, p, p, p, p, p, p]
             L.oracle_open_radius.argtypes = [i64, p, p, p, p, d, p, d, p]
@@ -143,12 +143,15 @@ def build_tree(skeys, nleaf: int = 16) -> Tree:
     return Tree(*[a[:nc].copy() for a in arrs])
 
 
-def groups(tree: Tree, ncrit: int = 32) -> tuple[np.ndarray, np.ndarray]:
+def groups(tree: Tree, ncrit: int = 32, pack: bool = False) -> tuple[np.ndarray, np.ndarray]:
+    """Walk groups in key order (begin, count); pack: consecutive siblings
+    packed greedily up to ncrit bodies."""
     cap = int(tree.body_count[0]) + 64      # groups hold >= 1 body each
     gb = np.zeros(cap, np.int32)
     gc = np.zeros(cap, np.int32)
     ng = lib().oracle_groups(tree.ncells, _ptr(tree.body_begin), _ptr(tree.body_count),
-                             _ptr(tree.nchild), _ptr(tree.parent), ncrit, cap, _ptr(gb), _ptr(gc))
+                             _ptr(tree.nchild), _ptr(tree.parent), ncrit, int(bool(pack)), cap,
+                             _ptr(gb), _ptr(gc))
     if ng < 0:
         raise MemoryError("oracle_groups")
     return gb[:ng].copy(), gc[:ng].copy()
@@ -261,7 +264,7 @@ class TreeForces:
 
 
 def tree_forces(pos, mass, theta: float, eps: float, nleaf: int = 16, ncrit: int = 32,
-                tau_abs: float = 0.0, tau_rel: float = 0.0) -> TreeForces:
+                tau_abs: float = 0.0, tau_rel: float = 0.0, pack: bool = False) -> TreeForces:
     """Keys -> sort -> move -> build -> groups -> moments -> walk (FP64)."""
     pos, mass = _f32(pos), _f32(mass)
     mn, S = domain(pos)
@@ -270,7 +273,7 @@ def tree_forces(pos, mass, theta: float, eps: float, nleaf: int = 16, ncrit: int
     skeys = k[perm]
     spos, smass = pos[perm], mass[perm]
     tree = build_tree(skeys, nleaf)
-    gb, gc = groups(tree, ncrit)
+    gb, gc = groups(tree, ncrit, pack)
     M, com, Q = moments(tree, spos, smass)
     ro = open_radius(tree, skeys, mn, S, com, theta)
     acc_s, pot_s, npc_s, npp_s, flag_s, nb_s = walk(spos, smass, tree, M, com, Q, ro, gb, gc, eps,
@@ -287,7 +290,7 @@ def tree_forces(pos, mass, theta: float, eps: float, nleaf: int = 16, ncrit: int
 
 
 def kdk_step(pos, vel, mass, acc0, dt: float, theta: float, eps: float, nleaf: int = 16,
-             ncrit: int = 32):
+             ncrit: int = 32, pack: bool = False):
     """One kick-drift-kick leapfrog step (shared time step).  acc0 is the
     acceleration at the start; positions are rounded to float32 after the
     drift (the stored state is float32), everything else is float64.
@@ -297,6 +300,6 @@ def kdk_step(pos, vel, mass, acc0, dt: float, theta: float, eps: float, nleaf: i
     vh = vel + 0.5 * dt * np.asarray(acc0, np.float64)
     x1 = pos + dt * vh
     x1f = x1.astype(np.float32)
-    tf = tree_forces(x1f, mass, theta, eps, nleaf, ncrit)
+    tf = tree_forces(x1f, mass, theta, eps, nleaf, ncrit, pack=pack)
     v1 = vh + 0.5 * dt * tf.acc
     return x1, v1, tf.acc, tf.pot

@@ -209,38 +209,65 @@ int64_t oracle_build(const uint64_t *skeys, int64_t n, int nleaf, int64_t cap,
  * bodies whose parent holds more than ncrit (the root when n <= ncrit),
  * listed in key order.  A leaf with more than ncrit bodies (possible only for
  * identical keys at the deepest level, or ncrit < nleaf) is cut into
- * consecutive runs of ncrit bodies.  Returns the group count or -1. */
+ * consecutive runs of ncrit bodies.
+ *
+ * pack != 0 (sibling packing, a reading of ours: the paper fixes no group
+ * rule): the groups above are then taken in key order, and a group that is a
+ * sibling of the previous one (same parent cell) joins the packed group that
+ * the previous one belongs to if the sum stays within ncrit bodies; else it
+ * starts a new packed group.  The root group and the runs of an oversize
+ * leaf never join or absorb a neighbour.  Every packed group is then a run of
+ * consecutive children of one cell.  Returns the group count or -1. */
 int64_t oracle_groups(int64_t ncells, const int32_t *body_begin,
                       const int32_t *body_count, const int32_t *nchild,
-                      const int32_t *parent, int ncrit, int64_t cap,
+                      const int32_t *parent, int ncrit, int pack, int64_t cap,
                       int32_t *g_begin, int32_t *g_count)
 {
     int64_t ng = 0;
+    int32_t *g_par = (int32_t *)malloc(sizeof(int32_t) * (size_t)(cap > 0 ? cap : 1));
+    if (!g_par) return -1;
     for (int64_t c = 0; c < ncells; c++) {
         int is_group = 0;
         if (body_count[c] <= ncrit && (c == 0 || body_count[parent[c]] > ncrit))
             is_group = 1;
         if (is_group) {
-            if (ng >= cap) return -1;
-            g_begin[ng] = body_begin[c]; g_count[ng] = body_count[c]; ng++;
+            if (ng >= cap) { free(g_par); return -1; }
+            g_begin[ng] = body_begin[c]; g_count[ng] = body_count[c];
+            g_par[ng] = c == 0 ? -1 : parent[c];
+            ng++;
         } else if (nchild[c] == 0 && body_count[c] > ncrit) {
             for (int32_t o = 0; o < body_count[c]; o += ncrit) {
-                if (ng >= cap) return -1;
+                if (ng >= cap) { free(g_par); return -1; }
                 g_begin[ng] = body_begin[c] + o;
                 g_count[ng] = (body_count[c] - o < ncrit) ? body_count[c] - o : ncrit;
+                g_par[ng] = -1;
                 ng++;
             }
         }
     }
     /* key order = order of first body */
     for (int64_t i = 1; i < ng; i++) {           /* insertion sort, stable */
-        int32_t b = g_begin[i], k = g_count[i];
+        int32_t b = g_begin[i], k = g_count[i], q = g_par[i];
         int64_t j = i - 1;
         while (j >= 0 && g_begin[j] > b) {
-            g_begin[j + 1] = g_begin[j]; g_count[j + 1] = g_count[j]; j--;
+            g_begin[j + 1] = g_begin[j]; g_count[j + 1] = g_count[j]; g_par[j + 1] = g_par[j]; j--;
         }
-        g_begin[j + 1] = b; g_count[j + 1] = k;
+        g_begin[j + 1] = b; g_count[j + 1] = k; g_par[j + 1] = q;
     }
+    if (pack && ng > 0) {
+        int64_t out = 0;                         /* packed group being filled */
+        for (int64_t i = 1; i < ng; i++) {
+            int sibling = g_par[i] >= 0 && g_par[i] == g_par[i - 1];
+            if (sibling && g_count[out] + g_count[i] <= ncrit) {
+                g_count[out] += g_count[i];
+            } else {
+                out++;
+                g_begin[out] = g_begin[i]; g_count[out] = g_count[i];
+            }
+        }
+        ng = out + 1;
+    }
+    free(g_par);
     return ng;
 }
 

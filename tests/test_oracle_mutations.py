@@ -29,6 +29,8 @@ MUTATIONS = [
     ("double mr3 = mj * rinv * rinv * rinv;", "double mr3 = mj * rinv * rinv;"),
     ("if (body_count[c] <= ncrit && (c == 0 || body_count[parent[c]] > ncrit))",
      "if (body_count[c] <= ncrit && (c == 0 || body_count[parent[c]] >= ncrit))"),
+    ("int sibling = g_par[i] >= 0 && g_par[i] == g_par[i - 1];", "int sibling = g_par[i] >= 0;"),
+    ("if (sibling && g_count[out] + g_count[i] <= ncrit) {", "if (sibling && g_count[out] + g_count[i] < ncrit) {"),
 ]
 
 

@@ -121,3 +121,85 @@ def test_groups_definition(orc, ncrit):
     # groups partition the bodies in key order
     assert gb[0] == 0 and np.all(gb[1:] == gb[:-1] + gc[:-1]) and gb[-1] + gc[-1] == 3000
     assert np.all(gc <= ncrit) and np.all(gc >= 1)
+
+
+def _minimal_groups_brute(sk, nleaf, ncrit):
+    """Groups of the unpacked rule from the recursive tree, as
+    (begin, count, parent id or None) in key order."""
+    out = []
+
+    def rec(c, parent):
+        if c["c"] <= ncrit and (parent is None or parent["c"] > ncrit):
+            out.append((c["b"], c["c"], None if parent is None else id(parent)))
+            return
+        if not c["ch"] and c["c"] > ncrit:
+            for o in range(0, c["c"], ncrit):
+                out.append((c["b"] + o, min(ncrit, c["c"] - o), None))
+            return
+        for ch in c["ch"]:
+            rec(ch, c)
+
+    rec(brute_tree(sk, nleaf)[0], None)
+    return out
+
+
+@pytest.mark.parametrize("ncrit", [1, 8, 32, 64])
+@pytest.mark.parametrize("seed", [7, 8])
+def test_packed_groups_brute_force(orc, ncrit, seed):
+    """Sibling packing: walking the recursive tree's unpacked groups in key
+    order, a group joins the previous packed group when both come from the
+    same parent cell and the sum stays <= ncrit."""
+    sk = clustered_keys(np.random.default_rng(seed), 3000)
+    t = orc.build_tree(sk, 16)
+    gb, gc = orc.groups(t, ncrit, pack=True)
+    want = []
+    prev_parent = None
+    for b, c, par in _minimal_groups_brute(sk, 16, ncrit):
+        if want and par is not None and par == prev_parent and want[-1][1] + c <= ncrit:
+            want[-1][1] += c
+        else:
+            want.append([b, c])
+        prev_parent = par
+    assert [[int(a), int(b)] for a, b in zip(gb, gc)] == want
+
+
+@pytest.mark.parametrize("ncrit", [8, 32, 64])
+def test_packed_groups_invariants_plummer(orc, ncrit):
+    """Every packed group is a run of consecutive children of one cell, each
+    child within ncrit bodies; the groups partition the bodies in key order;
+    packing is greedy (a following sibling that would fit was not left out);
+    and packing only merges unpacked groups."""
+    n = 20000
+    b = W.plummer(n, 5)
+    k = orc.keys(b.pos)
+    sk = k[orc.sort(k)]
+    t = orc.build_tree(sk, 16)
+    g0b, g0c = orc.groups(t, ncrit)
+    gb, gc = orc.groups(t, ncrit, pack=True)
+    assert gb[0] == 0 and np.all(gb[1:] == gb[:-1] + gc[:-1]) and gb[-1] + gc[-1] == n
+    assert np.all(gc <= ncrit) and np.all(gc >= 1)
+    assert set(gb.tolist()) <= set(g0b.tolist())          # boundaries are unpacked boundaries
+    assert len(gb) < len(g0b)
+    # cell lookup by (begin, count): the shallowest such cell (a cell with one
+    # child has its child's range; BFS order lists the parent first)
+    cell = {}
+    for i, (bb, cc) in enumerate(zip(t.body_begin, t.body_count)):
+        cell.setdefault((int(bb), int(cc)), i)
+    par0 = np.array([t.parent[cell[(int(x), int(y))]] if (int(x), int(y)) in cell and cell[(int(x), int(y))] != 0
+                     else -1 for x, y in zip(g0b, g0c)])
+    start = {int(x): i for i, x in enumerate(g0b)}
+    for j, (x, y) in enumerate(zip(gb, gc)):
+        i0 = start[int(x)]
+        i1 = i0
+        while g0b[i1] + g0c[i1] < x + y:
+            i1 += 1
+        members = np.arange(i0, i1 + 1)
+        assert g0c[members].sum() == y
+        if len(members) > 1:                                # one parent, consecutive children
+            p = par0[members[0]]
+            assert p >= 0 and np.all(par0[members] == p)
+            kids = [cell[(int(g0b[m]), int(g0c[m]))] for m in members]
+            assert kids == list(range(kids[0], kids[0] + len(kids)))
+        nxt = i1 + 1                                        # greedy: the next sibling did not fit
+        if nxt < len(g0b) and par0[nxt] >= 0 and par0[nxt] == par0[i1]:
+            assert y + g0c[nxt] > ncrit

@@ -110,3 +110,21 @@ def test_own_leaf_always_opened(orc):
     for th in (0.3, 1.0, 1.15):
         tf = orc.tree_forces(b.pos, b.mass, th, 0.01, nleaf=4, ncrit=16)
         assert tf.n_pp.min() >= 0
+
+
+@pytest.mark.parametrize("ncrit", [16, 64])
+def test_packed_groups_walk_reduces_to_direct_sum(orc, ncrit):
+    """With sibling-packed groups the walk at theta -> 0 still opens every
+    cell, so it is the direct sum to rounding; at theta = 0.75 it meets the
+    direct-sum gates and takes fewer groups than the unpacked rule."""
+    b = W.plummer(3000, 12)
+    tf = orc.tree_forces(b.pos, b.mass, theta=1e-9, eps=0.01, nleaf=16, ncrit=ncrit, pack=True)
+    da, dp = orc.direct(b.pos, b.mass, 0.01)
+    assert np.abs(tf.acc - da).max() <= 1e-9 * np.abs(da).max()
+    assert np.abs(tf.pot - dp).max() <= 1e-9 * np.abs(dp).max()
+    assert np.all(tf.n_pp == 2999) and np.all(tf.n_pc == 0)
+    t75 = orc.tree_forces(b.pos, b.mass, 0.75, 0.01, 16, ncrit, pack=True)
+    u75 = orc.tree_forces(b.pos, b.mass, 0.75, 0.01, 16, ncrit)
+    e = np.linalg.norm(t75.acc - da, axis=1) / np.linalg.norm(da, axis=1)
+    assert np.median(e) <= 1e-3 and np.quantile(e, 0.99) <= 1e-2
+    assert len(t75.gbeg) < len(u75.gbeg)
