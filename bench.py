@@ -43,11 +43,11 @@ UNIT = "particles/s"
 FLOP_PC, FLOP_PP = 65, 23           # flops per body-cell / body-body interaction
 SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
-def kernels_per_step(ncrit):
-    """reset, kick+drift+bbox, domains, keys, 8 sort passes, reorder, 4 build,
-    multipoles, open radius, walk (two instantiations when groups may exceed
-    32 bodies), kick."""
-    return 21 + (1 if ncrit > 32 else 0)
+def kernels_per_step(ncrit, group_pack=0):
+    """reset, kick+drift+bbox, domains, keys, 8 sort passes, reorder, 4 build
+    (+2 for sibling packing of the groups), multipoles, open radius, walk (two
+    instantiations when groups may exceed 32 bodies), kick."""
+    return 21 + (1 if ncrit > 32 else 0) + (2 if group_pack else 0)
 WALK_TRAFFIC_PER_LAUNCH = 67.15e6  # dram bytes of the walk stage (both launches), profiles/k_walk_plummer_n2e20.md
 
 
@@ -65,6 +65,8 @@ def parse():
     p.add_argument("--ncrit", type=int, default=64)
     p.add_argument("--nleaf", type=int, default=16)
     p.add_argument("--walk-warps", type=int, default=4)
+    p.add_argument("--group-pack", type=int, default=0, choices=[0, 1],
+                   help="sibling-packed walk groups (with --no-autotune; the autotuner picks otherwise)")
     p.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -84,7 +86,8 @@ def config(a, world):
     return {"workload": f"Plummer sphere N={a.n} (Henon units, seed {a.seed}), eps={a.eps}, "
                         f"theta={a.theta}, KDK leapfrog dt={a.dt:g}, full rebuild every step",
             "n": a.n, "theta": a.theta, "eps": a.eps, "dt": a.dt, "nleaf": a.nleaf,
-            "ncrit": a.ncrit, "walk_warps": a.walk_warps, "l2": "flushed between timed steps (256 MiB write)",
+            "ncrit": a.ncrit, "walk_warps": a.walk_warps, "group_pack": a.group_pack,
+            "l2": "flushed between timed steps (256 MiB write)",
             "parallelism": f"replicas x{world}"}
 
 
@@ -163,7 +166,7 @@ def cpu_model() -> str:
     return f"{platform.machine()} implementer {impl} part {part}"
 
 
-def cpu_oracle_sample(bodies, theta, eps, nleaf, ncrit, budget_s, seed=0):
+def cpu_oracle_sample(bodies, theta, eps, nleaf, ncrit, budget_s, seed=0, pack=0):
     """FP64 oracle tree-code on a bounded sample, timed per stage: domain and
     keys, sort, tree build (+ groups), moments (+ opening radii) for all
     bodies; the walk for a random sample of groups (extrapolated to all
@@ -182,7 +185,7 @@ def cpu_oracle_sample(bodies, theta, eps, nleaf, ncrit, budget_s, seed=0):
     st["sort_reorder"] = time.perf_counter() - t
     t = time.perf_counter()
     tree = oracle.build_tree(sk, nleaf)
-    gb, gc = oracle.groups(tree, ncrit)
+    gb, gc = oracle.groups(tree, ncrit, pack)
     st["build"] = time.perf_counter() - t
     t = time.perf_counter()
     M, com, Q = oracle.moments(tree, sp, sm)
@@ -231,11 +234,11 @@ def run_reference(a, rank, world):
     b = W.plummer(a.n, a.seed)
     per_step = max(4.0, min(a.cpu_budget, 150.0 / max(1, a.steps + a.warmup)))
     for _ in range(a.warmup):
-        cpu_oracle_sample(b, a.theta, a.eps, a.nleaf, a.ncrit, per_step)
+        cpu_oracle_sample(b, a.theta, a.eps, a.nleaf, a.ncrit, per_step, pack=a.group_pack)
     ts = []
     samp = None
     for s in range(a.steps):
-        samp = cpu_oracle_sample(b, a.theta, a.eps, a.nleaf, a.ncrit, per_step, seed=s)
+        samp = cpu_oracle_sample(b, a.theta, a.eps, a.nleaf, a.ncrit, per_step, seed=s, pack=a.group_pack)
         ts.append(samp["t_step_s"])
     t = sum(ts)
     value = a.n * a.steps / t
@@ -265,7 +268,7 @@ def run_ensemble(a, dev, stream, rank=0, world=1):
     lo, hi = D.shard_systems([s.n for s in everything], world, rank)
     systems = everything[lo:hi]
     theta, eps, dt = 0.75, 0.01, a.dt
-    ms, nc, w, stages, n = [], None, None, [0.0] * len(B.STAGES), 0
+    ms, nc, w, pk, stages, n = [], None, None, None, [0.0] * len(B.STAGES), 0
     if systems:
         pos = np.concatenate([s.pos for s in systems])
         vel = np.concatenate([s.vel for s in systems])
@@ -276,6 +279,7 @@ def run_ensemble(a, dev, stream, rank=0, world=1):
         bz.set_bodies(torch.from_numpy(pos).to(dev), torch.from_numpy(mass).to(dev), torch.from_numpy(vel).to(dev))
         bz.set_systems(off)
         nc, w, _ = B.bonsai_autotune(bz.ctx, theta, eps)
+        pk = B.bonsai_get_config(bz.ctx).group_pack
         B.bonsai_set_params(bz.ctx, theta, eps)
         for _ in range(max(3, a.warmup)):
             bz.step(dt)
@@ -300,7 +304,7 @@ def run_ensemble(a, dev, stream, rank=0, world=1):
             "n_min": int(min(s.n for s in everything)), "n_max": int(max(s.n for s in everything)),
             "ms_per_step": t, "particles_per_s": bodies / (total_ms / 1e3),
             "ranks": world, "systems_rank0": [lo, hi] if rank == 0 else None,
-            "ncrit": nc, "walk_warps": w, "theta": theta, "eps": eps,
+            "ncrit": nc, "walk_warps": w, "group_pack": pk, "theta": theta, "eps": eps,
             "last_step_stages_ms_rank0": {k: float(v) for k, v in zip(B.STAGES, stages)},
             "scaling": "strong (the 64 systems split over the ranks)",
             "what": "all systems of a rank in one bonsai_step: one sort, one build, one persistent walk, one graph"}
@@ -497,7 +501,7 @@ def run_sweep(a, dev, stream):
     for n, seed, thetas in cases:
         b = W.plummer(n, seed)
         for theta in thetas:
-            bz = B.Bonsai(B.Config(nleaf=16, ncrit=64, walk_warps=8), stream=stream)
+            bz = B.Bonsai(B.Config(nleaf=16, ncrit=64, walk_warps=8, group_pack=a.group_pack), stream=stream)
             bz.set_bodies(torch.from_numpy(b.pos).to(dev), torch.from_numpy(b.mass).to(dev),
                           torch.from_numpy(b.vel).to(dev))
             bz.build().multipoles().forces(theta, eps)
@@ -566,11 +570,13 @@ def run_ours(a, rank, world, local_rank):
     torch.cuda.set_stream(stream)
     b = W.plummer(a.n, a.seed)
     n = b.n
-    bz = B.Bonsai(B.Config(nleaf=a.nleaf, ncrit=a.ncrit, walk_warps=a.walk_warps), stream=stream)
+    bz = B.Bonsai(B.Config(nleaf=a.nleaf, ncrit=a.ncrit, walk_warps=a.walk_warps, group_pack=a.group_pack),
+                  stream=stream)
     bz.set_bodies(torch.from_numpy(b.pos).to(dev), torch.from_numpy(b.mass).to(dev),
                   torch.from_numpy(b.vel).to(dev))
     if not a.no_autotune:
         a.ncrit, a.walk_warps, _ = B.bonsai_autotune(bz.ctx, a.theta, a.eps)
+        a.group_pack = B.bonsai_get_config(bz.ctx).group_pack
     else:
         bz.build().multipoles().forces(a.theta, a.eps)
     B.bonsai_set_params(bz.ctx, a.theta, a.eps)
@@ -642,7 +648,7 @@ def run_ours(a, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        cpu = cpu_oracle_sample(b, a.theta, a.eps, a.nleaf, a.ncrit, a.cpu_budget)
+        cpu = cpu_oracle_sample(b, a.theta, a.eps, a.nleaf, a.ncrit, a.cpu_budget, pack=a.group_pack)
         cpu.pop("t_step_s")
 
     if rank == 0:
@@ -658,7 +664,7 @@ def run_ours(a, rank, world, local_rank):
                          "flops_basis": f"{FLOP_PC} per body-cell + {FLOP_PP} per body-body interaction"},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": kernels_per_step(a.ncrit) * a.steps,
+            "gpu_launches": kernels_per_step(a.ncrit, a.group_pack) * a.steps,
             "clocks": clocks,
             "stages_ms_per_step": {s: float(v) / a.steps for s, v in zip(B.STAGES, stages)},
             "interactions_per_body": {"pc": sum(npc) / (n * a.steps), "pp": sum(npp) / (n * a.steps)},

@@ -56,7 +56,12 @@ typedef struct {
     int list_capacity;    /* walk stack entries per warp, 64..8192 (256)      */
     int use_graph;        /* -1: direct launches; else replay bonsai_step
                              from a CUDA graph (default)                      */
-    int reserved[3];
+    int group_pack;       /* walk groups: 0 = the cells with at most ncrit
+                             bodies whose parent holds more (default);
+                             1 = those groups with consecutive siblings (same
+                             parent cell) packed greedily, in key order, up
+                             to ncrit bodies per group                        */
+    int reserved[2];
     long long max_spin;   /* bound on every device-side wait, polls (1<<24)   */
 } bonsai_config;
 
@@ -115,13 +120,18 @@ int bonsai_forces(bonsai_ctx *ctx, float theta, float eps, float *acc,
 int bonsai_step(bonsai_ctx *ctx, float dt);
 
 /* Autotuner: times the walk of the current bodies (CUDA events, mean of two
- * walks after one untimed) for every group size ncrit in {16, 32, 48, 64}
- * and walk thread-block width in {2, 4, 8} warps, keeps the fastest pair in
- * the context (rebuilding the tree and groups for it) and leaves forces at
- * (theta, eps) computed.  Candidates that overflow the walk stack are
- * skipped.  Any output pointer may be NULL. */
+ * walks after one untimed) for every group size ncrit in {16, 32, 48, 64},
+ * both group rules (group_pack 0 and 1) and walk thread-block width in
+ * {2, 4, 8} warps, keeps the fastest choice in the context (rebuilding the
+ * tree and groups for it) and leaves forces at (theta, eps) computed.
+ * Candidates that overflow the walk stack are skipped.  Any output pointer
+ * may be NULL; bonsai_get_config reports the chosen group rule. */
 int bonsai_autotune(bonsai_ctx *ctx, float theta, float eps, int *best_ncrit,
                     int *best_warps, float *best_ms);
+
+/* The context's current tuning knobs (after defaults and any autotuning):
+ * every field of *out is filled in (reserved fields 0). */
+int bonsai_get_config(const bonsai_ctx *ctx, bonsai_config *out);
 
 /* Sets theta and eps for bonsai_step without computing forces. */
 int bonsai_set_params(bonsai_ctx *ctx, float theta, float eps);

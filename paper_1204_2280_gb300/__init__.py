@@ -34,7 +34,7 @@ EXPORTS = ["bonsai_create", "bonsai_destroy", "bonsai_set_bodies", "bonsai_build
            "bonsai_mlp_last_error", "bonsai_mlp_set_params", "bonsai_mlp_get_params",
            "bonsai_mlp_fit_norm", "bonsai_mlp_predict", "bonsai_mlp_grad", "bonsai_mlp_train",
            "bonsai_learn_samples", "bonsai_judge", "bonsai_set_learned", "bonsai_forces_learned",
-           "bonsai_get_judge", "bonsai_set_judge_interval"]
+           "bonsai_get_judge", "bonsai_set_judge_interval", "bonsai_get_config"]
 
 MLP_IN, MLP_H, MLP_OUT = 12, 64, 3
 MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_OUT * MLP_H + MLP_OUT
@@ -51,7 +51,8 @@ class BonsaiError(RuntimeError):
 
 class Config(C.Structure):
     _fields_ = [("nleaf", C.c_int), ("ncrit", C.c_int), ("walk_warps", C.c_int),
-                ("list_capacity", C.c_int), ("use_graph", C.c_int), ("reserved", C.c_int * 3),
+                ("list_capacity", C.c_int), ("use_graph", C.c_int), ("group_pack", C.c_int),
+                ("reserved", C.c_int * 2),
                 ("max_spin", C.c_longlong)]
 
 
@@ -95,6 +96,7 @@ def lib():
         L.bonsai_set_systems.argtypes = [p, p, i]
         L.bonsai_get_domains.argtypes = [p, p, p]
         L.bonsai_autotune.argtypes = [p, f, f, p, p, p]
+        L.bonsai_get_config.argtypes = [p, C.POINTER(Config)]
         u64 = C.c_ulonglong
         L.bonsai_mlp_create.argtypes = [C.POINTER(p), u64]
         L.bonsai_mlp_destroy.argtypes = [p]
@@ -202,6 +204,12 @@ def bonsai_autotune(ctx, theta: float, eps: float):
     nc, w, ms = C.c_int(), C.c_int(), C.c_float()
     _check(ctx, lib().bonsai_autotune(ctx, theta, eps, C.byref(nc), C.byref(w), C.byref(ms)))
     return nc.value, w.value, ms.value
+
+
+def bonsai_get_config(ctx) -> Config:
+    cfg = Config()
+    _check(ctx, lib().bonsai_get_config(ctx, C.byref(cfg)))
+    return cfg
 
 
 def bonsai_set_params(ctx, theta: float, eps: float):

@@ -77,7 +77,9 @@ cudaError_t alloc_bodies(Ctx &c, long long n) {
     a.take(c.mono, ccap, plan); a.take(c.quadA, ccap, plan); a.take(c.quadB, ccap, plan);
     a.take(c.test, ccap, plan); a.take(c.delta, ccap, plan);
     a.take(c.shadow, 10 * (size_t)(ccap < 585 * MAX_SYSTEMS ? ccap : 585 * MAX_SYSTEMS), plan);
-    a.take(c.groups, n, plan); a.take(c.counts, n, plan); a.take(c.feat, FEAT_STRIDE * (size_t)n, plan);
+    a.take(c.groups, n, plan); a.take(c.groups_raw, n, plan);
+    a.take(c.group_lvl, n, plan); a.take(c.group_flag, n, plan); a.take(c.group_bcount, (n + PACK_THREADS - 1) / PACK_THREADS, plan);
+    a.take(c.counts, n, plan); a.take(c.feat, FEAT_STRIDE * (size_t)n, plan);
     a.take(c.stage, 7 * (size_t)n, plan);
     a.take(c.judge_targets, JUDGE_MAX, plan); a.take(c.judge_direct, JUDGE_MAX, plan);
     a.take(c.judge_partial, (size_t)JUDGE_SPLIT * JUDGE_MAX, plan);
@@ -157,12 +159,14 @@ int bonsai_create(bonsai_ctx **out, const bonsai_config *cfg, void *cuda_stream)
         if (cfg->walk_warps) c.walk_warps = cfg->walk_warps;
         if (cfg->max_spin) c.max_spin = cfg->max_spin;
         if (cfg->use_graph < 0) c.use_graph = 0;
+        c.group_pack = cfg->group_pack;
     }
     if (c.nleaf < 1 || c.nleaf > 64 || c.ncrit < 1 || c.ncrit > 64 || c.list_capacity < 64 ||
-        c.list_capacity > 8192 || c.max_spin < 1 || c.walk_warps < 1 || c.walk_warps > 8) {
+        c.list_capacity > 8192 || c.max_spin < 1 || c.walk_warps < 1 || c.walk_warps > 8 ||
+        c.group_pack < 0 || c.group_pack > 1) {
         int r = fail(nullptr, BONSAI_ERR_INVALID_ARG,
                      "bonsai_create: need 1<=nleaf<=64, 1<=ncrit<=64, 64<=list_capacity<=8192, "
-                     "1<=walk_warps<=8");
+                     "1<=walk_warps<=8, group_pack 0 or 1");
         delete ctx;
         return r;
     }
@@ -401,10 +405,12 @@ int bonsai_autotune(bonsai_ctx *ctx, float theta, float eps, int *best_ncrit, in
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 1e30f;
-    int bn = c.ncrit, bw = c.walk_warps;
+    int bn = c.ncrit, bw = c.walk_warps, bp = c.group_pack;
     cudaError_t e = cudaSuccess;
-    for (int nc : ncrits) {
+    for (int cand = 0; cand < 8; cand++) {
+        const int nc = ncrits[cand & 3], pk = cand >> 2;
         c.ncrit = nc;
+        c.group_pack = pk;
         if ((r = bonsai_build(ctx)) || (r = bonsai_multipoles(ctx))) break;
         for (int w : warps) {
             c.walk_warps = w;
@@ -427,7 +433,7 @@ int bonsai_autotune(bonsai_ctx *ctx, float theta, float eps, int *best_ncrit, in
                 if ((e = cudaMemset(&c.st->status, 0, sizeof(unsigned))) != cudaSuccess) break;
                 continue;
             }
-            if (ms / 2 < best) { best = ms / 2; bn = nc; bw = w; }
+            if (ms / 2 < best) { best = ms / 2; bn = nc; bw = w; bp = pk; }
         }
         if (e != cudaSuccess) break;
     }
@@ -437,6 +443,7 @@ int bonsai_autotune(bonsai_ctx *ctx, float theta, float eps, int *best_ncrit, in
     if (e != cudaSuccess) return fail(ctx, BONSAI_ERR_CUDA, "bonsai_autotune", e);
     c.ncrit = bn;
     c.walk_warps = bw;
+    c.group_pack = bp;
     if (c.step_graph) { cudaGraphExecDestroy(c.step_graph); c.step_graph = nullptr; }
     c.graph_n = -1;
     if ((r = bonsai_build(ctx)) || (r = bonsai_multipoles(ctx)) ||
@@ -445,6 +452,20 @@ int bonsai_autotune(bonsai_ctx *ctx, float theta, float eps, int *best_ncrit, in
     if (best_ncrit) *best_ncrit = bn;
     if (best_warps) *best_warps = bw;
     if (best_ms) *best_ms = best;
+    return BONSAI_OK;
+}
+
+int bonsai_get_config(const bonsai_ctx *ctx, bonsai_config *out) {
+    if (!ctx || !out) return BONSAI_ERR_INVALID_ARG;
+    const Ctx &c = ctx->c;
+    std::memset(out, 0, sizeof(*out));
+    out->nleaf = c.nleaf;
+    out->ncrit = c.ncrit;
+    out->walk_warps = c.walk_warps;
+    out->list_capacity = c.list_capacity;
+    out->use_graph = c.use_graph ? 1 : -1;
+    out->group_pack = c.group_pack;
+    out->max_spin = c.max_spin;
     return BONSAI_OK;
 }
 

@@ -9,7 +9,8 @@
 //     child_begin, nchild; leaf: begin, count | LEAF_BIT), level u8,
 //     parent u32, done u32, mono float4 (com, M), quadA float4 (-Q: xx yy zz xy),
 //     quadB float2 (-Q: xz yz), test float4 (com, r_open), delta float
-//   groups (capacity N): uint2 (begin, count)
+//   groups (capacity N): uint2 (begin, count); with sibling packing the
+//     unpacked groups (uint2), their levels (u8) and start flags (u8) too
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -47,6 +48,7 @@ constexpr int JUDGE_SPLIT = 64;                        // source splits of the j
 #define BUILD_THREADS_CFG 1024
 #endif
 constexpr int BUILD_THREADS = BUILD_THREADS_CFG;       // bodies per build block (multiple of 32, <= 1024)
+constexpr int PACK_THREADS = 1024;                     // unpacked groups per group-packing block
 
 // Device status bits (ORed by kernels, read and cleared by bonsai_sync).
 constexpr unsigned ST_CAPACITY = 1u;
@@ -78,6 +80,7 @@ struct DevState {
 struct Ctx {
     // configuration
     int nleaf = 16, ncrit = 64, walk_warps = 4, list_capacity = 256, use_graph = 1;
+    int group_pack = 0;               // 1: consecutive sibling groups packed up to ncrit bodies
     long long max_spin = 1ll << 24;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -109,6 +112,12 @@ struct Ctx {
     float2 *delta = nullptr;         // per cell: (|com - centre|, side l)
     double *shadow = nullptr;        // FP64 moments of the top levels (10 per cell)
     uint2 *groups = nullptr;
+    // sibling packing (group_pack = 1): the unpacked groups, their cell level
+    // (0xff: a run of an oversize leaf), packed-group start flags, and the
+    // number of starts per packing block
+    uint2 *groups_raw = nullptr;
+    uint8_t *group_lvl = nullptr, *group_flag = nullptr;
+    unsigned *group_bcount = nullptr;
     uint2 *counts = nullptr;         // per body (n_pc, n_pp), sorted order
     float *feat = nullptr;           // per body FEAT_STRIDE walk features (learned correction), sorted order
     // staging for host transfers and caller-order outputs

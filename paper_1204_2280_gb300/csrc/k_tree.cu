@@ -287,7 +287,7 @@ k_build_write(const unsigned long long *__restrict__ sk, const uint8_t *__restri
               int nleaf, int ncrit, const unsigned *__restrict__ blockcount, int nblocks, long long ccap,
               DevState *st,
               uint2 *cell_body, uint2 *cell_link, uint8_t *cell_level, uint32_t *cell_parent,
-              uint32_t *cell_done, uint32_t *cell_cb, uint2 *groups) {
+              uint32_t *cell_done, uint32_t *cell_cb, uint2 *groups, uint8_t *group_lvl) {
     extern __shared__ unsigned long long smem_u64[];
     __shared__ unsigned s_wc[NROWS][32];
     __shared__ unsigned s_base[NROWS];
@@ -383,11 +383,13 @@ k_build_write(const unsigned long long *__restrict__ sk, const uint8_t *__restri
         if (bc.lg <= bc.hi) {
             int e = b.run_end_at(sk, send, t, bc.lg);
             groups[g] = make_uint2((unsigned)t, (unsigned)(e - t));
+            if (group_lvl) group_lvl[g] = (uint8_t)bc.lg;
         } else {
             int e = b.run_end_at(sk, send, t, bc.hi);
             for (int k = 0; k < bc.ngrp; k++) {
                 int b0 = t + k * ncrit;
                 groups[g + k] = make_uint2((unsigned)b0, (unsigned)min(ncrit, e - b0));
+                if (group_lvl) group_lvl[g + k] = 0xffu;
             }
         }
     }
@@ -432,6 +434,116 @@ __global__ void k_build_link(const DevState *__restrict__ st, const uint32_t *__
         link_cell(c, st, cell_cb, cell_level, cell_link, cell_body, cell_parent);
 }
 
+// ---- Sibling packing of the walk groups (group_pack = 1) -------------------
+// The unpacked groups (above, in key order) are taken in order; a group that
+// is a sibling of the previous one (both cells of one parent) joins the
+// packed group the previous one belongs to while the sum stays <= ncrit
+// bodies.  Siblings are consecutive in the list (a larger child in between
+// puts its own descendants' groups there), and a cell has at most 8 children,
+// so every decision looks at most 7 groups back.  Two launches: start flags
+// with a count per block, then the block prefix and the packed groups.
+// Whether unpacked group g (> 0) is a sibling of group g - 1: two cells of
+// the same level l >= 1 (neither the root group nor a run of an oversize
+// leaf, level 0xff) with the same level-(l-1) key prefix in the same system.
+__device__ __forceinline__ bool group_sibling(unsigned g, const uint2 *__restrict__ graw,
+                                              const uint8_t *__restrict__ glvl,
+                                              const unsigned long long *__restrict__ sk,
+                                              const uint8_t *__restrict__ sysid) {
+    if (g == 0) return false;
+    const int l = glvl[g];
+    if (l == 0 || l > MAX_LEVEL || glvl[g - 1] != l) return false;
+    const unsigned a = graw[g - 1].x, b = graw[g].x;
+    return sysid[a] == sysid[b] && key_prefix(sk[a], l - 1) == key_prefix(sk[b], l - 1);
+}
+
+__device__ __forceinline__ unsigned block_sum_1024(unsigned v, unsigned *s_w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = __reduce_add_sync(0xffffffffu, v);
+    if (lane == 0) s_w[warp] = v;
+    __syncthreads();
+    unsigned t = lane < (int)(blockDim.x >> 5) ? s_w[lane] : 0u;
+    t = __reduce_add_sync(0xffffffffu, t);
+    __syncthreads();
+    return t;
+}
+
+// Pass 1 (grid-stride over chunks of PACK_THREADS unpacked groups):
+// flag[g] = 1 iff group g starts a packed group (greedy from the first group
+// of its sibling run); bcount[chunk] = flags set in the chunk.
+__global__ void __launch_bounds__(PACK_THREADS)
+k_group_mark(const DevState *__restrict__ st, const uint2 *__restrict__ graw, const uint8_t *__restrict__ glvl,
+             const unsigned long long *__restrict__ sk, const uint8_t *__restrict__ sysid, int ncrit,
+             uint8_t *gflag, unsigned *bcount) {
+    if (st->status & ST_TIMEOUT) return;
+    const unsigned ng = st->row_total[GROUP_ROW];
+    const unsigned nchunk = (ng + PACK_THREADS - 1) / PACK_THREADS;
+    for (unsigned ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
+        const unsigned g = ch * PACK_THREADS + threadIdx.x;
+        bool start = false;
+        if (g < ng) {
+            unsigned s = g;
+            for (int k = 0; k < 8 && group_sibling(s, graw, glvl, sk, sysid); k++) s--;
+            unsigned acc = graw[s].y;
+            start = true;
+            for (unsigned j = s + 1; j <= g; j++) {
+                const unsigned cj = graw[j].y;
+                start = acc + cj > (unsigned)ncrit;
+                acc = start ? cj : acc + cj;
+            }
+            gflag[g] = start ? 1u : 0u;
+        }
+        const int cnt = __syncthreads_count(start);
+        if (threadIdx.x == 0) bcount[ch] = (unsigned)cnt;
+    }
+}
+
+// Pass 2 (same chunks): packed group index = flags set before g (chunks
+// before this one, then a block scan); a start writes (first body, bodies up
+// to the next start).  Block 0 also stores the packed group count.
+__global__ void __launch_bounds__(PACK_THREADS)
+k_group_pack(DevState *st, const uint2 *__restrict__ graw, const uint8_t *__restrict__ gflag,
+             const unsigned *__restrict__ bcount, uint2 *groups) {
+    __shared__ unsigned s_w[32];
+    if (st->status & ST_TIMEOUT) return;
+    const unsigned ng = st->row_total[GROUP_ROW];
+    const unsigned nchunk = (ng + PACK_THREADS - 1) / PACK_THREADS;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (blockIdx.x == 0) {
+        unsigned v = 0;
+        for (unsigned i = threadIdx.x; i < nchunk; i += PACK_THREADS) v += bcount[i];
+        const unsigned tot = block_sum_1024(v, s_w);
+        if (threadIdx.x == 0) st->ngroups = tot;
+    }
+    for (unsigned ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
+        unsigned v = 0;
+        for (unsigned i = threadIdx.x; i < ch; i += PACK_THREADS) v += bcount[i];
+        const unsigned base = block_sum_1024(v, s_w);
+        const unsigned g = ch * PACK_THREADS + threadIdx.x;
+        const unsigned f = g < ng ? gflag[g] : 0u;
+        const unsigned m = __ballot_sync(0xffffffffu, f != 0u);
+        if (lane == 0) s_w[warp] = __popc(m);
+        __syncthreads();
+        if (warp == 0) {                          // exclusive scan of the warp counts
+            const unsigned w = s_w[lane];
+            unsigned x = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            s_w[lane] = x - w;
+        }
+        __syncthreads();
+        if (f) {
+            const unsigned idx = base + s_w[warp] + __popc(m & ((1u << lane) - 1u));
+            unsigned cnt = graw[g].y, j = g + 1;
+            for (int k = 0; k < 8 && j < ng && gflag[j] == 0u; k++, j++) cnt += graw[j].y;
+            groups[idx] = make_uint2(graw[g].x, cnt);
+        }
+        __syncthreads();                          // s_w is reused by the next chunk
+    }
+}
+
 cudaError_t launch_build(Ctx &c) {
     int n = (int)c.n;
     size_t smem = build_smem_bytes(c.nleaf, c.ncrit);
@@ -442,11 +554,23 @@ cudaError_t launch_build(Ctx &c) {
     k_build_scan<<<NROWS, 1024, 0, c.stream>>>(c.blockcount, c.nbblocks, c.st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    const bool pack = c.group_pack != 0;
     k_build_write<<<c.nbblocks, BUILD_THREADS, smem, c.stream>>>(
         c.keys, c.sysid, n, c.nleaf, c.ncrit, c.blockcount, c.nbblocks, c.ccap, c.st, c.cell_body,
-        c.cell_link, c.cell_level, c.cell_parent, c.cell_done, c.cell_cb, c.groups);
+        c.cell_link, c.cell_level, c.cell_parent, c.cell_done, c.cell_cb, pack ? c.groups_raw : c.groups,
+        pack ? c.group_lvl : nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (pack) {
+        // at most n unpacked groups: chunks of PACK_THREADS, two blocks per SM
+        const unsigned pb = (unsigned)min((long long)(n + PACK_THREADS - 1) / PACK_THREADS, 2ll * c.num_sms);
+        k_group_mark<<<pb, PACK_THREADS, 0, c.stream>>>(c.st, c.groups_raw, c.group_lvl, c.keys, c.sysid,
+                                                         c.ncrit, c.group_flag, c.group_bcount);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_group_pack<<<pb, PACK_THREADS, 0, c.stream>>>(c.st, c.groups_raw, c.group_flag, c.group_bcount,
+                                                         c.groups);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     const unsigned grid = (unsigned)min((c.ccap + 255) / 256, (long long)c.num_sms * 8);
     k_build_link<<<grid, 256, 0, c.stream>>>(c.st, c.cell_cb, c.cell_level, c.cell_link, c.cell_body,
                                              c.cell_parent);

@@ -1,6 +1,7 @@
-"""The autotuner picks a (group size, walk block width) pair by timing the
-walk; the tuned context must compute exactly what a context configured with
-that pair by hand computes (the block width never changes the arithmetic)."""
+"""The autotuner picks a group size, a group rule (sibling packing or not)
+and a walk block width by timing the walk; the tuned context must compute
+exactly what a context configured with that choice by hand computes (the
+block width never changes the arithmetic)."""
 import numpy as np
 import pytest
 
@@ -23,10 +24,12 @@ def test_autotune_result_is_consistent():
         bz.set_bodies(b.pos, b.mass, b.vel)
         nc, w, ms = B.bonsai_autotune(bz.ctx, 0.75, 0.01)
         assert nc in (16, 32, 48, 64) and w in (2, 4, 8) and ms > 0
+        cfg = B.bonsai_get_config(bz.ctx)
+        assert (cfg.ncrit, cfg.walk_warps) == (nc, w) and cfg.group_pack in (0, 1)
         a1, p1 = forces(bz, b.n)
         bz.step(1.0 / 64)
         bz.sync()
-    with B.Bonsai(B.Config(ncrit=nc, walk_warps=w)) as bz:
+    with B.Bonsai(B.Config(ncrit=nc, walk_warps=w, group_pack=cfg.group_pack)) as bz:
         bz.set_bodies(b.pos, b.mass, b.vel).build().multipoles()
         a2, p2 = forces(bz, b.n)
     assert np.array_equal(a1, a2) and np.array_equal(p1, p2)

@@ -30,10 +30,10 @@ def concat(systems):
     return pos, vel, mass, off
 
 
-def run(pos, mass, vel, off, ncrit=32, nleaf=16, theta=0.75, eps=0.01, steps=0, dt=1.0 / 64):
+def run(pos, mass, vel, off, ncrit=32, nleaf=16, theta=0.75, eps=0.01, steps=0, dt=1.0 / 64, pack=0):
     out = {}
     n = mass.shape[0]
-    with B.Bonsai(B.Config(nleaf=nleaf, ncrit=ncrit)) as bz:
+    with B.Bonsai(B.Config(nleaf=nleaf, ncrit=ncrit, group_pack=pack)) as bz:
         bz.set_bodies(pos, mass, vel)
         if off is not None:
             bz.set_systems(off)
@@ -78,14 +78,21 @@ def small_ensemble():
     return systems
 
 
-@pytest.mark.parametrize("ncrit", [32, 64])
-def test_ensemble_equals_separate_runs_bit_for_bit(ncrit):
+@pytest.mark.parametrize("ncrit,pack", [(32, 0), (64, 0), (64, 1)])
+def test_ensemble_equals_separate_runs_bit_for_bit(ncrit, pack):
+    """Also with sibling-packed groups: packing never joins groups of two
+    systems, and each system's packed groups are the oracle's."""
     systems = small_ensemble()
     pos, vel, mass, off = concat(systems)
-    ens = run(pos, mass, vel, off, ncrit=ncrit, steps=2)
+    ens = run(pos, mass, vel, off, ncrit=ncrit, steps=2, pack=pack)
     for s, sysb in enumerate(systems):
         lo, hi = off[s], off[s + 1]
-        one = run(sysb.pos, sysb.mass, sysb.vel, None, ncrit=ncrit, steps=2)
+        one = run(sysb.pos, sysb.mass, sysb.vel, None, ncrit=ncrit, steps=2, pack=pack)
+        if pack:
+            k = oracle.keys(sysb.pos)
+            tr = oracle.build_tree(k[oracle.sort(k)], 16)
+            ob, oc = oracle.groups(tr, ncrit, pack=True)
+            assert np.array_equal(one["groups"][0], ob) and np.array_equal(one["groups"][1], oc)
         assert np.array_equal(ens["keys"][lo:hi], one["keys"])
         assert np.array_equal(ens["perm"][lo:hi] - lo, one["perm"])
         t = system_cells(ens["tree"], lo, hi)

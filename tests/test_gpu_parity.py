@@ -27,7 +27,7 @@ pytestmark = pytest.mark.gpu
 TAU_ABS, TAU_REL = 2e-6, 1e-6
 
 
-def check_keys_tree(res, pos, nleaf, ncrit):
+def check_keys_tree(res, pos, nleaf, ncrit, pack=False):
     mn, S = oracle.domain(pos)
     k = oracle.keys(pos, mn, S)
     perm = oracle.sort(k)
@@ -40,7 +40,7 @@ def check_keys_tree(res, pos, nleaf, ncrit):
     assert g["body_begin"].shape[0] == t.ncells
     for f in ("body_begin", "body_count", "child_begin", "nchild", "level"):
         assert np.array_equal(g[f], getattr(t, f)), f
-    gb, gc = oracle.groups(t, ncrit)
+    gb, gc = oracle.groups(t, ncrit, pack)
     assert np.array_equal(res["groups"][0], gb) and np.array_equal(res["groups"][1], gc)
     return mn, S, k, perm, t
 
@@ -57,6 +57,24 @@ def test_keys_sort_tree_bit_exact_edge_cases(nleaf, ncrit):
     b = edge_bodies(20000, 3)
     res = gpu_run(b.pos, b.mass, forces=False, nleaf=nleaf, ncrit=ncrit)
     check_keys_tree(res, b.pos, nleaf, ncrit)
+
+
+@pytest.mark.parametrize("nleaf,ncrit", [(16, 32), (8, 16), (1, 1), (64, 8), (4, 32), (16, 64), (8, 48)])
+def test_packed_groups_bit_exact_edge_cases(nleaf, ncrit):
+    """Sibling-packed groups (group_pack = 1) are bit-identical to the
+    oracle's packing, also with duplicate positions (oversize leaves cut in
+    runs) and deep clumps."""
+    b = edge_bodies(20000, 3)
+    res = gpu_run(b.pos, b.mass, forces=False, nleaf=nleaf, ncrit=ncrit, group_pack=1)
+    check_keys_tree(res, b.pos, nleaf, ncrit, pack=True)
+
+
+@pytest.mark.parametrize("n", [1, 2, 17, 65, 4099, 100003, 1 << 20])
+def test_packed_groups_bit_exact_plummer(n):
+    """Packing across many packing blocks (2^20 bodies: ~23k unpacked groups)."""
+    b = W.plummer(n, 0)
+    res = gpu_run(b.pos, b.mass, forces=False, ncrit=64, group_pack=1)
+    check_keys_tree(res, b.pos, 16, 64, pack=True)
 
 
 def test_host_buffers_path():
@@ -99,6 +117,26 @@ def test_forces_vs_oracle_tree(theta, ncrit):
     assert res["tot"][1] == int(res["n_pp"].astype(np.int64).sum())
     # borderline bodies: within the approximation's own error of the oracle tree
     assert ea.max() <= 3e-2
+
+
+@pytest.mark.parametrize("theta,ncrit", [(0.75, 32), (0.5, 64), (0.75, 64), (1.0, 64)])
+def test_forces_vs_oracle_tree_packed_groups(theta, ncrit):
+    """The walk over sibling-packed groups against the oracle walking the
+    same packed groups."""
+    b = W.plummer(32768, 0)
+    res = gpu_run(b.pos, b.mass, theta=theta, eps=0.01, ncrit=ncrit, group_pack=1)
+    tf = oracle.tree_forces(b.pos, b.mass, theta, 0.01, 16, ncrit, TAU_ABS, TAU_REL, pack=True)
+    ok = ~tf.borderline
+    assert ok.mean() > 0.9, ok.mean()
+    ea = rel_err(res["acc"], tf.acc)
+    ep = np.abs(res["pot"] - tf.pot) / np.abs(tf.pot)
+    assert ea[ok].max() <= 1e-5 and ep[ok].max() <= 1e-5
+    assert np.array_equal(res["n_pc"][ok], tf.n_pc[ok]) and np.array_equal(res["n_pp"][ok], tf.n_pp[ok])
+    assert ea.max() <= 3e-2
+    if theta == 0.75:
+        a_d, _ = oracle.direct(b.pos, b.mass, 0.01)
+        e = rel_err(res["acc"], a_d)
+        assert np.median(e) <= 1e-3 and np.percentile(e, 99) <= 1e-2
 
 
 def test_forces_vs_direct_sum_gates():
