@@ -159,6 +159,16 @@ __device__ __forceinline__ float ord2f(int i) {
     return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff);
 }
 
+// Reciprocal square root on the MUFU unit (PTX rsqrt.approx.ftz.f32).  The
+// interaction kernels call it on r^2 + eps^2 >= eps^2, a normal float, where
+// it returns what rsqrtf returns, without the scaling steps that a
+// denormal-preserving build adds around every rsqrtf.
+__device__ __forceinline__ float rsqrt_mufu(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Number of leading tree levels shared by two keys (level 0 always shared):
 // prefix_l(a) == prefix_l(b) iff l <= cpl(a, b).
 __device__ __forceinline__ int key_cpl(unsigned long long a, unsigned long long b) {

@@ -60,7 +60,7 @@ k_direct_partial(const float4 *__restrict__ pos4, int n, const uint32_t *__restr
             const float2 dy = __fadd2_rn(make_float2(u.z, u.w), ny);
             const float2 dz = __fadd2_rn(make_float2(w.x, w.y), nz);
             const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, e2)));
-            const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+            const float2 rinv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
             const float2 mr = __fmul2_rn(make_float2(w.z, w.w), rinv);
             const float2 mr3 = __fmul2_rn(__fmul2_rn(mr, rinv), rinv);
             pq = __fadd2_rn(pq, mr);

@@ -86,7 +86,11 @@ __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__res
     m.q[3] = 3.f * fmaf(-sx, cy, sxy); m.q[4] = 3.f * fmaf(-sx, cz, sxz); m.q[5] = 3.f * fmaf(-sy, cz, syz);
     int lev = cell_level[c];
     store32(c, m, mono, qa, qb);
-    delta[c] = cell_delta(sk[b], lev, sysid[b], make_float3(m.x, m.y, m.z), stc);
+    // The first body's key shares the key prefix of the leaf and of every
+    // ancestor: it gives every geometric centre on the way up.
+    const unsigned long long kb = sk[b];
+    const int sysb = sysid[b];
+    delta[c] = cell_delta(kb, lev, sysb, make_float3(m.x, m.y, m.z), stc);
     if (lev < FP64_LEVELS) {
         double *s = shadow + 10 * (size_t)c;
         s[0] = m.M; s[1] = m.x; s[2] = m.y; s[3] = m.z;
@@ -174,8 +178,7 @@ __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__res
             }
         }
         store32(c, m, mono, qa, qb);
-        unsigned b0 = __ldcg(&cell_body[c].x);
-        delta[c] = cell_delta(sk[b0], lv, sysid[b0], make_float3(m.x, m.y, m.z), stc);
+        delta[c] = cell_delta(kb, lv, sysb, make_float3(m.x, m.y, m.z), stc);
     }
 }
 

@@ -117,7 +117,7 @@ __device__ __forceinline__ void pc_two(const float4 v0, const float4 v1, const f
     const float2 dy = __fadd2_rn(make_float2(v0.z, v0.w), m.ny);
     const float2 dz = __fadd2_rn(make_float2(v1.x, v1.y), m.nz);
     const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, eps2)));
-    const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 rinv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
     const float2 rinv2 = __fmul2_rn(rinv, rinv);
     const float2 mr = __fmul2_rn(make_float2(v1.z, v1.w), rinv);
     const float2 nqxx = make_float2(v2.x, v2.y), nqyy = make_float2(v2.z, v2.w);
@@ -143,7 +143,7 @@ __device__ __forceinline__ void pp_two(const float4 v0, const float4 v1, const M
     const float2 dy = __fadd2_rn(make_float2(v0.z, v0.w), m.ny);
     const float2 dz = __fadd2_rn(make_float2(v1.x, v1.y), m.nz);
     const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, eps2)));
-    const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 rinv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
     const float2 mr = __fmul2_rn(make_float2(v1.z, v1.w), rinv);
     const float2 mr3 = __fmul2_rn(__fmul2_rn(mr, rinv), rinv);
     P.p = __fadd2_rn(P.p, mr);
@@ -307,8 +307,16 @@ __device__ __forceinline__ void walk_pop(const unsigned *stk, int &sp, int lane,
 #ifndef WALK_MIN_BLOCKS2
 #define WALK_MIN_BLOCKS2 0
 #endif
+#ifndef WALK_MAXNREG1
+#define WALK_MAXNREG1 0             // > 0: register cap of the one-body-per-lane walk
+#endif
+#if WALK_MAXNREG1 > 0
+#define WALK_ATTRS __launch_bounds__(256) __maxnreg__(BPL == 1 ? WALK_MAXNREG1 : 255)
+#else
+#define WALK_ATTRS __launch_bounds__(256, BPL == 1 ? WALK_MIN_BLOCKS1 : WALK_MIN_BLOCKS2)
+#endif
 template <int BPL, bool FEAT>
-__global__ void __launch_bounds__(256, BPL == 1 ? WALK_MIN_BLOCKS1 : WALK_MIN_BLOCKS2)
+__global__ void WALK_ATTRS
 k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__ groups,
        const float4 *__restrict__ pos4, const float4 *__restrict__ test,
        const uint2 *__restrict__ link, const float4 *__restrict__ mono,
