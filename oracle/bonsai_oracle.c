@@ -218,6 +218,12 @@ int64_t oracle_build(const uint64_t *skeys, int64_t n, int nleaf, int64_t cap,
  * starts a new packed group.  The root group and the runs of an oversize
  * leaf never join or absorb a neighbour.  Every packed group is then a run of
  * consecutive children of one cell.  Returns the group count or -1. */
+static int cmp_first_int32(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
 int64_t oracle_groups(int64_t ncells, const int32_t *body_begin,
                       const int32_t *body_count, const int32_t *nchild,
                       const int32_t *parent, int ncrit, int pack, int64_t cap,
@@ -245,15 +251,18 @@ int64_t oracle_groups(int64_t ncells, const int32_t *body_begin,
             }
         }
     }
-    /* key order = order of first body */
-    for (int64_t i = 1; i < ng; i++) {           /* insertion sort, stable */
-        int32_t b = g_begin[i], k = g_count[i], q = g_par[i];
-        int64_t j = i - 1;
-        while (j >= 0 && g_begin[j] > b) {
-            g_begin[j + 1] = g_begin[j]; g_count[j + 1] = g_count[j]; g_par[j + 1] = g_par[j]; j--;
-        }
-        g_begin[j + 1] = b; g_count[j + 1] = k; g_par[j + 1] = q;
+    /* key order = order of first body (unique per group, so any sort gives
+     * the same order) */
+    int32_t *trip = (int32_t *)malloc(sizeof(int32_t) * 3 * (size_t)(ng > 0 ? ng : 1));
+    if (!trip) { free(g_par); return -1; }
+    for (int64_t i = 0; i < ng; i++) {
+        trip[3 * i] = g_begin[i]; trip[3 * i + 1] = g_count[i]; trip[3 * i + 2] = g_par[i];
     }
+    qsort(trip, (size_t)ng, 3 * sizeof(int32_t), cmp_first_int32);
+    for (int64_t i = 0; i < ng; i++) {
+        g_begin[i] = trip[3 * i]; g_count[i] = trip[3 * i + 1]; g_par[i] = trip[3 * i + 2];
+    }
+    free(trip);
     if (pack && ng > 0) {
         int64_t out = 0;                         /* packed group being filled */
         for (int64_t i = 1; i < ng; i++) {
