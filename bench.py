@@ -48,7 +48,10 @@ def kernels_per_step(ncrit, group_pack=0):
     (+2 for sibling packing of the groups), multipoles, open radius, walk (two
     instantiations when groups may exceed 32 bodies), kick."""
     return 21 + (1 if ncrit > 32 else 0) + (2 if group_pack else 0)
-WALK_TRAFFIC_PER_LAUNCH = 67.15e6  # dram bytes of the walk stage (both launches), profiles/k_walk_plummer_n2e20.md
+# DRAM bytes (read + write) of one walk launch from the ncu capture in
+# profiles/k_walk_plummer_n2e20.md, keyed by (N, ncrit, group_pack); other
+# choices have no capture and report null.
+WALK_TRAFFIC = {(1 << 20, 32, 1): 35.41e6}
 
 
 def parse():
@@ -480,7 +483,7 @@ def stage_bytes(n, ncells, ngroups):
 
 
 def run_sweep(a, dev, stream):
-    """Scaling sweep: Plummer spheres N = 2^15 .. 2^20 at theta = 0.75
+    """Scaling sweep (group knobs from the command line): Plummer spheres N = 2^15 .. 2^20 at theta = 0.75
     (interactions per body vs N), then N = 2^22 (seed 2) and 2^24 (seed 3)
     at theta in {0.5, 0.75, 1.0}; eps = 0.002, 5 KDK steps of dt = 1/256
     after 2 untimed ones.  Per stage: device ms per step and algorithmic
@@ -501,7 +504,8 @@ def run_sweep(a, dev, stream):
     for n, seed, thetas in cases:
         b = W.plummer(n, seed)
         for theta in thetas:
-            bz = B.Bonsai(B.Config(nleaf=16, ncrit=64, walk_warps=8, group_pack=a.group_pack), stream=stream)
+            bz = B.Bonsai(B.Config(nleaf=a.nleaf, ncrit=a.ncrit, walk_warps=a.walk_warps, group_pack=a.group_pack),
+                          stream=stream)
             bz.set_bodies(torch.from_numpy(b.pos).to(dev), torch.from_numpy(b.mass).to(dev),
                           torch.from_numpy(b.vel).to(dev))
             bz.build().multipoles().forces(theta, eps)
@@ -534,6 +538,7 @@ def run_sweep(a, dev, stream):
             t = sum(ms) / steps
             print(json.dumps({
                 "mode": "sweep", "n": n, "seed": seed, "theta": theta, "eps": eps, "dt": dt,
+                "nleaf": a.nleaf, "ncrit": a.ncrit, "group_pack": a.group_pack, "walk_warps": a.walk_warps,
                 "steps": steps, "ms_per_step": t, "particles_per_s": n / (t / 1e3),
                 "stage_ms": stage,
                 "stage_gbs": {k: sb[k] / (stage[k] / 1e3) / 1e9 for k in sb if stage[k] > 0},
@@ -659,7 +664,7 @@ def run_ours(a, rank, world, local_rank):
             "config": config(a, world),
             "roofline": {"bound": "alu", "kernel": "k_walk", "achieved": achieved,
                          "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                         "traffic": WALK_TRAFFIC_PER_LAUNCH,
+                         "traffic": WALK_TRAFFIC.get((a.n, a.ncrit, a.group_pack)),
                          "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
                          "flops_basis": f"{FLOP_PC} per body-cell + {FLOP_PP} per body-body interaction"},
             "cpu_baseline": cpu,

@@ -40,6 +40,12 @@ __device__ float2 cell_delta(unsigned long long k, int level, int sys, float3 co
 
 struct Mom32 { float M, x, y, z, q[6]; };
 
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned *p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 // The quadrupole arrays hold -Q (negation is exact): the walk consumes it in
 // that form, parents and the export negate it back.
 __device__ __forceinline__ void store32(int c, const Mom32 &m, float4 *mono, float4 *qa, float2 *qb) {
@@ -101,10 +107,12 @@ __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__res
     // the level-0 cells, one per system).
     while (lev != 0) {
         unsigned p = cell_parent[c];
-        __threadfence();
         unsigned nch = __ldcg(&cell_link[p].y);
-        if (atomicAdd(&cell_done[p], 1u) != nch - 1u) return;
-        __threadfence();
+        // Release: this cell's moments are visible to whoever reads the
+        // counter after this add; acquire: the last child to arrive sees
+        // every sibling's moments (each sibling's add heads a release
+        // sequence that this read-modify-write extends).
+        if (atom_add_acq_rel_gpu(&cell_done[p], 1u) != nch - 1u) return;
         c = p;
         unsigned cb = __ldcg(&cell_link[c].x);
         const int lv = cell_level[c];

@@ -35,7 +35,7 @@ namespace bonsai {
 constexpr int RING = 64;          // sources per ring
 constexpr int RPAIR = RING / 2;   // source pairs per ring
 #ifndef WALK_UNROLL
-#define WALK_UNROLL 4             // unroll depth of the tile loops
+#define WALK_UNROLL 8             // unroll depth of the tile loops (4: 1% slower, 16: 9% slower)
 #endif
 constexpr int kWalkUnroll = WALK_UNROLL;
 
