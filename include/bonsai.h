@@ -100,7 +100,8 @@ int bonsai_build(bonsai_ctx *ctx);
 
 /* Sect. 2 "multipole moments": per cell mass, centre of mass and traceless
  * quadrupole Q_ij = sum m (3 y_i y_j - |y|^2 delta_ij), y = x - com, computed
- * from the leaves up (FP64 for the top four levels).  Requires bonsai_build. */
+ * from the leaves up (FP64 for the root of each system).  Requires
+ * bonsai_build. */
 int bonsai_multipoles(bonsai_ctx *ctx);
 
 /* Sect. 2 "tree-traverse": softened accelerations and potentials under the

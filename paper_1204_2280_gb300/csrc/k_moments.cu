@@ -9,8 +9,10 @@
 //   Q_p = sum_k [ Q_k + M_k (3 d_k d_k^T - |d_k|^2 I) ],  d_k = com_k - com_p,
 // in one launch: each thread finishing a cell bumps its parent's arrival
 // counter and the last child to arrive combines the parent (no waiting).
-// The top four levels (at most 585 cells, the first ones in breadth-first
-// order) combine in FP64, from FP64 copies of children on those levels.
+// The levels below FP64_LEVELS (level 0: the root of each system) combine
+// in FP64, from FP64 copies of children on those levels.  One level: FP64
+// arithmetic runs at a small fraction of the FP32 rate here, and a combine is
+// a serial chain on one lane (each further level measured about 13 us).
 #include "common.cuh"
 
 namespace bonsai {
@@ -159,30 +161,40 @@ __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__res
             m.M = (float)dM; m.x = (float)cx; m.y = (float)cy; m.z = (float)cz;
             for (int i = 0; i < 6; i++) m.q[i] = (float)q[i];
         } else {
-            float4 ch0 = __ldcg(mono + cb);
-            float c0x = ch0.x, c0y = ch0.y, c0z = ch0.z;
+            // Children's moments loaded together (at most 8, unrolled): one
+            // round trip to L2 per level instead of one per child.
+            float4 mo[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++)
+                mo[k] = k < (int)nch ? __ldcg(mono + cb + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float c0x = mo[0].x, c0y = mo[0].y, c0z = mo[0].z;
             float fM = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
-            for (unsigned k = 0; k < nch; k++) {
-                float4 mo = __ldcg(mono + cb + k);
-                fM += mo.w;
-                ax = fmaf(mo.w, mo.x - c0x, ax);
-                ay = fmaf(mo.w, mo.y - c0y, ay);
-                az = fmaf(mo.w, mo.z - c0z, az);
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                if (k < (int)nch) {
+                    fM += mo[k].w;
+                    ax = fmaf(mo[k].w, mo[k].x - c0x, ax);
+                    ay = fmaf(mo[k].w, mo[k].y - c0y, ay);
+                    az = fmaf(mo[k].w, mo[k].z - c0z, az);
+                }
             }
             float inv2 = fM > 0.f ? 1.f / fM : 0.f;
             m.M = fM; m.x = c0x + ax * inv2; m.y = c0y + ay * inv2; m.z = c0z + az * inv2;
             for (int i = 0; i < 6; i++) m.q[i] = 0.f;
-            for (unsigned k = 0; k < nch; k++) {
-                float4 mo = __ldcg(mono + cb + k), a = __ldcg(qa + cb + k);
-                float2 q2 = __ldcg(qb + cb + k);
-                float dx = mo.x - m.x, dy = mo.y - m.y, dz = mo.z - m.z;
-                float d2 = dx * dx + dy * dy + dz * dz;
-                m.q[0] += -a.x + mo.w * (3.f * dx * dx - d2);
-                m.q[1] += -a.y + mo.w * (3.f * dy * dy - d2);
-                m.q[2] += -a.z + mo.w * (3.f * dz * dz - d2);
-                m.q[3] += -a.w + mo.w * (3.f * dx * dy);
-                m.q[4] += -q2.x + mo.w * (3.f * dx * dz);
-                m.q[5] += -q2.y + mo.w * (3.f * dy * dz);
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                if (k < (int)nch) {
+                    const float4 a = __ldcg(qa + cb + k);
+                    const float2 q2 = __ldcg(qb + cb + k);
+                    const float dx = mo[k].x - m.x, dy = mo[k].y - m.y, dz = mo[k].z - m.z;
+                    const float d2 = dx * dx + dy * dy + dz * dz;
+                    m.q[0] += -a.x + mo[k].w * (3.f * dx * dx - d2);
+                    m.q[1] += -a.y + mo[k].w * (3.f * dy * dy - d2);
+                    m.q[2] += -a.z + mo[k].w * (3.f * dz * dz - d2);
+                    m.q[3] += -a.w + mo[k].w * (3.f * dx * dy);
+                    m.q[4] += -q2.x + mo[k].w * (3.f * dx * dz);
+                    m.q[5] += -q2.y + mo[k].w * (3.f * dy * dz);
+                }
             }
         }
         store32(c, m, mono, qa, qb);
@@ -194,7 +206,7 @@ __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__res
 // then up the tree while it is the last child to arrive.  A thread per cell
 // of the capacity keeps many climbs in flight; a grid-stride loop that
 // serialises them per thread measured twice as slow.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_multipoles(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__ cell_body,
              const uint2 *__restrict__ cell_link, const uint8_t *__restrict__ cell_level,
              const uint32_t *__restrict__ cell_parent, uint32_t *cell_done,
