@@ -65,10 +65,10 @@ def parse():
     p.add_argument("--theta", type=float, default=0.75)
     p.add_argument("--eps", type=float, default=0.005)
     p.add_argument("--dt", type=float, default=1.0 / 128)
-    p.add_argument("--ncrit", type=int, default=64)
+    p.add_argument("--ncrit", type=int, default=32)
     p.add_argument("--nleaf", type=int, default=16)
-    p.add_argument("--walk-warps", type=int, default=4)
-    p.add_argument("--group-pack", type=int, default=0, choices=[0, 1],
+    p.add_argument("--walk-warps", type=int, default=8)
+    p.add_argument("--group-pack", type=int, default=1, choices=[0, 1],
                    help="sibling-packed walk groups (with --no-autotune; the autotuner picks otherwise)")
     p.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
     p.add_argument("--no-cpu-baseline", action="store_true")
