@@ -18,6 +18,9 @@
 
 namespace bonsai {
 
+#ifndef SORT_LOOKBACK
+#define SORT_LOOKBACK 8           // predecessor tiles read per look-back round trip (4: 6% slower at 2^20, 16: 4%)
+#endif
 #ifndef SORT_MIN_BLOCKS
 #define SORT_MIN_BLOCKS 2         // resident onesweep blocks per SM the register budget allows
 #endif
@@ -153,7 +156,7 @@ k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restric
             // Look back LB tiles per round trip (independent loads), then
             // consume them in order: aggregates are added, an inclusive
             // prefix ends the look-back, an unpublished tile is polled again.
-            constexpr int LB = 4;
+            constexpr int LB = SORT_LOOKBACK;
             int j = tile - 1;
             long long spins = 0;
             bool found = false;

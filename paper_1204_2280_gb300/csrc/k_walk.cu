@@ -215,15 +215,22 @@ __device__ __forceinline__ void eval_pp(const float4 *__restrict__ base, int pha
     commit<BPL>(P, A);
 }
 
-// Which instantiation walks a group of ng bodies: one body per lane up to
-// 32 bodies, two beyond.
-__host__ __device__ constexpr int walk_bpl(int ng) { return ng <= 32 ? 1 : 2; }
+// Which instantiation walks a group of ng bodies: one body per lane below
+// WALK_BPL2_FROM bodies (17..33), two from there on.  33 is the measured
+// best: two bodies per lane from 17 or 25 bodies on (16 body slots, two
+// phases) run the 2^20 walk 3% slower (128 registers, 16 warps per SM).
+#ifndef WALK_BPL2_FROM
+#define WALK_BPL2_FROM 33
+#endif
+static_assert(WALK_BPL2_FROM >= 17 && WALK_BPL2_FROM <= 33, "two bodies per lane need >= 16 body slots");
+__host__ __device__ constexpr int walk_bpl(int ng) { return ng < WALK_BPL2_FROM ? 1 : 2; }
 
 // log2 of the body slots of a group: one body per lane, next power of two
-// (>= 2: at most 16 phases share the 16 source pairs); two bodies, 32.
+// (>= 2: at most 16 phases share the 16 source pairs); two bodies per lane,
+// 16 slots (two phases) up to 32 bodies, 32 slots beyond.
 template <int BPL>
 __device__ __forceinline__ int walk_lg(int ng) {
-    if (BPL == 2) return 5;
+    if (BPL == 2) return ng <= 32 ? 4 : 5;
     return ng <= 2 ? 1 : 32 - __clz(ng - 1);
 }
 
@@ -232,7 +239,8 @@ template <int BPL, int STRIDE>
 __device__ __forceinline__ void tile_pc(int lg, const float4 *__restrict__ base, int phase, const float4 (&me)[BPL],
                                         const float2 eps2, Acc (&A)[BPL]) {
     if constexpr (BPL == 2) {
-        eval_pc<1, 2, STRIDE>(base, phase, me, eps2, A);
+        if (lg == 4) eval_pc<2, 2, STRIDE>(base, phase, me, eps2, A);
+        else eval_pc<1, 2, STRIDE>(base, phase, me, eps2, A);
     } else {
         switch (lg) {
             case 1: eval_pc<16, 1, STRIDE>(base, phase, me, eps2, A); break;
@@ -247,7 +255,8 @@ template <int BPL, int STRIDE>
 __device__ __forceinline__ void tile_pp(int lg, const float4 *__restrict__ base, int phase, const float4 (&me)[BPL],
                                         const float2 eps2, Acc (&A)[BPL]) {
     if constexpr (BPL == 2) {
-        eval_pp<1, 2, STRIDE>(base, phase, me, eps2, A);
+        if (lg == 4) eval_pp<2, 2, STRIDE>(base, phase, me, eps2, A);
+        else eval_pp<1, 2, STRIDE>(base, phase, me, eps2, A);
     } else {
         switch (lg) {
             case 1: eval_pp<16, 1, STRIDE>(base, phase, me, eps2, A); break;
@@ -570,7 +579,7 @@ static cudaError_t launch_walk_t(Ctx &c, float eps, const unsigned *gate, cudaSt
 // joined back into the context's stream (event edges inside a captured
 // step), so the tail of each launch overlaps the other's work.
 cudaError_t launch_walk(Ctx &c, float eps, bool features, const unsigned *gate) {
-    if (c.ncrit <= 32)
+    if (c.ncrit < WALK_BPL2_FROM)
         return features ? launch_walk_t<1, true>(c, eps, gate, c.stream) : launch_walk_t<1, false>(c, eps, gate, c.stream);
     cudaError_t e = cudaEventRecord(c.ev_fork, c.stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c.side, c.ev_fork, 0);
