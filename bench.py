@@ -51,7 +51,7 @@ def kernels_per_step(ncrit, group_pack=0):
 # DRAM bytes (read + write) of one walk launch from the ncu capture in
 # profiles/k_walk_plummer_n2e20.md, keyed by (N, ncrit, group_pack); other
 # choices have no capture and report null.
-WALK_TRAFFIC = {(1 << 20, 32, 1): 35.41e6}
+WALK_TRAFFIC = {(1 << 20, 32, 1): 35.97e6}
 
 
 def parse():

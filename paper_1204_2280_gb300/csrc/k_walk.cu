@@ -316,6 +316,12 @@ __device__ __forceinline__ void walk_pop(const unsigned *stk, int &sp, int lane,
 #ifndef WALK_MIN_BLOCKS2
 #define WALK_MIN_BLOCKS2 0
 #endif
+#ifndef WALK_SPEC_LOADS
+#define WALK_SPEC_LOADS 1           // 1: load a tested cell's moments with its MAC record
+#endif
+#ifndef WALK_SMALL_LAST
+#define WALK_SMALL_LAST 16          // > 0: groups of at most this many bodies in a second pass
+#endif
 #ifndef WALK_MAXNREG1
 #define WALK_MAXNREG1 0             // > 0: register cap of the one-body-per-lane walk
 #endif
@@ -351,10 +357,19 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
         unsigned g = 0;
         if (lane == 0) g = atomicAdd(queue, 1u);
         g = __shfl_sync(0xffffffffu, g, 0);
+#if WALK_SMALL_LAST
+        // two passes over the groups: larger ones first, then those of at
+        // most WALK_SMALL_LAST bodies (a shorter tail at the end of the walk)
+        const bool second = g >= ngroups;
+        if (second) g -= ngroups;
+#endif
         if (g >= ngroups) break;
         const uint2 gr = groups[g];
         const int gb = (int)gr.x, ng = (int)gr.y;
         if (walk_bpl(ng) != BPL) continue;          // another instantiation's group
+#if WALK_SMALL_LAST
+        if (second != (ng <= WALK_SMALL_LAST)) continue;
+#endif
         // Body slots and source phases.
         const int lg = walk_lg<BPL>(ng);
         const int slots = 1 << lg;
@@ -406,9 +421,17 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
 
             bool open = false, acc = false, isleaf = false;
             uint2 lk = make_uint2(0u, 0u);
+#if WALK_SPEC_LOADS
+            float4 cmo = make_float4(0.f, 0.f, 0.f, 0.f), cqa = cmo;
+            float2 cqb = make_float2(0.f, 0.f);
+#endif
             if (has) {
                 const float4 tc = __ldg(test + cell);
                 lk = __ldg(link + cell);
+#if WALK_SPEC_LOADS
+                // the moments, in case the cell is accepted: one round trip per round
+                cmo = __ldg(mono + cell); cqa = __ldg(quadA + cell); cqb = __ldg(quadB + cell);
+#endif
                 const float dx = fmaxf(fmaxf(bx0 - tc.x, tc.x - bx1), 0.f);
                 const float dy = fmaxf(fmaxf(by0 - tc.y, tc.y - by1), 0.f);
                 const float dz = fmaxf(fmaxf(bz0 - tc.z, tc.z - bz1), 0.f);
@@ -421,7 +444,11 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
             const unsigned am = __ballot_sync(0xffffffffu, acc);
             if (acc) {
                 const int s = (pc_head + pc_n + __popc(am & lt)) & (RING - 1);
+#if WALK_SPEC_LOADS
+                put_cell(R, s, cmo, cqa, cqb);
+#else
                 put_cell(R, s, __ldg(mono + cell), __ldg(quadA + cell), __ldg(quadB + cell));
+#endif
             }
             pc_n += __popc(am);
             npc += __popc(am);
