@@ -82,6 +82,8 @@ def parse():
     p.add_argument("--learned-merger", type=int, default=8, help="merger training snapshots")
     p.add_argument("--sweep", action="store_true",
                    help="per-stage scaling sweep instead of the bench line: one JSON line per (N, theta)")
+    p.add_argument("--sweep-cpu", type=float, default=0.0,
+                   help="with --sweep: also time the FP64 oracle per stage at theta = 0.75 (seconds of walk sample)")
     return p.parse_args()
 
 
@@ -169,7 +171,7 @@ def cpu_model() -> str:
     return f"{platform.machine()} implementer {impl} part {part}"
 
 
-def cpu_oracle_sample(bodies, theta, eps, nleaf, ncrit, budget_s, seed=0, pack=0):
+def cpu_oracle_sample(bodies, theta, eps, nleaf, ncrit, budget_s, seed=0, pack=0, direct=True):
     """FP64 oracle tree-code on a bounded sample, timed per stage: domain and
     keys, sort, tree build (+ groups), moments (+ opening radii) for all
     bodies; the walk for a random sample of groups (extrapolated to all
@@ -215,10 +217,12 @@ def cpu_oracle_sample(bodies, theta, eps, nleaf, ncrit, budget_s, seed=0, pack=0
     n = bodies.n
     st["walk"] = t_walk * n / max(nb, 1)
     t_step = t_tree + st["walk"]
-    idx = rng.choice(n, size=min(4096, n), replace=False)
-    t = time.perf_counter()
-    oracle.direct(bodies.pos, bodies.mass, eps, idx)
-    t_direct = time.perf_counter() - t
+    t_direct = None
+    if direct:
+        idx = rng.choice(n, size=min(4096, n), replace=False)
+        t = time.perf_counter()
+        oracle.direct(bodies.pos, bodies.mass, eps, idx)
+        t_direct = time.perf_counter() - t
     return {"value": n / t_step, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "cpu": cpu_model(),
             "sample": f"full tree build of all {n} bodies ({t_tree:.2f} s) + walk of {used} random "
@@ -483,13 +487,16 @@ def stage_bytes(n, ncells, ngroups):
 
 
 def run_sweep(a, dev, stream):
-    """Scaling sweep (group knobs from the command line): Plummer spheres N = 2^15 .. 2^20 at theta = 0.75
-    (interactions per body vs N), then N = 2^22 (seed 2) and 2^24 (seed 3)
+    """Scaling sweep (group knobs from the command line): Plummer spheres N = 2^15 .. 2^21 and 2^23 at
+    theta = 0.75 (interactions per body vs N), N = 2^22 (seed 2) and 2^24 (seed 3)
     at theta in {0.5, 0.75, 1.0}; eps = 0.002, 5 KDK steps of dt = 1/256
     after 2 untimed ones.  Per stage: device ms per step and algorithmic
     GB/s against the measured copy bandwidth; walk FP32 rate against the
     FP32 peak; FP64 energy drift over the timed steps; p99 force error of the
-    first evaluation at 4096 stratified bodies (the library's direct sum)."""
+    first evaluation at 4096 stratified bodies (the library's direct sum).
+    --sweep-cpu S adds the FP64 oracle's time per stage at theta = 0.75 on the
+    host cores (sorting + moving, build, multipoles, and the walk of a random
+    group sample of about S seconds extrapolated to N: the paper's Fig. 1)."""
     import numpy as np
     import torch
     import paper_1204_2280_gb300 as B
@@ -497,8 +504,8 @@ def run_sweep(a, dev, stream):
     import ctypes as C
     hbm = measured_hbm_gbs()
     eps, dt, steps = 0.002, 1.0 / 256, 5
-    cases = [(1 << k, 1, (0.75,)) for k in range(15, 21)]
-    cases += [(1 << 22, 2, (0.5, 0.75, 1.0)), (1 << 24, 3, (0.5, 0.75, 1.0))]
+    cases = [(1 << k, 1, (0.75,)) for k in range(15, 22)]
+    cases += [(1 << 22, 2, (0.5, 0.75, 1.0)), (1 << 23, 1, (0.75,)), (1 << 24, 3, (0.5, 0.75, 1.0))]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     tot = (C.c_ulonglong * 2)()
     for n, seed, thetas in cases:
@@ -533,6 +540,20 @@ def run_sweep(a, dev, stream):
             bz.close()
             stage = dict(zip(B.STAGES, (np.array(st).sum(0) / steps).tolist()))
             sb = stage_bytes(n, ncells, ngroups)
+            cpu = None
+            if a.sweep_cpu > 0 and theta == 0.75:
+                # The paper's Fig. 1 stages on the FP64 oracle (host cores):
+                # sorting + moving, tree construction, multipoles, walk.
+                c = cpu_oracle_sample(b, theta, eps, a.nleaf, a.ncrit, a.sweep_cpu, pack=a.group_pack, direct=False)
+                cs = c["stage_s"]
+                gpu_s = {"sort_move": (stage["keys"] + stage["sort"] + stage["reorder"]) / 1e3,
+                         "build": stage["build"] / 1e3, "multipoles": stage["multipoles"] / 1e3,
+                         "walk": stage["walk"] / 1e3}
+                cpu_s = {"sort_move": cs["domain_keys"] + cs["sort_reorder"], "build": cs["build"],
+                         "multipoles": cs["multipoles"], "walk": cs["walk"]}
+                cpu = {"cores": c["cores"], "stage_s": cpu_s, "gpu_stage_s": gpu_s,
+                       "cpu_over_gpu": {k: cpu_s[k] / gpu_s[k] for k in cpu_s},
+                       "sample": c["sample"]}
             walk_s = stage["walk"] / 1e3
             tflops = (FLOP_PC * npc + FLOP_PP * npp) / steps / walk_s / 1e12
             t = sum(ms) / steps
@@ -551,7 +572,7 @@ def run_sweep(a, dev, stream):
                 "ncells": ncells, "ngroups": ngroups,
                 "p99_acc_err_t0": p99,
                 "energy_drift": (d1[2] - d0[2]) / abs(d0[2]),
-                "hbm_peak_gbs": hbm, "fp32_peak_tflops": FP32_PEAK_TFLOPS}), flush=True)
+                "hbm_peak_gbs": hbm, "fp32_peak_tflops": FP32_PEAK_TFLOPS, "oracle": cpu}), flush=True)
 
 
 def measured_hbm_gbs():

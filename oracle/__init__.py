@@ -60,7 +60,7 @@ def lib():
             L.oracle_moments.argtypes = [i64, p, p, p, p, p, p, p]
             L.oracle_open_radius.argtypes = [i64, p, p, p, p, d, p, d, p]
             L.oracle_walk.argtypes = [i64, p, p, i64, p, p, p, p, p, p, p, p, i64, p, p,
-                                      d, d, d, p, p, p, p, p, p, p]
+                                      d, d, d, p, p, p, p, p, p, p, p]
             L.oracle_direct.argtypes = [p, p, i64, p, i64, d, p, p]
             L.oracle_energy.argtypes = [p, p, p, p, i64, p]
             L.oracle_pc_eval.argtypes = [p, p, d, p, d, p, p]
@@ -186,7 +186,10 @@ def cell_cube(tree: Tree, skeys, mn, S):
 
 
 def walk(spos, smass, tree: Tree, M, com, Q, r_open, gbeg, gcnt, eps: float,
-         tau_abs: float = 0.0, tau_rel: float = 0.0, bins: bool = False):
+         tau_abs: float = 0.0, tau_rel: float = 0.0, bins: bool = False, active=None):
+    """Group walk in sorted order; active (bool per sorted body, optional):
+    only those bodies take forces, each group's box is its active bodies'
+    box; the outputs of inactive bodies stay zero."""
     spos, smass = _f32(spos), _f32(smass)
     n = spos.shape[0]
     acc = np.zeros((n, 3))
@@ -201,7 +204,8 @@ def walk(spos, smass, tree: Tree, M, com, Q, r_open, gbeg, gcnt, eps: float,
                            _ptr(np.ascontiguousarray(Q)), _ptr(np.ascontiguousarray(r_open)),
                            gbeg.shape[0], _ptr(gbeg), _ptr(gcnt), float(eps), float(tau_abs),
                            float(tau_rel), _ptr(acc), _ptr(pot), _ptr(npc), _ptr(npp), _ptr(flag),
-                           _ptr(tree.level) if bins else None, _ptr(nb) if bins else None)
+                           _ptr(tree.level) if bins else None, _ptr(nb) if bins else None,
+                           _ptr(np.ascontiguousarray(active, np.int8)) if active is not None else None)
     if rc:
         raise ValueError("oracle_walk: a body's own leaf was accepted (theta too large)")
     if bins:
@@ -303,3 +307,119 @@ def kdk_step(pos, vel, mass, acc0, dt: float, theta: float, eps: float, nleaf: i
     tf = tree_forces(x1f, mass, theta, eps, nleaf, ncrit, pack=pack)
     v1 = vh + 0.5 * dt * tf.acc
     return x1, v1, tf.acc, tf.pot
+
+
+# ---------------------------------------------------------------------------
+# Block (hierarchical) time steps
+# ---------------------------------------------------------------------------
+# Sect. 1 and 3 of the paper: with the whole tree-code on the GPU, a block
+# time-step scheme walks only the N_active bodies that have to be updated
+# (the walk time falls by N / N_active), and between rebuilds only the
+# multipole moments are recomputed; the full tree is rebuilt when the walk
+# slows down.  The paper fixes no scheme; the readings here:
+#  * body i steps with dt_max / 2^k_i; k_i is the smallest level in
+#    [0, kmax] with dt_max / 2^k <= eta * sqrt(eps / |a_i|), decided in
+#    float32 as 16^k >= r, r = c * |a|^2, c = dt_max^4 / (eta^4 eps^2)
+#    (rounded to float32 once), |a|^2 summed x, y, z without fused operations;
+#  * a cycle of dt_max is 2^kmax substeps of dt_min = dt_max / 2^kmax, with
+#    every body synchronised at its start and end: at the start each body
+#    gets its level and an opening half kick a * dt_i / 2; each substep
+#    drifts every body by dt_min, refreshes the tree (a rebuild every
+#    `rebuild_every` substeps, else new moments of the existing cells at the
+#    current positions), walks the active bodies (those whose step ends now:
+#    s a multiple of 2^(kmax - k_i)) and gives them the closing half kick;
+#    before the last substep they then take a new level, no coarser than the
+#    substep allows (k >= kmax - trailing zeros of s), and the opening half
+#    kick of their next step.
+
+def block_constant(dt_max: float, eta: float, eps: float) -> np.float32:
+    """c = dt_max^4 / (eta^4 eps^2) in float64 from the float32 parameters,
+    then rounded to float32 (the level decision's constant)."""
+    d, e, s = float(np.float32(dt_max)), float(np.float32(eta)), float(np.float32(eps))
+    d2 = d * d
+    e2 = e * e
+    return np.float32((d2 * d2) / ((e2 * e2) * (s * s)))
+
+
+def block_level(acc, c32, kmax: int) -> np.ndarray:
+    """Level of each body from its acceleration (n, 3), in float32."""
+    a = np.asarray(acc, np.float32)
+    a2 = (a[:, 0] * a[:, 0] + a[:, 1] * a[:, 1]) + a[:, 2] * a[:, 2]
+    r = np.float32(c32) * a2
+    k = np.zeros(a.shape[0], np.int32)
+    for lev in range(1, kmax + 1):
+        k += (r > np.float32(16.0) ** (lev - 1)).astype(np.int32)
+    return k
+
+
+def _ctz(s: int) -> int:
+    return (s & -s).bit_length() - 1
+
+
+class _BlockTree:
+    """Tree of a rebuild: sort order, cells, groups and the build-time
+    geometry (keys, domain) that the opening radii keep until the next one."""
+
+    def __init__(self, x32, nleaf, ncrit, pack):
+        self.mn, self.S = domain(x32)
+        k = keys(x32, self.mn, self.S)
+        self.perm = sort(k)
+        self.skeys = k[self.perm]
+        self.tree = build_tree(self.skeys, nleaf)
+        self.gb, self.gc = groups(self.tree, ncrit, pack)
+
+    def forces(self, x32, mass, theta, eps, active):
+        """Accelerations and potentials (caller order) of the active bodies:
+        moments of the cells at the current positions, opening radii from
+        the build-time cell geometry and the current com, walk of the active
+        bodies."""
+        p = self.perm
+        spos, smass = np.ascontiguousarray(x32[p]), np.ascontiguousarray(mass[p])
+        M, com, Q = moments(self.tree, spos, smass)
+        ro = open_radius(self.tree, self.skeys, self.mn, self.S, com, theta)
+        acc_s, pot_s, _, _, _ = walk(spos, smass, self.tree, M, com, Q, ro, self.gb, self.gc, eps,
+                                     active=np.asarray(active)[p])
+        n = x32.shape[0]
+        acc = np.zeros((n, 3)); acc[p] = acc_s
+        pot = np.zeros(n); pot[p] = pot_s
+        return acc, pot
+
+
+def block_cycle(pos, vel, mass, acc, dt_max: float, kmax: int, eta: float, theta: float, eps: float,
+                nleaf: int = 16, ncrit: int = 32, pack: bool = False, rebuild_every: int = 1):
+    """One cycle of block time steps from a synchronised state (acc: the
+    acceleration at pos).  State in float64; the tree and forces see the
+    positions rounded to float32 (the stored state is float32).  Returns
+    (pos, vel, acc, pot, levels at the start, active bodies per substep)."""
+    mass = np.asarray(mass, np.float32)
+    x = np.array(pos, np.float64)
+    v = np.array(vel, np.float64)
+    a = np.array(acc, np.float64)
+    pot = np.zeros(x.shape[0])
+    nsub = 1 << kmax
+    dtm = dt_max / nsub
+    c32 = block_constant(dt_max, eta, eps)
+    lev = block_level(a, c32, kmax)
+    lev0 = lev.copy()
+    h = (1 << (kmax - lev)) * dtm / 2
+    v += a * h[:, None]
+    bt = None
+    nactive = []
+    for s in range(1, nsub + 1):
+        x += v * dtm
+        x32 = x.astype(np.float32)
+        if bt is None or (s - 1) % rebuild_every == 0:
+            bt = _BlockTree(x32, nleaf, ncrit, pack)
+        act = (s % (1 << (kmax - lev))) == 0
+        nactive.append(int(act.sum()))
+        an, pn = bt.forces(x32, mass, theta, eps, act)
+        a[act] = an[act]
+        pot[act] = pn[act]
+        h = (1 << (kmax - lev)) * dtm / 2
+        v[act] += a[act] * h[act][:, None]
+        if s < nsub:
+            new = np.maximum(block_level(a, c32, kmax), kmax - _ctz(s))
+            lev[act] = new[act]
+            h = (1 << (kmax - lev)) * dtm / 2
+            v[act] += a[act] * h[act][:, None]
+    return x, v, a, pot, lev0, nactive

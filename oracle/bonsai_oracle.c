@@ -412,7 +412,10 @@ int oracle_open_radius(int64_t ncells, const int32_t *body_begin,
  * A group is flagged borderline (flag[body] = 1 for its bodies) when some
  * tested cell had |dist - r_open| <= tau_abs + tau_rel * r_open, i.e. a
  * single-precision implementation may take the other decision there.
- * npc_bins (may be NULL, needs level): accepted cells per level bin. */
+ * npc_bins (may be NULL, needs level): accepted cells per level bin.
+ * active (may be NULL: every body): with block time steps only the active
+ * bodies take forces; a group's box is then the box of its active bodies and
+ * a group without one is skipped (outputs of inactive bodies untouched). */
 int oracle_walk(int64_t n, const float *spos, const float *smass,
                 int64_t ncells, const int32_t *body_begin,
                 const int32_t *body_count, const int32_t *child_begin,
@@ -421,7 +424,7 @@ int oracle_walk(int64_t n, const float *spos, const float *smass,
                 const int32_t *g_begin, const int32_t *g_count, double eps,
                 double tau_abs, double tau_rel, double *acc, double *pot,
                 int32_t *n_pc, int32_t *n_pp, int8_t *flag,
-                const int32_t *level, int32_t *npc_bins)
+                const int32_t *level, int32_t *npc_bins, const int8_t *active)
 {
     (void)n; (void)ncells;
     double eps2 = eps * eps;
@@ -437,9 +440,15 @@ int oracle_walk(int64_t n, const float *spos, const float *smass,
         for (int64_t g = 0; g < ngroups; g++) {
             int64_t gb = g_begin[g], ge = gb + g_count[g];
             float bmin[3], bmax[3];
-            for (int d = 0; d < 3; d++) bmin[d] = bmax[d] = spos[3 * gb + d];
-            for (int64_t i = gb; i < ge; i++)
+            int64_t first = gb;
+            if (active) {
+                while (first < ge && !active[first]) first++;
+                if (first == ge) continue;               /* no active body */
+            }
+            for (int d = 0; d < 3; d++) bmin[d] = bmax[d] = spos[3 * first + d];
+            for (int64_t i = first; i < ge; i++)
                 for (int d = 0; d < 3; d++) {
+                    if (active && !active[i]) break;
                     float v = spos[3 * i + d];
                     if (v < bmin[d]) bmin[d] = v;
                     if (v > bmax[d]) bmax[d] = v;
@@ -490,6 +499,7 @@ int oracle_walk(int64_t n, const float *spos, const float *smass,
             int32_t npp_group = 0;
             for (int64_t k = 0; k < nl; k++) npp_group += body_count[open_leaves[k]];
             for (int64_t i = gb; i < ge; i++) {
+                if (active && !active[i]) continue;
                 double xi = spos[3 * i], yi = spos[3 * i + 1], zi = spos[3 * i + 2];
                 double a[3] = {0, 0, 0}, phi = 0;
                 int32_t self_seen = 0;
