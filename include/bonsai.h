@@ -45,6 +45,8 @@ extern "C" {
 #define BONSAI_ERR_TIMEOUT     (-5)  /* a bounded device-side wait gave up    */
 #define BONSAI_ERR_NAN         (-6)  /* non-finite positions detected         */
 #define BONSAI_ERR_NOT_READY   (-7)  /* stage called before its inputs exist  */
+#define BONSAI_ERR_STALE       (-8)  /* block steps: bodies drifted out of a
+                                        refitted tree (rebuild more often)   */
 
 typedef struct bonsai_ctx bonsai_ctx;
 
@@ -120,6 +122,39 @@ int bonsai_forces(bonsai_ctx *ctx, float theta, float eps, float *acc,
  * multipoles), the walk and the second kick.  No host synchronisation. */
 int bonsai_step(bonsai_ctx *ctx, float dt);
 
+/* Block (hierarchical) time steps, paper Sect. 1 and 3: only the bodies
+ * whose step ends are walked, and between rebuilds only the moments of the
+ * cells are recomputed ("refit"); the paper names the scheme, not its rules,
+ * which are these.  Body i steps with dt_max / 2^k, k in [0, max_level] the
+ * smallest level with dt_max / 2^k <= eta * sqrt(eps / |a_i|) (decided in
+ * float32 as 16^k >= c |a|^2, c = dt_max^4 / (eta^4 eps^2) rounded to float
+ * once).  One call advances one cycle of dt_max = 2^max_level substeps of
+ * dt_max / 2^max_level, all bodies synchronised at both ends: opening half
+ * kicks at the start; per substep a drift of every body, a rebuild (every
+ * rebuild_every-th substep, starting with the first) or a refit, a walk of
+ * the bodies whose step ends (each group's box is its active bodies' box),
+ * and for those the closing half kick, a new level (never coarser than the
+ * substep's alignment allows) and the next opening half kick.  theta and
+ * eps are those of the last bonsai_forces / bonsai_set_params; without
+ * forces yet they are computed first.  max_level = 0 is bonsai_step(dt_max).
+ * One system only (BONSAI_ERR_INVALID_ARG otherwise); 0 <= max_level <= 20,
+ * rebuild_every >= 1.  No host synchronisation: bonsai_sync reports
+ * BONSAI_ERR_STALE when a refitted tree no longer held a walked body's leaf
+ * (the forces of that cycle are then not trustworthy: rebuild more often). */
+int bonsai_block_cycle(bonsai_ctx *ctx, float dt_max, int max_level, float eta,
+                       int rebuild_every);
+
+/* The level every body would take from its current acceleration under
+ * (dt_max, max_level, eta) and the context's eps: levels (N int32, caller
+ * order, host buffer).  A query; nothing changes.  Requires forces. */
+int bonsai_block_levels(bonsai_ctx *ctx, float dt_max, int max_level, float eta,
+                        int32_t *levels);
+
+/* Counters of the last block cycle: out[0] = body steps that ended (forces
+ * taken), out[1] / out[2] = body-cell / body-body interactions summed over
+ * its substeps.  Synchronises. */
+int bonsai_block_stats(bonsai_ctx *ctx, long long out[3]);
+
 /* Autotuner: times the walk of the current bodies (CUDA events, mean of two
  * walks after one untimed) for every group size ncrit in {16, 32, 48, 64},
  * both group rules (group_pack 0 and 1) and walk thread-block width in
@@ -147,7 +182,8 @@ int bonsai_get_bodies(bonsai_ctx *ctx, float *pos, float *vel, int on_device);
 int bonsai_diagnostics(bonsai_ctx *ctx, double out[8]);
 
 /* Synchronise the context's stream and return (and clear) the device status:
- * BONSAI_OK, BONSAI_ERR_CAPACITY, BONSAI_ERR_TIMEOUT or BONSAI_ERR_NAN. */
+ * BONSAI_OK or the first of BONSAI_ERR_TIMEOUT, BONSAI_ERR_STALE,
+ * BONSAI_ERR_CAPACITY, BONSAI_ERR_NAN that the device recorded. */
 int bonsai_sync(bonsai_ctx *ctx);
 
 /* Device time of each stage of the last bonsai_step in milliseconds, from

@@ -21,7 +21,7 @@ _lib = None
 
 BONSAI_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "CAPACITY", -5: "TIMEOUT", -6: "NAN",
-          -7: "NOT_READY"}
+          -7: "NOT_READY", -8: "STALE"}
 
 # Entry points declared in include/bonsai.h (checked by the CPU tests).
 EXPORTS = ["bonsai_create", "bonsai_destroy", "bonsai_set_bodies", "bonsai_build",
@@ -34,7 +34,8 @@ EXPORTS = ["bonsai_create", "bonsai_destroy", "bonsai_set_bodies", "bonsai_build
            "bonsai_mlp_last_error", "bonsai_mlp_set_params", "bonsai_mlp_get_params",
            "bonsai_mlp_fit_norm", "bonsai_mlp_predict", "bonsai_mlp_grad", "bonsai_mlp_train",
            "bonsai_learn_samples", "bonsai_judge", "bonsai_set_learned", "bonsai_forces_learned",
-           "bonsai_get_judge", "bonsai_set_judge_interval", "bonsai_get_config"]
+           "bonsai_get_judge", "bonsai_set_judge_interval", "bonsai_get_config", "bonsai_block_cycle",
+           "bonsai_block_levels", "bonsai_block_stats"]
 
 MLP_IN, MLP_H, MLP_OUT = 12, 64, 3
 MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_OUT * MLP_H + MLP_OUT
@@ -97,6 +98,9 @@ def lib():
         L.bonsai_get_domains.argtypes = [p, p, p]
         L.bonsai_autotune.argtypes = [p, f, f, p, p, p]
         L.bonsai_get_config.argtypes = [p, C.POINTER(Config)]
+        L.bonsai_block_cycle.argtypes = [p, f, i, f, i]
+        L.bonsai_block_levels.argtypes = [p, f, i, f, p]
+        L.bonsai_block_stats.argtypes = [p, p]
         u64 = C.c_ulonglong
         L.bonsai_mlp_create.argtypes = [C.POINTER(p), u64]
         L.bonsai_mlp_destroy.argtypes = [p]
@@ -210,6 +214,23 @@ def bonsai_get_config(ctx) -> Config:
     cfg = Config()
     _check(ctx, lib().bonsai_get_config(ctx, C.byref(cfg)))
     return cfg
+
+
+def bonsai_block_cycle(ctx, dt_max: float, max_level: int, eta: float, rebuild_every: int = 1):
+    _check(ctx, lib().bonsai_block_cycle(ctx, dt_max, int(max_level), eta, int(rebuild_every)))
+
+
+def bonsai_block_levels(ctx, dt_max: float, max_level: int, eta: float) -> np.ndarray:
+    n, _, _ = bonsai_get_sizes(ctx)
+    out = np.zeros(n, np.int32)
+    _check(ctx, lib().bonsai_block_levels(ctx, dt_max, int(max_level), eta, out.ctypes.data))
+    return out
+
+
+def bonsai_block_stats(ctx) -> tuple[int, int, int]:
+    out = np.zeros(3, np.int64)
+    _check(ctx, lib().bonsai_block_stats(ctx, out.ctypes.data))
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def bonsai_set_params(ctx, theta: float, eps: float):
@@ -463,6 +484,10 @@ class Bonsai:
 
     def step(self, dt):
         bonsai_step(self.ctx, dt)
+        return self
+
+    def block_cycle(self, dt_max, max_level, eta, rebuild_every=1):
+        bonsai_block_cycle(self.ctx, dt_max, max_level, eta, rebuild_every)
         return self
 
     def sync(self):

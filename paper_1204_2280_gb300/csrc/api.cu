@@ -511,6 +511,8 @@ int bonsai_sync(bonsai_ctx *ctx) {
     CK(cudaMemcpy(&s, &c.st->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
     CK(cudaMemset(&c.st->status, 0, sizeof(unsigned)));
     if (s & ST_TIMEOUT) return fail(ctx, BONSAI_ERR_TIMEOUT, "a bounded device-side wait gave up");
+    if (s & ST_STALE)     // the cause of any capacity overflow in the same walk
+        return fail(ctx, BONSAI_ERR_STALE, "block steps: a body left its cell of the refitted tree; rebuild more often");
     if (s & ST_CAPACITY) return fail(ctx, BONSAI_ERR_CAPACITY, "walk stack or cell capacity exceeded");
     if (s & ST_NAN) return fail(ctx, BONSAI_ERR_NAN, "non-finite body positions");
     return BONSAI_OK;

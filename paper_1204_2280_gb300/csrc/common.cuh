@@ -54,6 +54,7 @@ constexpr int PACK_THREADS = 1024;                     // unpacked groups per gr
 constexpr unsigned ST_CAPACITY = 1u;
 constexpr unsigned ST_TIMEOUT = 2u;
 constexpr unsigned ST_NAN = 4u;
+constexpr unsigned ST_STALE = 8u;                // block steps: a refitted tree no longer holds its bodies
 
 struct DevState {
     int dom[6 * MAX_SYSTEMS];         // per system: orderable-int min xyz, max xyz
@@ -75,6 +76,8 @@ struct DevState {
     unsigned fallback;                // 1: the judge asked for the fine-theta walk
     unsigned judge_tick;              // learned evaluations since the interval was set
     unsigned judge_on;                // 1: this evaluation is judged
+    unsigned long long cyc_active;    // block steps, last cycle: body steps ended (forces taken)
+    unsigned long long cyc_inter[2];  // block steps, last cycle: n_pc, n_pp summed over substeps
 };
 
 struct Ctx {
@@ -135,6 +138,12 @@ struct Ctx {
     float graph_dt = 0.f, graph_theta = 0.f, graph_eps = 0.f;
     long long graph_n = -1;
 
+    // block time steps: while a cycle's walk runs, block_kmax >= 0 and the
+    // walk takes only the bodies whose step ends at substep block_s (their
+    // level is vel4.w); -1 otherwise
+    int block_kmax = -1;
+    unsigned block_s = 0;
+
     // learned far-field correction (bonsai_set_learned): weights, thetas,
     // judge budget, and the judge's sample and scratch
     const float *mlp_P = nullptr, *mlp_norm = nullptr;
@@ -178,6 +187,13 @@ __device__ __forceinline__ int key_cpl(unsigned long long a, unsigned long long 
     return MAX_LEVEL - p / 3 - 1;
 }
 
+// Block time steps: a body of level k (stored as a float) takes forces at
+// substep s of a cycle of 2^kmax substeps iff s is a multiple of 2^(kmax - k).
+__device__ __forceinline__ bool block_active(float level, unsigned s, int kmax) {
+    const unsigned len = 1u << (kmax - (int)level);
+    return (s & (len - 1u)) == 0u;
+}
+
 // Shared levels of two bodies that may belong to different systems (-1: none).
 __device__ __forceinline__ int body_cpl(unsigned long long a, unsigned long long b, uint8_t sa, uint8_t sb) {
     return sa == sb ? key_cpl(a, b) : -1;
@@ -194,6 +210,7 @@ cudaError_t launch_fill_sysid(Ctx &c);
 cudaError_t launch_pack(Ctx &c, const float *pos, const float *mass, const float *vel);
 cudaError_t launch_bbox(Ctx &c);
 cudaError_t launch_kick_drift_bbox(Ctx &c, float dt);
+cudaError_t launch_drift_bbox(Ctx &c, float dt);
 cudaError_t launch_keys(Ctx &c);
 cudaError_t launch_sort(Ctx &c);
 cudaError_t launch_reorder(Ctx &c);

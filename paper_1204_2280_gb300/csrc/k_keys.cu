@@ -221,8 +221,10 @@ k_kick_drift_bbox1(const float4 *__restrict__ pos, const float4 *__restrict__ ve
     const float h = 0.5f * dt;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         float4 u = vel[i], x = pos[i];
-        const float4 a = acc[i];
-        u.x = fmaf(a.x, h, u.x); u.y = fmaf(a.y, h, u.y); u.z = fmaf(a.z, h, u.z);
+        if (acc) {                         // acc NULL: drift only
+            const float4 a = acc[i];
+            u.x = fmaf(a.x, h, u.x); u.y = fmaf(a.y, h, u.y); u.z = fmaf(a.z, h, u.z);
+        }
         x.x = fmaf(u.x, dt, x.x); x.y = fmaf(u.y, dt, x.y); x.z = fmaf(u.z, dt, x.z);
         bad |= !(isfinite(x.x) && isfinite(x.y) && isfinite(x.z));
         pos_o[i] = x; vel_o[i] = u; id_o[i] = id[i];
@@ -231,6 +233,16 @@ k_kick_drift_bbox1(const float4 *__restrict__ pos, const float4 *__restrict__ ve
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&st->status, ST_NAN);
     block_bbox_atomics(v, st);
+}
+
+// Drift of every body by dt into the pre-sort arrays, with the domain box
+// (one system): the input of a rebuild during block time steps.
+cudaError_t launch_drift_bbox(Ctx &c, float dt) {
+    const int n = (int)c.n;
+    const int grid = min((n + 255) / 256, c.num_sms * 8);
+    k_kick_drift_bbox1<<<grid, 256, 0, c.stream>>>(c.pos4, c.vel4, nullptr, c.id, n, dt, c.pos4_alt, c.vel4_alt,
+                                                    c.id_alt, c.st);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_kick_drift_bbox(Ctx &c, float dt) {

@@ -330,7 +330,7 @@ __device__ __forceinline__ void walk_pop(const unsigned *stk, int &sp, int lane,
 #else
 #define WALK_ATTRS __launch_bounds__(256, BPL == 1 ? WALK_MIN_BLOCKS1 : WALK_MIN_BLOCKS2)
 #endif
-template <int BPL, bool FEAT>
+template <int BPL, bool FEAT, bool BLOCK>
 __global__ void WALK_ATTRS
 k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__ groups,
        const float4 *__restrict__ pos4, const float4 *__restrict__ test,
@@ -338,7 +338,7 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
        const float4 *__restrict__ quadA, const float2 *__restrict__ quadB,
        const uint8_t *__restrict__ sysid, float eps, int stack_cap, unsigned max_rounds,
        float4 *acc4, uint2 *counts, const uint8_t *__restrict__ cell_level, float *feat,
-       const unsigned *__restrict__ gate) {
+       const unsigned *__restrict__ gate, const float4 *__restrict__ actv, unsigned act_s, int act_kmax) {
     extern __shared__ float4 smem4[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const size_t warp_bytes = sizeof(WarpRings) + (size_t)stack_cap * sizeof(unsigned);
@@ -383,6 +383,8 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
         for (int b = 0; b < BPL; b++) {
             const int slot = bslot + slots * b;
             live[b] = slot < ng;
+            // block time steps: only the bodies whose step ends at this substep
+            if (BLOCK && live[b]) live[b] = block_active(actv[gb + slot].w, act_s, act_kmax);
             bi[b] = gb + (live[b] ? slot : 0);
             me[b] = pos4[bi[b]];
             if (live[b]) {
@@ -398,6 +400,15 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
             bx1 = fmaxf(bx1, __shfl_xor_sync(0xffffffffu, bx1, o));
             by1 = fmaxf(by1, __shfl_xor_sync(0xffffffffu, by1, o));
             bz1 = fmaxf(bz1, __shfl_xor_sync(0xffffffffu, bz1, o));
+        }
+        // Live body slots (bit = slot); a group without one is skipped.
+        unsigned long long live_slots = 0ull;
+        bool stale = false;
+        if (BLOCK) {
+            const unsigned lm0 = __ballot_sync(0xffffffffu, phase == 0 && live[0]);
+            const unsigned lm1 = BPL == 2 ? __ballot_sync(0xffffffffu, phase == 0 && live[BPL - 1]) : 0u;
+            if ((lm0 | lm1) == 0u) continue;
+            live_slots = (unsigned long long)lm0 | ((unsigned long long)lm1 << slots);
         }
         Acc A[BPL];
 #pragma unroll
@@ -439,6 +450,14 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
                 open = d2 < tc.w * tc.w;
                 acc = !open;
                 isleaf = (lk.y & LEAF_BIT) != 0u;
+                // A refitted tree whose bodies have drifted: an accepted leaf
+                // must not hold a live body of this group (its own leaf).
+                if (BLOCK && acc && isleaf) {
+                    const int lo = max((int)lk.x, gb) - gb;
+                    const int hi = min((int)lk.x + (int)(lk.y & ~LEAF_BIT), gb + ng) - gb;
+                    if (lo < hi && ((live_slots >> lo) & (hi - lo >= 64 ? ~0ull : ((1ull << (hi - lo)) - 1ull))))
+                        stale = true;
+                }
             }
             // Accepted cells -> body-cell ring.
             const unsigned am = __ballot_sync(0xffffffffu, acc);
@@ -560,11 +579,14 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
                 }
             }
         }
+        const bool any_stale = BLOCK && __any_sync(0xffffffffu, stale);
         if (lane == 0) {
-            atomicAdd(&st->inter[0], (unsigned long long)npc * (unsigned long long)ng);
-            atomicAdd(&st->inter[1], (unsigned long long)(npp - 1u) * (unsigned long long)ng);
+            const unsigned long long nlive = BLOCK ? (unsigned long long)__popcll(live_slots) : (unsigned long long)ng;
+            atomicAdd(&st->inter[0], (unsigned long long)npc * nlive);
+            atomicAdd(&st->inter[1], (unsigned long long)(npp - 1u) * nlive);
             if (overflow) atomicOr(&st->status, ST_CAPACITY);
             if (timeout) atomicOr(&st->status, ST_TIMEOUT);
+            if (any_stale) atomicOr(&st->status, ST_STALE);
         }
         __syncwarp();
     }
@@ -576,7 +598,7 @@ size_t walk_smem_bytes(int warps, int stack_cap) {
 
 // Function attribute and occupancy are set up once per shape, before any
 // stream capture of a step (the first step always runs eagerly).
-template <int BPL, bool FEAT>
+template <int BPL, bool FEAT, bool BLOCK>
 static cudaError_t launch_walk_t(Ctx &c, float eps, const unsigned *gate, cudaStream_t stream) {
     const unsigned polls = (unsigned)(c.max_spin < 0xffffffffll ? c.max_spin : 0xffffffffll);
     const int warps = c.walk_warps;
@@ -584,19 +606,20 @@ static cudaError_t launch_walk_t(Ctx &c, float eps, const unsigned *gate, cudaSt
     static size_t attr_smem = 0, occ_smem = 0;
     static int occ_warps = 0, occ_per_sm = 0;
     if (smem > attr_smem) {
-        cudaError_t e = cudaFuncSetAttribute(k_walk<BPL, FEAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_walk<BPL, FEAT, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_smem = smem;
     }
     if (occ_warps != warps || occ_smem != smem) {
         int per = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk<BPL, FEAT>, warps * 32, smem);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk<BPL, FEAT, BLOCK>, warps * 32, smem);
         if (e != cudaSuccess) return e;
         occ_warps = warps; occ_smem = smem; occ_per_sm = per < 1 ? 1 : per;
     }
-    k_walk<BPL, FEAT><<<c.num_sms * occ_per_sm, warps * 32, smem, stream>>>(
+    k_walk<BPL, FEAT, BLOCK><<<c.num_sms * occ_per_sm, warps * 32, smem, stream>>>(
         c.st, c.st, c.groups, c.pos4, c.test, c.cell_link, c.mono, c.quadA, c.quadB, c.sysid, eps,
-        c.list_capacity, polls, c.acc4, c.counts, c.cell_level, c.feat, gate);
+        c.list_capacity, polls, c.acc4, c.counts, c.cell_level, c.feat, gate,
+        BLOCK ? c.vel4 : nullptr, c.block_s, c.block_kmax);
     return cudaGetLastError();
 }
 
@@ -606,14 +629,19 @@ static cudaError_t launch_walk_t(Ctx &c, float eps, const unsigned *gate, cudaSt
 // joined back into the context's stream (event edges inside a captured
 // step), so the tail of each launch overlaps the other's work.
 cudaError_t launch_walk(Ctx &c, float eps, bool features, const unsigned *gate) {
-    if (c.ncrit < WALK_BPL2_FROM)
-        return features ? launch_walk_t<1, true>(c, eps, gate, c.stream) : launch_walk_t<1, false>(c, eps, gate, c.stream);
+    // instantiations: plain, with learned features, or block time steps
+    auto one = [&](bool two, cudaStream_t st) -> cudaError_t {
+        if (c.block_kmax >= 0)
+            return two ? launch_walk_t<2, false, true>(c, eps, gate, st) : launch_walk_t<1, false, true>(c, eps, gate, st);
+        if (features)
+            return two ? launch_walk_t<2, true, false>(c, eps, gate, st) : launch_walk_t<1, true, false>(c, eps, gate, st);
+        return two ? launch_walk_t<2, false, false>(c, eps, gate, st) : launch_walk_t<1, false, false>(c, eps, gate, st);
+    };
+    if (c.ncrit < WALK_BPL2_FROM) return one(false, c.stream);
     cudaError_t e = cudaEventRecord(c.ev_fork, c.stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c.side, c.ev_fork, 0);
-    if (e == cudaSuccess)
-        e = features ? launch_walk_t<2, true>(c, eps, gate, c.side) : launch_walk_t<2, false>(c, eps, gate, c.side);
-    if (e == cudaSuccess)
-        e = features ? launch_walk_t<1, true>(c, eps, gate, c.stream) : launch_walk_t<1, false>(c, eps, gate, c.stream);
+    if (e == cudaSuccess) e = one(true, c.side);
+    if (e == cudaSuccess) e = one(false, c.stream);
     if (e == cudaSuccess) e = cudaEventRecord(c.ev_join, c.side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c.stream, c.ev_join, 0);
     return e;
