@@ -77,6 +77,7 @@ def parse():
     p.add_argument("--no-ensemble", action="store_true")
     p.add_argument("--ensemble-systems", type=int, default=64)
     p.add_argument("--no-learned", action="store_true")
+    p.add_argument("--no-block", action="store_true")
     p.add_argument("--learned-n", type=int, default=1 << 22)
     p.add_argument("--learned-plummer", type=int, default=8, help="Plummer training snapshots")
     p.add_argument("--learned-merger", type=int, default=8, help="merger training snapshots")
@@ -486,6 +487,86 @@ def stage_bytes(n, ncells, ngroups):
             "multipoles": 16 * n + 44 * ncells, "kick": 48 * n}
 
 
+def run_block(a, dev, stream):
+    """Block time steps (paper Sect. 1 and 3) on the bench workload: cycles
+    of dt_max = 8 dt (dt the bench step) in 2^3 substeps, levels from
+    eta sqrt(eps / |a|) for eta in {0.2, 0.4}, against 8 shared steps of dt
+    per cycle (the shared step must take the finest step the fastest bodies
+    need).  Rebuilt every substep (R = 1) and every 4th with refits between
+    (R = 4).  Per variant: device ms per cycle (CUDA events, L2 flushed
+    between cycles), body steps that ended and interactions per cycle, and
+    the FP64 energy error after the timed cycles (potentials of a fresh
+    rebuild at both ends, so every variant is measured with one estimator)."""
+    import torch
+    import paper_1204_2280_gb300 as B
+    from paper_1204_2280_gb300 import workloads as W
+    b = W.plummer(a.n, a.seed)
+    kmax, dt_max = 3, a.dt * 8
+    cfg = dict(nleaf=a.nleaf, ncrit=a.ncrit, walk_warps=a.walk_warps, group_pack=a.group_pack)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = {"n": a.n, "dt_max": dt_max, "max_level": kmax, "theta": a.theta, "eps": a.eps}
+    warm, timed = 2, 3
+
+    def timed_cycles(fn):
+        ms = []
+        for _ in range(timed):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return sum(ms) / len(ms)
+
+    def fresh():
+        bz = B.Bonsai(B.Config(**cfg), stream=stream)
+        bz.set_bodies(torch.from_numpy(b.pos).to(dev), torch.from_numpy(b.mass).to(dev),
+                      torch.from_numpy(b.vel).to(dev))
+        bz.build().multipoles().forces(a.theta, a.eps)
+        B.bonsai_set_params(bz.ctx, a.theta, a.eps)
+        return bz
+
+    def energy(bz):
+        bz.build().multipoles().forces(a.theta, a.eps)
+        return B.bonsai_diagnostics(bz.ctx)[2]
+
+    bz = fresh()
+    e0 = B.bonsai_diagnostics(bz.ctx)[2]
+    for _ in range(warm * 8):
+        bz.step(a.dt)
+    ms = timed_cycles(lambda: [bz.step(a.dt) for _ in range(8)])
+    e1 = energy(bz)
+    bz.sync()
+    bz.close()
+    out["shared"] = {"ms_per_cycle": ms, "body_steps_per_cycle": 8 * a.n,
+                     "energy_err": (e1 - e0) / abs(e0), "particles_per_s": 8 * a.n / (ms / 1e3)}
+    for eta in (0.2, 0.4):
+        for r in (1, 4):
+            bz = fresh()
+            if r == 1:
+                lev = B.bonsai_block_levels(bz.ctx, dt_max, kmax, eta)
+                out[f"levels_at_start_eta{eta}"] = [int((lev == k).sum()) for k in range(kmax + 1)]
+            e0 = B.bonsai_diagnostics(bz.ctx)[2]
+            for _ in range(warm):
+                bz.block_cycle(dt_max, kmax, eta, r)
+            ms = timed_cycles(lambda: bz.block_cycle(dt_max, kmax, eta, r))
+            act, npc, npp = B.bonsai_block_stats(bz.ctx)
+            e1 = energy(bz)
+            bz.sync()
+            bz.close()
+            out[f"eta{eta}_r{r}"] = {
+                "ms_per_cycle": ms, "body_steps_per_cycle": act, "active_fraction": act / (8 * a.n),
+                "interactions_per_body_step": (npc + npp) / max(act, 1), "energy_err": (e1 - e0) / abs(e0),
+                "speedup_vs_shared": out["shared"]["ms_per_cycle"] / ms,
+                "particles_per_s_equivalent": 8 * a.n / (ms / 1e3)}
+    out["what"] = ("cycle of dt_max = 8 dt: shared = 8 bonsai_steps of dt; etaE_rR = one bonsai_block_cycle "
+                   "(accuracy eta = E) with a rebuild every R substeps (refits between); "
+                   "particles_per_s_equivalent = 8 N / cycle time")
+    return out
+
+
 def run_sweep(a, dev, stream):
     """Scaling sweep (group knobs from the command line): Plummer spheres N = 2^15 .. 2^21 and 2^23 at
     theta = 0.75 (interactions per body vs N), N = 2^22 (seed 2) and 2^24 (seed 3)
@@ -670,6 +751,7 @@ def run_ours(a, rank, world, local_rank):
     bz.close()
 
     ens = None if a.no_ensemble else run_ensemble(a, dev, stream, rank, world)
+    blk = None if a.no_block else run_block(a, dev, stream)
     lrn = None if a.no_learned else run_learned(a, dev, stream)
 
     cpu = None
@@ -697,6 +779,7 @@ def run_ours(a, rank, world, local_rank):
             "interactions_per_s": (sum(npc) + sum(npp)) / (walk_ms / 1e3),
             "wall_s_timed_loop": t_wall,
             "ensemble": ens,
+            "block": blk,
             "learned": lrn,
         }
         print(json.dumps(line), flush=True)

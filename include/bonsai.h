@@ -45,8 +45,6 @@ extern "C" {
 #define BONSAI_ERR_TIMEOUT     (-5)  /* a bounded device-side wait gave up    */
 #define BONSAI_ERR_NAN         (-6)  /* non-finite positions detected         */
 #define BONSAI_ERR_NOT_READY   (-7)  /* stage called before its inputs exist  */
-#define BONSAI_ERR_STALE       (-8)  /* block steps: bodies drifted out of a
-                                        refitted tree (rebuild more often)   */
 
 typedef struct bonsai_ctx bonsai_ctx;
 
@@ -138,9 +136,11 @@ int bonsai_step(bonsai_ctx *ctx, float dt);
  * eps are those of the last bonsai_forces / bonsai_set_params; without
  * forces yet they are computed first.  max_level = 0 is bonsai_step(dt_max).
  * One system only (BONSAI_ERR_INVALID_ARG otherwise); 0 <= max_level <= 20,
- * rebuild_every >= 1.  No host synchronisation: bonsai_sync reports
- * BONSAI_ERR_STALE when a refitted tree no longer held a walked body's leaf
- * (the forces of that cycle are then not trustworthy: rebuild more often). */
+ * rebuild_every >= 1.  A refitted cell opens with 2 ext / theta + delta,
+ * ext the half side of its build-time cube enlarged to hold its bodies'
+ * current positions (a leaf from its bodies, a parent from its children), so
+ * a cell that holds a walked body is always opened for that body's group.
+ * No host synchronisation. */
 int bonsai_block_cycle(bonsai_ctx *ctx, float dt_max, int max_level, float eta,
                        int rebuild_every);
 
@@ -182,8 +182,7 @@ int bonsai_get_bodies(bonsai_ctx *ctx, float *pos, float *vel, int on_device);
 int bonsai_diagnostics(bonsai_ctx *ctx, double out[8]);
 
 /* Synchronise the context's stream and return (and clear) the device status:
- * BONSAI_OK or the first of BONSAI_ERR_TIMEOUT, BONSAI_ERR_STALE,
- * BONSAI_ERR_CAPACITY, BONSAI_ERR_NAN that the device recorded. */
+ * BONSAI_OK, BONSAI_ERR_CAPACITY, BONSAI_ERR_TIMEOUT or BONSAI_ERR_NAN. */
 int bonsai_sync(bonsai_ctx *ctx);
 
 /* Device time of each stage of the last bonsai_step in milliseconds, from

@@ -58,7 +58,8 @@ def lib():
             L.oracle_groups.argtypes = [i64, p, p, p, p, C.c_int, C.c_int, i64, p, p]
             L.oracle_groups.restype = i64
             L.oracle_moments.argtypes = [i64, p, p, p, p, p, p, p]
-            L.oracle_open_radius.argtypes = [i64, p, p, p, p, d, p, d, p]
+            L.oracle_open_radius.argtypes = [i64, p, p, p, p, d, p, d, p, p]
+            L.oracle_refit_extent.argtypes = [i64, p, p, p, p, p, p, p, d, p, p]
             L.oracle_walk.argtypes = [i64, p, p, i64, p, p, p, p, p, p, p, p, i64, p, p,
                                       d, d, d, p, p, p, p, p, p, p, p]
             L.oracle_direct.argtypes = [p, p, i64, p, i64, d, p, p]
@@ -168,12 +169,28 @@ def moments(tree: Tree, spos, smass):
     return M, com, Q
 
 
-def open_radius(tree: Tree, skeys, mn, S, com, theta: float) -> np.ndarray:
+def open_radius(tree: Tree, skeys, mn, S, com, theta: float, ext=None) -> np.ndarray:
+    """l / theta + |com - centre| per cell; with ext (a refit's enlarged
+    half sides, refit_extent) 2 ext / theta + |com - centre|."""
     ro = np.zeros(tree.ncells)
     lib().oracle_open_radius(tree.ncells, _ptr(tree.body_begin), _ptr(tree.level),
                              _ptr(np.ascontiguousarray(skeys, np.uint64)), _ptr(_f32(mn)),
-                             float(S), _ptr(np.ascontiguousarray(com)), float(theta), _ptr(ro))
+                             float(S), _ptr(np.ascontiguousarray(com)), float(theta), _ptr(ro),
+                             _ptr(np.ascontiguousarray(ext, np.float64)) if ext is not None else None)
     return ro
+
+
+def refit_extent(tree: Tree, skeys, mn, S, spos) -> np.ndarray:
+    """Half side of each cell's cube about its build-time centre enlarged to
+    hold its bodies at spos (sorted order), bounded from the leaves up."""
+    ext = np.zeros(tree.ncells)
+    rc = lib().oracle_refit_extent(tree.ncells, _ptr(tree.body_begin), _ptr(tree.body_count),
+                                   _ptr(tree.child_begin), _ptr(tree.nchild), _ptr(tree.level),
+                                   _ptr(np.ascontiguousarray(skeys, np.uint64)), _ptr(_f32(mn)), float(S),
+                                   _ptr(_f32(spos)), _ptr(ext))
+    if rc:
+        raise MemoryError("oracle_refit_extent")
+    return ext
 
 
 def cell_cube(tree: Tree, skeys, mn, S):
@@ -326,7 +343,8 @@ def kdk_step(pos, vel, mass, acc0, dt: float, theta: float, eps: float, nleaf: i
 #    gets its level and an opening half kick a * dt_i / 2; each substep
 #    drifts every body by dt_min, refreshes the tree (a rebuild every
 #    `rebuild_every` substeps, else new moments of the existing cells at the
-#    current positions), walks the active bodies (those whose step ends now:
+#    current positions with opening radii from each cell's build-time cube
+#    enlarged to hold its bodies), walks the active bodies (those whose step ends now:
 #    s a multiple of 2^(kmax - k_i)) and gives them the closing half kick;
 #    before the last substep they then take a new level, no coarser than the
 #    substep allows (k >= kmax - trailing zeros of s), and the opening half
@@ -371,12 +389,14 @@ class _BlockTree:
     def forces(self, x32, mass, theta, eps, active):
         """Accelerations and potentials (caller order) of the active bodies:
         moments of the cells at the current positions, opening radii from
-        the build-time cell geometry and the current com, walk of the active
-        bodies."""
+        each cell's cube enlarged to hold its current bodies (the plain
+        radius right after a rebuild) and the current com, walk of the
+        active bodies."""
         p = self.perm
         spos, smass = np.ascontiguousarray(x32[p]), np.ascontiguousarray(mass[p])
         M, com, Q = moments(self.tree, spos, smass)
-        ro = open_radius(self.tree, self.skeys, self.mn, self.S, com, theta)
+        ext = refit_extent(self.tree, self.skeys, self.mn, self.S, spos)
+        ro = open_radius(self.tree, self.skeys, self.mn, self.S, com, theta, ext)
         acc_s, pot_s, _, _, _ = walk(spos, smass, self.tree, M, com, Q, ro, self.gb, self.gc, eps,
                                      active=np.asarray(active)[p])
         n = x32.shape[0]

@@ -385,15 +385,63 @@ static void cell_cube(uint64_t key, int l, const float *mn, double S,
 int oracle_open_radius(int64_t ncells, const int32_t *body_begin,
                        const int32_t *level, const uint64_t *skeys,
                        const float *mn, double S, const double *com,
-                       double theta, double *r_open)
+                       double theta, double *r_open, const double *ext)
 {
     #pragma omp parallel for schedule(static)
     for (int64_t c = 0; c < ncells; c++) {
         double ctr[3], l;
         cell_cube(skeys[body_begin[c]], level[c], mn, S, ctr, &l);
+        if (ext) l = 2.0 * ext[c];      /* refit: the cube enlarged to hold the bodies */
         double dx = com[3 * c] - ctr[0], dy = com[3 * c + 1] - ctr[1], dz = com[3 * c + 2] - ctr[2];
         r_open[c] = l / theta + sqrt(dx * dx + dy * dy + dz * dz);
     }
+    return 0;
+}
+
+/* Block time steps, refit between rebuilds (Sect. 3: only the moments are
+ * recomputed): ext[c] = half side of a cube about the cell's build-time
+ * geometric centre that holds the cell's bodies at their current positions,
+ * at least l/2, bounded from the leaves up -- a leaf from its bodies, an
+ * internal cell as max(l/2, max_k |centre_k - centre|_inf + ext_k) over its
+ * children.  The opening radius of a refitted cell is then 2 ext / theta +
+ * delta: for theta < 2/sqrt(3) a cell holding a body of a group is always
+ * opened for that group.  At the build positions every body lies in its
+ * cell's cube, so ext = l/2 and the radius is the plain one. */
+int oracle_refit_extent(int64_t ncells, const int32_t *body_begin,
+                        const int32_t *body_count, const int32_t *child_begin,
+                        const int32_t *nchild, const int32_t *level,
+                        const uint64_t *skeys, const float *mn, double S,
+                        const float *spos, double *ext)
+{
+    double *ctr = (double *)malloc(sizeof(double) * 3 * (size_t)(ncells > 0 ? ncells : 1));
+    if (!ctr) return -1;
+    for (int64_t c = 0; c < ncells; c++) {
+        double l;
+        cell_cube(skeys[body_begin[c]], level[c], mn, S, ctr + 3 * c, &l);
+        ext[c] = 0.5 * l;
+    }
+    for (int64_t c = ncells - 1; c >= 0; c--) {   /* breadth-first order: children after parents */
+        double e = ext[c];
+        if (nchild[c] == 0) {
+            for (int64_t i = body_begin[c]; i < body_begin[c] + body_count[c]; i++)
+                for (int d = 0; d < 3; d++) {
+                    double t = fabs((double)spos[3 * i + d] - ctr[3 * c + d]);
+                    if (t > e) e = t;
+                }
+        } else {
+            for (int k = 0; k < nchild[c]; k++) {
+                int64_t ch = child_begin[c] + k;
+                double m = 0;
+                for (int d = 0; d < 3; d++) {
+                    double t = fabs(ctr[3 * ch + d] - ctr[3 * c + d]);
+                    if (t > m) m = t;
+                }
+                if (m + ext[ch] > e) e = m + ext[ch];
+            }
+        }
+        ext[c] = e;
+    }
+    free(ctr);
     return 0;
 }
 

@@ -21,7 +21,7 @@ _lib = None
 
 BONSAI_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "CAPACITY", -5: "TIMEOUT", -6: "NAN",
-          -7: "NOT_READY", -8: "STALE"}
+          -7: "NOT_READY"}
 
 # Entry points declared in include/bonsai.h (checked by the CPU tests).
 EXPORTS = ["bonsai_create", "bonsai_destroy", "bonsai_set_bodies", "bonsai_build",

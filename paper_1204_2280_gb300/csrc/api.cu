@@ -75,7 +75,7 @@ cudaError_t alloc_bodies(Ctx &c, long long n) {
     a.take(c.cell_level, ccap, plan); a.take(c.cell_parent, ccap, plan);
     a.take(c.cell_done, ccap, plan); a.take(c.cell_cb, ccap, plan);
     a.take(c.mono, ccap, plan); a.take(c.quadA, ccap, plan); a.take(c.quadB, ccap, plan);
-    a.take(c.test, ccap, plan); a.take(c.delta, ccap, plan);
+    a.take(c.test, ccap, plan); a.take(c.delta, ccap, plan); a.take(c.cext, ccap, plan);
     a.take(c.shadow, 10 * (size_t)(ccap < 585 * MAX_SYSTEMS ? ccap : 585 * MAX_SYSTEMS), plan);   // FP64 copies (levels < FP64_LEVELS <= 4)
     a.take(c.groups, n, plan); a.take(c.groups_raw, n, plan);
     a.take(c.group_lvl, n, plan); a.take(c.group_flag, n, plan); a.take(c.group_bcount, (n + PACK_THREADS - 1) / PACK_THREADS, plan);
@@ -511,8 +511,6 @@ int bonsai_sync(bonsai_ctx *ctx) {
     CK(cudaMemcpy(&s, &c.st->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
     CK(cudaMemset(&c.st->status, 0, sizeof(unsigned)));
     if (s & ST_TIMEOUT) return fail(ctx, BONSAI_ERR_TIMEOUT, "a bounded device-side wait gave up");
-    if (s & ST_STALE)     // the cause of any capacity overflow in the same walk
-        return fail(ctx, BONSAI_ERR_STALE, "block steps: a body left its cell of the refitted tree; rebuild more often");
     if (s & ST_CAPACITY) return fail(ctx, BONSAI_ERR_CAPACITY, "walk stack or cell capacity exceeded");
     if (s & ST_NAN) return fail(ctx, BONSAI_ERR_NAN, "non-finite body positions");
     return BONSAI_OK;

@@ -12,7 +12,9 @@
 //    every body synchronised at both ends: opening half kicks for all at the
 //    start; per substep a drift of every body, a rebuild (every
 //    `rebuild_every` substeps) or a refit (moments of the existing cells at
-//    the current positions), a walk of the bodies whose step ends, and their
+//    the current positions; opening radii from each cell's build-time cube
+//    enlarged to hold its bodies, so a cell holding a walked body is never
+//    accepted by that body's group), a walk of the bodies whose step ends, and their
 //    closing half kick, new level (never coarser than the substep allows)
 //    and opening half kick; the last substep only closes.
 // A body's level lives in vel4.w, which the rebuild's reorder carries along.
@@ -142,7 +144,8 @@ static cudaError_t block_cycle(Ctx &c, float dt_max, int kmax, float eta, int re
             k_block_refit_reset<<<cgrid, 256, 0, c.stream>>>(c.st, c.cell_done);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
-        if ((e = launch_multipoles(c)) != cudaSuccess) return e;
+        const bool rebuilt = (s - 1) % (unsigned)rebuild == 0u;
+        if ((e = rebuilt ? launch_multipoles(c) : launch_multipoles_refit(c)) != cudaSuccess) return e;
         if ((e = launch_open_radius(c, c.theta)) != cudaSuccess) return e;
         c.block_kmax = kmax;
         c.block_s = s;

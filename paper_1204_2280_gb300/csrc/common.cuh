@@ -54,7 +54,6 @@ constexpr int PACK_THREADS = 1024;                     // unpacked groups per gr
 constexpr unsigned ST_CAPACITY = 1u;
 constexpr unsigned ST_TIMEOUT = 2u;
 constexpr unsigned ST_NAN = 4u;
-constexpr unsigned ST_STALE = 8u;                // block steps: a refitted tree no longer holds its bodies
 
 struct DevState {
     int dom[6 * MAX_SYSTEMS];         // per system: orderable-int min xyz, max xyz
@@ -112,7 +111,8 @@ struct Ctx {
     uint32_t *cell_parent = nullptr, *cell_done = nullptr, *cell_cb = nullptr;
     float4 *mono = nullptr, *quadA = nullptr, *test = nullptr;
     float2 *quadB = nullptr;
-    float2 *delta = nullptr;         // per cell: (|com - centre|, side l)
+    float2 *delta = nullptr;         // per cell: (|com - centre|, side l; after a refit 2 ext)
+    float4 *cext = nullptr;          // per cell after a refit: build-time centre, half side ext holding its bodies
     double *shadow = nullptr;        // FP64 moments of the top levels (10 per cell)
     uint2 *groups = nullptr;
     // sibling packing (group_pack = 1): the unpacked groups, their cell level
@@ -216,6 +216,7 @@ cudaError_t launch_sort(Ctx &c);
 cudaError_t launch_reorder(Ctx &c);
 cudaError_t launch_build(Ctx &c);
 cudaError_t launch_multipoles(Ctx &c);
+cudaError_t launch_multipoles_refit(Ctx &c);
 cudaError_t launch_open_radius(Ctx &c, float theta, const unsigned *gate = nullptr);
 cudaError_t launch_walk(Ctx &c, float eps, bool features = false, const unsigned *gate = nullptr);
 cudaError_t launch_direct(Ctx &c, const uint32_t *targets, int ntar, float eps, float4 *partial, int nsplit,

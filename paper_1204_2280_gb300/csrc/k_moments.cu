@@ -27,17 +27,33 @@ __device__ __forceinline__ unsigned compact3(unsigned long long x) {
     return (unsigned)x;
 }
 
-// (|com - geometric centre|, side) of a cell at `level` of system `sys`
-// whose first body has key k.
-__device__ float2 cell_delta(unsigned long long k, int level, int sys, float3 com, const DevState *st) {
+// Geometric centre and side of a cell at `level` of system `sys` whose
+// first body has key k.
+__device__ __forceinline__ float cell_cube(unsigned long long k, int level, int sys, const DevState *st, float3 &c) {
     unsigned long long pre = key_prefix(k, level);
     float l = ldexpf(st->side[sys], -level);
     const float *mn = st->mn + 3 * sys;
-    float cx = fmaf((float)compact3(pre) + 0.5f, l, mn[0]);
-    float cy = fmaf((float)compact3(pre >> 1) + 0.5f, l, mn[1]);
-    float cz = fmaf((float)compact3(pre >> 2) + 0.5f, l, mn[2]);
-    float dx = com.x - cx, dy = com.y - cy, dz = com.z - cz;
-    return make_float2(sqrtf(dx * dx + dy * dy + dz * dz), l);
+    c.x = fmaf((float)compact3(pre) + 0.5f, l, mn[0]);
+    c.y = fmaf((float)compact3(pre >> 1) + 0.5f, l, mn[1]);
+    c.z = fmaf((float)compact3(pre >> 2) + 0.5f, l, mn[2]);
+    return l;
+}
+
+__device__ __forceinline__ float com_offset(float3 com, float3 c) {
+    float dx = com.x - c.x, dy = com.y - c.y, dz = com.z - c.z;
+    return sqrtf(dx * dx + dy * dy + dz * dz);
+}
+
+// (|com - geometric centre|, side) of a cell at `level` of system `sys`
+// whose first body has key k.
+__device__ float2 cell_delta(unsigned long long k, int level, int sys, float3 com, const DevState *st) {
+    float3 c;
+    const float l = cell_cube(k, level, sys, st, c);
+    return make_float2(com_offset(com, c), l);
+}
+
+__device__ __forceinline__ float dist_inf(float3 a, float3 b) {
+    return fmaxf(fabsf(a.x - b.x), fmaxf(fabsf(a.y - b.y), fabsf(a.z - b.z)));
 }
 
 struct Mom32 { float M, x, y, z, q[6]; };
@@ -56,13 +72,21 @@ __device__ __forceinline__ void store32(int c, const Mom32 &m, float4 *mono, flo
     qb[c] = make_float2(-m.q[4], -m.q[5]);
 }
 
+// REFIT (block time steps, between rebuilds): the bodies may have left the
+// cells they were sorted into.  Each cell also gets ext = half side of a cube
+// about its build-time centre that holds its bodies (at least l/2; a leaf
+// from its bodies, a parent as max(l/2, max_k |centre_k - centre|_inf +
+// ext_k)), stored with the centre in cext, and delta holds (|com - centre|,
+// 2 ext): the opening radius 2 ext / theta + delta then keeps every cell that
+// holds a body of a group opened for it (theta < 2 / sqrt(3)).
+template <bool REFIT>
 __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__restrict__ stc, DevState *st,
                                                const uint2 *__restrict__ cell_body, const uint2 *__restrict__ cell_link,
                                                const uint8_t *__restrict__ cell_level,
                                                const uint32_t *__restrict__ cell_parent, uint32_t *cell_done,
                                                const float4 *__restrict__ pos4, const unsigned long long *__restrict__ sk,
                                                const uint8_t *__restrict__ sysid, float4 *mono, float4 *qa, float2 *qb,
-                                               float2 *delta, double *shadow) {
+                                               float2 *delta, double *shadow, float4 *cext) {
     uint2 link = cell_link[c];
     if (!(link.y & LEAF_BIT)) return;
 
@@ -74,8 +98,12 @@ __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__res
     float4 x0 = pos4[b];
     float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
     float sxx = 0.f, syy = 0.f, szz = 0.f, sxy = 0.f, sxz = 0.f, syz = 0.f;
+    float3 ctr = make_float3(0.f, 0.f, 0.f);
+    float ext = 0.f;
+    if (REFIT) ext = 0.5f * cell_cube(sk[b], cell_level[c], sysid[b], stc, ctr);
     for (unsigned j = b; j < b + cnt; j++) {
         const float4 p = pos4[j];
+        if (REFIT) ext = fmaxf(ext, dist_inf(make_float3(p.x, p.y, p.z), ctr));
         const float ux = p.x - x0.x, uy = p.y - x0.y, uz = p.z - x0.z;
         const float wx = p.w * ux, wy = p.w * uy, wz = p.w * uz;
         M += p.w;
@@ -98,7 +126,12 @@ __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__res
     // ancestor: it gives every geometric centre on the way up.
     const unsigned long long kb = sk[b];
     const int sysb = sysid[b];
-    delta[c] = cell_delta(kb, lev, sysb, make_float3(m.x, m.y, m.z), stc);
+    if (REFIT) {
+        delta[c] = make_float2(com_offset(make_float3(m.x, m.y, m.z), ctr), 2.f * ext);
+        cext[c] = make_float4(ctr.x, ctr.y, ctr.z, ext);
+    } else {
+        delta[c] = cell_delta(kb, lev, sysb, make_float3(m.x, m.y, m.z), stc);
+    }
     if (lev < FP64_LEVELS) {
         double *s = shadow + 10 * (size_t)c;
         s[0] = m.M; s[1] = m.x; s[2] = m.y; s[3] = m.z;
@@ -198,7 +231,18 @@ __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__res
             }
         }
         store32(c, m, mono, qa, qb);
-        delta[c] = cell_delta(kb, lv, sysb, make_float3(m.x, m.y, m.z), stc);
+        if (REFIT) {
+            float3 pc;
+            float e = 0.5f * cell_cube(kb, lv, sysb, stc, pc);
+            for (unsigned k = 0; k < nch; k++) {
+                const float4 ce = __ldcg(cext + cb + k);
+                e = fmaxf(e, dist_inf(make_float3(ce.x, ce.y, ce.z), pc) + ce.w);
+            }
+            delta[c] = make_float2(com_offset(make_float3(m.x, m.y, m.z), pc), 2.f * e);
+            cext[c] = make_float4(pc.x, pc.y, pc.z, e);
+        } else {
+            delta[c] = cell_delta(kb, lv, sysb, make_float3(m.x, m.y, m.z), stc);
+        }
     }
 }
 
@@ -206,24 +250,35 @@ __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__res
 // then up the tree while it is the last child to arrive.  A thread per cell
 // of the capacity keeps many climbs in flight; a grid-stride loop that
 // serialises them per thread measured twice as slow.
+template <bool REFIT>
 __global__ void __launch_bounds__(256, 4)
 k_multipoles(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__ cell_body,
              const uint2 *__restrict__ cell_link, const uint8_t *__restrict__ cell_level,
              const uint32_t *__restrict__ cell_parent, uint32_t *cell_done,
              const float4 *__restrict__ pos4, const unsigned long long *__restrict__ sk,
              const uint8_t *__restrict__ sysid, float4 *mono, float4 *qa, float2 *qb, float2 *delta,
-             double *shadow) {
+             double *shadow, float4 *cext) {
     const unsigned c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= stc->ncells || (stc->status & ST_TIMEOUT)) return;
-    multipole_cell(c, stc, st, cell_body, cell_link, cell_level, cell_parent, cell_done, pos4, sk, sysid, mono, qa, qb,
-                   delta, shadow);
+    multipole_cell<REFIT>(c, stc, st, cell_body, cell_link, cell_level, cell_parent, cell_done, pos4, sk, sysid, mono,
+                          qa, qb, delta, shadow, cext);
 }
 
 cudaError_t launch_multipoles(Ctx &c) {
     const unsigned grid = (unsigned)((c.ccap + 255) / 256);
-    k_multipoles<<<grid, 256, 0, c.stream>>>(c.st, c.st, c.cell_body, c.cell_link, c.cell_level,
-                                             c.cell_parent, c.cell_done, c.pos4, c.keys, c.sysid,
-                                             c.mono, c.quadA, c.quadB, c.delta, c.shadow);
+    k_multipoles<false><<<grid, 256, 0, c.stream>>>(c.st, c.st, c.cell_body, c.cell_link, c.cell_level,
+                                                    c.cell_parent, c.cell_done, c.pos4, c.keys, c.sysid,
+                                                    c.mono, c.quadA, c.quadB, c.delta, c.shadow, nullptr);
+    return cudaGetLastError();
+}
+
+// Moments of the existing cells at the bodies' current positions (block time
+// steps between rebuilds), with each cell's cube enlarged to hold its bodies.
+cudaError_t launch_multipoles_refit(Ctx &c) {
+    const unsigned grid = (unsigned)((c.ccap + 255) / 256);
+    k_multipoles<true><<<grid, 256, 0, c.stream>>>(c.st, c.st, c.cell_body, c.cell_link, c.cell_level,
+                                                   c.cell_parent, c.cell_done, c.pos4, c.keys, c.sysid,
+                                                   c.mono, c.quadA, c.quadB, c.delta, c.shadow, c.cext);
     return cudaGetLastError();
 }
 

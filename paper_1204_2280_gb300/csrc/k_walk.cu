@@ -402,13 +402,12 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
             bz1 = fmaxf(bz1, __shfl_xor_sync(0xffffffffu, bz1, o));
         }
         // Live body slots (bit = slot); a group without one is skipped.
-        unsigned long long live_slots = 0ull;
-        bool stale = false;
-        if (BLOCK) {
+        unsigned nlive = (unsigned)ng;
+        if (BLOCK) {                               // a group without a live body is skipped
             const unsigned lm0 = __ballot_sync(0xffffffffu, phase == 0 && live[0]);
             const unsigned lm1 = BPL == 2 ? __ballot_sync(0xffffffffu, phase == 0 && live[BPL - 1]) : 0u;
-            if ((lm0 | lm1) == 0u) continue;
-            live_slots = (unsigned long long)lm0 | ((unsigned long long)lm1 << slots);
+            nlive = (unsigned)(__popc(lm0) + __popc(lm1));
+            if (nlive == 0u) continue;
         }
         Acc A[BPL];
 #pragma unroll
@@ -450,14 +449,6 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
                 open = d2 < tc.w * tc.w;
                 acc = !open;
                 isleaf = (lk.y & LEAF_BIT) != 0u;
-                // A refitted tree whose bodies have drifted: an accepted leaf
-                // must not hold a live body of this group (its own leaf).
-                if (BLOCK && acc && isleaf) {
-                    const int lo = max((int)lk.x, gb) - gb;
-                    const int hi = min((int)lk.x + (int)(lk.y & ~LEAF_BIT), gb + ng) - gb;
-                    if (lo < hi && ((live_slots >> lo) & (hi - lo >= 64 ? ~0ull : ((1ull << (hi - lo)) - 1ull))))
-                        stale = true;
-                }
             }
             // Accepted cells -> body-cell ring.
             const unsigned am = __ballot_sync(0xffffffffu, acc);
@@ -579,14 +570,11 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
                 }
             }
         }
-        const bool any_stale = BLOCK && __any_sync(0xffffffffu, stale);
         if (lane == 0) {
-            const unsigned long long nlive = BLOCK ? (unsigned long long)__popcll(live_slots) : (unsigned long long)ng;
-            atomicAdd(&st->inter[0], (unsigned long long)npc * nlive);
-            atomicAdd(&st->inter[1], (unsigned long long)(npp - 1u) * nlive);
+            atomicAdd(&st->inter[0], (unsigned long long)npc * (unsigned long long)nlive);
+            atomicAdd(&st->inter[1], (unsigned long long)(npp - 1u) * (unsigned long long)nlive);
             if (overflow) atomicOr(&st->status, ST_CAPACITY);
             if (timeout) atomicOr(&st->status, ST_TIMEOUT);
-            if (any_stale) atomicOr(&st->status, ST_STALE);
         }
         __syncwarp();
     }

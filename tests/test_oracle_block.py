@@ -121,3 +121,40 @@ def test_refit_between_rebuilds_stays_close(orc):
     assert np.percentile(dx, 99) <= 5e-4 and dx.max() <= 5e-3
     rel = np.linalg.norm(a4 - a1, axis=1) / np.linalg.norm(a1, axis=1)
     assert np.median(rel) <= 1e-3 and np.percentile(rel, 99) <= 2e-2
+
+
+def test_refit_extent_bounds_every_body(orc):
+    """At the build positions each cell's extent is l/2 exactly; after a
+    drift it bounds (max-norm about the build-time centre) every body of the
+    cell, exactly so for leaves; brute force over all cells."""
+    b = W.plummer(3000, 26)
+    mn, S = orc.domain(b.pos)
+    k = orc.keys(b.pos, mn, S)
+    perm = orc.sort(k)
+    tree = orc.build_tree(k[perm], 8)
+    sp = np.ascontiguousarray(b.pos[perm])
+    ctr, side = orc.cell_cube(tree, k[perm], mn, S)
+    assert np.array_equal(orc.refit_extent(tree, k[perm], mn, S, sp), side / 2)
+    moved = (sp + np.random.default_rng(3).standard_normal(sp.shape) * 0.05).astype(np.float32)
+    ext = orc.refit_extent(tree, k[perm], mn, S, moved)
+    for c in range(tree.ncells):
+        bb, bc = tree.body_begin[c], tree.body_count[c]
+        far = np.abs(moved[bb:bb + bc].astype(np.float64) - ctr[c]).max()
+        assert ext[c] >= far and ext[c] >= side[c] / 2
+        if tree.nchild[c] == 0:
+            assert ext[c] == max(far, side[c] / 2)
+
+
+def test_refit_streams_stay_accurate(orc):
+    """Two interpenetrating streams (x velocities +-20) refitted for 7 of 8
+    substeps: the enlarged cubes keep every walked body's own cells opened,
+    and the accelerations at the end meet the direct-sum gates."""
+    b = W.plummer(8192, 36)
+    vel = b.vel.copy()
+    vel[:, 0] += np.where(np.arange(b.n) % 2 == 0, 20.0, -20.0).astype(np.float32)
+    a0 = orc.tree_forces(b.pos, b.mass, 0.75, 0.01, 16, 32).acc
+    x, v, a, pot, lev0, nact = orc.block_cycle(b.pos, vel, b.mass, a0, 1.0 / 16, 3, 0.1, 0.75, 0.01,
+                                               16, 32, False, 8)
+    da, _ = orc.direct(x.astype(np.float32), b.mass, 0.01)
+    e = np.linalg.norm(a - da, axis=1) / np.linalg.norm(da, axis=1)
+    assert np.median(e) <= 1e-3 and np.percentile(e, 99) <= 1e-2

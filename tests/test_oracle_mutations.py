@@ -31,6 +31,7 @@ MUTATIONS = [
      "if (body_count[c] <= ncrit && (c == 0 || body_count[parent[c]] >= ncrit))"),
     ("int sibling = g_par[i] >= 0 && g_par[i] == g_par[i - 1];", "int sibling = g_par[i] >= 0;"),
     ("if (sibling && g_count[out] + g_count[i] <= ncrit) {", "if (sibling && g_count[out] + g_count[i] < ncrit) {"),
+    ("if (m + ext[ch] > e) e = m + ext[ch];", "if (ext[ch] > e) e = ext[ch];"),
 ]
 
 
@@ -49,6 +50,7 @@ def test_planted_mistake_is_caught(tmp_path, orig, mut):
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                         "tests/test_oracle_keys.py", "tests/test_oracle_tree.py",
                         "tests/test_oracle_moments.py", "tests/test_oracle_forces.py",
-                        "tests/test_oracle_walk.py", "tests/test_oracle_physics.py"],
+                        "tests/test_oracle_walk.py", "tests/test_oracle_physics.py",
+                        "tests/test_oracle_block.py"],
                        cwd=d, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, "planted mistake survived: " + mut
