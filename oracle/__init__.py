@@ -60,6 +60,9 @@ def lib():
             L.oracle_moments.argtypes = [i64, p, p, p, p, p, p, p]
             L.oracle_open_radius.argtypes = [i64, p, p, p, p, d, p, d, p, p]
             L.oracle_refit_extent.argtypes = [i64, p, p, p, p, p, p, p, d, p, p]
+            L.oracle_sph_kernel.argtypes = [d, d]
+            L.oracle_sph_kernel.restype = d
+            L.oracle_sph_density.argtypes = [p, p, p, i64, p, p]
             L.oracle_walk.argtypes = [i64, p, p, i64, p, p, p, p, p, p, p, p, i64, p, p,
                                       d, d, d, p, p, p, p, p, p, p, p]
             L.oracle_direct.argtypes = [p, p, i64, p, i64, d, p, p]
@@ -443,3 +446,23 @@ def block_cycle(pos, vel, mass, acc, dt_max: float, kmax: int, eta: float, theta
             h = (1 << (kmax - lev)) * dtm / 2
             v[act] += a[act] * h[act][:, None]
     return x, v, a, pot, lev0, nactive
+
+
+# ---------------------------------------------------------------------------
+# Neighbour search and SPH density (Sect. 3: the tree also serves these)
+# ---------------------------------------------------------------------------
+
+def sph_kernel(r: float, h: float) -> float:
+    """Cubic spline kernel of compact support h (3D)."""
+    return float(lib().oracle_sph_kernel(float(r), float(h)))
+
+
+def sph_density(pos, mass, h):
+    """Per body: density sum_j m_j W(r_ij, h_i) over the bodies j (itself
+    included) with r_ij < h_i, and their count.  O(N^2), the definition."""
+    pos, mass, h = _f32(pos), _f32(mass), _f32(h)
+    n = pos.shape[0]
+    rho = np.zeros(n)
+    cnt = np.zeros(n, np.int32)
+    lib().oracle_sph_density(_ptr(pos), _ptr(mass), _ptr(h), n, _ptr(rho), _ptr(cnt))
+    return rho, cnt

@@ -648,3 +648,48 @@ int oracle_cell_cube(int64_t ncells, const int32_t *body_begin,
         cell_cube(skeys[body_begin[c]], level[c], mn, S, centre + 3 * c, side + c);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Sect. 3: the tree also serves neighbour search and smoothed particle     */
+/* hydrodynamics.  The plain definitions, O(N^2).                           */
+/* ------------------------------------------------------------------------ */
+
+/* Cubic spline kernel of compact support h in three dimensions (Monaghan &
+ * Lattanzio 1985, written with q = r/h): W = 8/(pi h^3) (1 - 6q^2 + 6q^3)
+ * for q <= 1/2, 8/(pi h^3) 2 (1 - q)^3 for 1/2 < q <= 1, 0 beyond. */
+double oracle_sph_kernel(double r, double h)
+{
+    const double pi = 3.14159265358979323846;
+    double q = r / h, s = 8.0 / (pi * h * h * h);
+    if (q <= 0.5) return s * (1.0 - 6.0 * q * q + 6.0 * q * q * q);
+    if (q <= 1.0) { double t = 1.0 - q; return s * 2.0 * t * t * t; }
+    return 0.0;
+}
+
+/* For every body i: the neighbours are the bodies j (i included) with
+ * r^2 < h_i^2, decided in float32 as the GPU decides it (dx = x_j - x_i
+ * rounded, r^2 = fma(dz, dz, fma(dy, dy, dx * dx)), h_i^2 rounded); the
+ * density is rho_i = sum over the neighbours of m_j W(r_ij, h_i) in float64
+ * with r_ij from the float32 positions. */
+int oracle_sph_density(const float *pos, const float *mass, const float *h, int64_t n,
+                       double *rho, int32_t *nngb)
+{
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; i++) {
+        float xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
+        float h2 = h[i] * h[i];
+        double r = 0.0;
+        int32_t cnt = 0;
+        for (int64_t j = 0; j < n; j++) {
+            float dx = pos[3 * j] - xi, dy = pos[3 * j + 1] - yi, dz = pos[3 * j + 2] - zi;
+            float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            if (!(r2 < h2)) continue;
+            double ex = (double)pos[3 * j] - xi, ey = (double)pos[3 * j + 1] - yi, ez = (double)pos[3 * j + 2] - zi;
+            r += (double)mass[j] * oracle_sph_kernel(sqrt(ex * ex + ey * ey + ez * ez), (double)h[i]);
+            cnt++;
+        }
+        rho[i] = r;
+        nngb[i] = cnt;
+    }
+    return 0;
+}

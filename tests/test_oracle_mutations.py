@@ -32,6 +32,8 @@ MUTATIONS = [
     ("int sibling = g_par[i] >= 0 && g_par[i] == g_par[i - 1];", "int sibling = g_par[i] >= 0;"),
     ("if (sibling && g_count[out] + g_count[i] <= ncrit) {", "if (sibling && g_count[out] + g_count[i] < ncrit) {"),
     ("if (m + ext[ch] > e) e = m + ext[ch];", "if (ext[ch] > e) e = ext[ch];"),
+    ("return s * 2.0 * t * t * t; }", "return s * t * t * t; }"),
+    ("if (!(r2 < h2)) continue;", "if (!(r2 < 0.98f * h2)) continue;"),
 ]
 
 
@@ -51,6 +53,6 @@ def test_planted_mistake_is_caught(tmp_path, orig, mut):
                         "tests/test_oracle_keys.py", "tests/test_oracle_tree.py",
                         "tests/test_oracle_moments.py", "tests/test_oracle_forces.py",
                         "tests/test_oracle_walk.py", "tests/test_oracle_physics.py",
-                        "tests/test_oracle_block.py"],
+                        "tests/test_oracle_block.py", "tests/test_oracle_sph.py"],
                        cwd=d, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, "planted mistake survived: " + mut
