@@ -155,6 +155,24 @@ int bonsai_block_levels(bonsai_ctx *ctx, float dt_max, int max_level, float eta,
  * its substeps.  Synchronises. */
 int bonsai_block_stats(bonsai_ctx *ctx, long long out[3]);
 
+/* Neighbour search and SPH density on the octree (paper Sect. 3: the tree
+ * also serves neighbour search and smoothed particle hydrodynamics).  h: the
+ * smoothing length of every body (N floats, caller order).  The neighbours
+ * of body i are the bodies j, i itself included, with |x_j - x_i| < h_i,
+ * decided in float32 as r^2 < h_i^2 with dx = x_j - x_i rounded and
+ * r^2 = fma(dz, dz, fma(dy, dy, dx*dx)); nngb[i] is their count and
+ * rho[i] = sum_j m_j W(|x_j - x_i|, h_i), W the cubic spline kernel of
+ * compact support h: 8/(pi h^3) (1 - 6q^2 + 6q^3) for q = r/h <= 1/2,
+ * 8/(pi h^3) 2 (1 - q)^3 for 1/2 < q < 1.  The groups and traversal are the
+ * gravity walk's; a cell is searched iff its cube comes within the group's
+ * largest h of the group's box.  Outputs (N each, caller order, either may be
+ * NULL) on the side on_device says; h on the same side.  Needs a tree built
+ * from the current positions (bonsai_build or bonsai_step; not after a block
+ * cycle that ended on a refit: BONSAI_ERR_NOT_READY).  h > 0 is the caller's
+ * to ensure (h <= 0 gives no neighbours). */
+int bonsai_sph_density(bonsai_ctx *ctx, const float *h, float *rho, int32_t *nngb,
+                       int on_device);
+
 /* Autotuner: times the walk of the current bodies (CUDA events, mean of two
  * walks after one untimed) for every group size ncrit in {16, 32, 48, 64},
  * both group rules (group_pack 0 and 1) and walk thread-block width in

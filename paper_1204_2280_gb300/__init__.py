@@ -35,7 +35,7 @@ EXPORTS = ["bonsai_create", "bonsai_destroy", "bonsai_set_bodies", "bonsai_build
            "bonsai_mlp_fit_norm", "bonsai_mlp_predict", "bonsai_mlp_grad", "bonsai_mlp_train",
            "bonsai_learn_samples", "bonsai_judge", "bonsai_set_learned", "bonsai_forces_learned",
            "bonsai_get_judge", "bonsai_set_judge_interval", "bonsai_get_config", "bonsai_block_cycle",
-           "bonsai_block_levels", "bonsai_block_stats"]
+           "bonsai_block_levels", "bonsai_block_stats", "bonsai_sph_density"]
 
 MLP_IN, MLP_H, MLP_OUT = 12, 64, 3
 MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_OUT * MLP_H + MLP_OUT
@@ -101,6 +101,7 @@ def lib():
         L.bonsai_block_cycle.argtypes = [p, f, i, f, i]
         L.bonsai_block_levels.argtypes = [p, f, i, f, p]
         L.bonsai_block_stats.argtypes = [p, p]
+        L.bonsai_sph_density.argtypes = [p, p, p, p, i]
         u64 = C.c_ulonglong
         L.bonsai_mlp_create.argtypes = [C.POINTER(p), u64]
         L.bonsai_mlp_destroy.argtypes = [p]
@@ -231,6 +232,13 @@ def bonsai_block_stats(ctx) -> tuple[int, int, int]:
     out = np.zeros(3, np.int64)
     _check(ctx, lib().bonsai_block_stats(ctx, out.ctypes.data))
     return int(out[0]), int(out[1]), int(out[2])
+
+
+def bonsai_sph_density(ctx, h, rho=None, nngb=None):
+    """Neighbour counts and SPH densities (caller order) for smoothing
+    lengths h; torch CUDA tensors or numpy arrays, all on one side."""
+    (hp, d0), (rp, d1), (np_, d2) = _buf(h, np.float32), _buf(rho, np.float32), _buf(nngb, np.int32)
+    _check(ctx, lib().bonsai_sph_density(ctx, hp, rp, np_, _same_side(d0, d1, d2)))
 
 
 def bonsai_set_params(ctx, theta: float, eps: float):

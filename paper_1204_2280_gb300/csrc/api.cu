@@ -282,7 +282,7 @@ int bonsai_build(bonsai_ctx *ctx) {
     CK(launch_reset(c));
     CK(launch_bbox(c));
     CK(pipeline_tree(c));
-    c.built = true;
+    c.built = c.tree_fresh = true;
     c.moments_ready = c.have_acc = false;
     return BONSAI_OK;
 }
@@ -377,7 +377,7 @@ int bonsai_step(bonsai_ctx *ctx, float dt) {
         CK(pipeline_step(c, dt));
         c.graph_dt = dt; c.graph_theta = c.theta; c.graph_eps = c.eps; c.graph_n = c.n;
     }
-    c.built = c.moments_ready = c.have_acc = true;
+    c.built = c.moments_ready = c.have_acc = c.tree_fresh = true;
     c.timed_step = true;
     return BONSAI_OK;
 }

@@ -189,6 +189,7 @@ int bonsai_block_cycle(bonsai_ctx *ctx, float dt_max, int max_level, float eta, 
     cudaError_t e = block_cycle(c, dt_max, max_level, eta, rebuild_every);
     if (e != cudaSuccess) return bfail(ctx, BONSAI_ERR_CUDA, "bonsai_block_cycle", e);
     c.built = c.moments_ready = c.have_acc = true;
+    c.tree_fresh = ((1u << max_level) - 1u) % (unsigned)rebuild_every == 0u;   // the last substep rebuilt
     return BONSAI_OK;
 }
 

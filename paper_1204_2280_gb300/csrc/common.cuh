@@ -130,6 +130,7 @@ struct Ctx {
 
     // pipeline state
     bool have_bodies = false, built = false, moments_ready = false, have_acc = false;
+    bool tree_fresh = false;         // the tree was built from the current positions (no refit since)
     float theta = 0.75f, eps = 0.01f;
     cudaGraphExec_t step_graph = nullptr;
     static constexpr int NSTAGE = 8;
@@ -217,6 +218,8 @@ cudaError_t launch_reorder(Ctx &c);
 cudaError_t launch_build(Ctx &c);
 cudaError_t launch_multipoles(Ctx &c);
 cudaError_t launch_multipoles_refit(Ctx &c);
+cudaError_t launch_cell_cubes(Ctx &c);
+cudaError_t launch_sph_walk(Ctx &c, const float *hs, const float4 *cext, float *rho_s, int32_t *cnt_s);
 cudaError_t launch_open_radius(Ctx &c, float theta, const unsigned *gate = nullptr);
 cudaError_t launch_walk(Ctx &c, float eps, bool features = false, const unsigned *gate = nullptr);
 cudaError_t launch_direct(Ctx &c, const uint32_t *targets, int ntar, float eps, float4 *partial, int nsplit,

@@ -282,6 +282,27 @@ cudaError_t launch_multipoles_refit(Ctx &c) {
     return cudaGetLastError();
 }
 
+// cext[c] = (geometric centre, l / 2) of every cell from its first body's
+// key: the cubes the neighbour search tests (the bodies lie in them right
+// after a build).
+__global__ void k_cell_cubes(const DevState *__restrict__ st, const uint2 *__restrict__ cell_body,
+                             const uint8_t *__restrict__ cell_level, const unsigned long long *__restrict__ sk,
+                             const uint8_t *__restrict__ sysid, float4 *cext) {
+    const unsigned nc = st->ncells;
+    for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        const unsigned b = cell_body[c].x;
+        float3 ctr;
+        const float l = cell_cube(sk[b], cell_level[c], sysid[b], st, ctr);
+        cext[c] = make_float4(ctr.x, ctr.y, ctr.z, 0.5f * l);
+    }
+}
+
+cudaError_t launch_cell_cubes(Ctx &c) {
+    const unsigned grid = (unsigned)min((c.ccap + 255) / 256, (long long)c.num_sms * 8);
+    k_cell_cubes<<<grid, 256, 0, c.stream>>>(c.st, c.cell_body, c.cell_level, c.keys, c.sysid, c.cext);
+    return cudaGetLastError();
+}
+
 // test[c] = (com, l/theta + delta), l = S / 2^level: the opening radius of
 // the Barnes (1994) criterion as read here.
 __global__ void k_open_radius(const DevState *__restrict__ st, const float4 *__restrict__ mono,

@@ -636,3 +636,193 @@ cudaError_t launch_walk(Ctx &c, float eps, bool features, const unsigned *gate) 
 }
 
 }  // namespace bonsai
+
+// ---------------------------------------------------------------------------
+// Neighbour search and SPH density on the same tree (paper Sect. 3: the
+// tree also serves neighbour search and smoothed particle hydrodynamics).
+// The group walk with another opening rule and kernel: a cell is searched
+// iff its cube (build-time centre, half side ext) comes within h_max of the
+// group's box, h_max the largest smoothing length of the group; searched
+// leaves feed their bodies through a ring of 64 in shared memory; each body
+// i counts the sources j with r^2 < h_i^2 (r^2 = fma(dz, dz, fma(dy, dy,
+// dx dx)), dx = x_j - x_i rounded: the decision the oracle takes) and sums
+// m_j W(r, h_i), W the cubic spline of compact support h.  Up to 64 bodies
+// per group: two body slots per lane.
+namespace bonsai {
+
+constexpr int SPH_RING = 64;
+
+struct SphWarp {
+    float4 src[SPH_RING];
+};
+
+// 8 / pi: the cubic spline's normalisation in three dimensions.
+constexpr float SPH_NORM = 2.546479089470325f;
+
+// One ring of sources: plain float32 sums per body, then one compensated
+// (Kahan) add into the body's density.
+__device__ __forceinline__ void sph_tile(const float4 *__restrict__ src, int nsrc, const float4 (&me)[2],
+                                         const float (&h2)[2], const float (&ih)[2], const bool (&live)[2],
+                                         float (&rho)[2], float (&comp)[2], unsigned (&cnt)[2]) {
+    float part[2] = {0.f, 0.f};
+    for (int k = 0; k < nsrc; k++) {
+        const float4 s = src[k];
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            if (!live[b]) continue;
+            const float dx = __fsub_rn(s.x, me[b].x), dy = __fsub_rn(s.y, me[b].y), dz = __fsub_rn(s.z, me[b].z);
+            const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+            if (r2 < h2[b]) {
+                const float q = sqrtf(r2) * ih[b];
+                const float t = fmaxf(1.f - q, 0.f);
+                const float w = q <= 0.5f ? fmaf(6.f * q * q, q - 1.f, 1.f) : 2.f * t * t * t;
+                part[b] = fmaf(s.w, w, part[b]);
+                cnt[b]++;
+            }
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < 2; b++) kahan_add(rho[b], comp[b], part[b]);
+}
+
+__global__ void __launch_bounds__(128)
+k_sph_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__ groups,
+           const float4 *__restrict__ pos4, const float *__restrict__ hs, const float4 *__restrict__ cext,
+           const uint2 *__restrict__ link, const uint8_t *__restrict__ sysid, int stack_cap, unsigned max_rounds,
+           float *rho_s, int32_t *cnt_s) {
+    extern __shared__ float4 smem4[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t warp_bytes = sizeof(SphWarp) + (size_t)stack_cap * sizeof(unsigned);
+    char *wbase = (char *)smem4 + warp * warp_bytes;
+    SphWarp &R = *reinterpret_cast<SphWarp *>(wbase);
+    unsigned *stk = reinterpret_cast<unsigned *>(wbase + sizeof(SphWarp));
+    const unsigned ngroups = (stc->status & ST_TIMEOUT) ? 0u : stc->ngroups;
+    const unsigned lt = lanemask_lt_w();
+    while (true) {
+        unsigned g = 0;
+        if (lane == 0) g = atomicAdd(&st->walk_next, 1u);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= ngroups) break;
+        const uint2 gr = groups[g];
+        const int gb = (int)gr.x, ng = (int)gr.y;
+        bool live[2];
+        float4 me[2];
+        float h2[2], ih[2], rho[2] = {0.f, 0.f}, comp[2] = {0.f, 0.f};
+        unsigned cnt[2] = {0u, 0u};
+        float bx0 = INFINITY, by0 = INFINITY, bz0 = INFINITY, bx1 = -INFINITY, by1 = -INFINITY, bz1 = -INFINITY;
+        float hmax = 0.f;
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            const int slot = lane + 32 * b;
+            live[b] = slot < ng;
+            const int i = gb + (live[b] ? slot : 0);
+            me[b] = pos4[i];
+            const float h = hs[i];
+            h2[b] = __fmul_rn(h, h);
+            ih[b] = 1.f / h;
+            if (live[b]) {
+                bx0 = fminf(bx0, me[b].x); by0 = fminf(by0, me[b].y); bz0 = fminf(bz0, me[b].z);
+                bx1 = fmaxf(bx1, me[b].x); by1 = fmaxf(by1, me[b].y); bz1 = fmaxf(bz1, me[b].z);
+                hmax = fmaxf(hmax, h);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            bx0 = fminf(bx0, __shfl_xor_sync(0xffffffffu, bx0, o));
+            by0 = fminf(by0, __shfl_xor_sync(0xffffffffu, by0, o));
+            bz0 = fminf(bz0, __shfl_xor_sync(0xffffffffu, bz0, o));
+            bx1 = fmaxf(bx1, __shfl_xor_sync(0xffffffffu, bx1, o));
+            by1 = fmaxf(by1, __shfl_xor_sync(0xffffffffu, by1, o));
+            bz1 = fmaxf(bz1, __shfl_xor_sync(0xffffffffu, bz1, o));
+            hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+        }
+        // search radius with a relative slack: rounding may only open more
+        const float reach2 = hmax * hmax * 1.0001f;
+        int sp = 1, nsrc = 0;
+        if (lane == 0) stk[0] = (unsigned)sysid[gb] << 3;   // the root of the group's system
+        bool overflow = false, timeout = false;
+        unsigned rounds = 0;
+        __syncwarp();
+        while (sp > 0) {
+            if (++rounds > max_rounds) { timeout = true; break; }
+            unsigned cell;
+            bool has;
+            walk_pop(stk, sp, lane, cell, has);
+            bool open = false, isleaf = false;
+            uint2 lk = make_uint2(0u, 0u);
+            if (has) {
+                const float4 ce = __ldg(cext + cell);
+                lk = __ldg(link + cell);
+                const float dx = fmaxf(fmaxf(bx0 - (ce.x + ce.w), (ce.x - ce.w) - bx1), 0.f);
+                const float dy = fmaxf(fmaxf(by0 - (ce.y + ce.w), (ce.y - ce.w) - by1), 0.f);
+                const float dz = fmaxf(fmaxf(bz0 - (ce.z + ce.w), (ce.z - ce.w) - bz1), 0.f);
+                open = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) <= reach2;
+                isleaf = (lk.y & LEAF_BIT) != 0u;
+            }
+            const unsigned im = __ballot_sync(0xffffffffu, open && !isleaf);
+            const int np = __popc(im);
+            if (sp + np > stack_cap) {
+                overflow = true;
+            } else {
+                if (open && !isleaf) stk[sp + __popc(im & lt)] = (lk.x << 3) | ((lk.y - 1u) & 7u);
+                sp += np;
+            }
+            // searched leaves, one at a time: their bodies into the ring
+            unsigned lm = __ballot_sync(0xffffffffu, open && isleaf);
+            while (lm) {
+                const int src_lane = __ffs(lm) - 1;
+                lm &= lm - 1;
+                const unsigned first = __shfl_sync(0xffffffffu, lk.x, src_lane);
+                const int n_l = (int)(__shfl_sync(0xffffffffu, lk.y, src_lane) & ~LEAF_BIT);
+                for (int off = 0; off < n_l; off += 32) {
+                    const int take = min(32, n_l - off);
+                    if (nsrc + take > SPH_RING) {           // ring full: evaluate it
+                        __syncwarp();
+                        sph_tile(R.src, nsrc, me, h2, ih, live, rho, comp, cnt);
+                        __syncwarp();
+                        nsrc = 0;
+                    }
+                    if (lane < take) R.src[nsrc + lane] = __ldg(pos4 + first + off + lane);
+                    nsrc += take;
+                }
+            }
+            __syncwarp();
+        }
+        if (nsrc > 0) sph_tile(R.src, nsrc, me, h2, ih, live, rho, comp, cnt);
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            if (live[b]) {
+                rho_s[gb + lane + 32 * b] = (rho[b] - comp[b]) * (SPH_NORM * ih[b] * ih[b] * ih[b]);
+                cnt_s[gb + lane + 32 * b] = (int32_t)cnt[b];
+            }
+        }
+        if (lane == 0) {
+            if (overflow) atomicOr(&st->status, ST_CAPACITY);
+            if (timeout) atomicOr(&st->status, ST_TIMEOUT);
+        }
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_sph_walk(Ctx &c, const float *hs, const float4 *cext, float *rho_s, int32_t *cnt_s) {
+    const unsigned polls = (unsigned)(c.max_spin < 0xffffffffll ? c.max_spin : 0xffffffffll);
+    const int warps = 4;
+    const size_t smem = (size_t)warps * (sizeof(SphWarp) + (size_t)c.list_capacity * sizeof(unsigned));
+    static size_t attr_smem = 0;
+    static int per_sm = 0;
+    if (smem > attr_smem) {
+        cudaError_t e = cudaFuncSetAttribute(k_sph_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_smem = smem;
+        int per = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sph_walk, warps * 32, smem);
+        if (e != cudaSuccess) return e;
+        per_sm = per < 1 ? 1 : per;
+    }
+    k_sph_walk<<<c.num_sms * per_sm, warps * 32, smem, c.stream>>>(c.st, c.st, c.groups, c.pos4, hs, cext,
+                                                                    c.cell_link, c.sysid, c.list_capacity, polls,
+                                                                    rho_s, cnt_s);
+    return cudaGetLastError();
+}
+
+}  // namespace bonsai
