@@ -78,6 +78,7 @@ def parse():
     p.add_argument("--ensemble-systems", type=int, default=64)
     p.add_argument("--no-learned", action="store_true")
     p.add_argument("--no-block", action="store_true")
+    p.add_argument("--no-sph", action="store_true")
     p.add_argument("--learned-n", type=int, default=1 << 22)
     p.add_argument("--learned-plummer", type=int, default=8, help="Plummer training snapshots")
     p.add_argument("--learned-merger", type=int, default=8, help="merger training snapshots")
@@ -487,6 +488,63 @@ def stage_bytes(n, ncells, ngroups):
             "multipoles": 16 * n + 44 * ncells, "kick": 48 * n}
 
 
+def run_sph(a, dev, stream):
+    """Neighbour search and SPH density (paper Sect. 3) on the bench
+    workload's tree: smoothing lengths from the Plummer density at each
+    body's radius for about 48 neighbours; device ms per density pass (CUDA
+    events, L2 flushed between passes, tree built once), neighbours per body,
+    neighbour pairs per second; the oracle's O(N^2) definition timed on a
+    bounded sample of bodies beside it."""
+    import numpy as np
+    import torch
+    import paper_1204_2280_gb300 as B
+    from paper_1204_2280_gb300 import workloads as W
+    b = W.plummer(a.n, a.seed)
+    ah = 3 * np.pi / 16
+    r = np.linalg.norm(b.pos.astype(np.float64), axis=1)
+    nden = a.n * 3 / (4 * np.pi * ah ** 3) * (1 + r * r / (ah * ah)) ** -2.5
+    h = ((3 * 48 / (4 * np.pi * nden)) ** (1 / 3)).astype(np.float32)
+    bz = B.Bonsai(B.Config(nleaf=a.nleaf, ncrit=a.ncrit, walk_warps=a.walk_warps, group_pack=a.group_pack),
+                  stream=stream)
+    bz.set_bodies(torch.from_numpy(b.pos).to(dev), torch.from_numpy(b.mass).to(dev),
+                  torch.from_numpy(b.vel).to(dev))
+    bz.build()
+    th = torch.from_numpy(h).to(dev)
+    rho = torch.zeros(a.n, dtype=torch.float32, device=dev)
+    cnt = torch.zeros(a.n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        B.bonsai_sph_density(bz.ctx, th, rho, cnt)
+    ms = []
+    for _ in range(10):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.bonsai_sph_density(bz.ctx, th, rho, cnt)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    bz.sync()
+    bz.close()
+    c = cnt.cpu().numpy()
+    t = sum(ms) / len(ms)
+    out = {"n": a.n, "ms_per_pass": t, "neighbours_mean": float(c.mean()),
+           "neighbours_p5_p95": [float(np.percentile(c, 5)), float(np.percentile(c, 95))],
+           "neighbour_pairs_per_s": float(c.sum()) / (t / 1e3), "particles_per_s": a.n / (t / 1e3)}
+    if not a.no_cpu_baseline:
+        import oracle
+        ns = 4096                     # the oracle's O(N^2) definition on a sample of targets
+        idx = np.random.default_rng(0).choice(a.n, ns, replace=False)
+        t0 = time.perf_counter()
+        sub = W.Bodies(b.pos[idx], b.vel[idx], b.mass[idx])
+        oracle.sph_density(sub.pos, sub.mass, h[idx])
+        tc = time.perf_counter() - t0
+        out["cpu_oracle"] = {"what": f"O(N^2) definition on {ns} random bodies ({ns}^2 pairs) in {tc:.3f} s",
+                             "pairs_per_s": ns * ns / tc, "cores": os.cpu_count()}
+    return out
+
+
 def run_block(a, dev, stream):
     """Block time steps (paper Sect. 1 and 3) on the bench workload: cycles
     of dt_max = 8 dt (dt the bench step) in 2^3 substeps, levels from
@@ -752,6 +810,7 @@ def run_ours(a, rank, world, local_rank):
 
     ens = None if a.no_ensemble else run_ensemble(a, dev, stream, rank, world)
     blk = None if a.no_block else run_block(a, dev, stream)
+    sph = None if a.no_sph else run_sph(a, dev, stream)
     lrn = None if a.no_learned else run_learned(a, dev, stream)
 
     cpu = None
@@ -780,6 +839,7 @@ def run_ours(a, rank, world, local_rank):
             "wall_s_timed_loop": t_wall,
             "ensemble": ens,
             "block": blk,
+            "sph": sph,
             "learned": lrn,
         }
         print(json.dumps(line), flush=True)
