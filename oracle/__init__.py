@@ -62,7 +62,7 @@ def lib():
             L.oracle_refit_extent.argtypes = [i64, p, p, p, p, p, p, p, d, p, p]
             L.oracle_sph_kernel.argtypes = [d, d]
             L.oracle_sph_kernel.restype = d
-            L.oracle_sph_density.argtypes = [p, p, p, i64, p, p]
+            L.oracle_sph_density.argtypes = [p, p, p, i64, p, i64, p, p]
             L.oracle_walk.argtypes = [i64, p, p, i64, p, p, p, p, p, p, p, p, i64, p, p,
                                       d, d, d, p, p, p, p, p, p, p, p]
             L.oracle_direct.argtypes = [p, p, i64, p, i64, d, p, p]
@@ -457,12 +457,16 @@ def sph_kernel(r: float, h: float) -> float:
     return float(lib().oracle_sph_kernel(float(r), float(h)))
 
 
-def sph_density(pos, mass, h):
-    """Per body: density sum_j m_j W(r_ij, h_i) over the bodies j (itself
-    included) with r_ij < h_i, and their count.  O(N^2), the definition."""
+def sph_density(pos, mass, h, idx=None):
+    """Per body (or per body of idx): density sum_j m_j W(r_ij, h_i) over the
+    bodies j (itself included) with r_ij < h_i, and their count.  O(N) per
+    body over all N, the definition."""
     pos, mass, h = _f32(pos), _f32(mass), _f32(h)
     n = pos.shape[0]
-    rho = np.zeros(n)
-    cnt = np.zeros(n, np.int32)
-    lib().oracle_sph_density(_ptr(pos), _ptr(mass), _ptr(h), n, _ptr(rho), _ptr(cnt))
+    tar = None if idx is None else np.ascontiguousarray(idx, np.int64)
+    nt = n if tar is None else tar.shape[0]
+    rho = np.zeros(nt)
+    cnt = np.zeros(nt, np.int32)
+    lib().oracle_sph_density(_ptr(pos), _ptr(mass), _ptr(h), n, _ptr(tar) if tar is not None else None, nt,
+                             _ptr(rho), _ptr(cnt))
     return rho, cnt

@@ -670,12 +670,14 @@ double oracle_sph_kernel(double r, double h)
  * r^2 < h_i^2, decided in float32 as the GPU decides it (dx = x_j - x_i
  * rounded, r^2 = fma(dz, dz, fma(dy, dy, dx * dx)), h_i^2 rounded); the
  * density is rho_i = sum over the neighbours of m_j W(r_ij, h_i) in float64
- * with r_ij from the float32 positions. */
+ * with r_ij from the float32 positions.  targets (may be NULL: every body):
+ * the bodies i computed, outputs in that order. */
 int oracle_sph_density(const float *pos, const float *mass, const float *h, int64_t n,
-                       double *rho, int32_t *nngb)
+                       const int64_t *targets, int64_t ntar, double *rho, int32_t *nngb)
 {
     #pragma omp parallel for schedule(dynamic, 64)
-    for (int64_t i = 0; i < n; i++) {
+    for (int64_t t = 0; t < ntar; t++) {
+        const int64_t i = targets ? targets[t] : t;
         float xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
         float h2 = h[i] * h[i];
         double r = 0.0;
@@ -688,8 +690,8 @@ int oracle_sph_density(const float *pos, const float *mass, const float *h, int6
             r += (double)mass[j] * oracle_sph_kernel(sqrt(ex * ex + ey * ey + ez * ez), (double)h[i]);
             cnt++;
         }
-        rho[i] = r;
-        nngb[i] = cnt;
+        rho[t] = r;
+        nngb[t] = cnt;
     }
     return 0;
 }

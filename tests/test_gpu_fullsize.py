@@ -12,7 +12,10 @@ compute one by one:
   sampled-group check at each theta, the direct-sum gates at theta = 0.75 and
   p99 growing with theta.
 * N = 2^24 (seed 3, eps = 0.002, theta = 0.75): keys and permutation
-  bit-exact, direct-sum gates at 2048 sampled bodies."""
+  bit-exact, direct-sum gates at 2048 sampled bodies.
+* N = 2^20 in the bench's own configuration (ncrit 32, packed groups): the
+  2^20 checks above, the SPH density at 4096 sampled bodies and a block
+  time-step cycle against the oracle's."""
 import numpy as np
 import pytest
 
@@ -27,10 +30,10 @@ pytestmark = pytest.mark.gpu
 TAU_ABS, TAU_REL = 2e-6, 1e-6
 
 
-def gpu_forces(b, theta, eps, warps=4, tree=True):
+def gpu_forces(b, theta, eps, warps=4, tree=True, ncrit=64, pack=0):
     import torch
     out = {}
-    with B.Bonsai(B.Config(nleaf=16, ncrit=64, walk_warps=warps)) as bz:
+    with B.Bonsai(B.Config(nleaf=16, ncrit=ncrit, walk_warps=warps, group_pack=pack)) as bz:
         bz.set_bodies(torch.from_numpy(b.pos).cuda(), torch.from_numpy(b.mass).cuda())
         bz.build()
         out["domain"] = B.bonsai_get_domain(bz.ctx)
@@ -51,12 +54,12 @@ def gpu_forces(b, theta, eps, warps=4, tree=True):
     return out
 
 
-def oracle_setup(b, nleaf=16, ncrit=64):
+def oracle_setup(b, nleaf=16, ncrit=64, pack=False):
     mn, S = oracle.domain(b.pos)
     k = oracle.keys(b.pos, mn, S)
     perm = oracle.sort(k)
     t = oracle.build_tree(k[perm], nleaf)
-    gb, gc = oracle.groups(t, ncrit)
+    gb, gc = oracle.groups(t, ncrit, pack)
     M, com, Q = oracle.moments(t, b.pos[perm], b.mass[perm])
     return dict(mn=mn, S=S, k=k, perm=perm, tree=t, gb=gb, gc=gc, M=M, com=com, Q=Q)
 
@@ -110,14 +113,17 @@ def direct_errors(b, acc, pot, eps, nsample, seed, ref=None):
     return ea, ep
 
 
-def test_bench_workload_n2e20():
+@pytest.mark.parametrize("ncrit,pack", [(64, 0), (32, 1)])
+def test_bench_workload_n2e20(ncrit, pack):
+    """(32, 1) is the bench's autotuned configuration: ncrit 32 with
+    sibling-packed groups."""
     b = W.plummer(1 << 20, 1)
     eps, theta = 0.005, 0.75
-    res = gpu_forces(b, theta, eps, warps=4)
-    res8 = gpu_forces(b, theta, eps, warps=8, tree=False)
+    res = gpu_forces(b, theta, eps, warps=4, ncrit=ncrit, pack=pack)
+    res8 = gpu_forces(b, theta, eps, warps=8, tree=False, ncrit=ncrit, pack=pack)
     assert np.array_equal(res["acc"][theta], res8["acc"][theta])
     assert np.array_equal(res["pot"][theta], res8["pot"][theta])
-    o = oracle_setup(b)
+    o = oracle_setup(b, ncrit=ncrit, pack=bool(pack))
     check_structure(res, o)
     check_sampled_groups(b, o, res["acc"][theta], res["pot"][theta], res["counts"][theta], theta, eps, 512, 11)
     ea, ep = direct_errors(b, res["acc"][theta], res["pot"][theta], eps, 4096, 12)
@@ -159,3 +165,59 @@ def test_keys_and_direct_gates_n2e24():
     print(f"N=2^24 theta=0.75: acc median {np.median(ea):.3e} p99 {np.percentile(ea, 99):.3e}")
     assert np.median(ea) <= 1e-3 and np.percentile(ea, 99) <= 1e-2
     assert np.median(ep) <= 1e-3 and np.percentile(ep, 99) <= 1e-2
+
+
+def test_sph_density_n2e20_sampled():
+    """Neighbour search and SPH density on the bench workload's tree (ncrit
+    32, packed groups): counts bit-exact and densities within 2e-5 of the
+    definition at 4096 sampled bodies; h from the Plummer density at each
+    body's radius for about 48 neighbours."""
+    import torch
+    b = W.plummer(1 << 20, 1)
+    a = 3 * np.pi / 16
+    r = np.linalg.norm(b.pos.astype(np.float64), axis=1)
+    nden = b.n * 3 / (4 * np.pi * a ** 3) * (1 + r * r / (a * a)) ** -2.5
+    h = ((3 * 48 / (4 * np.pi * nden)) ** (1 / 3)).astype(np.float32)
+    with B.Bonsai(B.Config(nleaf=16, ncrit=32, group_pack=1, walk_warps=8)) as bz:
+        bz.set_bodies(torch.from_numpy(b.pos).cuda(), torch.from_numpy(b.mass).cuda()).build()
+        rho = torch.zeros(b.n, dtype=torch.float32, device="cuda")
+        cnt = torch.zeros(b.n, dtype=torch.int32, device="cuda")
+        B.bonsai_sph_density(bz.ctx, torch.from_numpy(h).cuda(), rho, cnt)
+        torch.cuda.synchronize()
+        bz.sync()
+    rho, cnt = rho.cpu().numpy(), cnt.cpu().numpy()
+    idx = W.sample_indices(b.n, 4096, 61)
+    orho, ocnt = oracle.sph_density(b.pos, b.mass, h, idx)
+    assert np.array_equal(cnt[idx], ocnt)
+    assert np.all(np.abs(rho[idx] - orho) <= 2e-5 * orho)
+    assert 30 < np.median(cnt) < 80
+
+
+def test_block_cycle_n2e20():
+    """One block time-step cycle on the bench workload (dt_max = 8 dt, 8
+    substeps, eta = 0.2, a rebuild every substep, ncrit 32 packed) against
+    the oracle's cycle: positions at 4096 sampled bodies within the float32
+    rounding of the trajectory (bodies whose level the two sides decide
+    differently at a boundary: within 1% of their displacement)."""
+    import torch
+    b = W.plummer(1 << 20, 1)
+    theta, eps, dt, kmax, eta = 0.75, 0.005, 1.0 / 16, 3, 0.2
+    with B.Bonsai(B.Config(nleaf=16, ncrit=32, group_pack=1, walk_warps=8)) as bz:
+        bz.set_bodies(torch.from_numpy(b.pos).cuda(), torch.from_numpy(b.mass).cuda(),
+                      torch.from_numpy(b.vel).cuda())
+        bz.build().multipoles().forces(theta, eps)
+        lev = B.bonsai_block_levels(bz.ctx, dt, kmax, eta)
+        bz.block_cycle(dt, kmax, eta, 1)
+        x = np.zeros((b.n, 3), np.float32)
+        B.bonsai_get_bodies(bz.ctx, x, None)
+        bz.sync()
+    a0 = oracle.tree_forces(b.pos, b.mass, theta, eps, 16, 32, pack=True).acc
+    ox, ov, oa, op, lev0, nact = oracle.block_cycle(b.pos, b.vel, b.mass, a0, dt, kmax, eta, theta, eps,
+                                                    16, 32, True, 1)
+    idx = W.sample_indices(b.n, 4096, 62)
+    same = (lev == lev0)[idx]
+    assert (lev == lev0).mean() > 0.999
+    disp = np.linalg.norm(ox[idx] - b.pos[idx], axis=1)
+    dx = np.linalg.norm(x[idx] - ox[idx], axis=1)
+    assert np.all(dx[same] <= 3e-7 * np.linalg.norm(ox[idx][same], axis=1) + 1e-4 * disp[same])
+    assert np.all(dx <= 1e-2 * disp + 1e-6)
