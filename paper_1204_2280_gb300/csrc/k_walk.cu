@@ -371,7 +371,19 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
         if (second != (ng <= WALK_SMALL_LAST)) continue;
 #endif
         // Body slots and source phases.
-        const int lg = walk_lg<BPL>(ng);
+        // Block time steps, groups of <= 32 bodies: the active bodies are
+        // compacted into the first body slots (in body order), so the slot
+        // count follows the active count (all active: the plain layout).
+        int nslot = ng;
+        if (BLOCK && BPL == 1) {
+            const bool a = lane < ng && block_active(actv[gb + lane].w, act_s, act_kmax);
+            const unsigned am = __ballot_sync(0xffffffffu, a);
+            nslot = __popc(am);
+            if (nslot == 0) continue;
+            if (a) R.leaf[__popc(am & lt)].x = (unsigned)lane;
+            __syncwarp();
+        }
+        const int lg = walk_lg<BPL>(nslot);
         const int slots = 1 << lg;
         const int bslot = lane & (slots - 1), phase = lane >> lg;
         bool live[BPL];
@@ -382,10 +394,15 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
 #pragma unroll
         for (int b = 0; b < BPL; b++) {
             const int slot = bslot + slots * b;
-            live[b] = slot < ng;
-            // block time steps: only the bodies whose step ends at this substep
-            if (BLOCK && live[b]) live[b] = block_active(actv[gb + slot].w, act_s, act_kmax);
-            bi[b] = gb + (live[b] ? slot : 0);
+            live[b] = slot < nslot;
+            int body = slot;
+            if (BLOCK && BPL == 1) {
+                if (live[b]) body = (int)R.leaf[slot].x;
+            } else if (BLOCK && live[b]) {
+                // only the bodies whose step ends at this substep
+                live[b] = block_active(actv[gb + slot].w, act_s, act_kmax);
+            }
+            bi[b] = gb + (live[b] ? body : 0);
             me[b] = pos4[bi[b]];
             if (live[b]) {
                 bx0 = fminf(bx0, me[b].x); by0 = fminf(by0, me[b].y); bz0 = fminf(bz0, me[b].z);
