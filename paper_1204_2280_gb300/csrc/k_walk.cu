@@ -792,14 +792,26 @@ k_sph_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restri
                 const unsigned first = __shfl_sync(0xffffffffu, lk.x, src_lane);
                 const int n_l = (int)(__shfl_sync(0xffffffffu, lk.y, src_lane) & ~LEAF_BIT);
                 for (int off = 0; off < n_l; off += 32) {
-                    const int take = min(32, n_l - off);
+                    // a body farther than h_max from the group's box is no
+                    // body's neighbour: only the others enter the ring
+                    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+                    bool keep = false;
+                    if (off + lane < n_l) {
+                        p = __ldg(pos4 + first + off + lane);
+                        const float ex = fmaxf(fmaxf(bx0 - p.x, p.x - bx1), 0.f);
+                        const float ey = fmaxf(fmaxf(by0 - p.y, p.y - by1), 0.f);
+                        const float ez = fmaxf(fmaxf(bz0 - p.z, p.z - bz1), 0.f);
+                        keep = fmaf(ez, ez, fmaf(ey, ey, ex * ex)) <= reach2;
+                    }
+                    const unsigned km = __ballot_sync(0xffffffffu, keep);
+                    const int take = __popc(km);
                     if (nsrc + take > SPH_RING) {           // ring full: evaluate it
                         __syncwarp();
                         sph_tile(R.src, nsrc, me, h2, ih, live, rho, comp, cnt);
                         __syncwarp();
                         nsrc = 0;
                     }
-                    if (lane < take) R.src[nsrc + lane] = __ldg(pos4 + first + off + lane);
+                    if (keep) R.src[nsrc + __popc(km & lt)] = p;
                     nsrc += take;
                 }
             }
