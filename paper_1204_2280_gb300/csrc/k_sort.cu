@@ -9,17 +9,19 @@
 //      warp-striped and ranked per warp: peers with equal digits by ballots,
 //      counts by shared-memory atomics (stable: item order, then lane order,
 //      then warp order);
-//   2. per digit the tile count is published and the prefix over earlier
-//      tiles found by decoupled look-back (bounded spin; on timeout a status
-//      bit is set and the kernel continues, so it always terminates);
-//   3. keys/values are reordered by digit in shared memory and written out so
-//      that consecutive threads write consecutive addresses of a digit run.
+//   2. per digit the tile count is published; the keys/values are reordered
+//      by digit in shared memory (tile-local offsets only), which frees their
+//      registers for the decoupled look-back that then finds the prefix over
+//      earlier tiles (bounded spin; on timeout a status bit is set and the
+//      kernel continues, so it always terminates);
+//   3. the tile is written out so that consecutive threads write consecutive
+//      addresses of a digit run.
 #include "common.cuh"
 
 namespace bonsai {
 
 #ifndef SORT_LOOKBACK
-#define SORT_LOOKBACK 8           // predecessor tiles read per look-back round trip (4: 6% slower at 2^20, 16: 4%)
+#define SORT_LOOKBACK 8           // predecessor tiles read per look-back round trip (16: 3% slower at 2^20, 32: 9%)
 #endif
 #ifndef SORT_MIN_BLOCKS
 #define SORT_MIN_BLOCKS 2         // resident onesweep blocks per SM the register budget allows
@@ -144,15 +146,31 @@ k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restric
     const unsigned tcount = run;
     unsigned dstart = block_excl_scan(tcount, s_warp);
     unsigned gbase = block_excl_scan(owner ? ghist[d] : 0u, s_warp);
+    unsigned *my = status + (size_t)tile * 256 + d;
     if (owner) {
         s_dstart[d] = dstart;
+        // publish the tile's count first: later tiles look back meanwhile
+        st_volatile(my, (tile == 0 ? FLAG_INC : FLAG_AGG) | tcount);
+    }
+    __syncthreads();
+
+    // Reorder the tile by digit in shared memory (needs only tile-local
+    // offsets), so that the look-back below runs with the items' registers
+    // free for more loads in flight.
+#pragma unroll
+    for (int it = 0; it < SORT_ITEMS; it++) {
+        int idx = wbase + it * 32 + lane;
+        if (idx < n) {
+            unsigned dd = dg[it];
+            unsigned pos = s_dstart[dd] + s_whist[warp][dd] + rk[it];
+            s_keys[pos] = k[it];
+            s_vals[pos] = v[it];
+        }
+    }
+    if (owner) {
         // Decoupled look-back over earlier tiles for digit d.
-        unsigned *my = status + (size_t)tile * 256 + d;
         unsigned prefix = 0;
-        if (tile == 0) {
-            st_volatile(my, FLAG_INC | tcount);
-        } else {
-            st_volatile(my, FLAG_AGG | tcount);
+        if (tile > 0) {
             // Look back LB tiles per round trip (independent loads), then
             // consume them in order: aggregates are added, an inclusive
             // prefix ends the look-back, an unpublished tile is polled again.
@@ -179,19 +197,6 @@ k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restric
             st_volatile(my, FLAG_INC | ((prefix + tcount) & VAL_MASK));
         }
         s_goff[d] = gbase + prefix;
-    }
-    __syncthreads();
-
-    // Reorder the tile by digit in shared memory.
-#pragma unroll
-    for (int it = 0; it < SORT_ITEMS; it++) {
-        int idx = wbase + it * 32 + lane;
-        if (idx < n) {
-            unsigned dd = dg[it];
-            unsigned pos = s_dstart[dd] + s_whist[warp][dd] + rk[it];
-            s_keys[pos] = k[it];
-            s_vals[pos] = v[it];
-        }
     }
     __syncthreads();
     const int nvalid = min(SORT_TILE, n - tile * SORT_TILE);
