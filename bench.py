@@ -45,9 +45,10 @@ SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
 def kernels_per_step(ncrit, group_pack=0):
     """reset, kick+drift+bbox, domains, keys, 8 sort passes, reorder, 4 build
-    (+2 for sibling packing of the groups), multipoles, open radius, walk (two
-    instantiations when groups may exceed 32 bodies), kick."""
-    return 21 + (1 if ncrit > 32 else 0) + (2 if group_pack else 0)
+    (+2 for sibling packing of the groups), multipoles (which also write the
+    MAC records), walk (two instantiations when groups may exceed 32 bodies),
+    kick."""
+    return 20 + (1 if ncrit > 32 else 0) + (2 if group_pack else 0)
 # DRAM bytes (read + write) of one walk launch from the ncu capture in
 # profiles/k_walk_plummer_n2e20.md, keyed by (N, ncrit, group_pack); other
 # choices have no capture and report null.
@@ -477,7 +478,7 @@ STAGE_BYTES = {
     "sort": "8 passes: pass 0 reads keys (8 B), later passes keys + values (12 B); each writes 12 B",
     "reorder": "perm, pos, vel, id read (40 B); pos, vel, id written (36 B)",
     "build": "sorted keys read (8 B/body); 16 B per cell and 8 B per group written",
-    "multipoles": "pos read (16 B/body); 44 B per cell written (com, M, Q, r_open)",
+    "multipoles": "pos read (16 B/body); 64 B per cell written (com, M, Q, delta, MAC record)",
     "kick": "vel, acc read (32 B); vel written (16 B)",
 }
 
@@ -485,7 +486,7 @@ STAGE_BYTES = {
 def stage_bytes(n, ncells, ngroups):
     return {"kick_drift_domain": 88 * n, "keys": 24 * n, "sort": (20 + 7 * 24) * n,
             "reorder": 76 * n, "build": 8 * n + 16 * ncells + 8 * ngroups,
-            "multipoles": 16 * n + 44 * ncells, "kick": 48 * n}
+            "multipoles": 16 * n + 64 * ncells, "kick": 48 * n}
 
 
 def run_sph(a, dev, stream):

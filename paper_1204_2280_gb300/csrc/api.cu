@@ -128,8 +128,11 @@ cudaError_t pipeline_step(Ctx &c, float dt) {
     STAGE(2, launch_sort(c));
     STAGE(3, launch_reorder(c));
     STAGE(4, launch_build(c));
-    STAGE(5, launch_multipoles(c));
-    STAGE(6, c.mlp_P ? pipeline_learned_forces(c, c.eps) : pipeline_forces(c, c.theta, c.eps));
+    // Plain steps: the multipole pass also writes the MAC records for the
+    // step's theta (the learned path sets its own opening angles).
+    const bool plain = c.mlp_P == nullptr;
+    STAGE(5, launch_multipoles(c, plain ? c.theta : 0.f));
+    STAGE(6, plain ? launch_walk(c, c.eps) : pipeline_learned_forces(c, c.eps));
     STAGE(7, launch_kick(c, dt));
 #undef STAGE
     return cudaEventRecordWithFlags(c.ev[8], c.stream, evf);

@@ -216,7 +216,7 @@ cudaError_t launch_keys(Ctx &c);
 cudaError_t launch_sort(Ctx &c);
 cudaError_t launch_reorder(Ctx &c);
 cudaError_t launch_build(Ctx &c);
-cudaError_t launch_multipoles(Ctx &c);
+cudaError_t launch_multipoles(Ctx &c, float theta = 0.f);
 cudaError_t launch_multipoles_refit(Ctx &c);
 cudaError_t launch_cell_cubes(Ctx &c);
 cudaError_t launch_sph_walk(Ctx &c, const float *hs, const float4 *cext, float *rho_s, int32_t *cnt_s);

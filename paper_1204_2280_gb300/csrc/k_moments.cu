@@ -72,6 +72,15 @@ __device__ __forceinline__ void store32(int c, const Mom32 &m, float4 *mono, flo
     qb[c] = make_float2(-m.q[4], -m.q[5]);
 }
 
+// delta[c] = (|com - centre|, side) and, when the step folds the opening
+// radius in (test != nullptr), the walk's MAC record of the cell,
+// test[c] = (com, side / theta + |com - centre|).
+__device__ __forceinline__ void put_delta(unsigned c, const Mom32 &m, float2 dl, float2 *delta, float4 *test,
+                                          float inv_theta) {
+    delta[c] = dl;
+    if (test) test[c] = make_float4(m.x, m.y, m.z, fmaf(dl.y, inv_theta, dl.x));
+}
+
 // REFIT (block time steps, between rebuilds): the bodies may have left the
 // cells they were sorted into.  Each cell also gets ext = half side of a cube
 // about its build-time centre that holds its bodies (at least l/2; a leaf
@@ -86,7 +95,8 @@ __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__res
                                                const uint32_t *__restrict__ cell_parent, uint32_t *cell_done,
                                                const float4 *__restrict__ pos4, const unsigned long long *__restrict__ sk,
                                                const uint8_t *__restrict__ sysid, float4 *mono, float4 *qa, float2 *qb,
-                                               float2 *delta, double *shadow, float4 *cext) {
+                                               float2 *delta, double *shadow, float4 *cext,
+                                               float4 *test, float inv_theta) {
     uint2 link = cell_link[c];
     if (!(link.y & LEAF_BIT)) return;
 
@@ -127,10 +137,10 @@ __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__res
     const unsigned long long kb = sk[b];
     const int sysb = sysid[b];
     if (REFIT) {
-        delta[c] = make_float2(com_offset(make_float3(m.x, m.y, m.z), ctr), 2.f * ext);
+        put_delta(c, m, make_float2(com_offset(make_float3(m.x, m.y, m.z), ctr), 2.f * ext), delta, test, inv_theta);
         cext[c] = make_float4(ctr.x, ctr.y, ctr.z, ext);
     } else {
-        delta[c] = cell_delta(kb, lev, sysb, make_float3(m.x, m.y, m.z), stc);
+        put_delta(c, m, cell_delta(kb, lev, sysb, make_float3(m.x, m.y, m.z), stc), delta, test, inv_theta);
     }
     if (lev < FP64_LEVELS) {
         double *s = shadow + 10 * (size_t)c;
@@ -238,10 +248,10 @@ __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__res
                 const float4 ce = __ldcg(cext + cb + k);
                 e = fmaxf(e, dist_inf(make_float3(ce.x, ce.y, ce.z), pc) + ce.w);
             }
-            delta[c] = make_float2(com_offset(make_float3(m.x, m.y, m.z), pc), 2.f * e);
+            put_delta(c, m, make_float2(com_offset(make_float3(m.x, m.y, m.z), pc), 2.f * e), delta, test, inv_theta);
             cext[c] = make_float4(pc.x, pc.y, pc.z, e);
         } else {
-            delta[c] = cell_delta(kb, lv, sysb, make_float3(m.x, m.y, m.z), stc);
+            put_delta(c, m, cell_delta(kb, lv, sysb, make_float3(m.x, m.y, m.z), stc), delta, test, inv_theta);
         }
     }
 }
@@ -257,18 +267,21 @@ k_multipoles(const DevState *__restrict__ stc, DevState *st, const uint2 *__rest
              const uint32_t *__restrict__ cell_parent, uint32_t *cell_done,
              const float4 *__restrict__ pos4, const unsigned long long *__restrict__ sk,
              const uint8_t *__restrict__ sysid, float4 *mono, float4 *qa, float2 *qb, float2 *delta,
-             double *shadow, float4 *cext) {
+             double *shadow, float4 *cext, float4 *test, float inv_theta) {
     const unsigned c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= stc->ncells || (stc->status & ST_TIMEOUT)) return;
     multipole_cell<REFIT>(c, stc, st, cell_body, cell_link, cell_level, cell_parent, cell_done, pos4, sk, sysid, mono,
-                          qa, qb, delta, shadow, cext);
+                          qa, qb, delta, shadow, cext, test, inv_theta);
 }
 
-cudaError_t launch_multipoles(Ctx &c) {
+// theta > 0: also the walk's MAC records for that opening angle (what
+// launch_open_radius writes), so that a step needs no separate pass.
+cudaError_t launch_multipoles(Ctx &c, float theta) {
     const unsigned grid = (unsigned)((c.ccap + 255) / 256);
     k_multipoles<false><<<grid, 256, 0, c.stream>>>(c.st, c.st, c.cell_body, c.cell_link, c.cell_level,
                                                     c.cell_parent, c.cell_done, c.pos4, c.keys, c.sysid,
-                                                    c.mono, c.quadA, c.quadB, c.delta, c.shadow, nullptr);
+                                                    c.mono, c.quadA, c.quadB, c.delta, c.shadow, nullptr,
+                                                    theta > 0.f ? c.test : nullptr, theta > 0.f ? 1.0f / theta : 0.f);
     return cudaGetLastError();
 }
 
@@ -278,7 +291,8 @@ cudaError_t launch_multipoles_refit(Ctx &c) {
     const unsigned grid = (unsigned)((c.ccap + 255) / 256);
     k_multipoles<true><<<grid, 256, 0, c.stream>>>(c.st, c.st, c.cell_body, c.cell_link, c.cell_level,
                                                    c.cell_parent, c.cell_done, c.pos4, c.keys, c.sysid,
-                                                   c.mono, c.quadA, c.quadB, c.delta, c.shadow, c.cext);
+                                                   c.mono, c.quadA, c.quadB, c.delta, c.shadow, c.cext,
+                                                   nullptr, 0.f);
     return cudaGetLastError();
 }
 
