@@ -46,13 +46,13 @@ FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
 def kernels_per_step(ncrit, group_pack=0):
     """reset, kick+drift+bbox, domains, keys, 8 sort passes, reorder, 4 build
     (+2 for sibling packing of the groups), multipoles (which also write the
-    MAC records), walk (two instantiations when groups may exceed 32 bodies),
-    kick."""
-    return 20 + (1 if ncrit > 32 else 0) + (2 if group_pack else 0)
-# DRAM bytes (read + write) of one walk launch from the ncu capture in
-# profiles/k_walk_plummer_n2e20.md, keyed by (N, ncrit, group_pack); other
-# choices have no capture and report null.
-WALK_TRAFFIC = {(1 << 20, 32, 1): 35.97e6}
+    MAC records), walk (a second instantiation when groups may exceed 16
+    bodies: three bodies per lane for 17..24, two for more than 32), kick."""
+    return 20 + (1 if ncrit > 16 else 0) + (2 if group_pack else 0)
+# DRAM bytes (read + write) of one step's walk (both instantiations) from
+# the ncu capture in profiles/k_walk_plummer_n2e20.md, keyed by (N, ncrit,
+# group_pack); other choices have no capture and report null.
+WALK_TRAFFIC = {}
 
 
 def parse():

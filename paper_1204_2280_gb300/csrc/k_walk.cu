@@ -18,9 +18,12 @@
 //    issue slot for two operations).  Groups of <= 32 bodies: a group of n
 //    bodies uses s = max(2, next_pow2(n)) body slots and the 32/s lanes
 //    sharing a body split the tile's 16 source pairs (summed at the end), so
-//    small groups still keep all lanes busy.  Groups of 33..64 bodies run in a
-//    second instantiation with two bodies per lane that share every source
-//    read;
+//    small groups still keep all lanes busy.  Groups of 17..24 bodies (at
+//    most 32 per group) run in a second instantiation with three bodies per
+//    lane in 8 body slots and four phases, 24 body places where one body per
+//    lane would leave 8..15 of 32 lanes empty; groups of 33..64 bodies (larger
+//    ncrit) in one with two bodies per lane.  The bodies of a lane share
+//    every source read;
 //  * each tile is summed in plain FP32 and added to the body's accumulators
 //    with Kahan compensation (one compensated add per tile and component).
 // Body-cell (monopole + traceless quadrupole, softened):
@@ -218,18 +221,30 @@ __device__ __forceinline__ void eval_pp(const float4 *__restrict__ base, int pha
 // Which instantiation walks a group of ng bodies: one body per lane below
 // WALK_BPL2_FROM bodies (17..33), two from there on.  33 is the measured
 // best: two bodies per lane from 17 or 25 bodies on (16 body slots, two
-// phases) run the 2^20 walk 3% slower (128 registers, 16 warps per SM).
+// phases: as many body places as one body per lane) run the 2^20 walk 3%
+// slower (128 registers, 16 warps per SM).
 #ifndef WALK_BPL2_FROM
 #define WALK_BPL2_FROM 33
 #endif
 static_assert(WALK_BPL2_FROM >= 17 && WALK_BPL2_FROM <= 33, "two bodies per lane need >= 16 body slots");
-__host__ __device__ constexpr int walk_bpl(int ng) { return ng < WALK_BPL2_FROM ? 1 : 2; }
+// With `three` (plain walks with groups of at most 32 bodies), groups of
+// 17..24 bodies go to a third instantiation with three bodies per lane in 8
+// body slots (four phases): 24 body places instead of the 32 lanes of one
+// body per lane, where 8..15 of them would hold no body.
+#ifndef WALK_BPL3
+#define WALK_BPL3 1
+#endif
+__host__ __device__ constexpr int walk_bpl(int ng, bool three) {
+    return three && ng > 16 && ng <= 24 ? 3 : ng < WALK_BPL2_FROM ? 1 : 2;
+}
 
 // log2 of the body slots of a group: one body per lane, next power of two
 // (>= 2: at most 16 phases share the 16 source pairs); two bodies per lane,
-// 16 slots (two phases) up to 32 bodies, 32 slots beyond.
+// 16 slots (two phases) up to 32 bodies, 32 slots beyond; three bodies per
+// lane, 8 slots (four phases).
 template <int BPL>
 __device__ __forceinline__ int walk_lg(int ng) {
+    if (BPL == 3) return 3;
     if (BPL == 2) return ng <= 32 ? 4 : 5;
     return ng <= 2 ? 1 : 32 - __clz(ng - 1);
 }
@@ -238,7 +253,9 @@ __device__ __forceinline__ int walk_lg(int ng) {
 template <int BPL, int STRIDE>
 __device__ __forceinline__ void tile_pc(int lg, const float4 *__restrict__ base, int phase, const float4 (&me)[BPL],
                                         const float2 eps2, Acc (&A)[BPL]) {
-    if constexpr (BPL == 2) {
+    if constexpr (BPL == 3) {
+        eval_pc<4, 3, STRIDE>(base, phase, me, eps2, A);
+    } else if constexpr (BPL == 2) {
         if (lg == 4) eval_pc<2, 2, STRIDE>(base, phase, me, eps2, A);
         else eval_pc<1, 2, STRIDE>(base, phase, me, eps2, A);
     } else {
@@ -254,7 +271,9 @@ __device__ __forceinline__ void tile_pc(int lg, const float4 *__restrict__ base,
 template <int BPL, int STRIDE>
 __device__ __forceinline__ void tile_pp(int lg, const float4 *__restrict__ base, int phase, const float4 (&me)[BPL],
                                         const float2 eps2, Acc (&A)[BPL]) {
-    if constexpr (BPL == 2) {
+    if constexpr (BPL == 3) {
+        eval_pp<4, 3, STRIDE>(base, phase, me, eps2, A);
+    } else if constexpr (BPL == 2) {
         if (lg == 4) eval_pp<2, 2, STRIDE>(base, phase, me, eps2, A);
         else eval_pp<1, 2, STRIDE>(base, phase, me, eps2, A);
     } else {
@@ -326,9 +345,9 @@ __device__ __forceinline__ void walk_pop(const unsigned *stk, int &sp, int lane,
 #define WALK_MAXNREG1 0             // > 0: register cap of the one-body-per-lane walk
 #endif
 #if WALK_MAXNREG1 > 0
-#define WALK_ATTRS __launch_bounds__(256) __maxnreg__(BPL == 1 ? WALK_MAXNREG1 : 255)
+#define WALK_ATTRS __launch_bounds__(256) __maxnreg__(BPL == 1 ? WALK_MAXNREG1 : BPL == 2 ? 255 : 128)
 #else
-#define WALK_ATTRS __launch_bounds__(256, BPL == 1 ? WALK_MIN_BLOCKS1 : WALK_MIN_BLOCKS2)
+#define WALK_ATTRS __launch_bounds__(256, BPL == 1 ? WALK_MIN_BLOCKS1 : BPL == 2 ? WALK_MIN_BLOCKS2 : 2)
 #endif
 template <int BPL, bool FEAT, bool BLOCK>
 __global__ void WALK_ATTRS
@@ -338,7 +357,8 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
        const float4 *__restrict__ quadA, const float2 *__restrict__ quadB,
        const uint8_t *__restrict__ sysid, float eps, int stack_cap, unsigned max_rounds,
        float4 *acc4, uint2 *counts, const uint8_t *__restrict__ cell_level, float *feat,
-       const unsigned *__restrict__ gate, const float4 *__restrict__ actv, unsigned act_s, int act_kmax) {
+       const unsigned *__restrict__ gate, const float4 *__restrict__ actv, unsigned act_s, int act_kmax,
+       bool three) {
     extern __shared__ float4 smem4[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const size_t warp_bytes = sizeof(WarpRings) + (size_t)stack_cap * sizeof(unsigned);
@@ -366,7 +386,7 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
         if (g >= ngroups) break;
         const uint2 gr = groups[g];
         const int gb = (int)gr.x, ng = (int)gr.y;
-        if (walk_bpl(ng) != BPL) continue;          // another instantiation's group
+        if (walk_bpl(ng, three) != BPL) continue;   // another instantiation's group
 #if WALK_SMALL_LAST
         if (second != (ng <= WALK_SMALL_LAST)) continue;
 #endif
@@ -604,7 +624,7 @@ size_t walk_smem_bytes(int warps, int stack_cap) {
 // Function attribute and occupancy are set up once per shape, before any
 // stream capture of a step (the first step always runs eagerly).
 template <int BPL, bool FEAT, bool BLOCK>
-static cudaError_t launch_walk_t(Ctx &c, float eps, const unsigned *gate, cudaStream_t stream) {
+static cudaError_t launch_walk_t(Ctx &c, float eps, const unsigned *gate, bool three, cudaStream_t stream) {
     const unsigned polls = (unsigned)(c.max_spin < 0xffffffffll ? c.max_spin : 0xffffffffll);
     const int warps = c.walk_warps;
     const size_t smem = walk_smem_bytes(warps, c.list_capacity);
@@ -624,7 +644,7 @@ static cudaError_t launch_walk_t(Ctx &c, float eps, const unsigned *gate, cudaSt
     k_walk<BPL, FEAT, BLOCK><<<c.num_sms * occ_per_sm, warps * 32, smem, stream>>>(
         c.st, c.st, c.groups, c.pos4, c.test, c.cell_link, c.mono, c.quadA, c.quadB, c.sysid, eps,
         c.list_capacity, polls, c.acc4, c.counts, c.cell_level, c.feat, gate,
-        BLOCK ? c.vel4 : nullptr, c.block_s, c.block_kmax);
+        BLOCK ? c.vel4 : nullptr, c.block_s, c.block_kmax, three);
     return cudaGetLastError();
 }
 
@@ -634,19 +654,28 @@ static cudaError_t launch_walk_t(Ctx &c, float eps, const unsigned *gate, cudaSt
 // joined back into the context's stream (event edges inside a captured
 // step), so the tail of each launch overlaps the other's work.
 cudaError_t launch_walk(Ctx &c, float eps, bool features, const unsigned *gate) {
+    // Second instantiation beside one body per lane: two bodies per lane for
+    // groups of more than 32 bodies, or, in plain walks with groups of at
+    // most 32 bodies, three per lane for groups of 17..24.
+    const bool three = WALK_BPL3 && !features && c.block_kmax < 0 && c.ncrit > 16 && c.ncrit < WALK_BPL2_FROM;
     // instantiations: plain, with learned features, or block time steps
-    auto one = [&](bool two, cudaStream_t st) -> cudaError_t {
+    auto one = [&](int bpl, cudaStream_t st) -> cudaError_t {
         if (c.block_kmax >= 0)
-            return two ? launch_walk_t<2, false, true>(c, eps, gate, st) : launch_walk_t<1, false, true>(c, eps, gate, st);
+            return bpl == 2 ? launch_walk_t<2, false, true>(c, eps, gate, false, st)
+                            : launch_walk_t<1, false, true>(c, eps, gate, false, st);
         if (features)
-            return two ? launch_walk_t<2, true, false>(c, eps, gate, st) : launch_walk_t<1, true, false>(c, eps, gate, st);
-        return two ? launch_walk_t<2, false, false>(c, eps, gate, st) : launch_walk_t<1, false, false>(c, eps, gate, st);
+            return bpl == 2 ? launch_walk_t<2, true, false>(c, eps, gate, false, st)
+                            : launch_walk_t<1, true, false>(c, eps, gate, false, st);
+        if (bpl == 3) return launch_walk_t<3, false, false>(c, eps, gate, true, st);
+        return bpl == 2 ? launch_walk_t<2, false, false>(c, eps, gate, false, st)
+                        : launch_walk_t<1, false, false>(c, eps, gate, three, st);
     };
-    if (c.ncrit < WALK_BPL2_FROM) return one(false, c.stream);
+    const int second = c.ncrit >= WALK_BPL2_FROM ? 2 : three ? 3 : 0;
+    if (second == 0) return one(1, c.stream);
     cudaError_t e = cudaEventRecord(c.ev_fork, c.stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c.side, c.ev_fork, 0);
-    if (e == cudaSuccess) e = one(true, c.side);
-    if (e == cudaSuccess) e = one(false, c.stream);
+    if (e == cudaSuccess) e = one(second, c.side);
+    if (e == cudaSuccess) e = one(1, c.stream);
     if (e == cudaSuccess) e = cudaEventRecord(c.ev_join, c.side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c.stream, c.ev_join, 0);
     return e;
