@@ -52,7 +52,7 @@ def kernels_per_step(ncrit, group_pack=0):
 # DRAM bytes (read + write) of one step's walk (both instantiations) from
 # the ncu capture in profiles/k_walk_plummer_n2e20.md, keyed by (N, ncrit,
 # group_pack); other choices have no capture and report null.
-WALK_TRAFFIC = {}
+WALK_TRAFFIC = {(1 << 20, 32, 1): 68.77e6}
 
 
 def parse():

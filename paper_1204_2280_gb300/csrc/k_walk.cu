@@ -227,10 +227,11 @@ __device__ __forceinline__ void eval_pp(const float4 *__restrict__ base, int pha
 #define WALK_BPL2_FROM 33
 #endif
 static_assert(WALK_BPL2_FROM >= 17 && WALK_BPL2_FROM <= 33, "two bodies per lane need >= 16 body slots");
-// With `three` (plain walks with groups of at most 32 bodies), groups of
-// 17..24 bodies go to a third instantiation with three bodies per lane in 8
-// body slots (four phases): 24 body places instead of the 32 lanes of one
-// body per lane, where 8..15 of them would hold no body.
+// With `three` (walks without learned features, groups of at most 32
+// bodies), groups of 17..24 bodies (active bodies, in a block substep) go to
+// a third instantiation with three bodies per lane in 8 body slots (four
+// phases): 24 body places instead of the 32 lanes of one body per lane,
+// where 8..15 of them would hold no body.
 #ifndef WALK_BPL3
 #define WALK_BPL3 1
 #endif
@@ -386,21 +387,30 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
         if (g >= ngroups) break;
         const uint2 gr = groups[g];
         const int gb = (int)gr.x, ng = (int)gr.y;
-        if (walk_bpl(ng, three) != BPL) continue;   // another instantiation's group
+        // groups this instantiation can never take (by size; without block
+        // time steps every body takes part, so the size decides)
+        if (!BLOCK && walk_bpl(ng, three) != BPL) continue;
+        if (BLOCK && ((BPL == 2 && walk_bpl(ng, three) != 2) || (BPL == 3 && ng <= 16))) continue;
 #if WALK_SMALL_LAST
         if (second != (ng <= WALK_SMALL_LAST)) continue;
 #endif
         // Body slots and source phases.
         // Block time steps, groups of <= 32 bodies: the active bodies are
-        // compacted into the first body slots (in body order), so the slot
-        // count follows the active count (all active: the plain layout).
+        // compacted into the first body slots (in body order), and the
+        // instantiation and slot count follow the active count (all active:
+        // the plain layout, so the same sums as a plain walk).
         int nslot = ng;
-        if (BLOCK && BPL == 1) {
-            const bool a = lane < ng && block_active(actv[gb + lane].w, act_s, act_kmax);
-            const unsigned am = __ballot_sync(0xffffffffu, a);
+        bool act = false;
+        unsigned am = 0u;
+        if (BLOCK && ng <= 32) {
+            act = lane < ng && block_active(actv[gb + lane].w, act_s, act_kmax);
+            am = __ballot_sync(0xffffffffu, act);
             nslot = __popc(am);
             if (nslot == 0) continue;
-            if (a) R.leaf[__popc(am & lt)].x = (unsigned)lane;
+        }
+        if (BLOCK && walk_bpl(nslot, three) != BPL) continue;   // another instantiation's group
+        if (BLOCK && BPL != 2) {
+            if (act) R.leaf[__popc(am & lt)].x = (unsigned)lane;
             __syncwarp();
         }
         const int lg = walk_lg<BPL>(nslot);
@@ -416,7 +426,7 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
             const int slot = bslot + slots * b;
             live[b] = slot < nslot;
             int body = slot;
-            if (BLOCK && BPL == 1) {
+            if (BLOCK && BPL != 2) {
                 if (live[b]) body = (int)R.leaf[slot].x;
             } else if (BLOCK && live[b]) {
                 // only the bodies whose step ends at this substep
@@ -441,9 +451,9 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
         // Live body slots (bit = slot); a group without one is skipped.
         unsigned nlive = (unsigned)ng;
         if (BLOCK) {                               // a group without a live body is skipped
-            const unsigned lm0 = __ballot_sync(0xffffffffu, phase == 0 && live[0]);
-            const unsigned lm1 = BPL == 2 ? __ballot_sync(0xffffffffu, phase == 0 && live[BPL - 1]) : 0u;
-            nlive = (unsigned)(__popc(lm0) + __popc(lm1));
+            nlive = 0u;
+#pragma unroll
+            for (int b = 0; b < BPL; b++) nlive += (unsigned)__popc(__ballot_sync(0xffffffffu, phase == 0 && live[b]));
             if (nlive == 0u) continue;
         }
         Acc A[BPL];
@@ -655,14 +665,17 @@ static cudaError_t launch_walk_t(Ctx &c, float eps, const unsigned *gate, bool t
 // step), so the tail of each launch overlaps the other's work.
 cudaError_t launch_walk(Ctx &c, float eps, bool features, const unsigned *gate) {
     // Second instantiation beside one body per lane: two bodies per lane for
-    // groups of more than 32 bodies, or, in plain walks with groups of at
-    // most 32 bodies, three per lane for groups of 17..24.
-    const bool three = WALK_BPL3 && !features && c.block_kmax < 0 && c.ncrit > 16 && c.ncrit < WALK_BPL2_FROM;
+    // groups of more than 32 bodies, or, in walks without learned features
+    // and with groups of at most 32 bodies, three per lane for groups of
+    // 17..24 (bodies that take part: the active ones of a block substep).
+    const bool three = WALK_BPL3 && !features && c.ncrit > 16 && c.ncrit < WALK_BPL2_FROM;
     // instantiations: plain, with learned features, or block time steps
     auto one = [&](int bpl, cudaStream_t st) -> cudaError_t {
-        if (c.block_kmax >= 0)
+        if (c.block_kmax >= 0) {
+            if (bpl == 3) return launch_walk_t<3, false, true>(c, eps, gate, true, st);
             return bpl == 2 ? launch_walk_t<2, false, true>(c, eps, gate, false, st)
-                            : launch_walk_t<1, false, true>(c, eps, gate, false, st);
+                            : launch_walk_t<1, false, true>(c, eps, gate, three, st);
+        }
         if (features)
             return bpl == 2 ? launch_walk_t<2, true, false>(c, eps, gate, false, st)
                             : launch_walk_t<1, true, false>(c, eps, gate, false, st);
