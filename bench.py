@@ -305,6 +305,8 @@ def run_ensemble(a, dev, stream, rank=0, world=1):
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
+        B.bonsai_set_stage_timing(bz.ctx, True)    # one more step, with stage events
+        bz.step(dt)
         stages = B.bonsai_get_stage_times(bz.ctx)
         bz.sync()
         bz.close()
@@ -315,7 +317,8 @@ def run_ensemble(a, dev, stream, rank=0, world=1):
             "ms_per_step": t, "particles_per_s": bodies / (total_ms / 1e3),
             "ranks": world, "systems_rank0": [lo, hi] if rank == 0 else None,
             "ncrit": nc, "walk_warps": w, "group_pack": pk, "theta": theta, "eps": eps,
-            "last_step_stages_ms_rank0": {k: float(v) for k, v in zip(B.STAGES, stages)},
+            "stages_ms_rank0": {k: float(v) for k, v in zip(B.STAGES, stages)},
+            "stages_from": "one step after the timed ones, with stage events in the step graph",
             "scaling": "strong (the 64 systems split over the ranks)",
             "what": "all systems of a rank in one bonsai_step: one sort, one build, one persistent walk, one graph"}
 
@@ -671,10 +674,17 @@ def run_sweep(a, dev, stream):
                 e1.record(stream)
                 e1.synchronize()
                 ms.append(e0.elapsed_time(e1))
-                st.append(B.bonsai_get_stage_times(bz.ctx))
-                B._check(bz.ctx, B.lib().bonsai_get_counts(bz.ctx, None, None, tot))
-                npc += int(tot[0]); npp += int(tot[1])
             d1 = B.bonsai_diagnostics(bz.ctx)
+            # stage times and interaction counts: as many further steps with
+            # stage events (the timed steps above run without them)
+            B.bonsai_set_stage_timing(bz.ctx, True)
+            for k in range(steps + 2):
+                flush.zero_()
+                bz.step(dt)
+                if k >= 2:
+                    st.append(B.bonsai_get_stage_times(bz.ctx))
+                    B._check(bz.ctx, B.lib().bonsai_get_counts(bz.ctx, None, None, tot))
+                    npc += int(tot[0]); npp += int(tot[1])
             _, ncells, ngroups = B.bonsai_get_sizes(bz.ctx)
             bz.sync()
             bz.close()
@@ -772,10 +782,6 @@ def run_ours(a, rank, world, local_rank):
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        stage_ms.append(B.bonsai_get_stage_times(bz.ctx))
-        B._check(bz.ctx, B.lib().bonsai_get_counts(bz.ctx, None, None, tot))
-        npc.append(int(tot[0])); npp.append(int(tot[1]))
-        flops.append(FLOP_PC * int(tot[0]) + FLOP_PP * int(tot[1]))
     t_wall = time.perf_counter() - t_wall0
     barrier()
     clocks = sampler.stop()
@@ -784,6 +790,22 @@ def run_ours(a, rank, world, local_rank):
     from paper_1204_2280_gb300 import dist as D
     total_ms, _ = D.combine(total_ms, float(n * a.steps))
     value = world * n * a.steps / (total_ms / 1e3)
+
+    # Stage breakdown and the walk's roofline: as many further steps with
+    # stage events in the step graph (they add ~40 us per step, so the timed
+    # steps above run without them), L2 flushed between steps.
+    B.bonsai_set_stage_timing(bz.ctx, True)
+    for _ in range(2):                          # eager, then re-captured with the events
+        bz.step(a.dt)
+    for _ in range(a.steps):
+        flush.zero_()
+        bz.step(a.dt)
+        stage_ms.append(B.bonsai_get_stage_times(bz.ctx))
+        B._check(bz.ctx, B.lib().bonsai_get_counts(bz.ctx, None, None, tot))
+        npc.append(int(tot[0])); npp.append(int(tot[1]))
+        flops.append(FLOP_PC * int(tot[0]) + FLOP_PP * int(tot[1]))
+    B.bonsai_set_stage_timing(bz.ctx, False)
+    bz.sync()
     stages = np.array(stage_ms).sum(0)
     walk_ms = float(stages[B.STAGES.index("walk")])
     achieved = sum(flops) / (walk_ms / 1e3) / 1e12
@@ -835,6 +857,7 @@ def run_ours(a, rank, world, local_rank):
             "gpu_launches": kernels_per_step(a.ncrit, a.group_pack) * a.steps,
             "clocks": clocks,
             "stages_ms_per_step": {s: float(v) / a.steps for s, v in zip(B.STAGES, stages)},
+            "stages_from": "as many further steps with stage events in the step graph (ms_per_step is timed without them)",
             "interactions_per_body": {"pc": sum(npc) / (n * a.steps), "pp": sum(npp) / (n * a.steps)},
             "interactions_per_s": (sum(npc) + sum(npp)) / (walk_ms / 1e3),
             "wall_s_timed_loop": t_wall,

@@ -203,12 +203,19 @@ int bonsai_diagnostics(bonsai_ctx *ctx, double out[8]);
  * BONSAI_OK, BONSAI_ERR_CAPACITY, BONSAI_ERR_TIMEOUT or BONSAI_ERR_NAN. */
 int bonsai_sync(bonsai_ctx *ctx);
 
-/* Device time of each stage of the last bonsai_step in milliseconds, from
- * CUDA events recorded on the context's stream between the stages (also when
- * the step is replayed from its graph).  ms[0] first kick + drift + domain,
- * [1] keys, [2] sort, [3] reorder, [4] tree build, [5] multipoles, [6] walk
- * (opening radii + traverse), [7] second kick.  Synchronises; writes
- * min(n, 8) values and returns that count (negative on error). */
+/* on != 0: later bonsai_step calls record CUDA events on the context's
+ * stream between their stages (also when the step is replayed from its
+ * graph) for bonsai_get_stage_times; 0 (the default): no events.  The nine
+ * event nodes cost about 40 us per step at N = 2^20, so timed runs measure
+ * steps without them.  Changing it re-captures the step graph. */
+int bonsai_set_stage_timing(bonsai_ctx *ctx, int on);
+
+/* Device time of each stage of the last bonsai_step in milliseconds (that
+ * step must have run with stage timing on: BONSAI_ERR_NOT_READY otherwise).
+ * ms[0] first kick + drift + domain, [1] keys, [2] sort, [3] reorder, [4]
+ * tree build, [5] multipoles (with the walk's MAC records), [6] walk, [7]
+ * second kick.  Synchronises; writes min(n, 8) values and returns that
+ * count (negative on error). */
 int bonsai_get_stage_times(bonsai_ctx *ctx, float *ms, int n);
 
 /* ---- introspection (copies to caller-owned HOST buffers; synchronises) -- */

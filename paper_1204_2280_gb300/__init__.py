@@ -29,7 +29,7 @@ EXPORTS = ["bonsai_create", "bonsai_destroy", "bonsai_set_bodies", "bonsai_build
            "bonsai_get_bodies", "bonsai_diagnostics", "bonsai_sync", "bonsai_get_sizes",
            "bonsai_get_domain", "bonsai_get_keys", "bonsai_get_tree", "bonsai_get_groups",
            "bonsai_get_moments", "bonsai_get_counts", "bonsai_last_error", "bonsai_version",
-           "bonsai_get_stage_times", "bonsai_sort_keys_static", "bonsai_set_systems",
+           "bonsai_get_stage_times", "bonsai_set_stage_timing", "bonsai_sort_keys_static", "bonsai_set_systems",
            "bonsai_get_domains", "bonsai_autotune", "bonsai_mlp_create", "bonsai_mlp_destroy",
            "bonsai_mlp_last_error", "bonsai_mlp_set_params", "bonsai_mlp_get_params",
            "bonsai_mlp_fit_norm", "bonsai_mlp_predict", "bonsai_mlp_grad", "bonsai_mlp_train",
@@ -93,6 +93,7 @@ def lib():
         L.bonsai_last_error.restype = C.c_char_p
         L.bonsai_version.restype = C.c_char_p
         L.bonsai_get_stage_times.argtypes = [p, p, i]
+        L.bonsai_set_stage_timing.argtypes = [p, i]
         L.bonsai_sort_keys_static.argtypes = [p, p, p, ll, p]
         L.bonsai_set_systems.argtypes = [p, p, i]
         L.bonsai_get_domains.argtypes = [p, p, p]
@@ -318,6 +319,10 @@ def bonsai_get_counts(ctx):
     tot = (C.c_ulonglong * 2)()
     _check(ctx, lib().bonsai_get_counts(ctx, a.ctypes.data, b.ctypes.data, tot))
     return a, b, (int(tot[0]), int(tot[1]))
+
+
+def bonsai_set_stage_timing(ctx, on: bool) -> None:
+    _check(ctx, lib().bonsai_set_stage_timing(ctx, 1 if on else 0))
 
 
 def bonsai_get_stage_times(ctx) -> np.ndarray:

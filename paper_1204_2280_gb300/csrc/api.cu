@@ -119,8 +119,8 @@ cudaError_t pipeline_step(Ctx &c, float dt) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if ((e = cudaStreamIsCapturing(c.stream, &cs)) != cudaSuccess) return e;
     const unsigned evf = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
-#define STAGE(i, call)                                                                 \
-    if ((e = cudaEventRecordWithFlags(c.ev[i], c.stream, evf)) != cudaSuccess) return e; \
+#define STAGE(i, call)                                                                                     \
+    if (c.stage_timing && (e = cudaEventRecordWithFlags(c.ev[i], c.stream, evf)) != cudaSuccess) return e; \
     if ((e = (call)) != cudaSuccess) return e;
     STAGE(0, launch_reset(c));
     if ((e = launch_kick_drift_bbox(c, dt)) != cudaSuccess) return e;
@@ -135,7 +135,7 @@ cudaError_t pipeline_step(Ctx &c, float dt) {
     STAGE(6, plain ? launch_walk(c, c.eps) : pipeline_learned_forces(c, c.eps));
     STAGE(7, launch_kick(c, dt));
 #undef STAGE
-    return cudaEventRecordWithFlags(c.ev[8], c.stream, evf);
+    return c.stage_timing ? cudaEventRecordWithFlags(c.ev[8], c.stream, evf) : cudaSuccess;
 }
 
 }  // namespace
@@ -354,7 +354,7 @@ int bonsai_step(bonsai_ctx *ctx, float dt) {
     // The first step with a given (dt, theta, eps, N) runs eagerly; the second
     // captures the step into a CUDA graph, later ones replay it.
     const bool same = c.graph_dt == dt && c.graph_theta == c.theta && c.graph_eps == c.eps &&
-                      c.graph_n == c.n;
+                      c.graph_n == c.n && c.graph_timing == c.stage_timing;
     if (c.use_graph && same && c.step_graph) {
         CK(cudaGraphLaunch(c.step_graph, c.stream));
     } else if (c.use_graph && same) {
@@ -379,16 +379,24 @@ int bonsai_step(bonsai_ctx *ctx, float dt) {
         if (c.step_graph) { cudaGraphExecDestroy(c.step_graph); c.step_graph = nullptr; }
         CK(pipeline_step(c, dt));
         c.graph_dt = dt; c.graph_theta = c.theta; c.graph_eps = c.eps; c.graph_n = c.n;
+        c.graph_timing = c.stage_timing;
     }
     c.built = c.moments_ready = c.have_acc = c.tree_fresh = true;
-    c.timed_step = true;
+    c.timed_step = c.stage_timing;
+    return BONSAI_OK;
+}
+
+int bonsai_set_stage_timing(bonsai_ctx *ctx, int on) {
+    if (!ctx) return BONSAI_ERR_INVALID_ARG;
+    ctx->c.stage_timing = on != 0;
     return BONSAI_OK;
 }
 
 int bonsai_get_stage_times(bonsai_ctx *ctx, float *ms, int n) {
     if (!ctx || !ms || n < 0) return BONSAI_ERR_INVALID_ARG;
     Ctx &c = ctx->c;
-    if (!c.timed_step) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_get_stage_times: no step yet");
+    if (!c.timed_step)
+        return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_get_stage_times: the last step recorded no stage times");
     CK(cudaStreamSynchronize(c.stream));
     int k = n < Ctx::NSTAGE ? n : Ctx::NSTAGE;
     for (int i = 0; i < k; i++) CK(cudaEventElapsedTime(&ms[i], c.ev[i], c.ev[i + 1]));

@@ -135,7 +135,9 @@ struct Ctx {
     cudaGraphExec_t step_graph = nullptr;
     static constexpr int NSTAGE = 8;
     cudaEvent_t ev[NSTAGE + 1] = {};
-    bool timed_step = false;
+    bool timed_step = false;         // the last bonsai_step recorded stage events
+    bool stage_timing = false;       // bonsai_step records stage events (bonsai_set_stage_timing)
+    bool graph_timing = false;       // the captured step graph holds them
     float graph_dt = 0.f, graph_theta = 0.f, graph_eps = 0.f;
     long long graph_n = -1;
 

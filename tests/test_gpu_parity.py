@@ -248,6 +248,45 @@ def test_multi_step_graph_replay_matches_direct_launches():
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
 
 
+def test_stage_timing_switch():
+    """Stage events are off by default (no stage times: NOT_READY), on after
+    bonsai_set_stage_timing (eight positive stage times, also from graph
+    replays), and either way the steps give bit-identical state."""
+    import torch
+    b = W.plummer(20000, 5)
+    outs = []
+    for timing in (False, True):
+        with B.Bonsai(B.Config(ncrit=32, group_pack=1)) as bz:
+            bz.set_bodies(b.pos, b.mass, b.vel)
+            B.bonsai_set_params(bz.ctx, 0.75, 0.01)
+            B.bonsai_set_stage_timing(bz.ctx, timing)
+            for _ in range(4):
+                bz.step(1.0 / 128)
+            if timing:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(torch.cuda.current_stream())
+                bz.step(1.0 / 128)
+                bz.sync()
+                e1.record(torch.cuda.current_stream())
+                e1.synchronize()
+                ms = B.bonsai_get_stage_times(bz.ctx)
+                assert ms.shape == (8,) and np.all(ms > 0)
+                assert ms.sum() <= e0.elapsed_time(e1) * 1.05 + 0.05
+            else:
+                with pytest.raises(B.BonsaiError) as ei:
+                    B.bonsai_get_stage_times(bz.ctx)
+                assert ei.value.code == -7
+                bz.step(1.0 / 128)
+            x = np.zeros((20000, 3), np.float32)
+            v = np.zeros((20000, 3), np.float32)
+            B.bonsai_get_bodies(bz.ctx, x, v)
+            bz.sync()
+            outs.append((x, v))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
 def test_capacity_overflow_reports_error_and_recovers():
     b = W.plummer(20000, 1)
     with B.Bonsai(B.Config(list_capacity=64)) as bz:
