@@ -76,7 +76,7 @@ cudaError_t alloc_bodies(Ctx &c, long long n) {
     a.take(c.cell_done, ccap, plan); a.take(c.cell_cb, ccap, plan);
     a.take(c.mono, ccap, plan); a.take(c.quadA, ccap, plan); a.take(c.quadB, ccap, plan);
     a.take(c.test, ccap, plan); a.take(c.delta, ccap, plan); a.take(c.cext, ccap, plan);
-    a.take(c.shadow, 10 * (size_t)(ccap < 585 * MAX_SYSTEMS ? ccap : 585 * MAX_SYSTEMS), plan);   // FP64 copies (levels < FP64_LEVELS <= 4)
+    a.take(c.shadow, 10 * (size_t)(ccap < 585 * MAX_SYSTEMS ? ccap : 585 * MAX_SYSTEMS), plan);   // FP64 root terms of the level-1 cells
     a.take(c.groups, n, plan); a.take(c.groups_raw, n, plan);
     a.take(c.group_lvl, n, plan); a.take(c.group_flag, n, plan); a.take(c.group_bcount, (n + PACK_THREADS - 1) / PACK_THREADS, plan);
     a.take(c.counts, n, plan); a.take(c.feat, FEAT_STRIDE * (size_t)n, plan);

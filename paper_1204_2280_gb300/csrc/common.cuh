@@ -25,7 +25,6 @@ constexpr int MAX_LEVEL = KEY_BITS_PER_AXIS;     // deepest level (root = 0)
 constexpr int NROWS = MAX_LEVEL + 2;             // 22 level rows + group row
 constexpr int GROUP_ROW = MAX_LEVEL + 1;
 constexpr uint32_t LEAF_BIT = 0x80000000u;
-constexpr int FP64_LEVELS = 1;                   // level 0 (each system's root) combines in FP64
 
 #ifndef SORT_THREADS_CFG
 #define SORT_THREADS_CFG 256

@@ -9,10 +9,13 @@
 //   Q_p = sum_k [ Q_k + M_k (3 d_k d_k^T - |d_k|^2 I) ],  d_k = com_k - com_p,
 // in one launch: each thread finishing a cell bumps its parent's arrival
 // counter and the last child to arrive combines the parent (no waiting).
-// The levels below FP64_LEVELS (level 0: the root of each system) combine
-// in FP64, from FP64 copies of children on those levels.  One level: FP64
-// arithmetic runs at a small fraction of the FP32 rate here, and a combine is
-// a serial chain on one lane (each further level measured about 13 us).
+// The root of each system (level 0) combines in FP64: FP64 arithmetic runs
+// at a small fraction of the FP32 rate here, so the thread finishing each
+// level-1 cell writes that cell's FP64 terms about the root cube's centre O
+// (the ones the root needs, computed on up to eight lanes of different warps
+// at once), and the root sums them and shifts to its own com:
+//   with e = com_k - O:  M = sum m_k,  com = O + (sum m_k e) / M,
+//   Q = sum [Q_k + m_k (3 e e^T - |e|^2 I)] - M (3 s s^T - |s|^2 I),  s = com - O.
 #include "common.cuh"
 
 namespace bonsai {
@@ -81,6 +84,25 @@ __device__ __forceinline__ void put_delta(unsigned c, const Mom32 &m, float2 dl,
     if (test) test[c] = make_float4(m.x, m.y, m.z, fmaf(dl.y, inv_theta, dl.x));
 }
 
+// FP64 terms of level-1 cell c for its root: with O the root cube's centre
+// (from a key inside the cell) and e = com - O, (m, m e, Q + m (3 e e^T -
+// |e|^2 I)); published by the arrival atomic on the root that follows.
+__device__ __forceinline__ void root_terms(unsigned c, const Mom32 &m, unsigned long long kb, int sysb,
+                                           const DevState *stc, double *shadow) {
+    float3 o;
+    cell_cube(kb, 0, sysb, stc, o);
+    const double M = m.M, ex = (double)m.x - o.x, ey = (double)m.y - o.y, ez = (double)m.z - o.z;
+    const double e2 = ex * ex + ey * ey + ez * ez;
+    double *t = shadow + 10 * (size_t)c;
+    t[0] = M; t[1] = M * ex; t[2] = M * ey; t[3] = M * ez;
+    t[4] = m.q[0] + M * (3 * ex * ex - e2);
+    t[5] = m.q[1] + M * (3 * ey * ey - e2);
+    t[6] = m.q[2] + M * (3 * ez * ez - e2);
+    t[7] = m.q[3] + M * (3 * ex * ey);
+    t[8] = m.q[4] + M * (3 * ex * ez);
+    t[9] = m.q[5] + M * (3 * ey * ez);
+}
+
 // REFIT (block time steps, between rebuilds): the bodies may have left the
 // cells they were sorted into.  Each cell also gets ext = half side of a cube
 // about its build-time centre that holds its bodies (at least l/2; a leaf
@@ -105,6 +127,8 @@ __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__res
     // central moments C = S - s c^T and Q = 3C - tr(C) I.  The offsets are
     // at most the cell size, so nothing cancels beyond FP32 rounding.
     unsigned b = link.x, cnt = link.y & ~LEAF_BIT;
+    int lev = cell_level[c];                         // level and parent, for the climb
+    unsigned p = lev != 0 ? cell_parent[c] : 0u;
     float4 x0 = pos4[b];
     float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
     float sxx = 0.f, syy = 0.f, szz = 0.f, sxy = 0.f, sxz = 0.f, syz = 0.f;
@@ -130,7 +154,6 @@ __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__res
     const float tr = Cxx + Cyy + Czz;
     m.q[0] = 3.f * Cxx - tr; m.q[1] = 3.f * Cyy - tr; m.q[2] = 3.f * Czz - tr;
     m.q[3] = 3.f * fmaf(-sx, cy, sxy); m.q[4] = 3.f * fmaf(-sx, cz, sxz); m.q[5] = 3.f * fmaf(-sy, cz, syz);
-    int lev = cell_level[c];
     store32(c, m, mono, qa, qb);
     // The first body's key shares the key prefix of the leaf and of every
     // ancestor: it gives every geometric centre on the way up.
@@ -142,67 +165,45 @@ __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__res
     } else {
         put_delta(c, m, cell_delta(kb, lev, sysb, make_float3(m.x, m.y, m.z), stc), delta, test, inv_theta);
     }
-    if (lev < FP64_LEVELS) {
-        double *s = shadow + 10 * (size_t)c;
-        s[0] = m.M; s[1] = m.x; s[2] = m.y; s[3] = m.z;
-        for (int k = 0; k < 6; k++) s[4 + k] = m.q[k];
-    }
 
     // Up the tree while this thread is the last child to finish (roots are
-    // the level-0 cells, one per system).
+    // the level-0 cells, one per system).  The tree is read-only here: the
+    // parent's link and level and the next parent are loaded with the
+    // arrival atomic, so only the children's moments wait for its acquire.
     while (lev != 0) {
-        unsigned p = cell_parent[c];
-        unsigned nch = __ldcg(&cell_link[p].y);
+        const uint2 plk = cell_link[p];          // (first child, child count) of the parent
+        const int lv = cell_level[p];
+        const unsigned gp = lv != 0 ? cell_parent[p] : 0u;
+        if (lev == 1) root_terms(c, m, kb, sysb, stc, shadow);
         // Release: this cell's moments are visible to whoever reads the
         // counter after this add; acquire: the last child to arrive sees
         // every sibling's moments (each sibling's add heads a release
         // sequence that this read-modify-write extends).
-        if (atom_add_acq_rel_gpu(&cell_done[p], 1u) != nch - 1u) return;
+        if (atom_add_acq_rel_gpu(&cell_done[p], 1u) != plk.y - 1u) return;
         c = p;
-        unsigned cb = __ldcg(&cell_link[c].x);
-        const int lv = cell_level[c];
+        p = gp;
+        const unsigned cb = plk.x, nch = plk.y;
         lev = lv;
-        if (lv < FP64_LEVELS) {
-            double dM = 0, c0x = 0, c0y = 0, c0z = 0, ax = 0, ay = 0, az = 0;
-            double ch[8][10];
+        if (lv == 0) {
+            float3 o;
+            cell_cube(kb, 0, sysb, stc, o);
+            double t[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
             for (unsigned k = 0; k < nch; k++) {
-                unsigned cc = cb + k;
-                if (lv + 1 < FP64_LEVELS) {
-                    for (int i = 0; i < 10; i++) ch[k][i] = __ldcg(shadow + 10 * (size_t)cc + i);
-                } else {
-                    float4 mo = __ldcg(mono + cc), a = __ldcg(qa + cc);
-                    float2 q2 = __ldcg(qb + cc);
-                    ch[k][0] = mo.w; ch[k][1] = mo.x; ch[k][2] = mo.y; ch[k][3] = mo.z;
-                    ch[k][4] = -a.x; ch[k][5] = -a.y; ch[k][6] = -a.z; ch[k][7] = -a.w;
-                    ch[k][8] = -q2.x; ch[k][9] = -q2.y;
-                }
+                const double *sk2 = shadow + 10 * (size_t)(cb + k);
+#pragma unroll
+                for (int i = 0; i < 10; i++) t[i] += __ldcg(sk2 + i);
             }
-            c0x = ch[0][1]; c0y = ch[0][2]; c0z = ch[0][3];
-            for (unsigned k = 0; k < nch; k++) {
-                dM += ch[k][0];
-                ax += ch[k][0] * (ch[k][1] - c0x);
-                ay += ch[k][0] * (ch[k][2] - c0y);
-                az += ch[k][0] * (ch[k][3] - c0z);
-            }
-            double inv2 = dM > 0 ? 1.0 / dM : 0.0;
-            double cx = c0x + ax * inv2, cy = c0y + ay * inv2, cz = c0z + az * inv2;
-            double q[6] = {0, 0, 0, 0, 0, 0};
-            for (unsigned k = 0; k < nch; k++) {
-                double mk = ch[k][0];
-                double dx = ch[k][1] - cx, dy = ch[k][2] - cy, dz = ch[k][3] - cz;
-                double d2 = dx * dx + dy * dy + dz * dz;
-                q[0] += ch[k][4] + mk * (3 * dx * dx - d2);
-                q[1] += ch[k][5] + mk * (3 * dy * dy - d2);
-                q[2] += ch[k][6] + mk * (3 * dz * dz - d2);
-                q[3] += ch[k][7] + mk * (3 * dx * dy);
-                q[4] += ch[k][8] + mk * (3 * dx * dz);
-                q[5] += ch[k][9] + mk * (3 * dy * dz);
-            }
-            double *s = shadow + 10 * (size_t)c;
-            s[0] = dM; s[1] = cx; s[2] = cy; s[3] = cz;
-            for (int i = 0; i < 6; i++) s[4 + i] = q[i];
-            m.M = (float)dM; m.x = (float)cx; m.y = (float)cy; m.z = (float)cz;
-            for (int i = 0; i < 6; i++) m.q[i] = (float)q[i];
+            const double inv2 = t[0] > 0 ? 1.0 / t[0] : 0.0;
+            const double sx = t[1] * inv2, sy = t[2] * inv2, sz = t[3] * inv2;   // com - O
+            const double s2 = sx * sx + sy * sy + sz * sz;
+            m.M = (float)t[0];
+            m.x = (float)(o.x + sx); m.y = (float)(o.y + sy); m.z = (float)(o.z + sz);
+            m.q[0] = (float)(t[4] - t[0] * (3 * sx * sx - s2));
+            m.q[1] = (float)(t[5] - t[0] * (3 * sy * sy - s2));
+            m.q[2] = (float)(t[6] - t[0] * (3 * sz * sz - s2));
+            m.q[3] = (float)(t[7] - t[0] * (3 * sx * sy));
+            m.q[4] = (float)(t[8] - t[0] * (3 * sx * sz));
+            m.q[5] = (float)(t[9] - t[0] * (3 * sy * sz));
         } else {
             // Children's moments loaded together (at most 8, unrolled): one
             // round trip to L2 per level instead of one per child.
@@ -268,8 +269,12 @@ k_multipoles(const DevState *__restrict__ stc, DevState *st, const uint2 *__rest
              const float4 *__restrict__ pos4, const unsigned long long *__restrict__ sk,
              const uint8_t *__restrict__ sysid, float4 *mono, float4 *qa, float2 *qb, float2 *delta,
              double *shadow, float4 *cext, float4 *test, float inv_theta) {
-    const unsigned c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= stc->ncells || (stc->status & ST_TIMEOUT)) return;
+    // Cells are numbered breadth first, so the deepest leaves, whose climbs
+    // to the root are the longest, have the largest numbers: blocks take
+    // the cells from the end so that those climbs start in the first wave.
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x, nc = stc->ncells;
+    if (i >= nc || (stc->status & ST_TIMEOUT)) return;
+    const unsigned c = nc - 1u - i;
     multipole_cell<REFIT>(c, stc, st, cell_body, cell_link, cell_level, cell_parent, cell_done, pos4, sk, sysid, mono,
                           qa, qb, delta, shadow, cext, test, inv_theta);
 }
