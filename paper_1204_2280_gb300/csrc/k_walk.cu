@@ -687,8 +687,11 @@ cudaError_t launch_walk(Ctx &c, float eps, bool features, const unsigned *gate) 
     if (second == 0) return one(1, c.stream);
     cudaError_t e = cudaEventRecord(c.ev_fork, c.stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c.side, c.ev_fork, 0);
-    if (e == cudaSuccess) e = one(second, c.side);
+    // One body per lane first: each persistent launch fills the registers,
+    // so the second starts as the first one's warps leave, and the first
+    // one's tail (its last groups, ~0.1 ms each) overlaps the second's work.
     if (e == cudaSuccess) e = one(1, c.stream);
+    if (e == cudaSuccess) e = one(second, c.side);
     if (e == cudaSuccess) e = cudaEventRecord(c.ev_join, c.side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c.stream, c.ev_join, 0);
     return e;
