@@ -61,7 +61,11 @@ typedef struct {
                              1 = those groups with consecutive siblings (same
                              parent cell) packed greedily, in key order, up
                              to ncrit bodies per group                        */
-    int reserved[2];
+    int arena_limit_mib;  /* 0: none; else bonsai_set_bodies refuses, with
+                             BONSAI_ERR_OOM, a device arena larger than this
+                             many MiB (a host-side cap that stands in for an
+                             out-of-memory device)                           */
+    int reserved;
     long long max_spin;   /* bound on every device-side wait, polls (1<<24)   */
 } bonsai_config;
 

@@ -53,7 +53,7 @@ class BonsaiError(RuntimeError):
 class Config(C.Structure):
     _fields_ = [("nleaf", C.c_int), ("ncrit", C.c_int), ("walk_warps", C.c_int),
                 ("list_capacity", C.c_int), ("use_graph", C.c_int), ("group_pack", C.c_int),
-                ("reserved", C.c_int * 2),
+                ("arena_limit_mib", C.c_int), ("reserved", C.c_int),
                 ("max_spin", C.c_longlong)]
 
 

@@ -84,6 +84,7 @@ cudaError_t alloc_bodies(Ctx &c, long long n) {
     a.take(c.judge_targets, JUDGE_MAX, plan); a.take(c.judge_direct, JUDGE_MAX, plan);
     a.take(c.judge_partial, (size_t)JUDGE_SPLIT * JUDGE_MAX, plan);
     char *base = nullptr;
+    if (c.arena_limit > 0 && (long long)a.off > c.arena_limit) return cudaErrorMemoryAllocation;
     cudaError_t e = cudaMalloc(&base, a.off);
     if (e != cudaSuccess) return e;
     for (auto &p : plan) *p.first = base + p.second;
@@ -163,13 +164,14 @@ int bonsai_create(bonsai_ctx **out, const bonsai_config *cfg, void *cuda_stream)
         if (cfg->max_spin) c.max_spin = cfg->max_spin;
         if (cfg->use_graph < 0) c.use_graph = 0;
         c.group_pack = cfg->group_pack;
+        c.arena_limit = cfg->arena_limit_mib > 0 ? (long long)cfg->arena_limit_mib << 20 : cfg->arena_limit_mib;
     }
     if (c.nleaf < 1 || c.nleaf > 64 || c.ncrit < 1 || c.ncrit > 64 || c.list_capacity < 64 ||
         c.list_capacity > 8192 || c.max_spin < 1 || c.walk_warps < 1 || c.walk_warps > 8 ||
-        c.group_pack < 0 || c.group_pack > 1) {
+        c.group_pack < 0 || c.group_pack > 1 || c.arena_limit < 0) {
         int r = fail(nullptr, BONSAI_ERR_INVALID_ARG,
                      "bonsai_create: need 1<=nleaf<=64, 1<=ncrit<=64, 64<=list_capacity<=8192, "
-                     "1<=walk_warps<=8, group_pack 0 or 1");
+                     "1<=walk_warps<=8, group_pack 0 or 1, arena_limit_mib >= 0");
         delete ctx;
         return r;
     }
@@ -218,7 +220,17 @@ int bonsai_set_bodies(bonsai_ctx *ctx, const float *pos, const float *mass, cons
     Ctx &c = ctx->c;
     if (!pos || !mass || n < 1 || n > (1ll << 26))
         return fail(ctx, BONSAI_ERR_INVALID_ARG, "bonsai_set_bodies: need pos, mass and 1 <= n <= 2^26");
-    if (n > c.ncap) CK(alloc_bodies(c, n));
+    if (n > c.ncap) {
+        const cudaError_t e = alloc_bodies(c, n);
+        if (e != cudaSuccess) {
+            // the old arena is gone: the context holds no bodies now
+            c.n = 0;
+            c.have_bodies = c.built = c.moments_ready = c.have_acc = c.tree_fresh = c.timed_step = false;
+            c.graph_n = -1;
+            return fail(ctx, e == cudaErrorMemoryAllocation ? BONSAI_ERR_OOM : BONSAI_ERR_CUDA,
+                        "bonsai_set_bodies: device arena", e);
+        }
+    }
     if (c.step_graph) { cudaGraphExecDestroy(c.step_graph); c.step_graph = nullptr; }
     c.graph_n = -1;
     c.n = n;
@@ -476,6 +488,7 @@ int bonsai_get_config(const bonsai_ctx *ctx, bonsai_config *out) {
     out->list_capacity = c.list_capacity;
     out->use_graph = c.use_graph ? 1 : -1;
     out->group_pack = c.group_pack;
+    out->arena_limit_mib = (int)(c.arena_limit >> 20);
     out->max_spin = c.max_spin;
     return BONSAI_OK;
 }

@@ -129,6 +129,7 @@ struct Ctx {
 
     // pipeline state
     bool have_bodies = false, built = false, moments_ready = false, have_acc = false;
+    long long arena_limit = 0;       // bytes; 0: no cap on the body arena
     bool tree_fresh = false;         // the tree was built from the current positions (no refit since)
     float theta = 0.75f, eps = 0.01f;
     cudaGraphExec_t step_graph = nullptr;

@@ -48,6 +48,27 @@ def test_invalid_arguments_rejected_without_gpu(libpath):
     assert b"ncrit" in L.bonsai_last_error(None)
     assert L.bonsai_build(None) == -1
     assert B.bonsai_version().startswith("bonsai-gb300")
+    neg = B.Config(arena_limit_mib=-1)
+    assert L.bonsai_create(C.byref(ctx), C.byref(neg), None) == -1
+    assert b"arena_limit_mib" in L.bonsai_last_error(None)
+
+
+def test_config_layout_matches_header(tmp_path):
+    """The binding's bonsai_config has the C struct's size and field offsets
+    (a probe compiled against include/bonsai.h by the host compiler)."""
+    import paper_1204_2280_gb300 as B
+    fields = [f[0] for f in B.Config._fields_]
+    probe = tmp_path / "probe.c"
+    probe.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "bonsai.h"\nint main(void) {\n'
+        '  printf("%zu\\n", sizeof(bonsai_config));\n'
+        + "".join(f'  printf("%zu\\n", offsetof(bonsai_config, {f}));\n' for f in fields)
+        + "  return 0;\n}\n")
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(probe), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got[0] == C.sizeof(B.Config)
+    assert got[1:] == [getattr(B.Config, f).offset for f in fields]
 
 
 def test_create_without_gpu_fails_cleanly(libpath):

@@ -287,6 +287,32 @@ def test_stage_timing_switch():
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
 
 
+def test_arena_cap_reports_oom_and_recovers():
+    """A context whose device arena is capped (a host-side stand-in for an
+    out-of-memory device) refuses a body set that needs more with
+    BONSAI_ERR_OOM, then holds no bodies (later stages: NOT_READY, nothing
+    reads the freed arena), and takes a body set that fits."""
+    big = W.plummer(1 << 20, 7)
+    with B.Bonsai(B.Config(arena_limit_mib=64)) as bz:
+        assert B.bonsai_get_config(bz.ctx).arena_limit_mib == 64
+        with pytest.raises(B.BonsaiError) as ei:
+            bz.set_bodies(big.pos, big.mass, big.vel)
+        assert ei.value.code == -2
+        with pytest.raises(B.BonsaiError) as ei:
+            bz.build()
+        assert ei.value.code == -7
+        small = W.plummer(4096, 8)
+        bz.set_bodies(small.pos, small.mass, small.vel).build().multipoles()
+        acc = np.zeros((4096, 3), np.float32)
+        pot = np.zeros(4096, np.float32)
+        bz.forces(0.75, 0.01, acc, pot)
+        bz.step(1.0 / 128)
+        bz.sync()
+    tf = oracle.tree_forces(small.pos, small.mass, 0.75, 0.01, 16, 64, TAU_ABS, TAU_REL)
+    ok = ~tf.borderline
+    assert rel_err(acc, tf.acc)[ok].max() <= 1e-5
+
+
 def test_capacity_overflow_reports_error_and_recovers():
     b = W.plummer(20000, 1)
     with B.Bonsai(B.Config(list_capacity=64)) as bz:
