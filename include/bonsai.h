@@ -276,7 +276,7 @@ int bonsai_get_counts(bonsai_ctx *ctx, uint32_t *n_pc, uint32_t *n_pp,
 int bonsai_sort_keys_static(const uint64_t *keys, uint64_t *sorted_keys,
                             uint32_t *perm, long long n, void *cuda_stream);
 
-/* ---- learned far-field correction (spec extension of Sect. 2) ----
+/* ---- learned far-field correction (an extension of the Sect. 2 walk) -----
  * A per-body MLP 12 -> 64 -> 64 -> 3 (ReLU; BF16 weights, inputs and hidden
  * activations, FP32 accumulation; inference on the tensor cores) predicts
  * the residual r = (a_direct - a_tree) / |a_tree| of the coarse-theta walk
