@@ -79,3 +79,14 @@ def test_create_without_gpu_fails_cleanly(libpath):
     ctx = C.c_void_p()
     rc = B.lib().bonsai_create(C.byref(ctx), None, None)
     assert rc == -3 and not ctx.value
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without the built library every entry point raises."""
+    import paper_1204_2280_gb300 as B
+    monkeypatch.setattr(B, "LIB_PATH", str(tmp_path / "libbonsai.so"))
+    monkeypatch.setattr(B, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        B.lib()
+    with pytest.raises(RuntimeError):
+        B.Bonsai(B.Config())
