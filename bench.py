@@ -58,9 +58,7 @@ WALK_TRAFFIC = {(1 << 20, 32, 1): 68.77e6}
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=None,
-                   help="timed steps (default 500: about a second of timed work, so that the "
-                        "200-ms clock samples fall under load; the reference arm's oracle steps: 10)")
+    p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=1 << 20)
@@ -89,10 +87,7 @@ def parse():
                    help="per-stage scaling sweep instead of the bench line: one JSON line per (N, theta)")
     p.add_argument("--sweep-cpu", type=float, default=0.0,
                    help="with --sweep: also time the FP64 oracle per stage at theta = 0.75 (seconds of walk sample)")
-    a = p.parse_args()
-    if a.steps is None:
-        a.steps = 10 if a.impl == "reference" else 500
-    return a
+    return p.parse_args()
 
 
 def config(a, world):
