@@ -409,11 +409,14 @@ class _BlockTree:
 
 
 def block_cycle(pos, vel, mass, acc, dt_max: float, kmax: int, eta: float, theta: float, eps: float,
-                nleaf: int = 16, ncrit: int = 32, pack: bool = False, rebuild_every: int = 1):
+                nleaf: int = 16, ncrit: int = 32, pack: bool = False, rebuild_every: int = 1,
+                clock: bool = False):
     """One cycle of block time steps from a synchronised state (acc: the
     acceleration at pos).  State in float64; the tree and forces see the
     positions rounded to float32 (the stored state is float32).  Returns
-    (pos, vel, acc, pot, levels at the start, active bodies per substep)."""
+    (pos, vel, acc, pot, levels at the start, active bodies per substep),
+    with clock=True also each body's time advanced by the steps it completed
+    (dt_max for every body when the cycle ends synchronised)."""
     mass = np.asarray(mass, np.float32)
     x = np.array(pos, np.float64)
     v = np.array(vel, np.float64)
@@ -428,6 +431,7 @@ def block_cycle(pos, vel, mass, acc, dt_max: float, kmax: int, eta: float, theta
     v += a * h[:, None]
     bt = None
     nactive = []
+    t_done = np.zeros(x.shape[0])
     for s in range(1, nsub + 1):
         x += v * dtm
         x32 = x.astype(np.float32)
@@ -440,11 +444,14 @@ def block_cycle(pos, vel, mass, acc, dt_max: float, kmax: int, eta: float, theta
         pot[act] = pn[act]
         h = (1 << (kmax - lev)) * dtm / 2
         v[act] += a[act] * h[act][:, None]
+        t_done[act] += 2 * h[act]
         if s < nsub:
             new = np.maximum(block_level(a, c32, kmax), kmax - _ctz(s))
             lev[act] = new[act]
             h = (1 << (kmax - lev)) * dtm / 2
             v[act] += a[act] * h[act][:, None]
+    if clock:
+        return x, v, a, pot, lev0, nactive, t_done
     return x, v, a, pot, lev0, nactive
 
 

@@ -158,3 +158,17 @@ def test_refit_streams_stay_accurate(orc):
     da, _ = orc.direct(x.astype(np.float32), b.mass, 0.01)
     e = np.linalg.norm(a - da, axis=1) / np.linalg.norm(da, axis=1)
     assert np.median(e) <= 1e-3 and np.percentile(e, 99) <= 1e-2
+
+
+def test_every_body_ends_the_cycle_synchronised(orc):
+    """With levels 0..3 in use, the steps each body completes in one cycle
+    add up to dt_max exactly, and a body walked at substep s had a step
+    ending there (s a multiple of its step length in substeps)."""
+    b, a0 = start(orc, 3000, 27, 0.75, 0.01)
+    dt, kmax = 1.0 / 16, 3
+    out = orc.block_cycle(b.pos, b.vel, b.mass, a0, dt, kmax, 0.2, 0.75, 0.01, clock=True)
+    lev0, nact, t_done = out[4], out[5], out[6]
+    assert set(np.unique(lev0).tolist()) >= {0, 1, 2, 3}
+    assert np.all(t_done == dt)
+    # every body is active at the last substep; some substeps walk a subset only
+    assert nact[-1] == 3000 and min(nact) < 3000
