@@ -10,9 +10,11 @@ Prints one JSON line (rank 0).  `value` = bodies advanced per second over all
 ranks (device time of the timed steps, CUDA events on the library's stream);
 `e2e` = the same through the C ABI with host buffers (pinned H2D of the
 bodies, full tree step, D2H of accelerations and potentials); `roofline` =
-the walk kernel's algorithmic FP32 rate against the FP32 peak of 152 SMs x
-128 lanes x 2 flop x 2070 MHz; `cpu_baseline` = the FP64 oracle tree-code on
-a bounded sample of the same workload on the host cores.
+the walk kernel's algorithmic FP32 rate against the FP32 peak measured in
+the same run by the library's FMA-chain microbenchmark (bonsai_bench_fma,
+cross-checked against the device's SM count x 128 lanes x 2 flop x the SM
+clock sampled under it); `cpu_baseline` = the FP64 oracle tree-code on a
+bounded sample of the same workload on the host cores.
 
 The line also carries the batched ensemble (64 spheres, one pipeline per
 step; sharded over the ranks under torchrun) and the plain-vs-learned
@@ -41,8 +43,47 @@ sys.path.insert(0, ROOT)
 METRIC = "particles/s per full tree step at equal 99th-pct force error, plain vs learned"
 UNIT = "particles/s"
 FLOP_PC, FLOP_PP = 65, 23           # flops per body-cell / body-body interaction
-SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
-FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+FP32_LANES = 128                    # FP32 lanes per SM (Blackwell)
+_FP32_PEAK = None
+
+
+def fp32_peak(local_rank: int = 0) -> dict:
+    """The FP32 peak of this GPU, measured once per process: the library's
+    FMA-chain microbenchmark (eight packed FP32x2 chains per thread, 8 blocks
+    of 256 threads per SM, about half a second) with nvidia-smi clocks
+    sampled meanwhile, beside SMs x 128 lanes x 2 flop x clock for the SM
+    count the device reports and the sampled median (and the maximum) clock."""
+    global _FP32_PEAK
+    if _FP32_PEAK is not None:
+        return _FP32_PEAK
+    import torch
+    import paper_1204_2280_gb300 as B
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    blocks, threads = 8 * sms, 256
+    ms, fl = B.bonsai_bench_fma(blocks, threads, 20000)            # calibrate
+    iters = max(20000, int(20000 * 500.0 / max(ms, 1e-3)))
+    smp = ClockSampler(gpu_index(local_rank))
+    smp.start()
+    time.sleep(0.2)
+    ms, fl = B.bonsai_bench_fma(blocks, threads, iters)
+    clk = smp.stop()
+    meas = fl / (ms / 1e3) / 1e12
+    mhz = clk.get("sm_mhz")
+    mx = clk.get("sm_max_mhz") or 2070.0
+    _FP32_PEAK = {
+        "tflops": meas, "ms": ms, "sms": sms, "sm_mhz_median": mhz, "sm_max_mhz": mx,
+        "derived_at_median_clock": sms * FP32_LANES * 2 * mhz * 1e6 / 1e12 if mhz else None,
+        "derived_at_max_clock": sms * FP32_LANES * 2 * mx * 1e6 / 1e12,
+        "clock_reasons": clk.get("reasons"),
+        "how": f"bonsai_bench_fma: {blocks} blocks x {threads} threads x {iters} iterations x 8 chains of "
+               f"packed FP32x2 FMA ({fl:.3e} flop in {ms:.1f} ms, CUDA events)"}
+    return _FP32_PEAK
+
+
+def fp32_peak_tflops(local_rank: int = 0) -> float:
+    return fp32_peak(local_rank)["tflops"]
+
+
 def kernels_per_step(ncrit, group_pack=0):
     """reset, kick+drift+bbox, domains, keys, 8 sort passes, reorder, 4 build
     (+2 for sibling packing of the groups), multipoles (which also write the
@@ -400,7 +441,7 @@ def run_learned(a, dev, stream):
     jint = 4096 * n
     judge = {"ms": jt, "interactions": jint, "interactions_per_s": jint / (jt / 1e3),
              "tflops": FLOP_PP * jint / (jt / 1e3) / 1e12,
-             "fp32_frac": FLOP_PP * jint / (jt / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+             "fp32_frac": FLOP_PP * jint / (jt / 1e3) / 1e12 / fp32_peak_tflops(),
              "what": "bonsai_judge: direct sum of 4096 stratified bodies against all N (23 flop per "
                      "interaction) + p99, host copy of the p99 included"}
     target = err["plummer"]["theta_1.0_mlp"]
@@ -716,13 +757,13 @@ def run_sweep(a, dev, stream):
                 "stage_hbm_frac": {k: sb[k] / (stage[k] / 1e3) / 1e9 / hbm for k in sb if stage[k] > 0},
                 "sort_reorder_build_hbm_frac": sum(sb[k] for k in ("sort", "reorder", "build")) /
                     (sum(stage[k] for k in ("sort", "reorder", "build")) / 1e3) / 1e9 / hbm,
-                "walk_tflops": tflops, "walk_fp32_frac": tflops / FP32_PEAK_TFLOPS,
+                "walk_tflops": tflops, "walk_fp32_frac": tflops / fp32_peak_tflops(),
                 "interactions_per_body": {"pc": npc / (steps * n), "pp": npp / (steps * n)},
                 "interactions_per_s": (npc + npp) / steps / walk_s,
                 "ncells": ncells, "ngroups": ngroups,
                 "p99_acc_err_t0": p99,
                 "energy_drift": (d1[2] - d0[2]) / abs(d0[2]),
-                "hbm_peak_gbs": hbm, "fp32_peak_tflops": FP32_PEAK_TFLOPS, "oracle": cpu}), flush=True)
+                "hbm_peak_gbs": hbm, "fp32_peak_tflops": fp32_peak_tflops(), "oracle": cpu}), flush=True)
 
 
 def measured_hbm_gbs():
@@ -809,6 +850,7 @@ def run_ours(a, rank, world, local_rank):
     stages = np.array(stage_ms).sum(0)
     walk_ms = float(stages[B.STAGES.index("walk")])
     achieved = sum(flops) / (walk_ms / 1e3) / 1e12
+    peak = fp32_peak(local_rank)
 
     # End to end through the C ABI with host buffers.
     e2e = None
@@ -848,9 +890,15 @@ def run_ours(a, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config(a, world),
             "roofline": {"bound": "alu", "kernel": "k_walk", "achieved": achieved,
-                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                         "peak": peak["tflops"], "unit": "TFLOP/s", "frac": achieved / peak["tflops"],
                          "traffic": WALK_TRAFFIC.get((a.n, a.ncrit, a.group_pack)),
-                         "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
+                         "peak_basis": {
+                             "measured": "FMA-chain microbenchmark in this run: " + peak["how"],
+                             "sms": peak["sms"], "sm_mhz_median": peak["sm_mhz_median"],
+                             "derived_at_median_clock": peak["derived_at_median_clock"],
+                             "derived_at_max_clock": peak["derived_at_max_clock"],
+                             "frac_of_derived_at_max_clock": achieved / peak["derived_at_max_clock"],
+                             "clock_reasons": peak["clock_reasons"]},
                          "flops_basis": f"{FLOP_PC} per body-cell + {FLOP_PP} per body-body interaction"},
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -258,23 +258,47 @@ int bonsai_get_counts(bonsai_ctx *ctx, uint32_t *n_pc, uint32_t *n_pp,
                       unsigned long long tot[2]);
 
 /* Stable sort of n 63-bit keys that allocates nothing.  No counterpart in
- * the paper: it exists for callers that cannot call cudaMalloc -- code being
- * captured into a CUDA graph (allocation is illegal there), latency-critical
- * loops (cudaMalloc/cudaFree may synchronise the device), or hosts whose own
- * allocator already owns the device memory.  keys (n, read only), sorted_keys
+ * the paper: it exists for callers that cannot call cudaMalloc -- latency-
+ * critical loops (cudaMalloc/cudaFree may synchronise the whole device), or
+ * hosts whose own caching allocator already owns the device memory (a second
+ * allocator would fail or fragment it).  keys (n, read only), sorted_keys
  * (n) and perm (n) are caller-owned DEVICE buffers on the current device;
  * sorted_keys[i] = keys[perm[i]], equal keys in input order.  All scratch is
  * one static device array (about 0.9 MiB, held by every GPU that loads the
  * library until exit), so n is limited to 65536 (larger n: INVALID_ARG).
- * The first call on a device looks up that array's device address and must
- * come before any stream capture.  Every call reuses the same scratch:
- * calls whose GPU work could overlap (other threads or streams) race and
- * must be serialised by the caller.  Work is ordered on cuda_stream (NULL:
- * the legacy default stream); the call synchronises that stream and returns
- * BONSAI_ERR_TIMEOUT if a bounded device-side wait gave up.  Error text:
- * bonsai_last_error(NULL). */
+ * The first call on a device looks up that array's device address and sets
+ * the sort kernel's shared-memory limit for that device.  Every call reuses
+ * the same scratch: calls whose GPU work could overlap (other threads or
+ * streams) race and must be serialised by the caller.  Work is ordered on
+ * cuda_stream (NULL: the legacy default stream); the call then reads a status
+ * word back and synchronises that stream, so it cannot run while the stream
+ * is being captured into a CUDA graph.  It returns BONSAI_ERR_TIMEOUT if a
+ * bounded device-side wait gave up.  Error text: bonsai_last_error(NULL). */
 int bonsai_sort_keys_static(const uint64_t *keys, uint64_t *sorted_keys,
                             uint32_t *perm, long long n, void *cuda_stream);
+
+/* ---- measurement and testing aids (no counterpart in the paper) --------- */
+
+/* FP32 peak microbenchmark for the walk's roofline: `blocks` blocks of
+ * `threads` threads on the current device each run `iters` iterations of
+ * eight independent chains of packed FP32x2 fused multiply-adds (the
+ * instruction the walk's interaction tiles are made of), timed with CUDA
+ * events on the legacy default stream.  *ms receives the kernel time and
+ * *flop the floating-point operations it performed (blocks x threads x iters
+ * x 8 chains x 2 lanes x 2), so the achieved rate is flop / ms.  Synchronises.
+ * 1 <= blocks <= 65535, 32 <= threads <= 1024 (a multiple of 32), iters >= 1. */
+int bonsai_bench_fma(int blocks, int threads, long long iters, float *ms, double *flop);
+
+/* Testing aid for the bounded device-side waits: while tile >= 0, sort tile
+ * `tile` (4096 keys) of every radix-sort pass of this context publishes no
+ * count, so the look-back of the tile after it polls max_spin times, gives
+ * up and sets the device's timeout status: bonsai_sync then returns
+ * BONSAI_ERR_TIMEOUT and the stages after the sort skip their work.  The
+ * keys are not sorted then and the bodies, reordered by an invalid
+ * permutation, are lost: load them again with bonsai_set_bodies.  Nothing
+ * faults (every position written stays inside the sort's buffers).  tile =
+ * -1 (the default) turns it off. */
+int bonsai_debug_hold_sort_tile(bonsai_ctx *ctx, int tile);
 
 /* ---- learned far-field correction (an extension of the Sect. 2 walk) -----
  * A per-body MLP 12 -> 64 -> 64 -> 3 (ReLU; BF16 weights, inputs and hidden
@@ -360,8 +384,8 @@ int bonsai_forces_learned(bonsai_ctx *ctx, float eps, float *acc, float *pot, in
 int bonsai_get_judge(bonsai_ctx *ctx, float *p99, int *fell_back);
 
 /* Text of the last error of ctx (or, for ctx == NULL, of the last failed
- * bonsai_create or bonsai_sort_keys_static of this thread).  Valid until the
- * next call on the context. */
+ * bonsai_create, bonsai_sort_keys_static or bonsai_bench_fma of this
+ * thread).  Valid until the next call on the context. */
 const char *bonsai_last_error(const bonsai_ctx *ctx);
 
 /* Library version string. */

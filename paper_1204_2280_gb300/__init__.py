@@ -35,7 +35,8 @@ EXPORTS = ["bonsai_create", "bonsai_destroy", "bonsai_set_bodies", "bonsai_build
            "bonsai_mlp_fit_norm", "bonsai_mlp_predict", "bonsai_mlp_grad", "bonsai_mlp_train",
            "bonsai_learn_samples", "bonsai_judge", "bonsai_set_learned", "bonsai_forces_learned",
            "bonsai_get_judge", "bonsai_set_judge_interval", "bonsai_get_config", "bonsai_block_cycle",
-           "bonsai_block_levels", "bonsai_block_stats", "bonsai_sph_density"]
+           "bonsai_block_levels", "bonsai_block_stats", "bonsai_sph_density", "bonsai_bench_fma",
+           "bonsai_debug_hold_sort_tile"]
 
 MLP_IN, MLP_H, MLP_OUT = 12, 64, 3
 MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_OUT * MLP_H + MLP_OUT
@@ -103,6 +104,8 @@ def lib():
         L.bonsai_block_levels.argtypes = [p, f, i, f, p]
         L.bonsai_block_stats.argtypes = [p, p]
         L.bonsai_sph_density.argtypes = [p, p, p, p, i]
+        L.bonsai_bench_fma.argtypes = [i, i, ll, p, p]
+        L.bonsai_debug_hold_sort_tile.argtypes = [p, i]
         u64 = C.c_ulonglong
         L.bonsai_mlp_create.argtypes = [C.POINTER(p), u64]
         L.bonsai_mlp_destroy.argtypes = [p]
@@ -334,13 +337,51 @@ def bonsai_get_stage_times(ctx) -> np.ndarray:
 
 
 def bonsai_sort_keys_static(keys, sorted_keys, perm, stream=None):
-    """Sort n <= 65536 device keys without any device allocation (see the
-    C header); keys/sorted_keys: int64 CUDA tensors holding the 63-bit keys,
-    perm: int32 CUDA tensor."""
+    """Sort n <= 65536 device keys without any device allocation (see the C
+    header).  keys, sorted_keys: contiguous int64 CUDA tensors holding the
+    63-bit keys; perm: contiguous int32 CUDA tensor; all on one device, with
+    at least n = keys.shape[0] elements each (the C side cannot check sizes or
+    devices, so they are checked here before anything runs).  stream: a
+    torch.cuda.Stream or raw cudaStream_t handle; None means torch's current
+    stream on the keys' device."""
+    import torch
     n = int(keys.shape[0])
-    s = None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
-    _check(None, lib().bonsai_sort_keys_static(keys.data_ptr(), sorted_keys.data_ptr(),
-                                               perm.data_ptr(), n, s))
+    args = (("keys", keys, torch.int64), ("sorted_keys", sorted_keys, torch.int64), ("perm", perm, torch.int32))
+    for name, t, dt in args:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"bonsai_sort_keys_static: {name} must be a torch tensor")
+        if t.dtype != dt:
+            raise TypeError(f"bonsai_sort_keys_static: {name} must be {dt}, not {t.dtype}")
+    for name, t, _ in args:
+        if t.numel() < n:
+            raise ValueError(f"bonsai_sort_keys_static: {name} holds {t.numel()} elements, needs {n}")
+        if not t.is_contiguous():
+            raise ValueError(f"bonsai_sort_keys_static: {name} must be contiguous")
+    for name, t, _ in args:
+        if not t.is_cuda:
+            raise ValueError(f"bonsai_sort_keys_static: {name} must be a CUDA tensor")
+    if not (keys.device == sorted_keys.device == perm.device):
+        raise ValueError("bonsai_sort_keys_static: keys, sorted_keys and perm must share one device")
+    with torch.cuda.device(keys.device):
+        if stream is None:
+            h = torch.cuda.current_stream(keys.device).cuda_stream
+        else:
+            h = int(getattr(stream, "cuda_stream", stream))
+        _check(None, lib().bonsai_sort_keys_static(keys.data_ptr(), sorted_keys.data_ptr(),
+                                                   perm.data_ptr(), n, C.c_void_p(h) if h else None))
+
+
+def bonsai_bench_fma(blocks: int, threads: int, iters: int) -> tuple[float, float]:
+    """FP32 FMA-chain microbenchmark on the current device: (ms, flop)."""
+    ms = C.c_float()
+    fl = C.c_double()
+    _check(None, lib().bonsai_bench_fma(int(blocks), int(threads), int(iters), C.byref(ms), C.byref(fl)))
+    return float(ms.value), float(fl.value)
+
+
+def bonsai_debug_hold_sort_tile(ctx, tile: int) -> None:
+    """Testing aid: sort tile `tile` publishes nothing (-1: off); see the header."""
+    _check(ctx, lib().bonsai_debug_hold_sort_tile(ctx, int(tile)))
 
 
 def bonsai_version() -> str:

@@ -583,22 +583,27 @@ int bonsai_get_keys(bonsai_ctx *ctx, uint64_t *keys, uint32_t *perm) {
     return BONSAI_OK;
 }
 
+// The introspection getters stream the cells through the context's staging
+// area (7 floats per body) in chunks: no allocation per call.
 int bonsai_get_tree(bonsai_ctx *ctx, int32_t *bb, int32_t *bc, int32_t *cb, int32_t *nc, int32_t *lv) {
     if (!ctx || !bb || !bc || !cb || !nc || !lv) return BONSAI_ERR_INVALID_ARG;
     Ctx &c = ctx->c;
     if (!c.built) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_get_tree: not built");
     int r = read_state(ctx);
     if (r) return r;
-    size_t nc_ = c.st_host->ncells;
-    int32_t *tmp = nullptr;
-    CK(cudaMalloc(&tmp, 5 * c.ccap * sizeof(int32_t)));
-    cudaError_t e = launch_tree_export(c, tmp, tmp + c.ccap, tmp + 2 * c.ccap, tmp + 3 * c.ccap, tmp + 4 * c.ccap);
+    const unsigned ncells = c.st_host->ncells;
+    const unsigned chunk = (unsigned)((7 * c.n) / 5);
+    int32_t *tmp = reinterpret_cast<int32_t *>(c.stage);
     int32_t *dst[5] = {bb, bc, cb, nc, lv};
-    for (int k = 0; k < 5 && e == cudaSuccess; k++)
-        e = cudaMemcpyAsync(dst[k], tmp + k * c.ccap, nc_ * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
-    cudaFree(tmp);
-    if (e != cudaSuccess) return fail(ctx, BONSAI_ERR_CUDA, "bonsai_get_tree", e);
+    for (unsigned c0 = 0; c0 < ncells; c0 += chunk) {
+        const unsigned cnt = ncells - c0 < chunk ? ncells - c0 : chunk;
+        CK(launch_tree_export(c, c0, cnt, tmp, tmp + cnt, tmp + 2 * (size_t)cnt, tmp + 3 * (size_t)cnt,
+                              tmp + 4 * (size_t)cnt));
+        for (int k = 0; k < 5; k++)
+            CK(cudaMemcpyAsync(dst[k] + c0, tmp + (size_t)k * cnt, cnt * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                               c.stream));
+        CK(cudaStreamSynchronize(c.stream));   // the next chunk reuses the staging area
+    }
     return BONSAI_OK;
 }
 
@@ -621,15 +626,18 @@ int bonsai_get_moments(bonsai_ctx *ctx, float *mono, float *quad) {
     if (!c.moments_ready) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_get_moments: no moments");
     int r = read_state(ctx);
     if (r) return r;
-    size_t nc_ = c.st_host->ncells;
-    float *tmp = nullptr;
-    CK(cudaMalloc(&tmp, 10 * c.ccap * sizeof(float)));
-    cudaError_t e = launch_moments_export(c, tmp, tmp + 4 * c.ccap);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(mono, tmp, 4 * nc_ * sizeof(float), cudaMemcpyDeviceToHost, c.stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(quad, tmp + 4 * c.ccap, 6 * nc_ * sizeof(float), cudaMemcpyDeviceToHost, c.stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
-    cudaFree(tmp);
-    if (e != cudaSuccess) return fail(ctx, BONSAI_ERR_CUDA, "bonsai_get_moments", e);
+    const unsigned ncells = c.st_host->ncells;
+    const unsigned chunk = (unsigned)((7 * c.n) / 10);
+    float *tmp = c.stage;
+    for (unsigned c0 = 0; c0 < ncells; c0 += chunk) {
+        const unsigned cnt = ncells - c0 < chunk ? ncells - c0 : chunk;
+        CK(launch_moments_export(c, c0, cnt, tmp, tmp + 4 * (size_t)cnt));
+        CK(cudaMemcpyAsync(mono + 4 * (size_t)c0, tmp, 4 * (size_t)cnt * sizeof(float), cudaMemcpyDeviceToHost,
+                           c.stream));
+        CK(cudaMemcpyAsync(quad + 6 * (size_t)c0, tmp + 4 * (size_t)cnt, 6 * (size_t)cnt * sizeof(float),
+                           cudaMemcpyDeviceToHost, c.stream));
+        CK(cudaStreamSynchronize(c.stream));
+    }
     return BONSAI_OK;
 }
 
@@ -646,6 +654,40 @@ int bonsai_get_counts(bonsai_ctx *ctx, uint32_t *n_pc, uint32_t *n_pp, unsigned 
     int r = read_state(ctx);
     if (r) return r;
     if (tot) { tot[0] = c.st_host->inter[0]; tot[1] = c.st_host->inter[1]; }
+    return BONSAI_OK;
+}
+
+int bonsai_debug_hold_sort_tile(bonsai_ctx *ctx, int tile) {
+    if (!ctx) return BONSAI_ERR_INVALID_ARG;
+    Ctx &c = ctx->c;
+    if (tile < -1) return fail(ctx, BONSAI_ERR_INVALID_ARG, "bonsai_debug_hold_sort_tile: need tile >= -1");
+    const unsigned v = (unsigned)(tile + 1);
+    CK(cudaMemcpyAsync(&c.st->hold_tile, &v, sizeof(unsigned), cudaMemcpyHostToDevice, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    return BONSAI_OK;
+}
+
+int bonsai_bench_fma(int blocks, int threads, long long iters, float *ms, double *flop) {
+    if (blocks < 1 || blocks > 65535 || threads < 32 || threads > 1024 || (threads & 31) || iters < 1 || !ms ||
+        !flop)
+        return fail(nullptr, BONSAI_ERR_INVALID_ARG,
+                    "bonsai_bench_fma: need 1 <= blocks <= 65535, threads a multiple of 32 in [32, 1024], iters >= 1");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float *sink = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMalloc(&sink, sizeof(float));
+    if (e == cudaSuccess) e = launch_fma_peak(blocks, threads, 1, sink);       // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, 0);
+    if (e == cudaSuccess) e = launch_fma_peak(blocks, threads, iters, sink);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    if (sink) cudaFree(sink);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail(nullptr, BONSAI_ERR_CUDA, "bonsai_bench_fma", e);
+    *flop = (double)blocks * threads * (double)iters * 8.0 * 2.0 * 2.0;
     return BONSAI_OK;
 }
 

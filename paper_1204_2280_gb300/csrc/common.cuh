@@ -76,6 +76,7 @@ struct DevState {
     unsigned judge_on;                // 1: this evaluation is judged
     unsigned long long cyc_active;    // block steps, last cycle: body steps ended (forces taken)
     unsigned long long cyc_inter[2];  // block steps, last cycle: n_pc, n_pp summed over substeps
+    unsigned hold_tile;               // testing aid: sort tile hold_tile - 1 never publishes (0: off)
 };
 
 struct Ctx {
@@ -160,6 +161,23 @@ struct Ctx {
     std::string err;
 };
 
+// ---- per-device one-time kernel set-up --------------------------------------
+constexpr int MAX_DEVICES = 64;
+
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) applies to the current
+// device only, so each call site records, per device, the largest size it
+// has already allowed.  Called before any stream capture of the launch.
+inline cudaError_t allow_dyn_smem(const void *fn, size_t bytes, size_t (&done)[MAX_DEVICES]) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    if (bytes <= done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done[dev] = bytes;
+    return e;
+}
+
 // ---- device helpers ------------------------------------------------------
 
 // Monotone map float -> int (signed compare order == float order).
@@ -242,9 +260,11 @@ cudaError_t launch_scatter_forces(Ctx &c, float *acc, float *pot);
 cudaError_t launch_scatter_bodies(Ctx &c, float *pos, float *vel);
 cudaError_t launch_scatter_counts(Ctx &c, uint32_t *npc, uint32_t *npp);
 cudaError_t launch_diag(Ctx &c);
-cudaError_t launch_tree_export(Ctx &c, int32_t *bb, int32_t *bc, int32_t *cb, int32_t *nc, int32_t *lv);
-cudaError_t launch_moments_export(Ctx &c, float *mono, float *quad);
+cudaError_t launch_tree_export(Ctx &c, unsigned c0, unsigned cnt, int32_t *bb, int32_t *bc, int32_t *cb,
+                               int32_t *nc, int32_t *lv);
+cudaError_t launch_moments_export(Ctx &c, unsigned c0, unsigned cnt, float *mono, float *quad);
 
+cudaError_t launch_fma_peak(int blocks, int threads, long long iters, float *sink);
 cudaError_t launch_judge_targets(Ctx &c);
 cudaError_t launch_gated_walk_reset(Ctx &c);
 cudaError_t pipeline_learned_forces(Ctx &c, float eps);

@@ -103,40 +103,67 @@ cudaError_t launch_diag(Ctx &c) {
     return cudaGetLastError();
 }
 
-__global__ void k_tree_export(const DevState *__restrict__ st, const uint2 *__restrict__ body,
-                              const uint2 *__restrict__ link, const uint8_t *__restrict__ level,
+// Introspection exports of cells [c0, c0 + cnt) into compact buffers (the
+// getters stream them through the context's staging area in chunks).
+__global__ void k_tree_export(const uint2 *__restrict__ body, const uint2 *__restrict__ link,
+                              const uint8_t *__restrict__ level, unsigned c0, unsigned cnt,
                               int32_t *bb, int32_t *bc, int32_t *cb, int32_t *nc, int32_t *lv) {
-    unsigned c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= st->ncells) return;
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    const unsigned c = c0 + i;
     uint2 b = body[c], l = link[c];
     bool leaf = (l.y & LEAF_BIT) != 0u;
-    bb[c] = (int32_t)b.x; bc[c] = (int32_t)b.y;
-    cb[c] = leaf ? 0 : (int32_t)l.x;
-    nc[c] = leaf ? 0 : (int32_t)l.y;
-    lv[c] = level[c];
+    bb[i] = (int32_t)b.x; bc[i] = (int32_t)b.y;
+    cb[i] = leaf ? 0 : (int32_t)l.x;
+    nc[i] = leaf ? 0 : (int32_t)l.y;
+    lv[i] = level[c];
 }
 
-cudaError_t launch_tree_export(Ctx &c, int32_t *bb, int32_t *bc, int32_t *cb, int32_t *nc, int32_t *lv) {
-    unsigned grid = (unsigned)((c.ccap + 255) / 256);
-    k_tree_export<<<grid, 256, 0, c.stream>>>(c.st, c.cell_body, c.cell_link, c.cell_level, bb, bc, cb, nc, lv);
+cudaError_t launch_tree_export(Ctx &c, unsigned c0, unsigned cnt, int32_t *bb, int32_t *bc, int32_t *cb,
+                               int32_t *nc, int32_t *lv) {
+    if (cnt == 0) return cudaSuccess;
+    k_tree_export<<<(cnt + 255) / 256, 256, 0, c.stream>>>(c.cell_body, c.cell_link, c.cell_level, c0, cnt, bb, bc,
+                                                            cb, nc, lv);
     return cudaGetLastError();
 }
 
-__global__ void k_moments_export(const DevState *__restrict__ st, const float4 *__restrict__ mono,
-                                 const float4 *__restrict__ qa, const float2 *__restrict__ qb,
-                                 float *m, float *q) {
-    unsigned c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= st->ncells) return;
+__global__ void k_moments_export(const float4 *__restrict__ mono, const float4 *__restrict__ qa,
+                                 const float2 *__restrict__ qb, unsigned c0, unsigned cnt, float *m, float *q) {
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    const unsigned c = c0 + i;
     float4 a = mono[c], b = qa[c];
     float2 d = qb[c];
-    m[4 * (size_t)c] = a.x; m[4 * (size_t)c + 1] = a.y; m[4 * (size_t)c + 2] = a.z; m[4 * (size_t)c + 3] = a.w;
-    float *o = q + 6 * (size_t)c;
+    m[4 * (size_t)i] = a.x; m[4 * (size_t)i + 1] = a.y; m[4 * (size_t)i + 2] = a.z; m[4 * (size_t)i + 3] = a.w;
+    float *o = q + 6 * (size_t)i;
     o[0] = -b.x; o[1] = -b.y; o[2] = -b.z; o[3] = -b.w; o[4] = -d.x; o[5] = -d.y;   // stored as -Q
 }
 
-cudaError_t launch_moments_export(Ctx &c, float *mono, float *quad) {
-    unsigned grid = (unsigned)((c.ccap + 255) / 256);
-    k_moments_export<<<grid, 256, 0, c.stream>>>(c.st, c.mono, c.quadA, c.quadB, mono, quad);
+cudaError_t launch_moments_export(Ctx &c, unsigned c0, unsigned cnt, float *mono, float *quad) {
+    if (cnt == 0) return cudaSuccess;
+    k_moments_export<<<(cnt + 255) / 256, 256, 0, c.stream>>>(c.mono, c.quadA, c.quadB, c0, cnt, mono, quad);
+    return cudaGetLastError();
+}
+
+// FP32 peak microbenchmark: eight independent chains of packed FP32x2 fused
+// multiply-adds per thread (x <- x * a + b keeps every value bounded for
+// |a| < 1).  The result feeds one conditional store so the chains stay live.
+__global__ void k_fma_peak(long long iters, float2 a, float2 b, float *sink) {
+    float2 x[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) x[k] = make_float2(threadIdx.x * 1e-3f + k, blockIdx.x * 1e-3f - k);
+    for (long long i = 0; i < iters; i++) {
+#pragma unroll
+        for (int k = 0; k < 8; k++) x[k] = __ffma2_rn(x[k], a, b);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; k++) s += x[k].x + x[k].y;
+    if (s == 1234.5f) sink[0] = s;
+}
+
+cudaError_t launch_fma_peak(int blocks, int threads, long long iters, float *sink) {
+    k_fma_peak<<<blocks, threads>>>(iters, make_float2(0.999f, 0.998f), make_float2(1e-3f, 2e-3f), sink);
     return cudaGetLastError();
 }
 

@@ -147,10 +147,15 @@ k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restric
     unsigned dstart = block_excl_scan(tcount, s_warp);
     unsigned gbase = block_excl_scan(owner ? ghist[d] : 0u, s_warp);
     unsigned *my = status + (size_t)tile * 256 + d;
+    // Testing aid (bonsai_debug_hold_sort_tile): a held tile publishes
+    // nothing, so the look-back of the next tile runs into its bounded wait.
+    // The positions a tile writes after giving up stay inside the output
+    // (its prefix can only fall short of the true one).
+    const bool held = st->hold_tile == (unsigned)tile + 1u;
     if (owner) {
         s_dstart[d] = dstart;
         // publish the tile's count first: later tiles look back meanwhile
-        st_volatile(my, (tile == 0 ? FLAG_INC : FLAG_AGG) | tcount);
+        if (!held) st_volatile(my, (tile == 0 ? FLAG_INC : FLAG_AGG) | tcount);
     }
     __syncthreads();
 
@@ -194,7 +199,7 @@ k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restric
                 if (q == 0 && ++spins > max_spin) { atomicOr(&st->status, ST_TIMEOUT); break; }
                 j -= q;
             }
-            st_volatile(my, FLAG_INC | ((prefix + tcount) & VAL_MASK));
+            if (!held) st_volatile(my, FLAG_INC | ((prefix + tcount) & VAL_MASK));
         }
         s_goff[d] = gbase + prefix;
     }
@@ -217,13 +222,9 @@ extern const size_t SORT_DYN_SMEM_BYTES = SORT_DYN_SMEM;
 // alternate so that the result always lands in c.keys / c.vals (the key
 // kernel writes to c.keys_alt when there are 9 passes).
 cudaError_t launch_sort(Ctx &c) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)SORT_DYN_SMEM);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static size_t attr_done[MAX_DEVICES] = {};
+    cudaError_t ea = allow_dyn_smem((const void *)k_onesweep, SORT_DYN_SMEM, attr_done);
+    if (ea != cudaSuccess) return ea;
     const int n = (int)c.n;
     const int npass = SORT_PASSES + (c.nsys > 1 ? 1 : 0);
     const int start = npass & 1;

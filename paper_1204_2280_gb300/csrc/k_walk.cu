@@ -638,20 +638,21 @@ static cudaError_t launch_walk_t(Ctx &c, float eps, const unsigned *gate, bool t
     const unsigned polls = (unsigned)(c.max_spin < 0xffffffffll ? c.max_spin : 0xffffffffll);
     const int warps = c.walk_warps;
     const size_t smem = walk_smem_bytes(warps, c.list_capacity);
-    static size_t attr_smem = 0, occ_smem = 0;
-    static int occ_warps = 0, occ_per_sm = 0;
-    if (smem > attr_smem) {
-        cudaError_t e = cudaFuncSetAttribute(k_walk<BPL, FEAT, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_smem = smem;
-    }
-    if (occ_warps != warps || occ_smem != smem) {
+    // per device: the attribute applies to one device, and the occupancy is
+    // that device's
+    static size_t attr_done[MAX_DEVICES] = {}, occ_smem[MAX_DEVICES] = {};
+    static int occ_warps[MAX_DEVICES] = {}, occ_per_sm[MAX_DEVICES] = {};
+    cudaError_t ea = allow_dyn_smem((const void *)k_walk<BPL, FEAT, BLOCK>, smem, attr_done);
+    if (ea != cudaSuccess) return ea;
+    const int dv = c.device;
+    if (dv < 0 || dv >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    if (occ_warps[dv] != warps || occ_smem[dv] != smem) {
         int per = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk<BPL, FEAT, BLOCK>, warps * 32, smem);
         if (e != cudaSuccess) return e;
-        occ_warps = warps; occ_smem = smem; occ_per_sm = per < 1 ? 1 : per;
+        occ_warps[dv] = warps; occ_smem[dv] = smem; occ_per_sm[dv] = per < 1 ? 1 : per;
     }
-    k_walk<BPL, FEAT, BLOCK><<<c.num_sms * occ_per_sm, warps * 32, smem, stream>>>(
+    k_walk<BPL, FEAT, BLOCK><<<c.num_sms * occ_per_sm[dv], warps * 32, smem, stream>>>(
         c.st, c.st, c.groups, c.pos4, c.test, c.cell_link, c.mono, c.quadA, c.quadB, c.sysid, eps,
         c.list_capacity, polls, c.acc4, c.counts, c.cell_level, c.feat, gate,
         BLOCK ? c.vel4 : nullptr, c.block_s, c.block_kmax, three);
@@ -882,18 +883,19 @@ cudaError_t launch_sph_walk(Ctx &c, const float *hs, const float4 *cext, float *
     const unsigned polls = (unsigned)(c.max_spin < 0xffffffffll ? c.max_spin : 0xffffffffll);
     const int warps = 4;
     const size_t smem = (size_t)warps * (sizeof(SphWarp) + (size_t)c.list_capacity * sizeof(unsigned));
-    static size_t attr_smem = 0;
-    static int per_sm = 0;
-    if (smem > attr_smem) {
-        cudaError_t e = cudaFuncSetAttribute(k_sph_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_smem = smem;
+    static size_t attr_done[MAX_DEVICES] = {}, occ_smem[MAX_DEVICES] = {};
+    static int per_sm[MAX_DEVICES] = {};
+    cudaError_t ea = allow_dyn_smem((const void *)k_sph_walk, smem, attr_done);
+    if (ea != cudaSuccess) return ea;
+    const int dv = c.device;
+    if (dv < 0 || dv >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    if (occ_smem[dv] != smem) {
         int per = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sph_walk, warps * 32, smem);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sph_walk, warps * 32, smem);
         if (e != cudaSuccess) return e;
-        per_sm = per < 1 ? 1 : per;
+        occ_smem[dv] = smem; per_sm[dv] = per < 1 ? 1 : per;
     }
-    k_sph_walk<<<c.num_sms * per_sm, warps * 32, smem, c.stream>>>(c.st, c.st, c.groups, c.pos4, hs, cext,
+    k_sph_walk<<<c.num_sms * per_sm[dv], warps * 32, smem, c.stream>>>(c.st, c.st, c.groups, c.pos4, hs, cext,
                                                                     c.cell_link, c.sysid, c.list_capacity, polls,
                                                                     rho_s, cnt_s);
     return cudaGetLastError();

@@ -398,13 +398,10 @@ cudaError_t launch_mlp_rows(cudaStream_t s, const float *P, const float *norm, c
 
 cudaError_t launch_mlp_grad(cudaStream_t s, const float *P, const float *norm, const float *X, const float *Y,
                             const uint32_t *idx, int bsz, float *grad, float *loss) {
-    static bool attr = false;
+    static size_t attr_done[MAX_DEVICES] = {};
     const size_t smem = sizeof(TrShared);
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    cudaError_t e = allow_dyn_smem((const void *)k_mlp_grad, smem, attr_done);
+    if (e != cudaSuccess) return e;
     k_mlp_grad<<<(bsz + TR_THREADS - 1) / TR_THREADS, TR_THREADS, smem, s>>>(P, norm, X, Y, idx, bsz, grad, loss);
     return cudaGetLastError();
 }

@@ -2,14 +2,14 @@
 // keys with all of its scratch in one file-scope device array, for callers
 // that must not allocate device memory.
 //
-// Who needs this: code that runs where cudaMalloc/cudaFree are not allowed or
-// not wanted -- inside a region that is being captured into a CUDA graph
-// (allocation calls are illegal there), in a latency-critical loop (cudaMalloc
-// and cudaFree can synchronise the whole device), or in a host application
-// whose own caching allocator has already reserved the device memory (a
-// second allocator would fail or fragment it).  Such a caller passes its own
-// input and output buffers and this entry point takes nothing else from the
-// device heap.
+// Who needs this: code that cannot call cudaMalloc/cudaFree around a sort --
+// a latency-critical loop (cudaMalloc and cudaFree can synchronise the whole
+// device and take milliseconds), or a host application whose own caching
+// allocator has already reserved the device memory (a second allocator would
+// fail or fragment it).  Such a caller passes its own input and output
+// buffers and this entry point takes nothing else from the device heap.
+// The call reads a status word back and synchronises its stream before it
+// returns, so it cannot be recorded into a CUDA graph by stream capture.
 //
 // The scratch (about 0.9 MiB) is a static __device__ array: every GPU on
 // which the library is loaded holds it until the process exits, and every
@@ -50,7 +50,7 @@ __global__ void k_static_clear(StaticSortScratch *s) {
     for (int i = t; i < SORT_PASSES * 256; i += gridDim.x * blockDim.x) s->st.hist[i] = 0u;
     for (int i = t; i < STATIC_SORT_TILES * 256; i += gridDim.x * blockDim.x) s->tile_status[i] = 0u;
     if (t < SORT_PASSES) s->st.sort_tile[t] = 0u;
-    if (t == 0) s->st.status = 0u;
+    if (t == 0) { s->st.status = 0u; s->st.hold_tile = 0u; }
 }
 
 __global__ void k_static_hist(const unsigned long long *__restrict__ keys, int n, StaticSortScratch *s) {
@@ -71,7 +71,6 @@ void set_global_error(const char *msg);   // api.cu: text of bonsai_last_error(N
 
 namespace {
 std::mutex g_setup_mu;
-constexpr int MAX_DEVICES = 64;
 StaticSortScratch *g_dev_ptr[MAX_DEVICES] = {};
 
 int set_err(int code, const char *msg) {
@@ -98,21 +97,18 @@ extern "C" int bonsai_sort_keys_static(const uint64_t *keys, uint64_t *sorted_ke
     StaticSortScratch *s = nullptr;
     {
         // Once per device, with that device current: the device address of
-        // the static scratch.  Do the first call outside any stream capture.
+        // the static scratch, and the sort kernel's shared-memory limit (a
+        // per-device attribute).
         std::lock_guard<std::mutex> lock(g_setup_mu);
         if (!g_dev_ptr[dev]) {
             void *p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
             if (e != cudaSuccess || !p)
                 return set_err(BONSAI_ERR_CUDA, "bonsai_sort_keys_static: cudaGetSymbolAddress failed");
-            static bool attr = false;
-            if (!attr) {
-                e = cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SORT_DYN_SMEM_BYTES);
-                if (e != cudaSuccess)
-                    return set_err(BONSAI_ERR_CUDA, "bonsai_sort_keys_static: kernel attribute setup failed");
-                attr = true;
-            }
+            e = cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)SORT_DYN_SMEM_BYTES);
+            if (e != cudaSuccess)
+                return set_err(BONSAI_ERR_CUDA, "bonsai_sort_keys_static: kernel attribute setup failed");
             g_dev_ptr[dev] = (StaticSortScratch *)p;
         }
         s = g_dev_ptr[dev];

@@ -90,3 +90,35 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         B.lib()
     with pytest.raises(RuntimeError):
         B.Bonsai(B.Config())
+
+
+def test_static_sort_binding_checks_before_any_launch():
+    """bonsai_sort_keys_static's binding rejects wrong dtypes, short outputs,
+    non-contiguous and non-CUDA tensors before it calls the library (the C
+    side gets raw pointers and cannot check them)."""
+    import torch
+    import paper_1204_2280_gb300 as B
+    n = 100
+    k = torch.zeros(n, dtype=torch.int64)
+    with pytest.raises(TypeError, match="perm must be torch.int32"):
+        B.bonsai_sort_keys_static(k, k.clone(), torch.zeros(n, dtype=torch.int64))
+    with pytest.raises(TypeError, match="sorted_keys must be torch.int64"):
+        B.bonsai_sort_keys_static(k, torch.zeros(n, dtype=torch.int32), torch.zeros(n, dtype=torch.int32))
+    with pytest.raises(ValueError, match="sorted_keys holds 99 elements, needs 100"):
+        B.bonsai_sort_keys_static(k, k[:99].clone(), torch.zeros(n, dtype=torch.int32))
+    with pytest.raises(ValueError, match="perm holds 50 elements"):
+        B.bonsai_sort_keys_static(k, k.clone(), torch.zeros(50, dtype=torch.int32))
+    with pytest.raises(ValueError, match="contiguous"):
+        B.bonsai_sort_keys_static(k, torch.zeros(2 * n, dtype=torch.int64)[::2], torch.zeros(n, dtype=torch.int32))
+    with pytest.raises(ValueError, match="must be a CUDA tensor"):
+        B.bonsai_sort_keys_static(k, k.clone(), torch.zeros(n, dtype=torch.int32))
+
+
+def test_bench_fma_and_hold_tile_reject_bad_arguments(libpath):
+    import paper_1204_2280_gb300 as B
+    L = B.lib()
+    ms, fl = C.c_float(), C.c_double()
+    assert L.bonsai_bench_fma(0, 256, 10, C.byref(ms), C.byref(fl)) == -1
+    assert L.bonsai_bench_fma(4, 100, 10, C.byref(ms), C.byref(fl)) == -1
+    assert b"bonsai_bench_fma" in L.bonsai_last_error(None)
+    assert L.bonsai_debug_hold_sort_tile(None, 3) == -1

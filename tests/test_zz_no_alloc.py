@@ -1,12 +1,17 @@
-"""bonsai_sort_keys_static: the radix sort for callers that cannot allocate
-device memory (graph-capture regions, latency-critical loops, hosts whose
-allocator owns the device).  Its scratch is a static device array shared by
-all calls, so this file runs last and checks two calls in a row (the second
-smaller than the first, so stale scratch from the first must not leak into
-it) against the sort of the existing build path, bit for bit."""
+"""bonsai_sort_keys_static: the key sort for callers that cannot call
+cudaMalloc around it -- a latency-critical loop (cudaMalloc/cudaFree can
+synchronise the whole device) or a host whose own caching allocator already
+owns the device memory.  Its scratch is one static device array shared by
+every call, so this file runs last (pytest collects it after the others) and
+checks calls in a row -- larger, then smaller, then tiny, so that stale
+scratch from one call must not leak into the next -- against both the
+oracle's stable sort of the same keys and the sort of the regular
+(allocating) pipeline, bit for bit.  It also checks that a call allocates
+nothing on the device and that it orders its work on a torch side stream."""
 import numpy as np
 import pytest
 
+import oracle
 import paper_1204_2280_gb300 as B
 from paper_1204_2280_gb300 import workloads as W
 
@@ -26,18 +31,59 @@ def context_sort(n, seed):
     return keys, sk, perm
 
 
-def test_static_sort_matches_context_sort_two_calls():
+def static_sort(keys, stream=None):
     import torch
-    for n, seed in [(65536, 21), (9001, 22)]:
+    n = keys.shape[0]
+    d_keys = torch.from_numpy(keys.view(np.int64).copy()).cuda()
+    d_out = torch.full((n,), -1, dtype=torch.int64, device="cuda")
+    d_perm = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    B.bonsai_sort_keys_static(d_keys, d_out, d_perm, stream)
+    torch.cuda.synchronize()
+    assert np.array_equal(d_keys.cpu().numpy().view(np.uint64), keys)   # input untouched
+    return d_out.cpu().numpy().view(np.uint64), d_perm.cpu().numpy().view(np.uint32)
+
+
+def test_static_sort_matches_oracle_and_context_sort_in_a_row():
+    for n, seed in [(65536, 21), (9001, 22), (4097, 23), (1, 24)]:
         keys, sk, perm = context_sort(n, seed)
-        d_keys = torch.from_numpy(keys.view(np.int64)).cuda()
-        d_out = torch.full((n,), -1, dtype=torch.int64, device="cuda")
-        d_perm = torch.full((n,), -1, dtype=torch.int32, device="cuda")
-        B.bonsai_sort_keys_static(d_keys, d_out, d_perm)
-        torch.cuda.synchronize()
-        assert np.array_equal(d_out.cpu().numpy().view(np.uint64), sk)
-        assert np.array_equal(d_perm.cpu().numpy().view(np.uint32), perm)
-        assert np.array_equal(d_keys.cpu().numpy().view(np.uint64), keys)   # input untouched
+        want = oracle.sort(keys)
+        got_k, got_p = static_sort(keys)
+        assert np.array_equal(got_p, want) and np.array_equal(got_k, keys[want])
+        assert np.array_equal(got_p, perm) and np.array_equal(got_k, sk)
+
+
+def test_static_sort_heavy_duplicates_on_a_side_stream():
+    """Many equal keys (16 distinct values over 65536 keys, spread over all
+    eight key bytes): equal keys keep their input order, as numpy's stable
+    argsort and the oracle's sort have them."""
+    import torch
+    rng = np.random.default_rng(5)
+    vals = rng.integers(0, 1 << 63, 16, dtype=np.uint64)
+    keys = vals[rng.integers(0, 16, 65536)]
+    s = torch.cuda.Stream()
+    got_k, got_p = static_sort(keys, s)
+    want = np.argsort(keys, kind="stable").astype(np.uint32)
+    assert np.array_equal(got_p, want) and np.array_equal(got_p, oracle.sort(keys))
+    assert np.array_equal(got_k, keys[want])
+
+
+def test_static_sort_allocates_nothing():
+    """Free device memory is the same before and after a call (the first call
+    on the device, which loads the kernels, has happened above or here)."""
+    import torch
+    keys = np.random.default_rng(6).integers(0, 1 << 63, 30000, dtype=np.uint64)
+    static_sort(keys)                                   # warm: modules loaded
+    d_keys = torch.from_numpy(keys.view(np.int64).copy()).cuda()
+    d_out = torch.empty(30000, dtype=torch.int64, device="cuda")
+    d_perm = torch.empty(30000, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    B.bonsai_sort_keys_static(d_keys, d_out, d_perm)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert np.array_equal(d_perm.cpu().numpy().view(np.uint32), oracle.sort(keys))
 
 
 def test_static_sort_rejects_sizes_beyond_its_scratch():
