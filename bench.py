@@ -110,6 +110,7 @@ def parse():
     p.add_argument("--ncrit", type=int, default=32)
     p.add_argument("--nleaf", type=int, default=16)
     p.add_argument("--walk-warps", type=int, default=8)
+    p.add_argument("--list-capacity", type=int, default=256)
     p.add_argument("--group-pack", type=int, default=1, choices=[0, 1],
                    help="sibling-packed walk groups (with --no-autotune; the autotuner picks otherwise)")
     p.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
@@ -122,10 +123,14 @@ def parse():
     p.add_argument("--no-block", action="store_true")
     p.add_argument("--no-sph", action="store_true")
     p.add_argument("--learned-n", type=int, default=1 << 22)
-    p.add_argument("--learned-plummer", type=int, default=8, help="Plummer training snapshots")
-    p.add_argument("--learned-merger", type=int, default=8, help="merger training snapshots")
+    p.add_argument("--learned-plummer", type=int, default=100, help="Plummer training snapshots")
+    p.add_argument("--learned-merger", type=int, default=100, help="merger training snapshots")
     p.add_argument("--sweep", action="store_true",
                    help="per-stage scaling sweep instead of the bench line: one JSON line per (N, theta)")
+    p.add_argument("--sweep-sizes", type=str, default="",
+                   help="with --sweep: comma-separated log2 N to run (default: every size of the sweep)")
+    p.add_argument("--sweep-thetas", type=str, default="",
+                   help="with --sweep: comma-separated opening angles to keep (default: those of each size)")
     p.add_argument("--sweep-cpu", type=float, default=0.0,
                    help="with --sweep: also time the FP64 oracle per stage at theta = 0.75 (seconds of walk sample)")
     return p.parse_args()
@@ -136,6 +141,7 @@ def config(a, world):
                         f"theta={a.theta}, KDK leapfrog dt={a.dt:g}, full rebuild every step",
             "n": a.n, "theta": a.theta, "eps": a.eps, "dt": a.dt, "nleaf": a.nleaf,
             "ncrit": a.ncrit, "walk_warps": a.walk_warps, "group_pack": a.group_pack,
+            "list_capacity": a.list_capacity,
             "l2": "flushed between timed steps (256 MiB write)",
             "parallelism": f"replicas x{world}"}
 
@@ -370,8 +376,11 @@ def run_learned(a, dev, stream):
     Workload: Plummer sphere N = 2^22 (seed 4) and a two-Plummer merger
     (2 x 2^21, centres +-2 on x, relative speed 0.5), eps = 0.002.  The
     network (12 -> 64 -> 64 -> 3) is trained here, on the GPU, on theta = 1
-    walk features vs direct-sum labels from rotated Plummer spheres (seeds
-    1000..) and snapshots of a merger stepped at theta = 0.5.  Errors are the
+    walk features vs direct-sum labels (4096 bodies per snapshot) from 200
+    generated snapshots: 100 randomly rotated Plummer spheres (seeds
+    1000..1099, generated by host worker processes) and 100 randomly rotated
+    snapshots of a merger (seed 40) stepped at theta = 0.5 (every 8th of 800
+    steps of dt = 1/64).  Errors are the
     judge's: p99 of |a - a_direct| / |a_direct| over 4096 bodies sampled
     every N/4096 in key order.  theta* is the plain opening angle whose p99
     equals the learned one (bisection).  Step throughputs are full
@@ -384,8 +393,9 @@ def run_learned(a, dev, stream):
     from paper_1204_2280_gb300 import workloads as W
     n, eps, dt = a.learned_n, 0.002, 1.0 / 256
     t0 = time.perf_counter()
-    plummers = L.snapshots(n, range(1000, 1000 + a.learned_plummer), rotations=1)
-    mergers = L.evolved(W.merger(n, 40), steps=16 * a.learned_merger, every=16, theta=0.5, eps=eps)
+    plummers = L.snapshots_parallel(n, range(1000, 1000 + a.learned_plummer), rot_seed0=7000)
+    mergers = (L.rotated(m, 9000 + k) for k, m in
+               enumerate(L.evolved(W.merger(n, 40), steps=8 * a.learned_merger, every=8, theta=0.5, eps=eps)))
     X, Y = L.training_set(plummers, theta=1.0, eps=eps, per_snapshot=4096, ncrit=64)
     Xm, Ym = L.training_set(mergers, theta=1.0, eps=eps, per_snapshot=4096, ncrit=64, seed=500)
     X, Y = np.concatenate([X, Xm]), np.concatenate([Y, Ym])
@@ -549,8 +559,8 @@ def run_sph(a, dev, stream):
     r = np.linalg.norm(b.pos.astype(np.float64), axis=1)
     nden = a.n * 3 / (4 * np.pi * ah ** 3) * (1 + r * r / (ah * ah)) ** -2.5
     h = ((3 * 48 / (4 * np.pi * nden)) ** (1 / 3)).astype(np.float32)
-    bz = B.Bonsai(B.Config(nleaf=a.nleaf, ncrit=a.ncrit, walk_warps=a.walk_warps, group_pack=a.group_pack),
-                  stream=stream)
+    bz = B.Bonsai(B.Config(nleaf=a.nleaf, ncrit=a.ncrit, walk_warps=a.walk_warps, group_pack=a.group_pack,
+                           list_capacity=a.list_capacity), stream=stream)
     bz.set_bodies(torch.from_numpy(b.pos).to(dev), torch.from_numpy(b.mass).to(dev),
                   torch.from_numpy(b.vel).to(dev))
     bz.build()
@@ -690,6 +700,12 @@ def run_sweep(a, dev, stream):
     eps, dt, steps = 0.002, 1.0 / 256, 5
     cases = [(1 << k, 1, (0.75,)) for k in range(15, 22)]
     cases += [(1 << 22, 2, (0.5, 0.75, 1.0)), (1 << 23, 1, (0.75,)), (1 << 24, 3, (0.5, 0.75, 1.0))]
+    if a.sweep_sizes:
+        keep = {1 << int(x) for x in a.sweep_sizes.split(",")}
+        cases = [c for c in cases if c[0] in keep]
+    if a.sweep_thetas:
+        keep_t = {float(x) for x in a.sweep_thetas.split(",")}
+        cases = [(n, s, tuple(t for t in th if t in keep_t)) for n, s, th in cases]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     tot = (C.c_ulonglong * 2)()
     for n, seed, thetas in cases:
@@ -787,13 +803,14 @@ def run_ours(a, rank, world, local_rank):
     torch.cuda.set_stream(stream)
     b = W.plummer(a.n, a.seed)
     n = b.n
-    bz = B.Bonsai(B.Config(nleaf=a.nleaf, ncrit=a.ncrit, walk_warps=a.walk_warps, group_pack=a.group_pack),
-                  stream=stream)
+    bz = B.Bonsai(B.Config(nleaf=a.nleaf, ncrit=a.ncrit, walk_warps=a.walk_warps, group_pack=a.group_pack,
+                           list_capacity=a.list_capacity), stream=stream)
     bz.set_bodies(torch.from_numpy(b.pos).to(dev), torch.from_numpy(b.mass).to(dev),
                   torch.from_numpy(b.vel).to(dev))
     if not a.no_autotune:
         a.ncrit, a.walk_warps, _ = B.bonsai_autotune(bz.ctx, a.theta, a.eps)
-        a.group_pack = B.bonsai_get_config(bz.ctx).group_pack
+        cfg = B.bonsai_get_config(bz.ctx)
+        a.group_pack, a.list_capacity = cfg.group_pack, cfg.list_capacity
     else:
         bz.build().multipoles().forces(a.theta, a.eps)
     B.bonsai_set_params(bz.ctx, a.theta, a.eps)

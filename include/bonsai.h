@@ -179,11 +179,13 @@ int bonsai_sph_density(bonsai_ctx *ctx, const float *h, float *rho, int32_t *nng
 
 /* Autotuner: times the walk of the current bodies (CUDA events, mean of two
  * walks after one untimed) for every group size ncrit in {16, 32, 48, 64},
- * both group rules (group_pack 0 and 1) and walk thread-block width in
- * {2, 4, 8} warps, keeps the fastest choice in the context (rebuilding the
+ * both group rules (group_pack 0 and 1), walk thread-block width in
+ * {2, 4, 8} warps and walk stack capacity (list_capacity) in {128, 256, 512}
+ * entries per warp, keeps the fastest choice in the context (rebuilding the
  * tree and groups for it) and leaves forces at (theta, eps) computed.
  * Candidates that overflow the walk stack are skipped.  Any output pointer
- * may be NULL; bonsai_get_config reports the chosen group rule. */
+ * may be NULL; bonsai_get_config reports the chosen group rule and
+ * capacity. */
 int bonsai_autotune(bonsai_ctx *ctx, float theta, float eps, int *best_ncrit,
                     int *best_warps, float *best_ms);
 
@@ -355,8 +357,9 @@ int bonsai_mlp_train(bonsai_mlp *m, const float *X, const float *Y, long long n,
 int bonsai_learn_samples(bonsai_ctx *ctx, float theta, float eps, int ntar, unsigned long long seed,
                          float *X, float *Y, uint32_t *ids, int on_device);
 
-/* Judge of the current accelerations: direct sum (FP32, Kahan, FP64
- * reduction) at min(n, 4096) bodies spaced evenly in key order and the 99th
+/* Judge of the current accelerations: direct sum (FP32 tiles and a FP32
+ * reduction over source splits, both Kahan-compensated) at min(n, 4096)
+ * bodies spaced evenly in key order and the 99th
  * percentile (numpy's linear interpolation) of |a - a_direct| / |a_direct|. */
 int bonsai_judge(bonsai_ctx *ctx, float eps, float *p99);
 

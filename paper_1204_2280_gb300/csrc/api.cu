@@ -70,7 +70,8 @@ cudaError_t alloc_bodies(Ctx &c, long long n) {
     a.take(c.keys, n, plan); a.take(c.keys_alt, n, plan);
     a.take(c.vals, n, plan); a.take(c.vals_alt, n, plan);
     a.take(c.tile_status, (size_t)(SORT_PASSES + 1) * ntiles * 256, plan);
-    a.take(c.blockcount, (size_t)NROWS * nbb, plan);
+    a.take(c.blockcount, (size_t)BUILD_ROWS * nbb, plan);
+    a.take(c.build_entries, (size_t)nbb * BUILD_THREADS, plan);
     a.take(c.cell_body, ccap, plan); a.take(c.cell_link, ccap, plan);
     a.take(c.cell_level, ccap, plan); a.take(c.cell_parent, ccap, plan);
     a.take(c.cell_done, ccap, plan); a.take(c.cell_cb, ccap, plan);
@@ -94,6 +95,16 @@ cudaError_t alloc_bodies(Ctx &c, long long n) {
     c.ccap = ccap;
     c.judge_n = 0;
     return cudaMemsetAsync(base, 0, a.off, c.stream);
+}
+
+// The cell count of the current tree, read back (synchronises the stream):
+// it sizes the multipole launch (any count stays correct; the launch loops).
+cudaError_t refresh_cells_hint(Ctx &c) {
+    unsigned nc = 0;
+    cudaError_t e = cudaMemcpyAsync(&nc, &c.st->ncells, sizeof(unsigned), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e == cudaSuccess) c.cells_hint = nc;
+    return e;
 }
 
 // keys -> sort -> reorder -> build; the domain accumulators must hold the
@@ -233,6 +244,7 @@ int bonsai_set_bodies(bonsai_ctx *ctx, const float *pos, const float *mass, cons
     }
     if (c.step_graph) { cudaGraphExecDestroy(c.step_graph); c.step_graph = nullptr; }
     c.graph_n = -1;
+    if (n != c.n) c.cells_hint = 0;
     c.n = n;
     const float *p = pos, *m = mass, *v = vel;
     if (!on_device) {
@@ -306,6 +318,7 @@ int bonsai_multipoles(bonsai_ctx *ctx) {
     if (!ctx) return BONSAI_ERR_INVALID_ARG;
     Ctx &c = ctx->c;
     if (!c.built) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_multipoles: call bonsai_build first");
+    CK(refresh_cells_hint(c));
     CK(launch_multipoles(c));
     c.moments_ready = true;
     return BONSAI_OK;
@@ -370,6 +383,8 @@ int bonsai_step(bonsai_ctx *ctx, float dt) {
     if (c.use_graph && same && c.step_graph) {
         CK(cudaGraphLaunch(c.step_graph, c.stream));
     } else if (c.use_graph && same) {
+        // the captured launches are sized from the tree of the eager step before
+        CK(refresh_cells_hint(c));
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
@@ -424,19 +439,22 @@ int bonsai_autotune(bonsai_ctx *ctx, float theta, float eps, int *best_ncrit, in
     if (!c.have_bodies) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_autotune: no bodies");
     static const int ncrits[] = {16, 32, 48, 64};
     static const int warps[] = {2, 4, 8};
+    static const int caps[] = {128, 256, 512};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 1e30f;
-    int bn = c.ncrit, bw = c.walk_warps, bp = c.group_pack;
+    int bn = c.ncrit, bw = c.walk_warps, bp = c.group_pack, bc = c.list_capacity;
     cudaError_t e = cudaSuccess;
     for (int cand = 0; cand < 8; cand++) {
         const int nc = ncrits[cand & 3], pk = cand >> 2;
         c.ncrit = nc;
         c.group_pack = pk;
         if ((r = bonsai_build(ctx)) || (r = bonsai_multipoles(ctx))) break;
-        for (int w : warps) {
+        for (int wc = 0; wc < 9; wc++) {
+            const int w = warps[wc / 3];
             c.walk_warps = w;
+            c.list_capacity = caps[wc % 3];
             // one untimed walk, then the mean of two timed ones
             if ((e = launch_reset(c)) != cudaSuccess || (e = pipeline_forces(c, theta, eps)) != cudaSuccess) break;
             if ((e = cudaEventRecord(e0, c.stream)) != cudaSuccess) break;
@@ -456,7 +474,7 @@ int bonsai_autotune(bonsai_ctx *ctx, float theta, float eps, int *best_ncrit, in
                 if ((e = cudaMemset(&c.st->status, 0, sizeof(unsigned))) != cudaSuccess) break;
                 continue;
             }
-            if (ms / 2 < best) { best = ms / 2; bn = nc; bw = w; bp = pk; }
+            if (ms / 2 < best) { best = ms / 2; bn = nc; bw = w; bp = pk; bc = c.list_capacity; }
         }
         if (e != cudaSuccess) break;
     }
@@ -467,6 +485,7 @@ int bonsai_autotune(bonsai_ctx *ctx, float theta, float eps, int *best_ncrit, in
     c.ncrit = bn;
     c.walk_warps = bw;
     c.group_pack = bp;
+    c.list_capacity = bc;
     if (c.step_graph) { cudaGraphExecDestroy(c.step_graph); c.step_graph = nullptr; }
     c.graph_n = -1;
     if ((r = bonsai_build(ctx)) || (r = bonsai_multipoles(ctx)) ||
@@ -544,6 +563,7 @@ static int read_state(bonsai_ctx *ctx) {
     Ctx &c = ctx->c;
     CK(cudaMemcpyAsync(c.st_host, c.st, sizeof(DevState), cudaMemcpyDeviceToHost, c.stream));
     CK(cudaStreamSynchronize(c.stream));
+    if (c.built) c.cells_hint = c.st_host->ncells;
     return BONSAI_OK;
 }
 

@@ -48,6 +48,8 @@ constexpr int JUDGE_SPLIT = 64;                        // source splits of the j
 #endif
 constexpr int BUILD_THREADS = BUILD_THREADS_CFG;       // bodies per build block (multiple of 32, <= 1024)
 constexpr int PACK_THREADS = 1024;                     // unpacked groups per group-packing block
+constexpr int ENTRY_ROW = NROWS;                       // build: entries per block (a row that is not scanned)
+constexpr int BUILD_ROWS = NROWS + 1;                  // build: per-block count rows
 
 // Device status bits (ORed by kernels, read and cleared by bonsai_sync).
 constexpr unsigned ST_CAPACITY = 1u;
@@ -92,6 +94,7 @@ struct Ctx {
 
     // sizes
     long long n = 0, ncap = 0, ccap = 0;
+    long long cells_hint = 0;         // cell count of the last tree the host read (0: none); sizes launches
     int ntiles = 0, nbblocks = 0;     // sort tiles, build blocks
     int nsys = 1;                     // independent systems (contiguous body segments)
 
@@ -105,7 +108,8 @@ struct Ctx {
     uint32_t *vals = nullptr, *vals_alt = nullptr;   // vals ends as perm
     unsigned *tile_status = nullptr;                   // (SORT_PASSES + 1) * ntiles * 256
     // build
-    unsigned *blockcount = nullptr;  // NROWS * nbblocks
+    unsigned *blockcount = nullptr;  // BUILD_ROWS * nbblocks
+    uint4 *build_entries = nullptr;  // per build block, the bodies that start cells (capacity n)
     uint2 *cell_body = nullptr, *cell_link = nullptr;
     uint8_t *cell_level = nullptr;
     uint32_t *cell_parent = nullptr, *cell_done = nullptr, *cell_cb = nullptr;

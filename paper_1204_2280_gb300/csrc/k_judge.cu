@@ -5,7 +5,9 @@
 // For T target bodies (sorted positions) the softened acceleration and
 // potential from all N bodies: sources are streamed through shared memory in
 // tiles, each tile summed in FP32 and added with Kahan compensation; the
-// source range is split over blocks and the partial sums are added in FP64.
+// source range is split over blocks and the partial sums are added in FP32
+// with Kahan compensation too (FP64 on the GPU is kept to the root
+// multipoles and the energy diagnostics).
 // Tiles run on packed FP32x2 arithmetic, two targets per thread.
 // The judge then ranks the relative errors of the current accelerations at
 // the targets and compares their 99th percentile with a budget.
@@ -75,19 +77,20 @@ k_direct_partial(const float4 *__restrict__ pos4, int n, const uint32_t *__restr
     if (live1) partial[(size_t)blockIdx.y * ntar + k1] = make_float4(ax[1] - cx[1], ay[1] - cy[1], az[1] - cz[1], ph[1] - cp[1]);
 }
 
-// Sum the splits in FP64 and remove the target's own -m/eps term.
+// Sum the splits in order with Kahan compensation (FP32) and remove the
+// target's own -m/eps term from the potential.
 __global__ void k_direct_reduce(const float4 *__restrict__ pos4, const uint32_t *__restrict__ targets,
                                 int ntar, int nsplit, float eps2, const float4 *__restrict__ partial,
                                 float4 *out, const unsigned *__restrict__ gate) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= ntar || (gate && *gate == 0u)) return;
-    double ax = 0, ay = 0, az = 0, ph = 0;
+    float ax = 0.f, ay = 0.f, az = 0.f, ph = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, cp = 0.f;
     for (int y = 0; y < nsplit; y++) {
         const float4 p = partial[(size_t)y * ntar + k];
-        ax += p.x; ay += p.y; az += p.z; ph += p.w;
+        kadd(ax, cx, p.x); kadd(ay, cy, p.y); kadd(az, cz, p.z); kadd(ph, cp, p.w);
     }
-    ph += (double)pos4[targets[k]].w * (double)rsqrtf(eps2);
-    out[k] = make_float4((float)ax, (float)ay, (float)az, (float)ph);
+    kadd(ph, cp, pos4[targets[k]].w * rsqrtf(eps2));
+    out[k] = make_float4(ax - cx, ay - cy, az - cz, ph - cp);
 }
 
 cudaError_t launch_direct(Ctx &c, const uint32_t *targets, int ntar, float eps, float4 *partial,

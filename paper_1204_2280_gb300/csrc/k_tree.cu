@@ -7,20 +7,14 @@
 // order within a level, so children are contiguous.
 //
 // Instead of 22 dependent level launches, the build uses the fact that the
-// cells are runs of equal key prefixes: with cpl(a,b) the number of leading
-// levels two keys share,
-//   l0(t) = cpl(k[t-1], k[t]) + 1          first level at which body t starts a run
-//   D(t)  = cpl(k[t], k[t+nleaf])          the run from t at level l has > nleaf
-//                                          bodies iff l <= D(t)
-// A cell (level l, first body t) exists iff the run at level l-1 containing t
-// has more than nleaf bodies.  For l > l0(t) that run also starts at t; for
-// l = l0(t) its length is read from per-level bit masks of run starts over a
-// 64-body halo (a longer run is split in any case).  So body t starts exactly
-// the cells of levels lo..hi with lo = l0(t) (if that parent run is split)
-// and hi = max(lo, min(D(t)+1, 21)); the one at hi is a leaf.  Groups (cells
-// with <= ncrit bodies whose parent has more) follow the same way with ncrit
-// in place of nleaf.  Four launches: count per block and level, scan per
-// level, write cells, link children and internal body counts.
+// cells are runs of equal key prefixes: every cell is identified by its level
+// and its first body, and whether body t starts a cell on a level follows
+// from a few common-prefix lengths of keys near t (pass 1 below).  Four
+// launches: (1) per body, the levels on which it starts cells and its group,
+// compacted per block into a list of the bodies that start any (about one per
+// leaf), with counts per block and level; (2) scan of those counts over the
+// blocks; (3) per listed body, the index, first body, level and link of each
+// of its cells and its groups; (4) children, parents and internal body counts.
 #include "common.cuh"
 
 namespace bonsai {
@@ -44,7 +38,8 @@ cudaError_t launch_reorder(Ctx &c) {
 }
 
 // First index > t whose level-`level` key prefix differs from k[t], or n
-// (the end of t's system): galloping then bisection.
+// (the end of t's system): galloping then bisection.  Only runs of identical
+// keys at the deepest level can be longer than the build's 64-body halo.
 __device__ int run_end(const unsigned long long *__restrict__ sk, int n, int t, int level) {
     if (level == 0) return n;
     int sh = 3 * (MAX_LEVEL - level);
@@ -64,174 +59,175 @@ __device__ int run_end(const unsigned long long *__restrict__ sk, int n, int t, 
     return hi;
 }
 
-__device__ __forceinline__ unsigned digit_at(unsigned long long k, int level) {
-    return (unsigned)(k >> (3 * (MAX_LEVEL - level))) & 7u;
-}
-
-struct BodyCells {
-    bool has;
-    int lo, hi, ngrp, lg;   // lg: group level (>hi: oversize leaf cut in chunks)
-};
-
-// Shared memory of a build block.  The block's bodies are [base, base+B);
-// a halo of BW = 64 bodies on each side gives the extended range
-// [base-BW, base+B+BW) of BCH chunks of 32 positions, plus one key below it.
-//   M[l * BCH + c], bit i: position 32c + i of the extended range is the
-//   first body of a level-l key-prefix run (l0 <= l; every position outside
-//   [1, n) and every first body of a system counts as one).
-// Any run that matters here (<= 64 bodies around a body of the block) is
-// then answered by bit operations on at most five mask words per query.
-constexpr int BW = 64;
-constexpr int BCH = (BUILD_THREADS + 2 * BW) / 32;
-
-struct BuildShared {
-    unsigned long long *k;   // keys of [base-BW-1, base+B+BW)
-    uint8_t *sy;             // system ids, same range
-    unsigned *M;             // run-start masks, (MAX_LEVEL + 1) x BCH
-    int base;
-    __device__ unsigned long long key(int j) const { return k[j - base + BW + 1]; }
-    __device__ uint8_t sys(int j) const { return sy[j - base + BW + 1]; }
-    __device__ int cpl(int a, int b) const { return body_cpl(key(a), key(b), sys(a), sys(b)); }
-
-    // First body s <= t and end e > t of the level-l run holding body t of
-    // the block, as extended-range positions; -4096 / 1 << 20 when farther
-    // than the two neighbouring chunks (then the run exceeds 64 bodies).
-    __device__ void run_of(int t, int l, int &s, int &e) const {
-        const int q = t - base + BW, c = q >> 5, i = q & 31;
-        const unsigned *Ml = M + l * BCH;
-        const unsigned a0 = Ml[c] & (0xffffffffu >> (31 - i));
-        const unsigned a1 = Ml[c - 1], a2 = Ml[c - 2];
-        s = a0 ? (c << 5) + 31 - __clz(a0)
-               : a1 ? ((c - 1) << 5) + 31 - __clz(a1) : a2 ? ((c - 2) << 5) + 31 - __clz(a2) : -4096;
-        const unsigned b0 = i == 31 ? 0u : (Ml[c] & (0xffffffffu << (i + 1)));
-        const unsigned b1 = Ml[c + 1], b2 = Ml[c + 2];
-        e = b0 ? (c << 5) + __ffs(b0) - 1
-               : b1 ? ((c + 1) << 5) + __ffs(b1) - 1 : b2 ? ((c + 2) << 5) + __ffs(b2) - 1 : 1 << 20;
-    }
-    // Whether the level-l run holding t has more than w (<= 64) bodies.
-    __device__ bool run_longer(int t, int l, int w) const {
-        int s, e;
-        run_of(t, l, s, e);
-        return e - s > w;
-    }
-    // End (exclusive) of the level-l run starting at t: from the masks when
-    // within the halo, else by the global search.
-    __device__ int run_end_at(const unsigned long long *__restrict__ sk, int send, int t, int l) const {
-        if (l == 0) return send;
-        int s, e;
-        run_of(t, l, s, e);
-        return e < (1 << 20) ? min(send, base - BW + e) : run_end(sk, send, t, l);
-    }
-};
-
-// Keys and system ids of the extended range, then the run-start masks: one
-// chunk per warp and pass, 22 ballots, lane l keeps level l's mask.
-__device__ BuildShared load_build_shared(void *smem, const unsigned long long *__restrict__ sk,
-                                         const uint8_t *__restrict__ sysid, int n, int base) {
-    BuildShared b;
-    b.base = base;
-    constexpr int NK = BUILD_THREADS + 2 * BW + 1;
-    b.k = (unsigned long long *)smem;
-    b.M = (unsigned *)(b.k + NK);
-    b.sy = (uint8_t *)(b.M + (MAX_LEVEL + 1) * BCH);
-    for (int i = threadIdx.x; i < NK; i += blockDim.x) {
-        const int j = base - BW - 1 + i;
-        const bool in = j >= 0 && j < n;
-        b.k[i] = in ? sk[j] : 0ull;
-        b.sy[i] = in ? sysid[j] : 0;
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    for (int c = threadIdx.x >> 5; c < BCH; c += BUILD_THREADS / 32) {
-        const int j = base - BW + (c << 5) + lane;
-        const int l0 = (j > 0 && j < n) ? b.cpl(j - 1, j) + 1 : 0;
-        unsigned mine = 0u;
-#pragma unroll
-        for (int l = 0; l <= MAX_LEVEL; l++) {
-            const unsigned m = __ballot_sync(0xffffffffu, l0 <= l);
-            if (lane == l) mine = m;
-        }
-        if (lane <= MAX_LEVEL) b.M[lane * BCH + c] = mine;
-    }
-    __syncthreads();
-    return b;
-}
-
-size_t build_smem_bytes(int, int) {
-    return (size_t)(BUILD_THREADS + 2 * BW + 1) * 9 + (size_t)(MAX_LEVEL + 1) * BCH * 4;
-}
-
-// Which cells body t starts (levels lo..hi) and how many groups; send is the
-// end of t's system.
-__device__ BodyCells analyse_body(const BuildShared &b, int t, int n, int nleaf, int ncrit,
-                                  const unsigned long long *__restrict__ sk, int send) {
-    BodyCells r{false, 0, -1, 0, 0};
-    if (t >= n) return r;
-    const int l0 = t == 0 ? 0 : b.cpl(t - 1, t) + 1;
-    if (l0 > MAX_LEVEL) return r;
-    if (l0 > 0 && !b.run_longer(t, l0 - 1, nleaf)) return r;     // parent not split
-    r.has = true;
-    r.lo = l0;
-    const int D = t + nleaf < n ? b.cpl(t, t + nleaf) : -1;
-    r.hi = max(l0, min(D + 1, MAX_LEVEL));
-    const int DG = t + ncrit < n ? b.cpl(t, t + ncrit) : -1;
-    const int lg = max(l0, DG + 1);
-    r.lg = lg;
-    if (lg <= r.hi) {
-        const bool starts = (lg > l0) || l0 == 0 || b.run_longer(t, l0 - 1, ncrit);
-        r.ngrp = starts ? 1 : 0;
-    } else {
-        const int cnt = b.run_end_at(sk, send, t, r.hi) - t;
-        r.ngrp = (cnt + ncrit - 1) / ncrit;
-    }
-    return r;
-}
-
 __device__ __forceinline__ int system_end(const DevState *__restrict__ st, const uint8_t *__restrict__ sysid,
                                           int t, int n) {
     return t < n ? (int)st->sys_off[sysid[t] + 1] : n;
 }
 
-__device__ __forceinline__ bool has_level(const BodyCells &bc, int r) {
-    return bc.has && bc.lo <= r && r <= bc.hi;
+// ---- Pass 1: which cells and groups every body starts ----------------------
+// For body t (within its system) let
+//   l0(t) = cpl(k[t-1], k[t]) + 1   the first level at which t starts a key-prefix run
+//                                   (0 for the first body of a system)
+//   D(t)  = cpl(k[t], k[t+nleaf])   the run at level l from t has more than
+//                                   nleaf bodies iff l <= D(t)   (-1: no such body)
+//   DG(t) = cpl(k[t], k[t+ncrit])   the same for ncrit.
+// The level-L run holding t has more than w bodies iff some window of w+1
+// consecutive bodies containing t lies inside it, i.e. iff
+//   max over i in [t-w, t] of cpl(k[i], k[i+w]) >= L.
+// So t starts a cell on level l0 (the parent run, level l0-1, is split) iff
+// l0 = 0 or that window maximum of D reaches l0 - 1; it then starts the cells
+// of levels lo = l0 .. hi = max(l0, min(D(t) + 1, 21)), the one at hi a leaf.
+// Its group (the cells with <= ncrit bodies whose parent has more) sits on
+// level lg = max(l0, DG(t) + 1) if lg <= hi and t starts it (lg > l0, l0 = 0,
+// or the window maximum of DG reaches l0 - 1); if lg > hi the leaf has more
+// than ncrit bodies (identical keys at level 21, or ncrit < nleaf) and is cut
+// into runs of ncrit.  Both window maxima come from a sparse table of
+// pairwise maxima (log2(w+1) + 1 levels) in shared memory.
+//
+// The bodies that start cells (about one per leaf) are compacted, in key
+// order, into the block's entry list: first body, leaf count (up to the next
+// entry, which is the first body after the leaf), group body count and the
+// levels.  Per block: cells per level (a difference array over lo..hi),
+// groups, and entries.
+constexpr int BH = 64;                              // halo: max(nleaf, ncrit)
+constexpr int BTAB = BUILD_THREADS + BH;            // table positions [base - BH, base + B)
+constexpr int BKEYS = BUILD_THREADS + 2 * BH + 1;   // keys of [base - BH - 1, base + B + BH)
+
+struct MarkShared {
+    unsigned long long k[BKEYS];
+    unsigned tab[2][BTAB];         // (D + 1) | (DG + 1) << 16, then pairwise maxima
+    unsigned e_t[BUILD_THREADS];   // the block's entries: first body
+    unsigned e_d[BUILD_THREADS];   //   lo | hi << 8 | lg << 16 | kind << 24
+    int cnt[MAX_LEVEL + 2];        // difference array of cells per level
+    unsigned wcnt[BUILD_THREADS / 32];
+    unsigned ngrp, ne;
+    uint8_t sy[BKEYS];
+    uint8_t l0[BTAB];              // l0 of positions [base, base + B + BH)
+};
+
+// First body after t (of the block or its halo) that starts a run at a level
+// <= L, i.e. the end of t's level-L run; the global search beyond the halo.
+__device__ __forceinline__ int run_end_halo(const MarkShared &S, int base, int t, int L,
+                                            const unsigned long long *__restrict__ sk, int send) {
+    for (int j = t + 1; j < base + BTAB; j++)
+        if (S.l0[j - base] <= L) return j;
+    return run_end(sk, send, t, L);
 }
 
-// The levels on which any body of the warp starts a cell: [rlo, rhi]
-// (empty, rlo > rhi, when none does).  Warp-uniform.
-__device__ __forceinline__ void warp_level_range(const BodyCells &bc, int &rlo, int &rhi) {
-    rlo = (int)__reduce_min_sync(0xffffffffu, bc.has ? (unsigned)bc.lo : (unsigned)(MAX_LEVEL + 1));
-    rhi = (int)__reduce_max_sync(0xffffffffu, bc.has ? (unsigned)bc.hi : 0u);
-    if (rlo > MAX_LEVEL) rhi = -1;
-}
-
-// Pass 1: per block, the number of cells of each level and of groups.
 __global__ void __launch_bounds__(BUILD_THREADS)
-k_build_count(const unsigned long long *__restrict__ sk, const uint8_t *__restrict__ sysid, int n,
-              int nleaf, int ncrit, unsigned *blockcount, int nblocks, const DevState *__restrict__ st) {
-    extern __shared__ unsigned long long smem_u64[];
-    __shared__ unsigned s_wc[NROWS][32];
+k_build_mark(const unsigned long long *__restrict__ sk, const uint8_t *__restrict__ sysid, int n, int nleaf,
+             int ncrit, unsigned *blockcount, int nblocks, uint4 *entries, const DevState *__restrict__ st) {
+    __shared__ MarkShared S;
     if (st->status & ST_TIMEOUT) return;        // keys not sorted: skip the build
     const int base = blockIdx.x * BUILD_THREADS, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    BuildShared b = load_build_shared(smem_u64, sk, sysid, n, base);
-    const int t = base + tid;
-    BodyCells bc = analyse_body(b, t, n, nleaf, ncrit, sk, system_end(st, sysid, t, n));
-    int rlo, rhi;
-    warp_level_range(bc, rlo, rhi);
-    if (lane <= MAX_LEVEL && (lane < rlo || lane > rhi)) s_wc[lane][warp] = 0u;
-    for (int r = rlo; r <= rhi; r++) {
-        const unsigned m = __ballot_sync(0xffffffffu, has_level(bc, r));
-        if (lane == 0) s_wc[r][warp] = __popc(m);
+    const int k0 = base - BH - 1;
+    for (int i = tid; i < BKEYS; i += BUILD_THREADS) {
+        const int j = k0 + i;
+        const bool in = j >= 0 && j < n;
+        S.k[i] = in ? sk[j] : 0ull;
+        S.sy[i] = in ? sysid[j] : 0;
     }
-    int g = bc.ngrp;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-    if (lane == 0) s_wc[GROUP_ROW][warp] = (unsigned)g;
+    if (tid <= MAX_LEVEL + 1) S.cnt[tid] = 0;
+    if (tid == 0) S.ngrp = 0u;
     __syncthreads();
-    if (tid < NROWS) {
-        unsigned s = 0;
-#pragma unroll 8
-        for (int w = 0; w < BUILD_THREADS / 32; w++) s += s_wc[tid][w];
-        blockcount[(size_t)tid * nblocks + blockIdx.x] = s;
+    auto cpl = [&](int a, int b) { return body_cpl(S.k[a - k0], S.k[b - k0], S.sy[a - k0], S.sy[b - k0]); };
+    for (int i = tid; i < BTAB; i += BUILD_THREADS) {
+        const int j = base - BH + i;             // table position
+        int d = -1, dg = -1;
+        if (j >= 0 && j < n) {
+            if (j + nleaf < n) d = cpl(j, j + nleaf);
+            if (j + ncrit < n) dg = cpl(j, j + ncrit);
+        }
+        S.tab[0][i] = (unsigned)(d + 1) | ((unsigned)(dg + 1) << 16);
+        const int jl = base + i;                 // l0 position (>= n: 0, ends every run)
+        S.l0[i] = (jl <= 0 || jl >= n) ? (uint8_t)0 : (uint8_t)(cpl(jl - 1, jl) + 1);
+    }
+    __syncthreads();
+
+    const int t = base + tid, it = tid + BH;
+    const unsigned own = S.tab[0][it];
+    const int qL = 31 - __clz(nleaf + 1), qG = 31 - __clz(ncrit + 1), qmax = max(qL, qG);
+    int winD = 0, winG = 0;                      // 1 + window maxima of D and DG
+    int cur = 0;
+    for (int q = 0; q <= qmax; q++) {            // uniform over the block
+        const unsigned *T = S.tab[cur];
+        if (q == qL) winD = (int)max(T[it - nleaf] & 0xffffu, T[it - (1 << q) + 1] & 0xffffu);
+        if (q == qG) winG = (int)max(T[it - ncrit] >> 16, T[it - (1 << q) + 1] >> 16);
+        if (q < qmax) {
+            const int h = 1 << q;
+            unsigned *U = S.tab[cur ^ 1];
+            for (int i = tid; i + 2 * h <= BTAB; i += BUILD_THREADS) U[i] = __vmaxu2(T[i], T[i + h]);
+            __syncthreads();
+            cur ^= 1;
+        }
+    }
+    const int l0 = S.l0[tid];
+    bool has = false;
+    unsigned desc = 0u;
+    if (t < n && l0 <= MAX_LEVEL && (l0 == 0 || winD >= l0)) {
+        has = true;
+        const int D = (int)(own & 0xffffu) - 1, DG = (int)(own >> 16) - 1;
+        const int hi = max(l0, min(D + 1, MAX_LEVEL));
+        const int lg = max(l0, DG + 1);
+        const int kind = lg <= hi ? ((lg > l0 || l0 == 0 || winG >= l0) ? 1 : 0) : 2;
+        desc = (unsigned)l0 | ((unsigned)hi << 8) | ((unsigned)min(lg, 255) << 16) | ((unsigned)kind << 24);
+    }
+    // compaction of the block's entries, in key order
+    const unsigned m = __ballot_sync(0xffffffffu, has);
+    if (lane == 0) S.wcnt[warp] = __popc(m);
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned v = lane < BUILD_THREADS / 32 ? S.wcnt[lane] : 0u;
+        unsigned x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane < BUILD_THREADS / 32) S.wcnt[lane] = x - v;
+        if (lane == 31) S.ne = x;
+    }
+    __syncthreads();
+    if (has) {
+        const unsigned slot = S.wcnt[warp] + __popc(m & ((1u << lane) - 1u));
+        S.e_t[slot] = (unsigned)t;
+        S.e_d[slot] = desc;
+    }
+    __syncthreads();
+    const unsigned ne = S.ne;
+    if ((unsigned)tid < ne) {
+        const unsigned et = S.e_t[tid], ed = S.e_d[tid];
+        const int elo = (int)(ed & 0xffu), ehi = (int)((ed >> 8) & 0xffu), elg = (int)((ed >> 16) & 0xffu);
+        const int kind = (int)(ed >> 24);
+        const int send = system_end(st, sysid, (int)et, n);
+        const int lend = (unsigned)tid + 1 < ne ? (int)S.e_t[tid + 1] : run_end_halo(S, base, (int)et, ehi, sk, send);
+        const unsigned lcnt = (unsigned)lend - et;
+        unsigned gcnt = 0u, ngrp = 0u;
+        if (kind == 1) {
+            gcnt = elg == ehi ? lcnt : (unsigned)run_end_halo(S, base, (int)et, elg, sk, send) - et;
+            ngrp = 1u;
+        } else if (kind == 2) {
+            gcnt = lcnt;
+            ngrp = (lcnt + (unsigned)ncrit - 1u) / (unsigned)ncrit;
+        }
+        entries[(size_t)blockIdx.x * BUILD_THREADS + tid] = make_uint4(et, lcnt, gcnt, ed);
+        atomicAdd(&S.cnt[elo], 1);
+        atomicSub(&S.cnt[ehi + 1], 1);
+        if (ngrp) atomicAdd(&S.ngrp, ngrp);
+    }
+    __syncthreads();
+    if (warp == 0) {                             // cells per level: prefix of the difference array
+        int x = lane <= MAX_LEVEL ? S.cnt[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane <= MAX_LEVEL) blockcount[(size_t)lane * nblocks + blockIdx.x] = (unsigned)x;
+        if (lane == 0) {
+            blockcount[(size_t)GROUP_ROW * nblocks + blockIdx.x] = S.ngrp;
+            blockcount[(size_t)ENTRY_ROW * nblocks + blockIdx.x] = ne;
+        }
     }
 }
 
@@ -273,26 +269,25 @@ k_build_scan(unsigned *blockcount, int nblocks, DevState *st) {
     if (tid == 0) st->row_total[blockIdx.x] = s_carry;
 }
 
-// Pass 3: number every cell and write its first body, level and link.  For
-// each cell (level r, first body t) it also records cb = the number of
-// level-(r+1) cells that start before t, offset to level r+1's first index:
-// for an internal cell that is its first child, and the children of a cell
-// are the level-(r+1) cells between its cb and the next cell's cb.  Leaves
-// get their body count here (a short search); internal cells in pass 4.
-#ifndef BUILD_WRITE_MIN_BLOCKS
-#define BUILD_WRITE_MIN_BLOCKS 2        // two 1024-thread blocks per SM (32 registers)
-#endif
-__global__ void __launch_bounds__(BUILD_THREADS, BUILD_WRITE_MIN_BLOCKS)
-k_build_write(const unsigned long long *__restrict__ sk, const uint8_t *__restrict__ sysid, int n,
-              int nleaf, int ncrit, const unsigned *__restrict__ blockcount, int nblocks, long long ccap,
-              DevState *st,
-              uint2 *cell_body, uint2 *cell_link, uint8_t *cell_level, uint32_t *cell_parent,
-              uint32_t *cell_done, uint32_t *cell_cb, uint2 *groups, uint8_t *group_lvl) {
-    extern __shared__ unsigned long long smem_u64[];
-    __shared__ unsigned s_wc[NROWS][32];
+// Pass 3 (over the entries of each body block): number every cell and write
+// its first body, level and link.  The cell of level r started by entry t
+// has index level_start[r] + (cells of level r started before t); it also
+// records cb = the number of level-(r+1) cells that start before t, offset to
+// level r+1's first index: for an internal cell that is its first child, and
+// the children of a cell are the level-(r+1) cells between its cb and the
+// next cell's cb.  Leaves get their body count here; internal cells in pass 4.
+constexpr int WRITE_THREADS = 256;
+
+__global__ void __launch_bounds__(WRITE_THREADS)
+k_build_write(const uint4 *__restrict__ entries, int ncrit, const unsigned *__restrict__ blockcount, int nblocks,
+              long long ccap, DevState *st, uint2 *cell_body, uint2 *cell_link, uint8_t *cell_level,
+              uint32_t *cell_parent, uint32_t *cell_done, uint32_t *cell_cb, uint2 *groups, uint8_t *group_lvl) {
+    constexpr int NW = WRITE_THREADS / 32;
+    __shared__ unsigned s_wc[NROWS][NW];
     __shared__ unsigned s_base[NROWS];
+    __shared__ unsigned s_tot[NROWS];
     __shared__ int s_ok;
-    const int base = blockIdx.x * BUILD_THREADS, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (st->status & ST_TIMEOUT) return;        // keys not sorted: skip the build
     if (warp == 0) {                             // level offsets: one lane per row
         const bool lvl = lane <= MAX_LEVEL;
@@ -321,77 +316,81 @@ k_build_write(const unsigned long long *__restrict__ sk, const uint8_t *__restri
     }
     __syncthreads();
     if (!s_ok) return;
-    BuildShared b = load_build_shared(smem_u64, sk, sysid, n, base);
-    const int t = base + tid;
-    const int send = system_end(st, sysid, t, n);
-    BodyCells bc = analyse_body(b, t, n, nleaf, ncrit, sk, send);
+    const unsigned ne = blockcount[(size_t)ENTRY_ROW * nblocks + blockIdx.x];
     const unsigned lt = (1u << lane) - 1u;
-    int rlo, rhi;
-    warp_level_range(bc, rlo, rhi);
-
-    if (lane <= MAX_LEVEL && (lane < rlo || lane > rhi)) s_wc[lane][warp] = 0u;
-    for (int r = rlo; r <= rhi; r++) {
-        const unsigned m = __ballot_sync(0xffffffffu, has_level(bc, r));
-        if (lane == 0) s_wc[r][warp] = __popc(m);
-    }
-    int gx = bc.ngrp;                            // inclusive warp scan of group counts
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, gx, o);
-        if (lane >= o) gx += y;
-    }
-    if (lane == 31) s_wc[GROUP_ROW][warp] = (unsigned)gx;
-    gx -= bc.ngrp;
-    __syncthreads();
-    constexpr int NW = BUILD_THREADS / 32;
-    for (int row = warp; row < NROWS; row += NW) {   // exclusive prefix across warps per row
-        unsigned v = lane < NW ? s_wc[row][lane] : 0u, x = v;
+    for (unsigned r0 = 0; r0 < ne; r0 += WRITE_THREADS) {   // rounds of entries (uniform)
+        const unsigned i = r0 + (unsigned)tid;
+        const bool valid = i < ne;
+        const uint4 e = valid ? entries[(size_t)blockIdx.x * BUILD_THREADS + i] : make_uint4(0u, 0u, 0u, 0u);
+        const int lo = valid ? (int)(e.w & 0xffu) : MAX_LEVEL + 1;
+        const int hi = valid ? (int)((e.w >> 8) & 0xffu) : -1;
+        const int lg = (int)((e.w >> 16) & 0xffu), kind = (int)(e.w >> 24);
+        const unsigned t = e.x;
+        const unsigned ngrp = kind == 1 ? 1u : kind == 2 ? (e.z + (unsigned)ncrit - 1u) / (unsigned)ncrit : 0u;
+        const int rlo = (int)__reduce_min_sync(0xffffffffu, (unsigned)lo);
+        const int rhi = (int)__reduce_max_sync(0xffffffffu, (unsigned)(hi + 1)) - 1;   // -1: no entry
+        if (lane <= MAX_LEVEL && (lane < rlo || lane > rhi)) s_wc[lane][warp] = 0u;
+        for (int r = rlo; r <= rhi; r++) {
+            const unsigned mm = __ballot_sync(0xffffffffu, lo <= r && r <= hi);
+            if (lane == 0) s_wc[r][warp] = __popc(mm);
+        }
+        unsigned gx = ngrp;                      // inclusive warp scan of group counts
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            unsigned y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+            const unsigned y = __shfl_up_sync(0xffffffffu, gx, o);
+            if (lane >= o) gx += y;
         }
-        __syncwarp();
-        if (lane < NW) s_wc[row][lane] = x - v;
-    }
-    __syncthreads();
-
-    unsigned bcur = rlo <= rhi ? __ballot_sync(0xffffffffu, has_level(bc, rlo)) : 0u;
-    for (int r = rlo; r <= rhi; r++) {
-        const unsigned bnext = r < MAX_LEVEL ? __ballot_sync(0xffffffffu, has_level(bc, r + 1)) : 0u;
-        if (has_level(bc, r)) {
-            const unsigned c = s_base[r] + s_wc[r][warp] + __popc(bcur & lt);
-            const unsigned cb = r < MAX_LEVEL ? s_base[r + 1] + s_wc[r + 1][warp] + __popc(bnext & lt) : 0u;
-            cell_cb[c] = cb;
-            cell_level[c] = (uint8_t)r;
-            cell_done[c] = 0u;
-            if (r == 0) cell_parent[c] = 0xffffffffu;
-            if (r == bc.hi) {
-                int cnt = b.run_end_at(sk, send, t, r) - t;
-                cell_body[c] = make_uint2((unsigned)t, (unsigned)cnt);
-                cell_link[c] = make_uint2((unsigned)t, (unsigned)cnt | LEAF_BIT);
+        if (lane == 31) s_wc[GROUP_ROW][warp] = gx;
+        gx -= ngrp;
+        __syncthreads();
+        for (int row = warp; row < NROWS; row += NW) {   // exclusive prefix across warps per row
+            const unsigned v = lane < NW ? s_wc[row][lane] : 0u;
+            unsigned x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane < NW) s_wc[row][lane] = x - v;
+            if (lane == NW - 1) s_tot[row] = x;
+        }
+        __syncthreads();
+        unsigned bcur = rlo <= rhi ? __ballot_sync(0xffffffffu, lo <= rlo && rlo <= hi) : 0u;
+        for (int r = rlo; r <= rhi; r++) {
+            const unsigned bnext = r < MAX_LEVEL ? __ballot_sync(0xffffffffu, lo <= r + 1 && r + 1 <= hi) : 0u;
+            if (lo <= r && r <= hi) {
+                const unsigned c = s_base[r] + s_wc[r][warp] + __popc(bcur & lt);
+                const unsigned cb = r < MAX_LEVEL ? s_base[r + 1] + s_wc[r + 1][warp] + __popc(bnext & lt) : 0u;
+                cell_cb[c] = cb;
+                cell_level[c] = (uint8_t)r;
+                cell_done[c] = 0u;
+                if (r == 0) cell_parent[c] = 0xffffffffu;
+                if (r == hi) {
+                    cell_body[c] = make_uint2(t, e.y);
+                    cell_link[c] = make_uint2(t, e.y | LEAF_BIT);
+                } else {
+                    cell_body[c] = make_uint2(t, 0u);
+                    cell_link[c] = make_uint2(cb, 0u);
+                }
+            }
+            bcur = bnext;
+        }
+        if (ngrp) {                              // groups in key order
+            const unsigned g = s_base[GROUP_ROW] + s_wc[GROUP_ROW][warp] + gx;
+            if (kind == 1) {
+                groups[g] = make_uint2(t, e.z);
+                if (group_lvl) group_lvl[g] = (uint8_t)lg;
             } else {
-                cell_body[c] = make_uint2((unsigned)t, 0u);
-                cell_link[c] = make_uint2(cb, 0u);
+                for (unsigned k = 0; k < ngrp; k++) {
+                    const unsigned b0 = t + k * (unsigned)ncrit;
+                    groups[g + k] = make_uint2(b0, min((unsigned)ncrit, e.z - k * (unsigned)ncrit));
+                    if (group_lvl) group_lvl[g + k] = 0xffu;
+                }
             }
         }
-        bcur = bnext;
-    }
-    // Groups in key order.
-    if (bc.ngrp > 0) {
-        unsigned g = s_base[GROUP_ROW] + s_wc[GROUP_ROW][warp] + (unsigned)gx;
-        if (bc.lg <= bc.hi) {
-            int e = b.run_end_at(sk, send, t, bc.lg);
-            groups[g] = make_uint2((unsigned)t, (unsigned)(e - t));
-            if (group_lvl) group_lvl[g] = (uint8_t)bc.lg;
-        } else {
-            int e = b.run_end_at(sk, send, t, bc.hi);
-            for (int k = 0; k < bc.ngrp; k++) {
-                int b0 = t + k * ncrit;
-                groups[g + k] = make_uint2((unsigned)b0, (unsigned)min(ncrit, e - b0));
-                if (group_lvl) group_lvl[g + k] = 0xffu;
-            }
-        }
+        __syncthreads();                         // s_wc is rebuilt by the next round
+        if (tid < NROWS) s_base[tid] += s_tot[tid];
+        __syncthreads();
     }
 }
 
@@ -546,19 +545,17 @@ k_group_pack(DevState *st, const uint2 *__restrict__ graw, const uint8_t *__rest
 
 cudaError_t launch_build(Ctx &c) {
     int n = (int)c.n;
-    size_t smem = build_smem_bytes(c.nleaf, c.ncrit);
-    k_build_count<<<c.nbblocks, BUILD_THREADS, smem, c.stream>>>(c.keys, c.sysid, n, c.nleaf, c.ncrit,
-                                                                 c.blockcount, c.nbblocks, c.st);
+    k_build_mark<<<c.nbblocks, BUILD_THREADS, 0, c.stream>>>(c.keys, c.sysid, n, c.nleaf, c.ncrit, c.blockcount,
+                                                             c.nbblocks, c.build_entries, c.st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_build_scan<<<NROWS, 1024, 0, c.stream>>>(c.blockcount, c.nbblocks, c.st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const bool pack = c.group_pack != 0;
-    k_build_write<<<c.nbblocks, BUILD_THREADS, smem, c.stream>>>(
-        c.keys, c.sysid, n, c.nleaf, c.ncrit, c.blockcount, c.nbblocks, c.ccap, c.st, c.cell_body,
-        c.cell_link, c.cell_level, c.cell_parent, c.cell_done, c.cell_cb, pack ? c.groups_raw : c.groups,
-        pack ? c.group_lvl : nullptr);
+    k_build_write<<<c.nbblocks, WRITE_THREADS, 0, c.stream>>>(
+        c.build_entries, c.ncrit, c.blockcount, c.nbblocks, c.ccap, c.st, c.cell_body, c.cell_link, c.cell_level,
+        c.cell_parent, c.cell_done, c.cell_cb, pack ? c.groups_raw : c.groups, pack ? c.group_lvl : nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (pack) {

@@ -37,6 +37,32 @@ def snapshots(n: int, plummer_seeds, rotations: int = 1, merger_seeds=(), rot_se
             k += 1
 
 
+def _rotated_plummer(args):
+    n, seed, rot_seed = args
+    return rotated(W.plummer(n, seed), rot_seed)
+
+
+def snapshots_parallel(n: int, plummer_seeds, rot_seed0: int = 7000, workers: int = 0):
+    """The rotated Plummer spheres of snapshots(n, plummer_seeds), generated
+    by a pool of host processes (spawned, so that no CUDA state is
+    inherited) and yielded in seed order as they are consumed."""
+    import multiprocessing as mp
+    import os
+    from concurrent.futures import ProcessPoolExecutor
+    seeds = list(plummer_seeds)
+    workers = workers or max(1, min(len(seeds), (os.cpu_count() or 2) - 1))
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        jobs = [(n, s, rot_seed0 + k) for k, s in enumerate(seeds)]
+        window = 2 * workers                  # bounded look-ahead: at most this many snapshots held
+        futs = [ex.submit(_rotated_plummer, j) for j in jobs[:window]]
+        for k in range(len(jobs)):
+            b = futs[k].result()
+            futs[k] = None
+            if k + window < len(jobs):
+                futs.append(ex.submit(_rotated_plummer, jobs[k + window]))
+            yield b
+
+
 def evolved(b: W.Bodies, steps: int, every: int, theta: float = 0.5, eps: float = 0.002,
             dt: float = 1.0 / 64, ncrit: int = 64):
     """Snapshots of a system stepped by the plain tree-code at theta: the

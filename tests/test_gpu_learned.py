@@ -193,38 +193,44 @@ def test_learned_step_graph_replay_matches_eager():
 
 def test_trained_network_gain_and_judged_fallback():
     """Train on rotated Plummer spheres and mergers (N = 2^16) at theta = 1,
-    evaluate on a held-out sphere.  The correction lowers the mean-square
-    residual it was trained on; with the budget set at 1.5x the theta = 0.5
-    p99 the judge rejects the coarse + learned forces and the fallback walk
-    delivers theta = 0.5 forces within the budget."""
+    evaluate on held-out systems (Plummer seed 4, a merger of seed 40).
+    Gain pin: on both, the correction lowers the mean-square residual it was
+    fit to and the 99th-percentile force error of the judge (4096 bodies,
+    direct sum) below that of plain theta = 1.  Fallback: with the budget
+    between the theta = 0.5 and the learned p99 the judge rejects the coarse
+    + learned forces and the fallback walk delivers theta = 0.5 forces within
+    the budget; with the budget above the learned p99 it keeps them."""
     n, eps = 1 << 16, 0.01
-    train = list(L.snapshots(n, range(10, 18), rotations=2, merger_seeds=(30, 31)))
+    train = list(L.snapshots(n, range(10, 26), rotations=2, merger_seeds=(30, 31, 32, 33)))
     X, Y = L.training_set(train, theta=1.0, eps=eps, per_snapshot=4096, ncrit=64)
-    net, losses = L.train(X, Y, epochs=40, batch=4096, lr=2e-3, wd=1e-4, seed=0)
+    net, losses = L.train(X, Y, epochs=60, batch=4096, lr=2e-3, wd=1e-4, seed=0)
     assert losses[-1] < losses[0]
-    held = W.plummer(n, 4)
-    with B.Bonsai(B.Config(ncrit=64)) as bz:
-        bz.set_bodies(held.pos, held.mass).build().multipoles()
-        # held-out mean-square residual, the quantity the network was fit to
-        Xh, Yh, _ = B.bonsai_learn_samples(bz.ctx, 1.0, eps, 4096, 99)
-        ysig = net.get_params()[1][-1]
-        mse0 = float(np.mean(Yh.astype(np.float64) ** 2))
-        mse1 = float(np.mean((Yh - ysig * net.predict(Xh)).astype(np.float64) ** 2))
-        bz.forces(1.0, eps)
-        p_plain = B.bonsai_judge(bz.ctx, eps)
-        B.bonsai_set_learned(bz.ctx, net, 1.0, 0.5, 1e30)
-        B.bonsai_forces_learned(bz.ctx, eps)
-        p_learned, fell = B.bonsai_get_judge(bz.ctx)
-        assert not fell
-        bz.forces(0.5, eps)
-        p_fine = B.bonsai_judge(bz.ctx, eps)
-        budget = 1.5 * p_fine
-        B.bonsai_set_learned(bz.ctx, net, 1.0, 0.5, budget)
-        B.bonsai_forces_learned(bz.ctx, eps)
-        p_judged, fell2 = B.bonsai_get_judge(bz.ctx)
-        p_after = B.bonsai_judge(bz.ctx, eps)
-    print(f"held-out mse {mse0:.4e} -> {mse1:.4e}; p99: theta=1 {p_plain:.4e}  "
-          f"theta=1+MLP {p_learned:.4e}  theta=0.5 {p_fine:.4e}")
-    assert mse1 < mse0
-    assert p_learned > budget and fell2 and p_judged == p_learned
-    assert p_after <= budget
+    ysig = net.get_params()[1][-1]
+    for held in (W.plummer(n, 4), W.merger(n, 40)):
+        with B.Bonsai(B.Config(ncrit=64)) as bz:
+            bz.set_bodies(held.pos, held.mass).build().multipoles()
+            Xh, Yh, _ = B.bonsai_learn_samples(bz.ctx, 1.0, eps, 4096, 99)
+            mse0 = float(np.mean(Yh.astype(np.float64) ** 2))
+            mse1 = float(np.mean((Yh - ysig * net.predict(Xh)).astype(np.float64) ** 2))
+            bz.forces(1.0, eps)
+            p_plain = B.bonsai_judge(bz.ctx, eps)
+            B.bonsai_set_learned(bz.ctx, net, 1.0, 0.5, 1e30)
+            B.bonsai_forces_learned(bz.ctx, eps)
+            p_learned, fell = B.bonsai_get_judge(bz.ctx)
+            assert not fell
+            bz.forces(0.5, eps)
+            p_fine = B.bonsai_judge(bz.ctx, eps)
+            print(f"held-out mse {mse0:.4e} -> {mse1:.4e}; p99: theta=1 {p_plain:.4e}  "
+                  f"theta=1+MLP {p_learned:.4e}  theta=0.5 {p_fine:.4e}")
+            assert mse1 < mse0
+            assert p_learned < p_plain                     # the gain pin
+            assert p_fine < p_learned
+            budget = (p_fine * p_learned) ** 0.5           # between theta = 0.5 and the learned p99
+            B.bonsai_set_learned(bz.ctx, net, 1.0, 0.5, budget)
+            B.bonsai_forces_learned(bz.ctx, eps)
+            p_judged, fell2 = B.bonsai_get_judge(bz.ctx)
+            assert fell2 and p_judged == p_learned
+            assert B.bonsai_judge(bz.ctx, eps) <= budget
+            B.bonsai_set_learned(bz.ctx, net, 1.0, 0.5, 1.01 * p_learned)
+            B.bonsai_forces_learned(bz.ctx, eps)
+            assert B.bonsai_get_judge(bz.ctx) == (p_learned, False)
