@@ -122,6 +122,7 @@ def parse():
     p.add_argument("--no-learned", action="store_true")
     p.add_argument("--no-block", action="store_true")
     p.add_argument("--no-sph", action="store_true")
+    p.add_argument("--no-sweep", action="store_true", help="leave the compact scaling record out of the bench line")
     p.add_argument("--learned-n", type=int, default=1 << 22)
     p.add_argument("--learned-plummer", type=int, default=100, help="Plummer training snapshots")
     p.add_argument("--learned-merger", type=int, default=100, help="merger training snapshots")
@@ -680,106 +681,140 @@ def run_block(a, dev, stream):
     return out
 
 
-def run_sweep(a, dev, stream):
-    """Scaling sweep (group knobs from the command line): Plummer spheres N = 2^15 .. 2^21 and 2^23 at
-    theta = 0.75 (interactions per body vs N), N = 2^22 (seed 2) and 2^24 (seed 3)
-    at theta in {0.5, 0.75, 1.0}; eps = 0.002, 5 KDK steps of dt = 1/256
-    after 2 untimed ones.  Per stage: device ms per step and algorithmic
-    GB/s against the measured copy bandwidth; walk FP32 rate against the
-    FP32 peak; FP64 energy drift over the timed steps; p99 force error of the
-    first evaluation at 4096 stratified bodies (the library's direct sum).
-    --sweep-cpu S adds the FP64 oracle's time per stage at theta = 0.75 on the
-    host cores (sorting + moving, build, multipoles, and the walk of a random
-    group sample of about S seconds extrapolated to N: the paper's Fig. 1)."""
+SWEEP_CASES = [(1 << k, 1, (0.75,)) for k in range(15, 22)] + [
+    (1 << 22, 2, (0.5, 0.75, 1.0)), (1 << 23, 1, (0.75,)), (1 << 24, 3, (0.5, 0.75, 1.0))]
+
+
+def sweep_case(a, dev, stream, b, n, seed, theta, cpu_budget=0.0):
+    """One (N, theta) case of the scaling sweep (group knobs from `a`):
+    eps = 0.002, 5 KDK steps of dt = 1/256 after 2 untimed ones (CUDA events,
+    L2 flushed between steps), then as many stage-timed steps.  Per stage:
+    device ms per step and algorithmic GB/s against the measured copy
+    bandwidth; walk FP32 rate against the measured FP32 peak; FP64 energy
+    drift over the timed steps; p99 force error of the first evaluation at
+    4096 stratified bodies (the library's direct sum)."""
     import numpy as np
     import torch
     import paper_1204_2280_gb300 as B
-    from paper_1204_2280_gb300 import workloads as W
     import ctypes as C
     hbm = measured_hbm_gbs()
     eps, dt, steps = 0.002, 1.0 / 256, 5
-    cases = [(1 << k, 1, (0.75,)) for k in range(15, 22)]
-    cases += [(1 << 22, 2, (0.5, 0.75, 1.0)), (1 << 23, 1, (0.75,)), (1 << 24, 3, (0.5, 0.75, 1.0))]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    tot = (C.c_ulonglong * 2)()
+    bz = B.Bonsai(B.Config(nleaf=a.nleaf, ncrit=a.ncrit, walk_warps=a.walk_warps, group_pack=a.group_pack,
+                           list_capacity=a.list_capacity), stream=stream)
+    bz.set_bodies(torch.from_numpy(b.pos).to(dev), torch.from_numpy(b.mass).to(dev),
+                  torch.from_numpy(b.vel).to(dev))
+    bz.build().multipoles().forces(theta, eps)
+    p99 = B.bonsai_judge(bz.ctx, eps)
+    d0 = B.bonsai_diagnostics(bz.ctx)
+    for _ in range(2):
+        bz.step(dt)
+    bz.sync()
+    ms, st, npc, npp = [], [], 0, 0
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bz.step(dt)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    d1 = B.bonsai_diagnostics(bz.ctx)
+    # stage times and interaction counts: as many further steps with stage
+    # events (the timed steps above run without them)
+    B.bonsai_set_stage_timing(bz.ctx, True)
+    for k in range(steps + 2):
+        flush.zero_()
+        bz.step(dt)
+        if k >= 2:
+            st.append(B.bonsai_get_stage_times(bz.ctx))
+            B._check(bz.ctx, B.lib().bonsai_get_counts(bz.ctx, None, None, tot))
+            npc += int(tot[0]); npp += int(tot[1])
+    _, ncells, ngroups = B.bonsai_get_sizes(bz.ctx)
+    bz.sync()
+    bz.close()
+    del flush
+    stage = dict(zip(B.STAGES, (np.array(st).sum(0) / steps).tolist()))
+    sb = stage_bytes(n, ncells, ngroups)
+    cpu = None
+    if cpu_budget > 0 and theta == 0.75:
+        # The paper's Fig. 1 stages on the FP64 oracle (host cores):
+        # sorting + moving, tree construction, multipoles, walk.
+        c = cpu_oracle_sample(b, theta, eps, a.nleaf, a.ncrit, cpu_budget, pack=a.group_pack, direct=False)
+        cs = c["stage_s"]
+        gpu_s = {"sort_move": (stage["keys"] + stage["sort"] + stage["reorder"]) / 1e3,
+                 "build": stage["build"] / 1e3, "multipoles": stage["multipoles"] / 1e3,
+                 "walk": stage["walk"] / 1e3}
+        cpu_s = {"sort_move": cs["domain_keys"] + cs["sort_reorder"], "build": cs["build"],
+                 "multipoles": cs["multipoles"], "walk": cs["walk"]}
+        cpu = {"cores": c["cores"], "stage_s": cpu_s, "gpu_stage_s": gpu_s,
+               "cpu_over_gpu": {k: cpu_s[k] / gpu_s[k] for k in cpu_s},
+               "sample": c["sample"]}
+    walk_s = stage["walk"] / 1e3
+    tflops = (FLOP_PC * npc + FLOP_PP * npp) / steps / walk_s / 1e12
+    t = sum(ms) / steps
+    return {
+        "mode": "sweep", "n": n, "seed": seed, "theta": theta, "eps": eps, "dt": dt,
+        "nleaf": a.nleaf, "ncrit": a.ncrit, "group_pack": a.group_pack, "walk_warps": a.walk_warps,
+        "list_capacity": a.list_capacity,
+        "steps": steps, "ms_per_step": t, "particles_per_s": n / (t / 1e3),
+        "stage_ms": stage,
+        "stage_gbs": {k: sb[k] / (stage[k] / 1e3) / 1e9 for k in sb if stage[k] > 0},
+        "stage_hbm_frac": {k: sb[k] / (stage[k] / 1e3) / 1e9 / hbm for k in sb if stage[k] > 0},
+        "sort_reorder_build_hbm_frac": sum(sb[k] for k in ("sort", "reorder", "build")) /
+            (sum(stage[k] for k in ("sort", "reorder", "build")) / 1e3) / 1e9 / hbm,
+        "walk_tflops": tflops, "walk_fp32_frac": tflops / fp32_peak_tflops(),
+        "interactions_per_body": {"pc": npc / (steps * n), "pp": npp / (steps * n)},
+        "interactions_per_s": (npc + npp) / steps / walk_s,
+        "ncells": ncells, "ngroups": ngroups,
+        "p99_acc_err_t0": p99,
+        "energy_drift": (d1[2] - d0[2]) / abs(d0[2]),
+        "hbm_peak_gbs": hbm, "fp32_peak_tflops": fp32_peak_tflops(), "oracle": cpu}
+
+
+def run_sweep(a, dev, stream):
+    """Scaling sweep (group knobs from the command line): Plummer spheres N =
+    2^15 .. 2^21 and 2^23 at theta = 0.75 (interactions per body vs N), N =
+    2^22 (seed 2) and 2^24 (seed 3) at theta in {0.5, 0.75, 1.0}; one JSON
+    line per case (sweep_case).  --sweep-cpu S adds the FP64 oracle's time
+    per stage at theta = 0.75 on the host cores (sorting + moving, build,
+    multipoles, and the walk of a random group sample of about S seconds
+    extrapolated to N: the paper's Fig. 1)."""
+    from paper_1204_2280_gb300 import workloads as W
+    cases = list(SWEEP_CASES)
     if a.sweep_sizes:
         keep = {1 << int(x) for x in a.sweep_sizes.split(",")}
         cases = [c for c in cases if c[0] in keep]
     if a.sweep_thetas:
         keep_t = {float(x) for x in a.sweep_thetas.split(",")}
         cases = [(n, s, tuple(t for t in th if t in keep_t)) for n, s, th in cases]
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    tot = (C.c_ulonglong * 2)()
     for n, seed, thetas in cases:
         b = W.plummer(n, seed)
         for theta in thetas:
-            bz = B.Bonsai(B.Config(nleaf=a.nleaf, ncrit=a.ncrit, walk_warps=a.walk_warps, group_pack=a.group_pack),
-                          stream=stream)
-            bz.set_bodies(torch.from_numpy(b.pos).to(dev), torch.from_numpy(b.mass).to(dev),
-                          torch.from_numpy(b.vel).to(dev))
-            bz.build().multipoles().forces(theta, eps)
-            p99 = B.bonsai_judge(bz.ctx, eps)
-            d0 = B.bonsai_diagnostics(bz.ctx)
-            for _ in range(2):
-                bz.step(dt)
-            bz.sync()
-            ms, st, npc, npp = [], [], 0, 0
-            for _ in range(steps):
-                flush.zero_()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                bz.step(dt)
-                e1.record(stream)
-                e1.synchronize()
-                ms.append(e0.elapsed_time(e1))
-            d1 = B.bonsai_diagnostics(bz.ctx)
-            # stage times and interaction counts: as many further steps with
-            # stage events (the timed steps above run without them)
-            B.bonsai_set_stage_timing(bz.ctx, True)
-            for k in range(steps + 2):
-                flush.zero_()
-                bz.step(dt)
-                if k >= 2:
-                    st.append(B.bonsai_get_stage_times(bz.ctx))
-                    B._check(bz.ctx, B.lib().bonsai_get_counts(bz.ctx, None, None, tot))
-                    npc += int(tot[0]); npp += int(tot[1])
-            _, ncells, ngroups = B.bonsai_get_sizes(bz.ctx)
-            bz.sync()
-            bz.close()
-            stage = dict(zip(B.STAGES, (np.array(st).sum(0) / steps).tolist()))
-            sb = stage_bytes(n, ncells, ngroups)
-            cpu = None
-            if a.sweep_cpu > 0 and theta == 0.75:
-                # The paper's Fig. 1 stages on the FP64 oracle (host cores):
-                # sorting + moving, tree construction, multipoles, walk.
-                c = cpu_oracle_sample(b, theta, eps, a.nleaf, a.ncrit, a.sweep_cpu, pack=a.group_pack, direct=False)
-                cs = c["stage_s"]
-                gpu_s = {"sort_move": (stage["keys"] + stage["sort"] + stage["reorder"]) / 1e3,
-                         "build": stage["build"] / 1e3, "multipoles": stage["multipoles"] / 1e3,
-                         "walk": stage["walk"] / 1e3}
-                cpu_s = {"sort_move": cs["domain_keys"] + cs["sort_reorder"], "build": cs["build"],
-                         "multipoles": cs["multipoles"], "walk": cs["walk"]}
-                cpu = {"cores": c["cores"], "stage_s": cpu_s, "gpu_stage_s": gpu_s,
-                       "cpu_over_gpu": {k: cpu_s[k] / gpu_s[k] for k in cpu_s},
-                       "sample": c["sample"]}
-            walk_s = stage["walk"] / 1e3
-            tflops = (FLOP_PC * npc + FLOP_PP * npp) / steps / walk_s / 1e12
-            t = sum(ms) / steps
-            print(json.dumps({
-                "mode": "sweep", "n": n, "seed": seed, "theta": theta, "eps": eps, "dt": dt,
-                "nleaf": a.nleaf, "ncrit": a.ncrit, "group_pack": a.group_pack, "walk_warps": a.walk_warps,
-                "steps": steps, "ms_per_step": t, "particles_per_s": n / (t / 1e3),
-                "stage_ms": stage,
-                "stage_gbs": {k: sb[k] / (stage[k] / 1e3) / 1e9 for k in sb if stage[k] > 0},
-                "stage_hbm_frac": {k: sb[k] / (stage[k] / 1e3) / 1e9 / hbm for k in sb if stage[k] > 0},
-                "sort_reorder_build_hbm_frac": sum(sb[k] for k in ("sort", "reorder", "build")) /
-                    (sum(stage[k] for k in ("sort", "reorder", "build")) / 1e3) / 1e9 / hbm,
-                "walk_tflops": tflops, "walk_fp32_frac": tflops / fp32_peak_tflops(),
-                "interactions_per_body": {"pc": npc / (steps * n), "pp": npp / (steps * n)},
-                "interactions_per_s": (npc + npp) / steps / walk_s,
-                "ncells": ncells, "ngroups": ngroups,
-                "p99_acc_err_t0": p99,
-                "energy_drift": (d1[2] - d0[2]) / abs(d0[2]),
-                "hbm_peak_gbs": hbm, "fp32_peak_tflops": fp32_peak_tflops(), "oracle": cpu}), flush=True)
+            print(json.dumps(sweep_case(a, dev, stream, b, n, seed, theta, a.sweep_cpu)), flush=True)
+
+
+def compact_sweep(a, dev, stream):
+    """The bench line's scaling record (the paper's Fig. 1 / Fig. 2 on this
+    GPU): the sweep's cases at theta = 0.75 for N = 2^16, 2^18, 2^22 and 2^24
+    (seeds as in the sweep) with the bench's tuned group knobs; per case the
+    step time, per-stage ms and algorithmic GB/s, the sort + reorder + build
+    fraction of the copy bandwidth, the walk's FP32 fraction and the
+    interactions per body."""
+    from paper_1204_2280_gb300 import workloads as W
+    out = []
+    keep = ("n", "seed", "ms_per_step", "particles_per_s", "stage_ms", "stage_gbs", "stage_hbm_frac",
+            "sort_reorder_build_hbm_frac", "walk_tflops", "walk_fp32_frac", "interactions_per_body",
+            "ncells", "ngroups", "p99_acc_err_t0")
+    for n, seed, _ in SWEEP_CASES:
+        if n in (1 << 16, 1 << 18, 1 << 22, 1 << 24):
+            r = sweep_case(a, dev, stream, W.plummer(n, seed), n, seed, 0.75)
+            out.append({k: r[k] for k in keep})
+    return {"theta": 0.75, "eps": 0.002, "dt": 1.0 / 256, "cases": out,
+            "what": "5 timed KDK steps per N after 2 untimed, stage times from as many stage-timed steps; "
+                    "GB/s are algorithmic bytes (STAGE_BYTES) over stage time"}
 
 
 def measured_hbm_gbs():
@@ -890,6 +925,7 @@ def run_ours(a, rank, world, local_rank):
                "what": "set_bodies(host pos, mass, vel) + build + multipoles + forces(host acc, pot)"}
     bz.close()
 
+    swp = compact_sweep(a, dev, stream) if (rank == 0 and not a.no_sweep) else None
     ens = None if a.no_ensemble else run_ensemble(a, dev, stream, rank, world)
     blk = None if a.no_block else run_block(a, dev, stream)
     sph = None if a.no_sph else run_sph(a, dev, stream)
@@ -926,6 +962,7 @@ def run_ours(a, rank, world, local_rank):
             "interactions_per_body": {"pc": sum(npc) / (n * a.steps), "pp": sum(npp) / (n * a.steps)},
             "interactions_per_s": (sum(npc) + sum(npp)) / (walk_ms / 1e3),
             "wall_s_timed_loop": t_wall,
+            "sweep": swp,
             "ensemble": ens,
             "block": blk,
             "sph": sph,

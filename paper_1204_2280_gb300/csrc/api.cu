@@ -69,7 +69,7 @@ cudaError_t alloc_bodies(Ctx &c, long long n) {
     a.take(c.id, n, plan); a.take(c.id_alt, n, plan); a.take(c.sysid, n, plan);
     a.take(c.keys, n, plan); a.take(c.keys_alt, n, plan);
     a.take(c.vals, n, plan); a.take(c.vals_alt, n, plan);
-    a.take(c.tile_status, (size_t)(SORT_PASSES + 1) * ntiles * 256, plan);
+    a.take(c.tile_status, (size_t)(SORT_PASSES + 1) * ntiles * SORT_RADIX, plan);
     a.take(c.blockcount, (size_t)BUILD_ROWS * nbb, plan);
     a.take(c.build_entries, (size_t)nbb * BUILD_THREADS, plan);
     a.take(c.cell_body, ccap, plan); a.take(c.cell_link, ccap, plan);

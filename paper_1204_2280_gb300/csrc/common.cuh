@@ -32,10 +32,16 @@ constexpr uint32_t LEAF_BIT = 0x80000000u;
 #ifndef SORT_ITEMS_CFG
 #define SORT_ITEMS_CFG 16
 #endif
-constexpr int SORT_THREADS = SORT_THREADS_CFG;          // >= 256: thread d owns digit d
+#ifndef SORT_BITS_CFG
+#define SORT_BITS_CFG 8
+#endif
+constexpr int SORT_THREADS = SORT_THREADS_CFG;          // >= 256 (a multiple of 32)
 constexpr int SORT_ITEMS = SORT_ITEMS_CFG;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;   // 4096 keys per tile
-constexpr int SORT_PASSES = 8;                         // 8-bit digits, 63-bit keys
+constexpr int SORT_BITS = SORT_BITS_CFG;               // digit width of a radix pass
+constexpr int SORT_RADIX = 1 << SORT_BITS;             // digit values (>= 256: the system-id pass)
+constexpr int SORT_PASSES = (63 + SORT_BITS - 1) / SORT_BITS;   // passes over the 63-bit keys
+constexpr int SORT_DPT = SORT_RADIX > SORT_THREADS ? SORT_RADIX / SORT_THREADS : 1;   // digits per owner thread
 constexpr int MAX_SYSTEMS = 256;                       // ensemble: one more pass on the system id
 constexpr int MLP_IN = 12, MLP_H = 64, MLP_OUT = 3;    // learned correction 12 -> 64 -> 64 -> 3
 constexpr int MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_OUT * MLP_H + MLP_OUT;
@@ -62,7 +68,7 @@ struct DevState {
     float side[MAX_SYSTEMS];          // per system: domain side S
     float scale[MAX_SYSTEMS];         // per system: 2^21 / S
     unsigned sys_off[MAX_SYSTEMS + 1];    // first body of each system (+ n)
-    unsigned hist[(SORT_PASSES + 1) * 256]; // digit histograms (+ system sizes)
+    unsigned hist[(SORT_PASSES + 1) * SORT_RADIX]; // digit histograms (+ system sizes)
     unsigned sort_tile[SORT_PASSES + 1];    // tile tickets per pass
     unsigned ncells, ngroups;
     unsigned row_total[NROWS];        // cells per level, groups
@@ -106,7 +112,7 @@ struct Ctx {
     // sort
     unsigned long long *keys = nullptr, *keys_alt = nullptr;
     uint32_t *vals = nullptr, *vals_alt = nullptr;   // vals ends as perm
-    unsigned *tile_status = nullptr;                   // (SORT_PASSES + 1) * ntiles * 256
+    unsigned *tile_status = nullptr;                   // (SORT_PASSES + 1) * ntiles * SORT_RADIX
     // build
     unsigned *blockcount = nullptr;  // BUILD_ROWS * nbblocks
     uint4 *build_entries = nullptr;  // per build block, the bodies that start cells (capacity n)

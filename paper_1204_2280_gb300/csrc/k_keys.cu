@@ -23,7 +23,7 @@ __global__ void k_reset(DevState *st, int what, int nsys) {
             st->dom[6 * sys + d] = 0x7fffffff;
             st->dom[6 * sys + 3 + d] = (int)0x80000000;
         }
-        for (int i = t; i < (SORT_PASSES + 1) * 256; i += blockDim.x) st->hist[i] = 0;
+        for (int i = t; i < (SORT_PASSES + 1) * SORT_RADIX; i += blockDim.x) st->hist[i] = 0;
         if (t < SORT_PASSES + 1) st->sort_tile[t] = 0;
     }
     if (what & 2) {                        // walk inputs
@@ -295,9 +295,9 @@ __global__ void k_domains(DevState *st, int nsys) {
             frexpf(S, &ex);                // S = 2^(ex-1)
             st->side[sys] = S;
             st->scale[sys] = ldexpf(1.f, KEY_BITS_PER_AXIS - (ex - 1));
-            st->hist[SORT_PASSES * 256 + sys] = st->sys_off[sys + 1] - st->sys_off[sys];
+            st->hist[SORT_PASSES * SORT_RADIX + sys] = st->sys_off[sys + 1] - st->sys_off[sys];
         } else {
-            st->hist[SORT_PASSES * 256 + sys] = 0u;
+            st->hist[SORT_PASSES * SORT_RADIX + sys] = 0u;
         }
     }
 }
@@ -316,9 +316,9 @@ constexpr int KEYS_ITEMS = 8;
 __global__ void __launch_bounds__(KEYS_THREADS)
 k_keys(const float4 *__restrict__ p, const uint8_t *__restrict__ sysid, int n, int nsys,
        DevState *st, unsigned long long *keys, unsigned *status0, int nstatus) {
-    __shared__ unsigned h[SORT_PASSES * 256];
+    __shared__ unsigned h[SORT_PASSES * SORT_RADIX];
     __shared__ float4 s_dom[MAX_SYSTEMS];   // mn xyz, scale
-    for (int i = threadIdx.x; i < SORT_PASSES * 256; i += blockDim.x) h[i] = 0;
+    for (int i = threadIdx.x; i < SORT_PASSES * SORT_RADIX; i += blockDim.x) h[i] = 0;
     for (int i = threadIdx.x; i < nsys; i += blockDim.x)
         s_dom[i] = make_float4(st->mn[3 * i], st->mn[3 * i + 1], st->mn[3 * i + 2], st->scale[i]);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nstatus; i += gridDim.x * blockDim.x)
@@ -339,11 +339,11 @@ k_keys(const float4 *__restrict__ p, const uint8_t *__restrict__ sysid, int n, i
             keys[i] = key;
 #pragma unroll
             for (int d = 0; d < SORT_PASSES; d++)
-                atomicAdd(&h[d * 256 + (unsigned)((key >> (8 * d)) & 0xffu)], 1u);
+                atomicAdd(&h[d * SORT_RADIX + (unsigned)((key >> (SORT_BITS * d)) & (SORT_RADIX - 1))], 1u);
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < SORT_PASSES * 256; i += blockDim.x)
+    for (int i = threadIdx.x; i < SORT_PASSES * SORT_RADIX; i += blockDim.x)
         if (h[i]) atomicAdd(&st->hist[i], h[i]);
 }
 
@@ -352,11 +352,13 @@ cudaError_t launch_keys(Ctx &c) {
     int per = KEYS_THREADS * KEYS_ITEMS;
     cudaError_t e = launch_domains(c);
     if (e != cudaSuccess) return e;
-    // With several systems the sort takes one more pass and so starts from
-    // the alternate buffer, to end in c.keys.
-    unsigned long long *out = c.nsys > 1 ? c.keys_alt : c.keys;
+    // The sort ping-pongs between c.keys and c.keys_alt and must end in
+    // c.keys: with an odd number of passes (one more on the system id for an
+    // ensemble) it starts from the alternate buffer.
+    const int npass = SORT_PASSES + (c.nsys > 1 ? 1 : 0);
+    unsigned long long *out = (npass & 1) ? c.keys_alt : c.keys;
     k_keys<<<(n + per - 1) / per, KEYS_THREADS, 0, c.stream>>>(c.pos4_alt, c.sysid, n, c.nsys, c.st, out,
-                                                              c.tile_status, c.ntiles * 256);
+                                                              c.tile_status, c.ntiles * SORT_RADIX);
     return cudaGetLastError();
 }
 

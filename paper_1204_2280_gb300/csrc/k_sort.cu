@@ -1,15 +1,17 @@
 // k_sort.cu -- stable LSD radix sort of (63-bit Morton key, u32 index).
 //
 // Paper Sect. 2, "sorting": bodies are ordered along the space-filling curve
-// by their keys; equal keys keep their input order (stable).  Eight passes of
-// 8-bit digits cover the 63 key bits.  Each pass is one "onesweep" launch:
-// the digit histograms of all passes come from the key kernel, so a pass
-// reads every key/value once and writes it once (24 B per body per pass):
+// by their keys; equal keys keep their input order (stable).  Passes of
+// SORT_BITS-bit digits (8 by default: eight passes) cover the 63 key bits.
+// Each pass is one "onesweep" launch: the digit histograms of all passes
+// come from the key kernel, so a pass reads every key/value once and writes
+// it once (24 B per body per pass):
 //   1. a tile of 4096 keys is taken in ticket order (atomic counter), loaded
 //      warp-striped and ranked per warp: peers with equal digits by ballots,
 //      counts by shared-memory atomics (stable: item order, then lane order,
 //      then warp order);
-//   2. per digit the tile count is published; the keys/values are reordered
+//   2. per digit the tile count is published (each owner thread holds
+//      SORT_DPT consecutive digits); the keys/values are reordered
 //      by digit in shared memory (tile-local offsets only), which frees their
 //      registers for the decoupled look-back that then finds the prefix over
 //      earlier tiles (bounded spin; on timeout a status bit is set and the
@@ -70,18 +72,19 @@ k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restric
            const unsigned *__restrict__ ghist, unsigned *status, unsigned *status_next,
            unsigned *ticket, int ntiles, DevState *st, long long max_spin,
            const uint8_t *__restrict__ dsrc) {
+    constexpr unsigned R = SORT_RADIX, DMASK = SORT_RADIX - 1;
     extern __shared__ unsigned long long s_keys[];                 // SORT_TILE keys
     uint32_t *s_vals = (uint32_t *)(s_keys + SORT_TILE);          // SORT_TILE values
-    __shared__ unsigned s_whist[SORT_THREADS / 32][256];
-    __shared__ unsigned s_dstart[256], s_goff[256], s_warp[SORT_THREADS / 32];
+    __shared__ unsigned s_whist[SORT_THREADS / 32][SORT_RADIX];
+    __shared__ unsigned s_dstart[SORT_RADIX], s_goff[SORT_RADIX], s_warp[SORT_THREADS / 32];
     __shared__ unsigned s_tile;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (status_next)
-        for (int i = blockIdx.x * SORT_THREADS + tid; i < ntiles * 256; i += gridDim.x * SORT_THREADS)
+        for (int i = blockIdx.x * SORT_THREADS + tid; i < ntiles * (int)R; i += gridDim.x * SORT_THREADS)
             status_next[i] = 0u;
     if (tid == 0) s_tile = atomicAdd(ticket, 1u);
-    for (int i = tid; i < (SORT_THREADS / 32) * 256; i += SORT_THREADS) (&s_whist[0][0])[i] = 0u;
+    for (int i = tid; i < (SORT_THREADS / 32) * (int)R; i += SORT_THREADS) (&s_whist[0][0])[i] = 0u;
     __syncthreads();
     const int tile = (int)s_tile;
     const int wbase = tile * SORT_TILE + warp * (SORT_ITEMS * 32);
@@ -96,14 +99,15 @@ k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restric
         k[it] = ok ? kin[idx] : ~0ull;
         v[it] = vin ? (ok ? vin[idx] : 0u) : (uint32_t)idx;
     }
-    // Digit of each item: a byte of the key, or (dsrc) the byte dsrc[value],
-    // the system id of the body's pre-sort position.
-    unsigned char dg[SORT_ITEMS];
+    // Digit of each item: SORT_BITS bits of the key, or (dsrc) the byte
+    // dsrc[value], the system id of the body's pre-sort position.
+    unsigned short dg[SORT_ITEMS];
 #pragma unroll
     for (int it = 0; it < SORT_ITEMS; it++)
-        dg[it] = dsrc ? (wbase + it * 32 + lane < n ? dsrc[v[it]] : 0) : (unsigned char)((k[it] >> shift) & 0xffu);
-    // Rank within the warp: peers with the same digit by 8 ballots; the
-    // lowest peer adds the peer count to the warp's digit counter with a
+        dg[it] = dsrc ? (unsigned short)(wbase + it * 32 + lane < n ? dsrc[v[it]] : 0)
+                      : (unsigned short)((k[it] >> shift) & DMASK);
+    // Rank within the warp: peers with the same digit by SORT_BITS ballots;
+    // the lowest peer adds the peer count to the warp's digit counter with a
     // shared-memory atomic that returns the count before it.  A warp's
     // atomics execute in program order, so item order (then lane order) is
     // kept: stable.  All atomics are issued before the first result is used.
@@ -112,17 +116,17 @@ k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restric
 #pragma unroll
     for (int it = 0; it < SORT_ITEMS; it++) {
         const int idx = wbase + it * 32 + lane;
-        const unsigned d = idx < n ? (unsigned)dg[it] : 256u;
-        unsigned peers = __ballot_sync(0xffffffffu, d < 256u);
-        if (d >= 256u) peers = ~peers;
+        const unsigned d = idx < n ? (unsigned)dg[it] : R;
+        unsigned peers = __ballot_sync(0xffffffffu, d < R);
+        if (d >= R) peers = ~peers;
 #pragma unroll
-        for (int bit = 0; bit < 8; bit++) {
+        for (int bit = 0; bit < SORT_BITS; bit++) {
             const bool on = (d >> bit) & 1u;
             const unsigned bm = __ballot_sync(0xffffffffu, on);
             peers &= on ? bm : ~bm;
         }
         pe[it] = peers;
-        old[it] = (d < 256u && (peers & lt) == 0u) ? atomicAdd(&s_whist[warp][d], (unsigned)__popc(peers)) : 0u;
+        old[it] = (d < R && (peers & lt) == 0u) ? atomicAdd(&s_whist[warp][d], (unsigned)__popc(peers)) : 0u;
     }
 #pragma unroll
     for (int it = 0; it < SORT_ITEMS; it++) {
@@ -131,31 +135,44 @@ k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restric
     }
     __syncthreads();
 
-    // Thread d < 256 owns digit d: exclusive prefix over warps, tile count.
-    const unsigned d = (unsigned)tid;
-    const bool owner = tid < 256;
-    unsigned run = 0;
-    if (owner) {
+    // Thread t owns the SORT_DPT consecutive digits from d0 = t * SORT_DPT:
+    // exclusive prefix over warps, tile counts, then block-wide digit starts.
+    const unsigned d0 = (unsigned)tid * SORT_DPT;
+    const bool owner = d0 < R;
+    unsigned tcount[SORT_DPT], gh[SORT_DPT];
+    unsigned tsum = 0, gsum = 0;
 #pragma unroll
-        for (int w = 0; w < SORT_THREADS / 32; w++) {
-            unsigned c = s_whist[w][d];
-            s_whist[w][d] = run;
-            run += c;
+    for (int q = 0; q < SORT_DPT; q++) {
+        unsigned run = 0;
+        if (owner) {
+#pragma unroll
+            for (int w = 0; w < SORT_THREADS / 32; w++) {
+                unsigned c = s_whist[w][d0 + q];
+                s_whist[w][d0 + q] = run;
+                run += c;
+            }
         }
+        tcount[q] = run;
+        gh[q] = owner ? ghist[d0 + q] : 0u;
+        tsum += run;
+        gsum += gh[q];
     }
-    const unsigned tcount = run;
-    unsigned dstart = block_excl_scan(tcount, s_warp);
-    unsigned gbase = block_excl_scan(owner ? ghist[d] : 0u, s_warp);
-    unsigned *my = status + (size_t)tile * 256 + d;
+    const unsigned dstart0 = block_excl_scan(tsum, s_warp);
+    const unsigned gbase0 = block_excl_scan(gsum, s_warp);
     // Testing aid (bonsai_debug_hold_sort_tile): a held tile publishes
     // nothing, so the look-back of the next tile runs into its bounded wait.
     // The positions a tile writes after giving up stay inside the output
     // (its prefix can only fall short of the true one).
     const bool held = st->hold_tile == (unsigned)tile + 1u;
     if (owner) {
-        s_dstart[d] = dstart;
-        // publish the tile's count first: later tiles look back meanwhile
-        if (!held) st_volatile(my, (tile == 0 ? FLAG_INC : FLAG_AGG) | tcount);
+        unsigned ds = dstart0;
+#pragma unroll
+        for (int q = 0; q < SORT_DPT; q++) {
+            s_dstart[d0 + q] = ds;
+            ds += tcount[q];
+            // publish the tile's count first: later tiles look back meanwhile
+            if (!held) st_volatile(status + (size_t)tile * R + d0 + q, (tile == 0 ? FLAG_INC : FLAG_AGG) | tcount[q]);
+        }
     }
     __syncthreads();
 
@@ -173,41 +190,47 @@ k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restric
         }
     }
     if (owner) {
-        // Decoupled look-back over earlier tiles for digit d.
-        unsigned prefix = 0;
-        if (tile > 0) {
-            // Look back LB tiles per round trip (independent loads), then
-            // consume them in order: aggregates are added, an inclusive
-            // prefix ends the look-back, an unpublished tile is polled again.
-            constexpr int LB = SORT_LOOKBACK;
-            int j = tile - 1;
-            long long spins = 0;
-            bool found = false;
-            while (!found) {
-                unsigned sv[LB];
+        unsigned gb = gbase0;
 #pragma unroll
-                for (int q = 0; q < LB; q++)
-                    sv[q] = j - q >= 0 ? ld_volatile(status + (size_t)(j - q) * 256 + d) : FLAG_INC;
-                int q = 0;
-                for (; q < LB; q++) {
-                    const unsigned f = sv[q] & ~VAL_MASK;
-                    if (f == 0u) break;
-                    prefix += sv[q] & VAL_MASK;
-                    if (f == FLAG_INC) { found = true; break; }
+        for (int q = 0; q < SORT_DPT; q++) {
+            const unsigned d = d0 + q;
+            // Decoupled look-back over earlier tiles for digit d.
+            unsigned prefix = 0;
+            if (tile > 0) {
+                // Look back LB tiles per round trip (independent loads), then
+                // consume them in order: aggregates are added, an inclusive
+                // prefix ends the look-back, an unpublished tile is polled again.
+                constexpr int LB = SORT_LOOKBACK;
+                int j = tile - 1;
+                long long spins = 0;
+                bool found = false;
+                while (!found) {
+                    unsigned sv[LB];
+#pragma unroll
+                    for (int qq = 0; qq < LB; qq++)
+                        sv[qq] = j - qq >= 0 ? ld_volatile(status + (size_t)(j - qq) * R + d) : FLAG_INC;
+                    int qq = 0;
+                    for (; qq < LB; qq++) {
+                        const unsigned f = sv[qq] & ~VAL_MASK;
+                        if (f == 0u) break;
+                        prefix += sv[qq] & VAL_MASK;
+                        if (f == FLAG_INC) { found = true; break; }
+                    }
+                    if (found) break;
+                    if (qq == 0 && ++spins > max_spin) { atomicOr(&st->status, ST_TIMEOUT); break; }
+                    j -= qq;
                 }
-                if (found) break;
-                if (q == 0 && ++spins > max_spin) { atomicOr(&st->status, ST_TIMEOUT); break; }
-                j -= q;
+                if (!held) st_volatile(status + (size_t)tile * R + d, FLAG_INC | ((prefix + tcount[q]) & VAL_MASK));
             }
-            if (!held) st_volatile(my, FLAG_INC | ((prefix + tcount) & VAL_MASK));
+            s_goff[d] = gb + prefix;
+            gb += gh[q];
         }
-        s_goff[d] = gbase + prefix;
     }
     __syncthreads();
     const int nvalid = min(SORT_TILE, n - tile * SORT_TILE);
     for (int p = tid; p < nvalid; p += SORT_THREADS) {
         unsigned long long key = s_keys[p];
-        unsigned dd = dsrc ? (unsigned)dsrc[s_vals[p]] : (unsigned)((key >> shift) & 0xffu);
+        unsigned dd = dsrc ? (unsigned)dsrc[s_vals[p]] : (unsigned)((key >> shift) & DMASK);
         unsigned g = s_goff[dd] + ((unsigned)p - s_dstart[dd]);
         kout[g] = key;
         vout[g] = s_vals[p];
@@ -217,10 +240,10 @@ k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restric
 constexpr size_t SORT_DYN_SMEM = (size_t)SORT_TILE * (sizeof(unsigned long long) + sizeof(uint32_t));
 extern const size_t SORT_DYN_SMEM_BYTES = SORT_DYN_SMEM;
 
-// 8 passes over the key bytes; with several systems a 9th stable pass on the
-// system id groups the bodies by system (key order inside each).  Buffers
-// alternate so that the result always lands in c.keys / c.vals (the key
-// kernel writes to c.keys_alt when there are 9 passes).
+// SORT_PASSES passes over the key digits; with several systems one more
+// stable pass on the system id groups the bodies by system (key order inside
+// each).  Buffers alternate so that the result always lands in c.keys /
+// c.vals (the key kernel writes to c.keys_alt for an odd number of passes).
 cudaError_t launch_sort(Ctx &c) {
     static size_t attr_done[MAX_DEVICES] = {};
     cudaError_t ea = allow_dyn_smem((const void *)k_onesweep, SORT_DYN_SMEM, attr_done);
@@ -230,12 +253,12 @@ cudaError_t launch_sort(Ctx &c) {
     const int start = npass & 1;
     unsigned long long *kb[2] = {c.keys, c.keys_alt};
     uint32_t *vb[2] = {c.vals, c.vals_alt};
-    const size_t plane = (size_t)c.ntiles * 256;
+    const size_t plane = (size_t)c.ntiles * SORT_RADIX;
     for (int p = 0; p < npass; p++) {
         const int src = (p + start) & 1, dst = src ^ 1;
         k_onesweep<<<c.ntiles, SORT_THREADS, SORT_DYN_SMEM, c.stream>>>(
-            kb[src], p == 0 ? nullptr : vb[src], kb[dst], vb[dst], n, p < SORT_PASSES ? 8 * p : 0,
-            c.st->hist + 256 * p,
+            kb[src], p == 0 ? nullptr : vb[src], kb[dst], vb[dst], n, p < SORT_PASSES ? SORT_BITS * p : 0,
+            c.st->hist + SORT_RADIX * p,
             c.tile_status + plane * p, p + 1 < npass ? c.tile_status + plane * (p + 1) : nullptr,
             c.st->sort_tile + p, c.ntiles, c.st, c.max_spin, p == SORT_PASSES ? c.sysid : nullptr);
         cudaError_t e = cudaGetLastError();

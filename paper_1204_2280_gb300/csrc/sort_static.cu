@@ -35,7 +35,7 @@ struct StaticSortScratch {
     DevState st;                                                 // histograms, tickets, status
     unsigned long long keys_alt[STATIC_SORT_MAX_N];
     uint32_t vals_alt[STATIC_SORT_MAX_N];
-    unsigned tile_status[SORT_PASSES * STATIC_SORT_TILES * 256];
+    unsigned tile_status[SORT_PASSES * STATIC_SORT_TILES * SORT_RADIX];
 };
 
 // Device-resident scratch.  Host code must never pass this name to a kernel:
@@ -47,23 +47,24 @@ static __device__ __align__(256) StaticSortScratch g_sort_scratch;
 // histograms of the keys.
 __global__ void k_static_clear(StaticSortScratch *s) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    for (int i = t; i < SORT_PASSES * 256; i += gridDim.x * blockDim.x) s->st.hist[i] = 0u;
-    for (int i = t; i < STATIC_SORT_TILES * 256; i += gridDim.x * blockDim.x) s->tile_status[i] = 0u;
+    for (int i = t; i < SORT_PASSES * SORT_RADIX; i += gridDim.x * blockDim.x) s->st.hist[i] = 0u;
+    for (int i = t; i < STATIC_SORT_TILES * SORT_RADIX; i += gridDim.x * blockDim.x) s->tile_status[i] = 0u;
     if (t < SORT_PASSES) s->st.sort_tile[t] = 0u;
     if (t == 0) { s->st.status = 0u; s->st.hold_tile = 0u; }
 }
 
 __global__ void k_static_hist(const unsigned long long *__restrict__ keys, int n, StaticSortScratch *s) {
-    __shared__ unsigned h[SORT_PASSES * 256];
-    for (int i = threadIdx.x; i < SORT_PASSES * 256; i += blockDim.x) h[i] = 0u;
+    __shared__ unsigned h[SORT_PASSES * SORT_RADIX];
+    for (int i = threadIdx.x; i < SORT_PASSES * SORT_RADIX; i += blockDim.x) h[i] = 0u;
     __syncthreads();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         unsigned long long k = keys[i];
 #pragma unroll
-        for (int d = 0; d < SORT_PASSES; d++) atomicAdd(&h[d * 256 + (unsigned)((k >> (8 * d)) & 0xffu)], 1u);
+        for (int d = 0; d < SORT_PASSES; d++)
+            atomicAdd(&h[d * SORT_RADIX + (unsigned)((k >> (SORT_BITS * d)) & (SORT_RADIX - 1))], 1u);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < SORT_PASSES * 256; i += blockDim.x)
+    for (int i = threadIdx.x; i < SORT_PASSES * SORT_RADIX; i += blockDim.x)
         if (h[i]) atomicAdd(&s->st.hist[i], h[i]);
 }
 
@@ -117,18 +118,19 @@ extern "C" int bonsai_sort_keys_static(const uint64_t *keys, uint64_t *sorted_ke
     const int nn = (int)n, ntiles = (nn + SORT_TILE - 1) / SORT_TILE;
     k_static_clear<<<16, 256, 0, st>>>(s);
     k_static_hist<<<16, 256, 0, st>>>((const unsigned long long *)keys, nn, s);
-    // Ping-pong between the scratch and the caller's output buffers; pass 7
-    // (odd) lands in the outputs.
+    // Ping-pong between the scratch and the caller's output buffers so that
+    // the last pass lands in the outputs: pass p reads buffer set p (the
+    // caller's keys for p = 0) and writes set p + 1, where set j >= 1 is the
+    // outputs when SORT_PASSES - j is even and the scratch otherwise.
     unsigned long long *kb[2] = {(unsigned long long *)sorted_keys, s->keys_alt};
     uint32_t *vb[2] = {perm, s->vals_alt};
-    const size_t plane = (size_t)STATIC_SORT_TILES * 256;
-    // Pass p reads buffer p & 1 (the caller's keys for p = 0) and writes
-    // buffer 1 - (p & 1).
+    const size_t plane = (size_t)STATIC_SORT_TILES * SORT_RADIX;
     for (int p = 0; p < SORT_PASSES; p++) {
-        const unsigned long long *kin = p == 0 ? (const unsigned long long *)keys : kb[p & 1];
-        const uint32_t *vin = p == 0 ? nullptr : vb[p & 1];
+        const int in_set = (SORT_PASSES - p) & 1, out_set = (SORT_PASSES - p - 1) & 1;
+        const unsigned long long *kin = p == 0 ? (const unsigned long long *)keys : kb[in_set];
+        const uint32_t *vin = p == 0 ? nullptr : vb[in_set];
         k_onesweep<<<ntiles, SORT_THREADS, SORT_DYN_SMEM_BYTES, st>>>(
-            kin, vin, kb[1 - (p & 1)], vb[1 - (p & 1)], nn, 8 * p, s->st.hist + 256 * p,
+            kin, vin, kb[out_set], vb[out_set], nn, SORT_BITS * p, s->st.hist + SORT_RADIX * p,
             s->tile_status + plane * p, p + 1 < SORT_PASSES ? s->tile_status + plane * (p + 1) : nullptr,
             s->st.sort_tile + p, ntiles, &s->st, 1ll << 24, nullptr);
     }
