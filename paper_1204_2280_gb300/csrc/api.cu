@@ -81,7 +81,8 @@ cudaError_t alloc_bodies(Ctx &c, long long n) {
     a.take(c.groups, n, plan); a.take(c.groups_raw, n, plan);
     a.take(c.group_lvl, n, plan); a.take(c.group_flag, n, plan); a.take(c.group_bcount, (n + PACK_THREADS - 1) / PACK_THREADS, plan);
     a.take(c.counts, n, plan); a.take(c.feat, FEAT_STRIDE * (size_t)n, plan);
-    a.take(c.stage, 7 * (size_t)n, plan);
+    const long long stage_floats = 7 * n > STAGE_MIN_FLOATS ? 7 * n : STAGE_MIN_FLOATS;
+    a.take(c.stage, (size_t)stage_floats, plan);
     a.take(c.judge_targets, JUDGE_MAX, plan); a.take(c.judge_direct, JUDGE_MAX, plan);
     a.take(c.judge_partial, (size_t)JUDGE_SPLIT * JUDGE_MAX, plan);
     char *base = nullptr;
@@ -90,6 +91,7 @@ cudaError_t alloc_bodies(Ctx &c, long long n) {
     if (e != cudaSuccess) return e;
     for (auto &p : plan) *p.first = base + p.second;
     c.ncap = n;
+    c.stage_floats = stage_floats;
     c.ntiles = (int)ntiles;
     c.nbblocks = (int)nbb;
     c.ccap = ccap;
@@ -604,7 +606,8 @@ int bonsai_get_keys(bonsai_ctx *ctx, uint64_t *keys, uint32_t *perm) {
 }
 
 // The introspection getters stream the cells through the context's staging
-// area (7 floats per body) in chunks: no allocation per call.
+// area (7 floats per body, at least STAGE_MIN_FLOATS) in chunks of at least
+// 409 cells: no allocation per call.
 int bonsai_get_tree(bonsai_ctx *ctx, int32_t *bb, int32_t *bc, int32_t *cb, int32_t *nc, int32_t *lv) {
     if (!ctx || !bb || !bc || !cb || !nc || !lv) return BONSAI_ERR_INVALID_ARG;
     Ctx &c = ctx->c;
@@ -612,7 +615,7 @@ int bonsai_get_tree(bonsai_ctx *ctx, int32_t *bb, int32_t *bc, int32_t *cb, int3
     int r = read_state(ctx);
     if (r) return r;
     const unsigned ncells = c.st_host->ncells;
-    const unsigned chunk = (unsigned)((7 * c.n) / 5);
+    const unsigned chunk = (unsigned)(c.stage_floats / 5);       // 5 int32 per cell
     int32_t *tmp = reinterpret_cast<int32_t *>(c.stage);
     int32_t *dst[5] = {bb, bc, cb, nc, lv};
     for (unsigned c0 = 0; c0 < ncells; c0 += chunk) {
@@ -647,7 +650,7 @@ int bonsai_get_moments(bonsai_ctx *ctx, float *mono, float *quad) {
     int r = read_state(ctx);
     if (r) return r;
     const unsigned ncells = c.st_host->ncells;
-    const unsigned chunk = (unsigned)((7 * c.n) / 10);
+    const unsigned chunk = (unsigned)(c.stage_floats / 10);      // 10 floats per cell
     float *tmp = c.stage;
     for (unsigned c0 = 0; c0 < ncells; c0 += chunk) {
         const unsigned cnt = ncells - c0 < chunk ? ncells - c0 : chunk;

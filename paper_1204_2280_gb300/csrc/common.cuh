@@ -54,6 +54,7 @@ constexpr int JUDGE_SPLIT = 64;                        // source splits of the j
 #endif
 constexpr int BUILD_THREADS = BUILD_THREADS_CFG;       // bodies per build block (multiple of 32, <= 1024)
 constexpr int PACK_THREADS = 1024;                     // unpacked groups per group-packing block
+constexpr long long STAGE_MIN_FLOATS = 4096;           // staging area floor (getters stream cells through it)
 constexpr int ENTRY_ROW = NROWS;                       // build: entries per block (a row that is not scanned)
 constexpr int BUILD_ROWS = NROWS + 1;                  // build: per-block count rows
 
@@ -134,7 +135,8 @@ struct Ctx {
     uint2 *counts = nullptr;         // per body (n_pc, n_pp), sorted order
     float *feat = nullptr;           // per body FEAT_STRIDE walk features (learned correction), sorted order
     // staging for host transfers and caller-order outputs
-    float *stage = nullptr;          // 7 floats per body
+    float *stage = nullptr;          // 7 floats per body, at least STAGE_MIN_FLOATS
+    long long stage_floats = 0;      // its size
     DevState *st = nullptr;          // device
     DevState *st_host = nullptr;     // pinned mirror for reads
 
