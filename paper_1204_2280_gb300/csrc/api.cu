@@ -615,6 +615,7 @@ int bonsai_get_tree(bonsai_ctx *ctx, int32_t *bb, int32_t *bc, int32_t *cb, int3
     int r = read_state(ctx);
     if (r) return r;
     const unsigned ncells = c.st_host->ncells;
+    CK(launch_internal_counts(c));
     const unsigned chunk = (unsigned)(c.stage_floats / 5);       // 5 int32 per cell
     int32_t *tmp = reinterpret_cast<int32_t *>(c.stage);
     int32_t *dst[5] = {bb, bc, cb, nc, lv};

@@ -248,6 +248,7 @@ cudaError_t launch_keys(Ctx &c);
 cudaError_t launch_sort(Ctx &c);
 cudaError_t launch_reorder(Ctx &c);
 cudaError_t launch_build(Ctx &c);
+cudaError_t launch_internal_counts(Ctx &c);
 cudaError_t launch_multipoles(Ctx &c, float theta = 0.f);
 cudaError_t launch_multipoles_refit(Ctx &c);
 cudaError_t launch_cell_cubes(Ctx &c);

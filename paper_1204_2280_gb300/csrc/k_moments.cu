@@ -103,20 +103,6 @@ __device__ __forceinline__ void root_terms(unsigned c, const Mom32 &m, unsigned 
     t[9] = m.q[5] + M * (3 * ey * ez);
 }
 
-// Sums over the MG lanes of a cell's lane group (xor butterfly: every lane
-// ends with the same value, the adds being commutative).
-constexpr int MG = 8;   // lanes per cell: a leaf's bodies, a parent's (<= 8) children
-__device__ __forceinline__ float group_sum(float v, unsigned gm) {
-#pragma unroll
-    for (int o = MG / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gm, v, o);
-    return v;
-}
-__device__ __forceinline__ float group_max(float v, unsigned gm) {
-#pragma unroll
-    for (int o = MG / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(gm, v, o));
-    return v;
-}
-
 // REFIT (block time steps, between rebuilds): the bodies may have left the
 // cells they were sorted into.  Each cell also gets ext = half side of a cube
 // about its build-time centre that holds its bodies (at least l/2; a leaf
@@ -124,15 +110,9 @@ __device__ __forceinline__ float group_max(float v, unsigned gm) {
 // ext_k)), stored with the centre in cext, and delta holds (|com - centre|,
 // 2 ext): the opening radius 2 ext / theta + delta then keeps every cell that
 // holds a body of a group opened for it (theta < 2 / sqrt(3)).
-//
-// One cell per group of MG lanes (sl = lane within the group, gm = the
-// group's lane mask): a leaf's bodies are spread over the lanes and its sums
-// reduced by shuffles; each parent's children (at most eight) are loaded and
-// combined one per lane.  The group's first lane stores and takes the
-// arrival atomics.
 template <bool REFIT>
-__device__ __forceinline__ void multipole_cell(unsigned c, int sl, unsigned gm, const DevState *__restrict__ stc,
-                                               const uint2 *__restrict__ cell_link,
+__device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__restrict__ stc, DevState *st,
+                                               const uint2 *__restrict__ cell_body, const uint2 *__restrict__ cell_link,
                                                const uint8_t *__restrict__ cell_level,
                                                const uint32_t *__restrict__ cell_parent, uint32_t *cell_done,
                                                const float4 *__restrict__ pos4, const unsigned long long *__restrict__ sk,
@@ -141,36 +121,40 @@ __device__ __forceinline__ void multipole_cell(unsigned c, int sl, unsigned gm, 
                                                float4 *test, float inv_theta) {
     uint2 link = cell_link[c];
     if (!(link.y & LEAF_BIT)) return;
-    const int leader = (threadIdx.x & 31) & ~(MG - 1);
 
     // Leaf from its bodies in one pass: mass, first and second moments of
     // the offsets u = x - x0 from the first body; then with c = s/M the
     // central moments C = S - s c^T and Q = 3C - tr(C) I.  The offsets are
     // at most the cell size, so nothing cancels beyond FP32 rounding.
-    const unsigned b = link.x, cnt = link.y & ~LEAF_BIT;
+    unsigned b = link.x, cnt = link.y & ~LEAF_BIT;
     int lev = cell_level[c];                         // level and parent, for the climb
     unsigned p = lev != 0 ? cell_parent[c] : 0u;
-    const float4 x0 = pos4[b];
+    float4 x0 = pos4[b];
     float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
     float sxx = 0.f, syy = 0.f, szz = 0.f, sxy = 0.f, sxz = 0.f, syz = 0.f;
     float3 ctr = make_float3(0.f, 0.f, 0.f);
     float ext = 0.f;
-    if (REFIT) ext = 0.5f * cell_cube(sk[b], lev, sysid[b], stc, ctr);
-    for (unsigned j = b + sl; j < b + cnt; j += MG) {
-        const float4 q = pos4[j];
-        if (REFIT) ext = fmaxf(ext, dist_inf(make_float3(q.x, q.y, q.z), ctr));
-        const float ux = q.x - x0.x, uy = q.y - x0.y, uz = q.z - x0.z;
-        const float wx = q.w * ux, wy = q.w * uy, wz = q.w * uz;
-        M += q.w;
-        sx += wx; sy += wy; sz += wz;
-        sxx = fmaf(wx, ux, sxx); syy = fmaf(wy, uy, syy); szz = fmaf(wz, uz, szz);
-        sxy = fmaf(wx, uy, sxy); sxz = fmaf(wx, uz, sxz); syz = fmaf(wy, uz, syz);
+    if (REFIT) ext = 0.5f * cell_cube(sk[b], cell_level[c], sysid[b], stc, ctr);
+    // The bodies' loads are issued LB at a time (one round trip per LB
+    // bodies instead of one per body); the sums still run in body order.
+    constexpr unsigned LB = 4;
+    for (unsigned j0 = b; j0 < b + cnt; j0 += LB) {
+        float4 pb[LB];
+#pragma unroll
+        for (unsigned u = 0; u < LB; u++) pb[u] = j0 + u < b + cnt ? pos4[j0 + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (unsigned u = 0; u < LB; u++) {
+            if (j0 + u >= b + cnt) break;
+            const float4 p = pb[u];
+            if (REFIT) ext = fmaxf(ext, dist_inf(make_float3(p.x, p.y, p.z), ctr));
+            const float ux = p.x - x0.x, uy = p.y - x0.y, uz = p.z - x0.z;
+            const float wx = p.w * ux, wy = p.w * uy, wz = p.w * uz;
+            M += p.w;
+            sx += wx; sy += wy; sz += wz;
+            sxx = fmaf(wx, ux, sxx); syy = fmaf(wy, uy, syy); szz = fmaf(wz, uz, szz);
+            sxy = fmaf(wx, uy, sxy); sxz = fmaf(wx, uz, sxz); syz = fmaf(wy, uz, syz);
+        }
     }
-    M = group_sum(M, gm);
-    sx = group_sum(sx, gm); sy = group_sum(sy, gm); sz = group_sum(sz, gm);
-    sxx = group_sum(sxx, gm); syy = group_sum(syy, gm); szz = group_sum(szz, gm);
-    sxy = group_sum(sxy, gm); sxz = group_sum(sxz, gm); syz = group_sum(syz, gm);
-    if (REFIT) ext = group_max(ext, gm);
     Mom32 m;
     m.M = M;
     const float inv = M > 0.f ? 1.f / M : 0.f;
@@ -180,22 +164,19 @@ __device__ __forceinline__ void multipole_cell(unsigned c, int sl, unsigned gm, 
     const float tr = Cxx + Cyy + Czz;
     m.q[0] = 3.f * Cxx - tr; m.q[1] = 3.f * Cyy - tr; m.q[2] = 3.f * Czz - tr;
     m.q[3] = 3.f * fmaf(-sx, cy, sxy); m.q[4] = 3.f * fmaf(-sx, cz, sxz); m.q[5] = 3.f * fmaf(-sy, cz, syz);
+    store32(c, m, mono, qa, qb);
     // The first body's key shares the key prefix of the leaf and of every
     // ancestor: it gives every geometric centre on the way up.
     const unsigned long long kb = sk[b];
     const int sysb = sysid[b];
-    if (sl == 0) {
-        store32(c, m, mono, qa, qb);
-        if (REFIT) {
-            put_delta(c, m, make_float2(com_offset(make_float3(m.x, m.y, m.z), ctr), 2.f * ext), delta, test,
-                      inv_theta);
-            cext[c] = make_float4(ctr.x, ctr.y, ctr.z, ext);
-        } else {
-            put_delta(c, m, cell_delta(kb, lev, sysb, make_float3(m.x, m.y, m.z), stc), delta, test, inv_theta);
-        }
+    if (REFIT) {
+        put_delta(c, m, make_float2(com_offset(make_float3(m.x, m.y, m.z), ctr), 2.f * ext), delta, test, inv_theta);
+        cext[c] = make_float4(ctr.x, ctr.y, ctr.z, ext);
+    } else {
+        put_delta(c, m, cell_delta(kb, lev, sysb, make_float3(m.x, m.y, m.z), stc), delta, test, inv_theta);
     }
 
-    // Up the tree while this group holds the last child to finish (roots are
+    // Up the tree while this thread is the last child to finish (roots are
     // the level-0 cells, one per system).  The tree is read-only here: the
     // parent's link and level and the next parent are loaded with the
     // arrival atomic, so only the children's moments wait for its acquire.
@@ -203,23 +184,17 @@ __device__ __forceinline__ void multipole_cell(unsigned c, int sl, unsigned gm, 
         const uint2 plk = cell_link[p];          // (first child, child count) of the parent
         const int lv = cell_level[p];
         const unsigned gp = lv != 0 ? cell_parent[p] : 0u;
-        if (lev == 1 && sl == 0) root_terms(c, m, kb, sysb, stc, shadow);
-        // Release: this cell's moments (stored by the group's first lane)
-        // are visible to whoever reads the counter after this add; acquire:
-        // the last child to arrive sees every sibling's moments (each
-        // sibling's add heads a release sequence that this read-modify-write
-        // extends), and the warp barrier passes that view to the group.
-        unsigned old = 0u;
-        if (sl == 0) old = atom_add_acq_rel_gpu(&cell_done[p], 1u);
-        old = __shfl_sync(gm, old, leader);
-        if (old != plk.y - 1u) return;
-        __syncwarp(gm);
+        if (lev == 1) root_terms(c, m, kb, sysb, stc, shadow);
+        // Release: this cell's moments are visible to whoever reads the
+        // counter after this add; acquire: the last child to arrive sees
+        // every sibling's moments (each sibling's add heads a release
+        // sequence that this read-modify-write extends).
+        if (atom_add_acq_rel_gpu(&cell_done[p], 1u) != plk.y - 1u) return;
         c = p;
         p = gp;
         const unsigned cb = plk.x, nch = plk.y;
         lev = lv;
         if (lv == 0) {
-            if (sl != 0) return;
             float3 o;
             cell_cube(kb, 0, sysb, stc, o);
             double t[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -229,103 +204,108 @@ __device__ __forceinline__ void multipole_cell(unsigned c, int sl, unsigned gm, 
                 for (int i = 0; i < 10; i++) t[i] += __ldcg(sk2 + i);
             }
             const double inv2 = t[0] > 0 ? 1.0 / t[0] : 0.0;
-            const double sx2 = t[1] * inv2, sy2 = t[2] * inv2, sz2 = t[3] * inv2;   // com - O
-            const double s2 = sx2 * sx2 + sy2 * sy2 + sz2 * sz2;
+            const double sx = t[1] * inv2, sy = t[2] * inv2, sz = t[3] * inv2;   // com - O
+            const double s2 = sx * sx + sy * sy + sz * sz;
             m.M = (float)t[0];
-            m.x = (float)(o.x + sx2); m.y = (float)(o.y + sy2); m.z = (float)(o.z + sz2);
-            m.q[0] = (float)(t[4] - t[0] * (3 * sx2 * sx2 - s2));
-            m.q[1] = (float)(t[5] - t[0] * (3 * sy2 * sy2 - s2));
-            m.q[2] = (float)(t[6] - t[0] * (3 * sz2 * sz2 - s2));
-            m.q[3] = (float)(t[7] - t[0] * (3 * sx2 * sy2));
-            m.q[4] = (float)(t[8] - t[0] * (3 * sx2 * sz2));
-            m.q[5] = (float)(t[9] - t[0] * (3 * sy2 * sz2));
+            m.x = (float)(o.x + sx); m.y = (float)(o.y + sy); m.z = (float)(o.z + sz);
+            m.q[0] = (float)(t[4] - t[0] * (3 * sx * sx - s2));
+            m.q[1] = (float)(t[5] - t[0] * (3 * sy * sy - s2));
+            m.q[2] = (float)(t[6] - t[0] * (3 * sz * sz - s2));
+            m.q[3] = (float)(t[7] - t[0] * (3 * sx * sy));
+            m.q[4] = (float)(t[8] - t[0] * (3 * sx * sz));
+            m.q[5] = (float)(t[9] - t[0] * (3 * sy * sz));
         } else {
-            // Child sl of the parent on lane sl: mass and com first (about
-            // the first child's com), then the parallel-axis terms.
-            const bool mine = (unsigned)sl < nch;
-            const float4 mo = mine ? __ldcg(mono + cb + sl) : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 a = mine ? __ldcg(qa + cb + sl) : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float2 q2 = mine ? __ldcg(qb + cb + sl) : make_float2(0.f, 0.f);
-            const float c0x = __shfl_sync(gm, mo.x, leader), c0y = __shfl_sync(gm, mo.y, leader),
-                        c0z = __shfl_sync(gm, mo.z, leader);
-            const float fM = group_sum(mo.w, gm);
-            const float ax = group_sum(mo.w * (mo.x - c0x), gm), ay = group_sum(mo.w * (mo.y - c0y), gm),
-                        az = group_sum(mo.w * (mo.z - c0z), gm);
-            const float inv2 = fM > 0.f ? 1.f / fM : 0.f;
-            m.M = fM; m.x = c0x + ax * inv2; m.y = c0y + ay * inv2; m.z = c0z + az * inv2;
-            const float dx = mo.x - m.x, dy = mo.y - m.y, dz = mo.z - m.z;
-            const float d2 = dx * dx + dy * dy + dz * dz;
-            const float w = mo.w;     // 0 on lanes without a child: their terms vanish
-            m.q[0] = group_sum(-a.x + w * (3.f * dx * dx - d2), gm);
-            m.q[1] = group_sum(-a.y + w * (3.f * dy * dy - d2), gm);
-            m.q[2] = group_sum(-a.z + w * (3.f * dz * dz - d2), gm);
-            m.q[3] = group_sum(-a.w + w * (3.f * dx * dy), gm);
-            m.q[4] = group_sum(-q2.x + w * (3.f * dx * dz), gm);
-            m.q[5] = group_sum(-q2.y + w * (3.f * dy * dz), gm);
-        }
-        float3 pc = make_float3(0.f, 0.f, 0.f);
-        float e = 0.f;
-        if (REFIT) {
-            e = 0.5f * cell_cube(kb, lv, sysb, stc, pc);
-            if (lv == 0) {
-                for (unsigned k = 0; k < nch; k++) {
-                    const float4 ce = __ldcg(cext + cb + k);
-                    e = fmaxf(e, dist_inf(make_float3(ce.x, ce.y, ce.z), pc) + ce.w);
+            // Children's moments loaded together (at most 8, unrolled): one
+            // round trip to L2 per level instead of one per child.
+            float4 mo[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++)
+                mo[k] = k < (int)nch ? __ldcg(mono + cb + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float c0x = mo[0].x, c0y = mo[0].y, c0z = mo[0].z;
+            float fM = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                if (k < (int)nch) {
+                    fM += mo[k].w;
+                    ax = fmaf(mo[k].w, mo[k].x - c0x, ax);
+                    ay = fmaf(mo[k].w, mo[k].y - c0y, ay);
+                    az = fmaf(mo[k].w, mo[k].z - c0z, az);
                 }
-            } else {
-                const float4 ce = (unsigned)sl < nch ? __ldcg(cext + cb + sl) : make_float4(pc.x, pc.y, pc.z, 0.f);
-                e = group_max(fmaxf(e, dist_inf(make_float3(ce.x, ce.y, ce.z), pc) + ce.w), gm);
+            }
+            float inv2 = fM > 0.f ? 1.f / fM : 0.f;
+            m.M = fM; m.x = c0x + ax * inv2; m.y = c0y + ay * inv2; m.z = c0z + az * inv2;
+            for (int i = 0; i < 6; i++) m.q[i] = 0.f;
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                if (k < (int)nch) {
+                    const float4 a = __ldcg(qa + cb + k);
+                    const float2 q2 = __ldcg(qb + cb + k);
+                    const float dx = mo[k].x - m.x, dy = mo[k].y - m.y, dz = mo[k].z - m.z;
+                    const float d2 = dx * dx + dy * dy + dz * dz;
+                    m.q[0] += -a.x + mo[k].w * (3.f * dx * dx - d2);
+                    m.q[1] += -a.y + mo[k].w * (3.f * dy * dy - d2);
+                    m.q[2] += -a.z + mo[k].w * (3.f * dz * dz - d2);
+                    m.q[3] += -a.w + mo[k].w * (3.f * dx * dy);
+                    m.q[4] += -q2.x + mo[k].w * (3.f * dx * dz);
+                    m.q[5] += -q2.y + mo[k].w * (3.f * dy * dz);
+                }
             }
         }
-        if (sl == 0) {
-            store32(c, m, mono, qa, qb);
-            if (REFIT) {
-                put_delta(c, m, make_float2(com_offset(make_float3(m.x, m.y, m.z), pc), 2.f * e), delta, test,
-                          inv_theta);
-                cext[c] = make_float4(pc.x, pc.y, pc.z, e);
-            } else {
-                put_delta(c, m, cell_delta(kb, lv, sysb, make_float3(m.x, m.y, m.z), stc), delta, test, inv_theta);
+        store32(c, m, mono, qa, qb);
+        if (REFIT) {
+            float3 pc;
+            float e = 0.5f * cell_cube(kb, lv, sysb, stc, pc);
+            for (unsigned k = 0; k < nch; k++) {
+                const float4 ce = __ldcg(cext + cb + k);
+                e = fmaxf(e, dist_inf(make_float3(ce.x, ce.y, ce.z), pc) + ce.w);
             }
+            put_delta(c, m, make_float2(com_offset(make_float3(m.x, m.y, m.z), pc), 2.f * e), delta, test, inv_theta);
+            cext[c] = make_float4(pc.x, pc.y, pc.z, e);
+        } else {
+            put_delta(c, m, cell_delta(kb, lv, sysb, make_float3(m.x, m.y, m.z), stc), delta, test, inv_theta);
         }
     }
 }
 
-// Groups of MG lanes take the cells from the end of the breadth-first
-// numbering (the deepest leaves, whose climbs to the root are the longest,
-// have the largest numbers, so those climbs start in the first wave); a
-// grid-stride loop covers any cell count, and the launch is sized from the
-// last known count so that nearly every group takes a single cell.
+// One thread per cell (leaves do the work): leaf moments from the bodies,
+// then up the tree while it is the last child to arrive.  A thread per cell
+// keeps many climbs in flight (a grid-stride loop that serialises several
+// cells per thread measured twice as slow), so the launch is sized from the
+// last known cell count (plus an eighth) and the loop only covers a tree
+// that grew beyond it.
 template <bool REFIT>
 __global__ void __launch_bounds__(256, 4)
-k_multipoles(const DevState *__restrict__ stc, const uint2 *__restrict__ cell_link,
-             const uint8_t *__restrict__ cell_level, const uint32_t *__restrict__ cell_parent, uint32_t *cell_done,
+k_multipoles(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__ cell_body,
+             const uint2 *__restrict__ cell_link, const uint8_t *__restrict__ cell_level,
+             const uint32_t *__restrict__ cell_parent, uint32_t *cell_done,
              const float4 *__restrict__ pos4, const unsigned long long *__restrict__ sk,
              const uint8_t *__restrict__ sysid, float4 *mono, float4 *qa, float2 *qb, float2 *delta,
              double *shadow, float4 *cext, float4 *test, float inv_theta) {
+    // Cells are numbered breadth first, so the deepest leaves, whose climbs
+    // to the root are the longest, have the largest numbers: blocks take
+    // the cells from the end so that those climbs start in the first wave.
     const unsigned nc = stc->ncells;
     if (stc->status & ST_TIMEOUT) return;
-    const int lane = threadIdx.x & 31, sl = lane & (MG - 1);
-    const unsigned gm = ((1u << MG) - 1u) << (lane & ~(MG - 1));
-    const unsigned ngroups = gridDim.x * (blockDim.x / MG);
-    for (unsigned i = (blockIdx.x * blockDim.x + threadIdx.x) / MG; i < nc; i += ngroups)
-        multipole_cell<REFIT>(nc - 1u - i, sl, gm, stc, cell_link, cell_level, cell_parent, cell_done, pos4, sk,
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
+        multipole_cell<REFIT>(nc - 1u - i, stc, st, cell_body, cell_link, cell_level, cell_parent, cell_done, pos4, sk,
                               sysid, mono, qa, qb, delta, shadow, cext, test, inv_theta);
 }
 
-// Launch size: one lane group per cell of the last known cell count (plus an
+// Launch size: one thread per cell of the last known cell count (plus an
 // eighth), or of a typical count for the leaf size when none is known.
 static unsigned multipole_blocks(const Ctx &c) {
     long long cells = c.cells_hint > 0 ? c.cells_hint + c.cells_hint / 8 + 1024 : 8 * c.n / c.nleaf + 1024;
     if (cells > c.ccap) cells = c.ccap;
-    return (unsigned)((cells * MG + 255) / 256);
+    return (unsigned)((cells + 255) / 256);
 }
 
 // theta > 0: also the walk's MAC records for that opening angle (what
 // launch_open_radius writes), so that a step needs no separate pass.
 cudaError_t launch_multipoles(Ctx &c, float theta) {
     k_multipoles<false><<<multipole_blocks(c), 256, 0, c.stream>>>(
-        c.st, c.cell_link, c.cell_level, c.cell_parent, c.cell_done, c.pos4, c.keys, c.sysid, c.mono, c.quadA,
-        c.quadB, c.delta, c.shadow, nullptr, theta > 0.f ? c.test : nullptr, theta > 0.f ? 1.0f / theta : 0.f);
+        c.st, c.st, c.cell_body, c.cell_link, c.cell_level, c.cell_parent, c.cell_done, c.pos4, c.keys, c.sysid,
+        c.mono, c.quadA, c.quadB, c.delta, c.shadow, nullptr, theta > 0.f ? c.test : nullptr,
+        theta > 0.f ? 1.0f / theta : 0.f);
     return cudaGetLastError();
 }
 
@@ -333,8 +313,8 @@ cudaError_t launch_multipoles(Ctx &c, float theta) {
 // steps between rebuilds), with each cell's cube enlarged to hold its bodies.
 cudaError_t launch_multipoles_refit(Ctx &c) {
     k_multipoles<true><<<multipole_blocks(c), 256, 0, c.stream>>>(
-        c.st, c.cell_link, c.cell_level, c.cell_parent, c.cell_done, c.pos4, c.keys, c.sysid, c.mono, c.quadA,
-        c.quadB, c.delta, c.shadow, c.cext, nullptr, 0.f);
+        c.st, c.st, c.cell_body, c.cell_link, c.cell_level, c.cell_parent, c.cell_done, c.pos4, c.keys, c.sysid,
+        c.mono, c.quadA, c.quadB, c.delta, c.shadow, c.cext, nullptr, 0.f);
     return cudaGetLastError();
 }
 

@@ -14,7 +14,9 @@
 // compacted per block into a list of the bodies that start any (about one per
 // leaf), with counts per block and level; (2) scan of those counts over the
 // blocks; (3) per listed body, the index, first body, level and link of each
-// of its cells and its groups; (4) children, parents and internal body counts.
+// of its cells and its groups; (4) child counts and parents.  Internal
+// cells' body counts, which no stage of a step reads, are derived on demand
+// for the tree getter (k_internal_counts).
 #include "common.cuh"
 
 namespace bonsai {
@@ -275,7 +277,7 @@ k_build_scan(unsigned *blockcount, int nblocks, DevState *st) {
 // records cb = the number of level-(r+1) cells that start before t, offset to
 // level r+1's first index: for an internal cell that is its first child, and
 // the children of a cell are the level-(r+1) cells between its cb and the
-// next cell's cb.  Leaves get their body count here; internal cells in pass 4.
+// next cell's cb.  Leaves get their body count here.
 constexpr int WRITE_THREADS = 256;
 
 __global__ void __launch_bounds__(WRITE_THREADS)
@@ -394,43 +396,55 @@ k_build_write(const uint4 *__restrict__ entries, int ncrit, const unsigned *__re
     }
 }
 
-// Child count, children's parent and body count of internal cell c.
-__device__ __forceinline__ void link_cell(unsigned c, const DevState *__restrict__ st,
-                                               const uint32_t *__restrict__ cell_cb,
-                                               const uint8_t *__restrict__ cell_level, uint2 *cell_link,
-                                               uint2 *cell_body, uint32_t *cell_parent) {
-    if (cell_link[c].y & LEAF_BIT) return;
-    auto nchild_of = [&](unsigned d, int l) {
-        unsigned next = (d + 1 < st->level_start[l + 1]) ? cell_cb[d + 1] : st->level_start[l + 2];
-        return next - cell_cb[d];
-    };
-    const int l = cell_level[c];
-    const unsigned cb = cell_cb[c];
-    const unsigned nch = nchild_of(c, l);
-    cell_link[c] = make_uint2(cb, nch);
-    for (unsigned k = 0; k < nch; k++) cell_parent[cb + k] = c;
-    unsigned d = cb + nch - 1;                   // last child, then its last child, ...
-    int ld = l + 1;
-    uint2 lk = cell_link[d];
-    for (int it = 0; it < MAX_LEVEL && !(lk.y & LEAF_BIT); it++) {   // at most 21 levels
-        d = cell_cb[d] + nchild_of(d, ld) - 1;
-        ld++;
-        lk = cell_link[d];
-    }
-    const unsigned t = cell_body[c].x;
-    cell_body[c].y = lk.x + (lk.y & ~LEAF_BIT) - t;
+// Child count and the children's parent of internal cell c: the children
+// are the level-(l+1) cells from cb(c) up to the cb of the next cell of level
+// l (or the end of level l+1).
+__device__ __forceinline__ unsigned child_count(unsigned d, int l, const DevState *__restrict__ st,
+                                                const uint32_t *__restrict__ cell_cb) {
+    const unsigned next = (d + 1 < st->level_start[l + 1]) ? cell_cb[d + 1] : st->level_start[l + 2];
+    return next - cell_cb[d];
 }
 
-// Pass 4 (grid-stride over the cells, internal cells only): child count from the cb of the next
-// cell of the same level, parent pointers of the children, and the body
-// count from the descent along last children to a leaf.
+// Pass 4 (grid-stride over the cells, internal cells only): child count
+// and parent pointers of the children.
 __global__ void k_build_link(const DevState *__restrict__ st, const uint32_t *__restrict__ cell_cb,
-                             const uint8_t *__restrict__ cell_level, uint2 *cell_link,
-                             uint2 *cell_body, uint32_t *cell_parent) {
+                             const uint8_t *__restrict__ cell_level, uint2 *cell_link, uint32_t *cell_parent) {
     if (st->status & ST_TIMEOUT) return;
     const unsigned ncells = st->ncells;
-    for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x)
-        link_cell(c, st, cell_cb, cell_level, cell_link, cell_body, cell_parent);
+    for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+        if (cell_link[c].y & LEAF_BIT) continue;
+        const unsigned cb = cell_cb[c], nch = child_count(c, cell_level[c], st, cell_cb);
+        cell_link[c] = make_uint2(cb, nch);
+        for (unsigned k = 0; k < nch; k++) cell_parent[cb + k] = c;
+    }
+}
+
+// Body counts of the internal cells, which no stage of a step reads (the
+// walk and the multipoles take leaves' body ranges and internal cells' child
+// ranges from the links): filled on demand for the tree getter.  A cell ends
+// where its last descendant leaf ends: descend along last children (at most
+// 21 levels).
+__global__ void k_internal_counts(const DevState *__restrict__ st, const uint32_t *__restrict__ cell_cb,
+                                  const uint8_t *__restrict__ cell_level, const uint2 *__restrict__ cell_link,
+                                  uint2 *cell_body) {
+    const unsigned ncells = st->ncells;
+    for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+        uint2 lk = cell_link[c];
+        if (lk.y & LEAF_BIT) continue;
+        unsigned d = lk.x + lk.y - 1;            // last child, then its last child, ...
+        lk = cell_link[d];
+        for (int it = 0; it < MAX_LEVEL && !(lk.y & LEAF_BIT); it++) {
+            d = lk.x + lk.y - 1;
+            lk = cell_link[d];
+        }
+        cell_body[c].y = lk.x + (lk.y & ~LEAF_BIT) - cell_body[c].x;
+    }
+}
+
+cudaError_t launch_internal_counts(Ctx &c) {
+    const unsigned grid = (unsigned)min((c.ccap + 255) / 256, (long long)c.num_sms * 8);
+    k_internal_counts<<<grid, 256, 0, c.stream>>>(c.st, c.cell_cb, c.cell_level, c.cell_link, c.cell_body);
+    return cudaGetLastError();
 }
 
 // ---- Sibling packing of the walk groups (group_pack = 1) -------------------
@@ -569,8 +583,7 @@ cudaError_t launch_build(Ctx &c) {
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const unsigned grid = (unsigned)min((c.ccap + 255) / 256, (long long)c.num_sms * 8);
-    k_build_link<<<grid, 256, 0, c.stream>>>(c.st, c.cell_cb, c.cell_level, c.cell_link, c.cell_body,
-                                             c.cell_parent);
+    k_build_link<<<grid, 256, 0, c.stream>>>(c.st, c.cell_cb, c.cell_level, c.cell_link, c.cell_parent);
     return cudaGetLastError();
 }
 
