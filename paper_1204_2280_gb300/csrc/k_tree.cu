@@ -104,16 +104,28 @@ struct MarkShared {
     unsigned wcnt[BUILD_THREADS / 32];
     unsigned ngrp, ne;
     uint8_t sy[BKEYS];
-    uint8_t l0[BTAB];              // l0 of positions [base, base + B + BH)
+    uint8_t l0[BTAB];              // l0 of positions [base, base + B + BH) (the block's own are read)
 };
 
-// First body after t (of the block or its halo) that starts a run at a level
-// <= L, i.e. the end of t's level-L run; the global search beyond the halo.
-__device__ __forceinline__ int run_end_halo(const MarkShared &S, int base, int t, int L,
-                                            const unsigned long long *__restrict__ sk, int send) {
-    for (int j = t + 1; j < base + BTAB; j++)
-        if (S.l0[j - base] <= L) return j;
-    return run_end(sk, send, t, L);
+// End of the level-L run from body t (L >= 1), i.e. the first body after t
+// whose key differs from k[t] above level L: a binary search over the
+// block's keys and halo (the prefix shared with k[t] only shrinks along the
+// sorted keys; positions past n or in another system share nothing), then
+// the global search when the run reaches past the halo (identical keys at
+// the deepest level).
+__device__ __forceinline__ int run_end_local(const MarkShared &S, int k0, int base, int t, int L, int n,
+                                             const unsigned long long *__restrict__ sk, int send) {
+    const int last = base + BUILD_THREADS + BH - 1;          // last key in shared memory
+    const unsigned long long kt = S.k[t - k0];
+    const uint8_t st = S.sy[t - k0];
+    auto inside = [&](int j) { return j < n && S.sy[j - k0] == st && key_cpl(kt, S.k[j - k0]) >= L; };
+    if (last > t && inside(last)) return run_end(sk, send, t, L);
+    int lo = t, hi = last;                                    // inside(lo), !inside(hi)
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (inside(mid)) lo = mid; else hi = mid;
+    }
+    return hi;
 }
 
 __global__ void __launch_bounds__(BUILD_THREADS)
@@ -198,15 +210,27 @@ k_build_mark(const unsigned long long *__restrict__ sk, const uint8_t *__restric
     __syncthreads();
     const unsigned ne = S.ne;
     if ((unsigned)tid < ne) {
+        // A leaf ends where the next entry starts (the first body after a
+        // leaf starts a cell); a group at level lg < hi ends at the first
+        // later entry that starts on a level <= lg.  Only at the end of the
+        // block's entries does a run end come from the keys.
         const unsigned et = S.e_t[tid], ed = S.e_d[tid];
         const int elo = (int)(ed & 0xffu), ehi = (int)((ed >> 8) & 0xffu), elg = (int)((ed >> 16) & 0xffu);
         const int kind = (int)(ed >> 24);
         const int send = system_end(st, sysid, (int)et, n);
-        const int lend = (unsigned)tid + 1 < ne ? (int)S.e_t[tid + 1] : run_end_halo(S, base, (int)et, ehi, sk, send);
+        const int lend = (unsigned)tid + 1 < ne ? (int)S.e_t[tid + 1]
+                                               : run_end_local(S, k0, base, (int)et, ehi, n, sk, send);
         const unsigned lcnt = (unsigned)lend - et;
         unsigned gcnt = 0u, ngrp = 0u;
         if (kind == 1) {
-            gcnt = elg == ehi ? lcnt : (unsigned)run_end_halo(S, base, (int)et, elg, sk, send) - et;
+            if (elg == ehi) {
+                gcnt = lcnt;
+            } else {
+                unsigned j = (unsigned)tid + 1;
+                while (j < ne && (S.e_d[j] & 0xffu) > (unsigned)elg) j++;
+                const int gend = j < ne ? (int)S.e_t[j] : run_end_local(S, k0, base, (int)et, elg, n, sk, send);
+                gcnt = (unsigned)gend - et;
+            }
             ngrp = 1u;
         } else if (kind == 2) {
             gcnt = lcnt;
