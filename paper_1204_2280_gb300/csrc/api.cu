@@ -59,7 +59,7 @@ void free_bodies(Ctx &c) {
 cudaError_t alloc_bodies(Ctx &c, long long n) {
     free_bodies(c);
     const long long ntiles = (n + SORT_TILE - 1) / SORT_TILE;
-    const long long nbb = (n + BUILD_THREADS - 1) / BUILD_THREADS;
+    const long long nbb = (n + BUILD_BODIES - 1) / BUILD_BODIES;
     // Cells: at most n leaves and n/(nleaf+1) internal cells per level.
     const long long ccap = n + (long long)MAX_LEVEL * (n / (c.nleaf + 1)) + 64;
     std::vector<std::pair<void **, size_t>> plan;
@@ -71,7 +71,7 @@ cudaError_t alloc_bodies(Ctx &c, long long n) {
     a.take(c.vals, n, plan); a.take(c.vals_alt, n, plan);
     a.take(c.tile_status, (size_t)(SORT_PASSES + 1) * ntiles * SORT_RADIX, plan);
     a.take(c.blockcount, (size_t)BUILD_ROWS * nbb, plan);
-    a.take(c.build_entries, (size_t)nbb * BUILD_THREADS, plan);
+    a.take(c.build_entries, (size_t)nbb * BUILD_BODIES, plan);
     a.take(c.cell_body, ccap, plan); a.take(c.cell_link, ccap, plan);
     a.take(c.cell_level, ccap, plan); a.take(c.cell_parent, ccap, plan);
     a.take(c.cell_done, ccap, plan); a.take(c.cell_cb, ccap, plan);

@@ -52,7 +52,8 @@ constexpr int JUDGE_SPLIT = 64;                        // source splits of the j
 #ifndef BUILD_THREADS_CFG
 #define BUILD_THREADS_CFG 1024
 #endif
-constexpr int BUILD_THREADS = BUILD_THREADS_CFG;       // bodies per build block (multiple of 32, <= 1024)
+constexpr int BUILD_THREADS = BUILD_THREADS_CFG;       // threads per build block (multiple of 32, <= 1024)
+constexpr int BUILD_BODIES = 2 * BUILD_THREADS;        // bodies per build block (two per thread)
 constexpr int PACK_THREADS = 1024;                     // unpacked groups per group-packing block
 constexpr long long STAGE_MIN_FLOATS = 4096;           // staging area floor (getters stream cells through it)
 constexpr int ENTRY_ROW = NROWS;                       // build: entries per block (a row that is not scanned)

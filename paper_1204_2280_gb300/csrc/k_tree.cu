@@ -92,20 +92,22 @@ __device__ __forceinline__ int system_end(const DevState *__restrict__ st, const
 // levels.  Per block: cells per level (a difference array over lo..hi),
 // groups, and entries.
 constexpr int BH = 64;                              // halo: max(nleaf, ncrit)
-constexpr int BTAB = BUILD_THREADS + BH;            // table positions [base - BH, base + B)
-constexpr int BKEYS = BUILD_THREADS + 2 * BH + 1;   // keys of [base - BH - 1, base + B + BH)
+constexpr int BB = BUILD_BODIES;                    // bodies per block (two per thread)
+constexpr int BTAB = BB + BH;                       // table positions [base - BH, base + BB)
+constexpr int BKEYS = BB + 2 * BH + 1;              // keys of [base - BH - 1, base + BB + BH)
 
 struct MarkShared {
     unsigned long long k[BKEYS];
-    unsigned tab[2][BTAB];         // (D + 1) | (DG + 1) << 16, then pairwise maxima
-    unsigned e_t[BUILD_THREADS];   // the block's entries: first body
-    unsigned e_d[BUILD_THREADS];   //   lo | hi << 8 | lg << 16 | kind << 24
+    unsigned tab[2][BTAB];         // (D + 1) | (DG + 1) << 16, then maxima over 2^q positions
+    unsigned e_t[BB];              // the block's entries: first body
+    unsigned e_d[BB];              //   lo | hi << 8 | lg << 16 | kind << 24
     int cnt[MAX_LEVEL + 2];        // difference array of cells per level
-    unsigned wcnt[BUILD_THREADS / 32];
+    unsigned wcnt[2][BUILD_THREADS / 32];
     unsigned ngrp, ne;
     uint8_t sy[BKEYS];
-    uint8_t l0[BTAB];              // l0 of positions [base, base + B + BH) (the block's own are read)
 };
+
+size_t build_mark_smem_bytes() { return sizeof(MarkShared); }
 
 // End of the level-L run from body t (L >= 1), i.e. the first body after t
 // whose key differs from k[t] above level L: a binary search over the
@@ -115,7 +117,7 @@ struct MarkShared {
 // the deepest level).
 __device__ __forceinline__ int run_end_local(const MarkShared &S, int k0, int base, int t, int L, int n,
                                              const unsigned long long *__restrict__ sk, int send) {
-    const int last = base + BUILD_THREADS + BH - 1;          // last key in shared memory
+    const int last = base + BB + BH - 1;                     // last key in shared memory
     const unsigned long long kt = S.k[t - k0];
     const uint8_t st = S.sy[t - k0];
     auto inside = [&](int j) { return j < n && S.sy[j - k0] == st && key_cpl(kt, S.k[j - k0]) >= L; };
@@ -128,12 +130,22 @@ __device__ __forceinline__ int run_end_local(const MarkShared &S, int k0, int ba
     return hi;
 }
 
+// Maximum of the packed (16-bit) fields over table positions [it - w, it]
+// from maxima over 2^q positions (w + 1 >= 2^q): overlapping lookups.
+__device__ __forceinline__ unsigned window_max(const unsigned *T, int it, int w, int q) {
+    const int h = 1 << q;
+    unsigned m = T[it - h + 1];
+    for (int a = it - w; a < it - h + 1; a += h) m = __vmaxu2(m, T[a]);
+    return m;
+}
+
 __global__ void __launch_bounds__(BUILD_THREADS)
 k_build_mark(const unsigned long long *__restrict__ sk, const uint8_t *__restrict__ sysid, int n, int nleaf,
              int ncrit, unsigned *blockcount, int nblocks, uint4 *entries, const DevState *__restrict__ st) {
-    __shared__ MarkShared S;
+    extern __shared__ unsigned long long mark_smem[];
+    MarkShared &S = *reinterpret_cast<MarkShared *>(mark_smem);
     if (st->status & ST_TIMEOUT) return;        // keys not sorted: skip the build
-    const int base = blockIdx.x * BUILD_THREADS, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int base = blockIdx.x * BB, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int k0 = base - BH - 1;
     for (int i = tid; i < BKEYS; i += BUILD_THREADS) {
         const int j = k0 + i;
@@ -153,80 +165,103 @@ k_build_mark(const unsigned long long *__restrict__ sk, const uint8_t *__restric
             if (j + ncrit < n) dg = cpl(j, j + ncrit);
         }
         S.tab[0][i] = (unsigned)(d + 1) | ((unsigned)(dg + 1) << 16);
-        const int jl = base + i;                 // l0 position (>= n: 0, ends every run)
-        S.l0[i] = (jl <= 0 || jl >= n) ? (uint8_t)0 : (uint8_t)(cpl(jl - 1, jl) + 1);
     }
     __syncthreads();
 
-    const int t = base + tid, it = tid + BH;
-    const unsigned own = S.tab[0][it];
-    const int qL = 31 - __clz(nleaf + 1), qG = 31 - __clz(ncrit + 1), qmax = max(qL, qG);
-    int winD = 0, winG = 0;                      // 1 + window maxima of D and DG
+    // This thread's bodies t[h] = base + tid + h * BUILD_THREADS (h = 0, 1):
+    // own l0, D, DG, then the window maxima from maxima over 2^qb positions,
+    // qb = floor(log2(min(nleaf, ncrit) + 1)) capped at 16 positions.
+    int t[2], l0[2];
+    unsigned own[2];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        t[h] = base + tid + h * BUILD_THREADS;
+        own[h] = S.tab[0][t[h] - base + BH];
+        l0[h] = (t[h] <= 0 || t[h] >= n) ? 0 : cpl(t[h] - 1, t[h]) + 1;
+    }
+    const int qb = min(4, 31 - __clz(min(nleaf, ncrit) + 1));
     int cur = 0;
-    for (int q = 0; q <= qmax; q++) {            // uniform over the block
+    for (int q = 0; q < qb; q++) {               // uniform over the block
+        const int hq = 1 << q;
         const unsigned *T = S.tab[cur];
-        if (q == qL) winD = (int)max(T[it - nleaf] & 0xffffu, T[it - (1 << q) + 1] & 0xffffu);
-        if (q == qG) winG = (int)max(T[it - ncrit] >> 16, T[it - (1 << q) + 1] >> 16);
-        if (q < qmax) {
-            const int h = 1 << q;
-            unsigned *U = S.tab[cur ^ 1];
-            for (int i = tid; i + 2 * h <= BTAB; i += BUILD_THREADS) U[i] = __vmaxu2(T[i], T[i + h]);
-            __syncthreads();
-            cur ^= 1;
+        unsigned *U = S.tab[cur ^ 1];
+        for (int i = tid; i + 2 * hq <= BTAB; i += BUILD_THREADS) U[i] = __vmaxu2(T[i], T[i + hq]);
+        __syncthreads();
+        cur ^= 1;
+    }
+    bool has[2];
+    unsigned desc[2];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int it = t[h] - base + BH;
+        const int winD = (int)(window_max(S.tab[cur], it, nleaf, qb) & 0xffffu);   // 1 + max D
+        has[h] = t[h] < n && l0[h] <= MAX_LEVEL && (l0[h] == 0 || winD >= l0[h]);
+        desc[h] = 0u;
+        if (has[h]) {
+            const int D = (int)(own[h] & 0xffffu) - 1, DG = (int)(own[h] >> 16) - 1;
+            const int hi = max(l0[h], min(D + 1, MAX_LEVEL));
+            const int lg = max(l0[h], DG + 1);
+            int kind = 2;
+            if (lg <= hi) {
+                const int winG = (int)(window_max(S.tab[cur], it, ncrit, qb) >> 16);   // 1 + max DG
+                kind = (lg > l0[h] || l0[h] == 0 || winG >= l0[h]) ? 1 : 0;
+            }
+            desc[h] = (unsigned)l0[h] | ((unsigned)hi << 8) | ((unsigned)min(lg, 255) << 16) | ((unsigned)kind << 24);
         }
     }
-    const int l0 = S.l0[tid];
-    bool has = false;
-    unsigned desc = 0u;
-    if (t < n && l0 <= MAX_LEVEL && (l0 == 0 || winD >= l0)) {
-        has = true;
-        const int D = (int)(own & 0xffffu) - 1, DG = (int)(own >> 16) - 1;
-        const int hi = max(l0, min(D + 1, MAX_LEVEL));
-        const int lg = max(l0, DG + 1);
-        const int kind = lg <= hi ? ((lg > l0 || l0 == 0 || winG >= l0) ? 1 : 0) : 2;
-        desc = (unsigned)l0 | ((unsigned)hi << 8) | ((unsigned)min(lg, 255) << 16) | ((unsigned)kind << 24);
+    // compaction of the block's entries, in key order (first half, then second)
+    unsigned m[2];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        m[h] = __ballot_sync(0xffffffffu, has[h]);
+        if (lane == 0) S.wcnt[h][warp] = __popc(m[h]);
     }
-    // compaction of the block's entries, in key order
-    const unsigned m = __ballot_sync(0xffffffffu, has);
-    if (lane == 0) S.wcnt[warp] = __popc(m);
     __syncthreads();
     if (warp == 0) {
-        const unsigned v = lane < BUILD_THREADS / 32 ? S.wcnt[lane] : 0u;
-        unsigned x = v;
+        constexpr int NW = BUILD_THREADS / 32;
+        unsigned carry = 0u;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+        for (int h = 0; h < 2; h++) {
+            const unsigned v = lane < NW ? S.wcnt[h][lane] : 0u;
+            unsigned x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane < NW) S.wcnt[h][lane] = carry + x - v;
+            carry += __shfl_sync(0xffffffffu, x, 31);
         }
-        if (lane < BUILD_THREADS / 32) S.wcnt[lane] = x - v;
-        if (lane == 31) S.ne = x;
+        if (lane == 0) S.ne = carry;
     }
     __syncthreads();
-    if (has) {
-        const unsigned slot = S.wcnt[warp] + __popc(m & ((1u << lane) - 1u));
-        S.e_t[slot] = (unsigned)t;
-        S.e_d[slot] = desc;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        if (has[h]) {
+            const unsigned slot = S.wcnt[h][warp] + __popc(m[h] & ((1u << lane) - 1u));
+            S.e_t[slot] = (unsigned)t[h];
+            S.e_d[slot] = desc[h];
+        }
     }
     __syncthreads();
     const unsigned ne = S.ne;
-    if ((unsigned)tid < ne) {
+    for (unsigned e = (unsigned)tid; e < ne; e += BUILD_THREADS) {
         // A leaf ends where the next entry starts (the first body after a
         // leaf starts a cell); a group at level lg < hi ends at the first
         // later entry that starts on a level <= lg.  Only at the end of the
         // block's entries does a run end come from the keys.
-        const unsigned et = S.e_t[tid], ed = S.e_d[tid];
+        const unsigned et = S.e_t[e], ed = S.e_d[e];
         const int elo = (int)(ed & 0xffu), ehi = (int)((ed >> 8) & 0xffu), elg = (int)((ed >> 16) & 0xffu);
         const int kind = (int)(ed >> 24);
         const int send = system_end(st, sysid, (int)et, n);
-        const int lend = (unsigned)tid + 1 < ne ? (int)S.e_t[tid + 1]
-                                               : run_end_local(S, k0, base, (int)et, ehi, n, sk, send);
+        const int lend = e + 1 < ne ? (int)S.e_t[e + 1] : run_end_local(S, k0, base, (int)et, ehi, n, sk, send);
         const unsigned lcnt = (unsigned)lend - et;
         unsigned gcnt = 0u, ngrp = 0u;
         if (kind == 1) {
             if (elg == ehi) {
                 gcnt = lcnt;
             } else {
-                unsigned j = (unsigned)tid + 1;
+                unsigned j = e + 1;
                 while (j < ne && (S.e_d[j] & 0xffu) > (unsigned)elg) j++;
                 const int gend = j < ne ? (int)S.e_t[j] : run_end_local(S, k0, base, (int)et, elg, n, sk, send);
                 gcnt = (unsigned)gend - et;
@@ -236,7 +271,7 @@ k_build_mark(const unsigned long long *__restrict__ sk, const uint8_t *__restric
             gcnt = lcnt;
             ngrp = (lcnt + (unsigned)ncrit - 1u) / (unsigned)ncrit;
         }
-        entries[(size_t)blockIdx.x * BUILD_THREADS + tid] = make_uint4(et, lcnt, gcnt, ed);
+        entries[(size_t)blockIdx.x * BB + e] = make_uint4(et, lcnt, gcnt, ed);
         atomicAdd(&S.cnt[elo], 1);
         atomicSub(&S.cnt[ehi + 1], 1);
         if (ngrp) atomicAdd(&S.ngrp, ngrp);
@@ -347,7 +382,7 @@ k_build_write(const uint4 *__restrict__ entries, int ncrit, const unsigned *__re
     for (unsigned r0 = 0; r0 < ne; r0 += WRITE_THREADS) {   // rounds of entries (uniform)
         const unsigned i = r0 + (unsigned)tid;
         const bool valid = i < ne;
-        const uint4 e = valid ? entries[(size_t)blockIdx.x * BUILD_THREADS + i] : make_uint4(0u, 0u, 0u, 0u);
+        const uint4 e = valid ? entries[(size_t)blockIdx.x * BB + i] : make_uint4(0u, 0u, 0u, 0u);
         const int lo = valid ? (int)(e.w & 0xffu) : MAX_LEVEL + 1;
         const int hi = valid ? (int)((e.w >> 8) & 0xffu) : -1;
         const int lg = (int)((e.w >> 16) & 0xffu), kind = (int)(e.w >> 24);
@@ -583,9 +618,12 @@ k_group_pack(DevState *st, const uint2 *__restrict__ graw, const uint8_t *__rest
 
 cudaError_t launch_build(Ctx &c) {
     int n = (int)c.n;
-    k_build_mark<<<c.nbblocks, BUILD_THREADS, 0, c.stream>>>(c.keys, c.sysid, n, c.nleaf, c.ncrit, c.blockcount,
-                                                             c.nbblocks, c.build_entries, c.st);
-    cudaError_t e = cudaGetLastError();
+    static size_t attr_done[MAX_DEVICES] = {};
+    cudaError_t e = allow_dyn_smem((const void *)k_build_mark, sizeof(MarkShared), attr_done);
+    if (e != cudaSuccess) return e;
+    k_build_mark<<<c.nbblocks, BUILD_THREADS, sizeof(MarkShared), c.stream>>>(
+        c.keys, c.sysid, n, c.nleaf, c.ncrit, c.blockcount, c.nbblocks, c.build_entries, c.st);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_build_scan<<<NROWS, 1024, 0, c.stream>>>(c.blockcount, c.nbblocks, c.st);
     e = cudaGetLastError();
