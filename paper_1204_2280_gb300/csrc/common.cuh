@@ -53,7 +53,11 @@ constexpr int JUDGE_SPLIT = 64;                        // source splits of the j
 #define BUILD_THREADS_CFG 1024
 #endif
 constexpr int BUILD_THREADS = BUILD_THREADS_CFG;       // threads per build block (multiple of 32, <= 1024)
-constexpr int BUILD_BODIES = 2 * BUILD_THREADS;        // bodies per build block (two per thread)
+#ifndef BUILD_BPT_CFG
+#define BUILD_BPT_CFG 4
+#endif
+constexpr int BUILD_BPT = BUILD_BPT_CFG;               // bodies per thread of the build's analysis pass
+constexpr int BUILD_BODIES = BUILD_BPT * BUILD_THREADS;   // bodies per build block
 constexpr int PACK_THREADS = 1024;                     // unpacked groups per group-packing block
 constexpr long long STAGE_MIN_FLOATS = 4096;           // staging area floor (getters stream cells through it)
 constexpr int ENTRY_ROW = NROWS;                       // build: entries per block (a row that is not scanned)

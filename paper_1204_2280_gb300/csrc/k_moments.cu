@@ -137,7 +137,7 @@ __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__res
     if (REFIT) ext = 0.5f * cell_cube(sk[b], cell_level[c], sysid[b], stc, ctr);
     // The bodies' loads are issued LB at a time (one round trip per LB
     // bodies instead of one per body); the sums still run in body order.
-    constexpr unsigned LB = 4;
+    constexpr unsigned LB = 8;
     for (unsigned j0 = b; j0 < b + cnt; j0 += LB) {
         float4 pb[LB];
 #pragma unroll

@@ -92,7 +92,7 @@ __device__ __forceinline__ int system_end(const DevState *__restrict__ st, const
 // levels.  Per block: cells per level (a difference array over lo..hi),
 // groups, and entries.
 constexpr int BH = 64;                              // halo: max(nleaf, ncrit)
-constexpr int BB = BUILD_BODIES;                    // bodies per block (two per thread)
+constexpr int BB = BUILD_BODIES;                    // bodies per block (BUILD_BPT per thread)
 constexpr int BTAB = BB + BH;                       // table positions [base - BH, base + BB)
 constexpr int BKEYS = BB + 2 * BH + 1;              // keys of [base - BH - 1, base + BB + BH)
 
@@ -102,7 +102,7 @@ struct MarkShared {
     unsigned e_t[BB];              // the block's entries: first body
     unsigned e_d[BB];              //   lo | hi << 8 | lg << 16 | kind << 24
     int cnt[MAX_LEVEL + 2];        // difference array of cells per level
-    unsigned wcnt[2][BUILD_THREADS / 32];
+    unsigned wcnt[BUILD_BPT][BUILD_THREADS / 32];
     unsigned ngrp, ne;
     uint8_t sy[BKEYS];
 };
@@ -168,13 +168,13 @@ k_build_mark(const unsigned long long *__restrict__ sk, const uint8_t *__restric
     }
     __syncthreads();
 
-    // This thread's bodies t[h] = base + tid + h * BUILD_THREADS (h = 0, 1):
-    // own l0, D, DG, then the window maxima from maxima over 2^qb positions,
-    // qb = floor(log2(min(nleaf, ncrit) + 1)) capped at 16 positions.
-    int t[2], l0[2];
-    unsigned own[2];
+    // This thread's bodies t[h] = base + tid + h * BUILD_THREADS (h <
+    // BUILD_BPT): own l0, D, DG, then the window maxima from maxima over 2^qb
+    // positions, qb = floor(log2(min(nleaf, ncrit) + 1)) capped at 16 positions.
+    int t[BUILD_BPT], l0[BUILD_BPT];
+    unsigned own[BUILD_BPT];
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
+    for (int h = 0; h < BUILD_BPT; h++) {
         t[h] = base + tid + h * BUILD_THREADS;
         own[h] = S.tab[0][t[h] - base + BH];
         l0[h] = (t[h] <= 0 || t[h] >= n) ? 0 : cpl(t[h] - 1, t[h]) + 1;
@@ -189,10 +189,10 @@ k_build_mark(const unsigned long long *__restrict__ sk, const uint8_t *__restric
         __syncthreads();
         cur ^= 1;
     }
-    bool has[2];
-    unsigned desc[2];
+    bool has[BUILD_BPT];
+    unsigned desc[BUILD_BPT];
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
+    for (int h = 0; h < BUILD_BPT; h++) {
         const int it = t[h] - base + BH;
         const int winD = (int)(window_max(S.tab[cur], it, nleaf, qb) & 0xffffu);   // 1 + max D
         has[h] = t[h] < n && l0[h] <= MAX_LEVEL && (l0[h] == 0 || winD >= l0[h]);
@@ -209,10 +209,11 @@ k_build_mark(const unsigned long long *__restrict__ sk, const uint8_t *__restric
             desc[h] = (unsigned)l0[h] | ((unsigned)hi << 8) | ((unsigned)min(lg, 255) << 16) | ((unsigned)kind << 24);
         }
     }
-    // compaction of the block's entries, in key order (first half, then second)
-    unsigned m[2];
+    // compaction of the block's entries, in key order (slice h of the block's
+    // bodies before slice h + 1)
+    unsigned m[BUILD_BPT];
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
+    for (int h = 0; h < BUILD_BPT; h++) {
         m[h] = __ballot_sync(0xffffffffu, has[h]);
         if (lane == 0) S.wcnt[h][warp] = __popc(m[h]);
     }
@@ -221,7 +222,7 @@ k_build_mark(const unsigned long long *__restrict__ sk, const uint8_t *__restric
         constexpr int NW = BUILD_THREADS / 32;
         unsigned carry = 0u;
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
+        for (int h = 0; h < BUILD_BPT; h++) {
             const unsigned v = lane < NW ? S.wcnt[h][lane] : 0u;
             unsigned x = v;
 #pragma unroll
@@ -236,7 +237,7 @@ k_build_mark(const unsigned long long *__restrict__ sk, const uint8_t *__restric
     }
     __syncthreads();
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
+    for (int h = 0; h < BUILD_BPT; h++) {
         if (has[h]) {
             const unsigned slot = S.wcnt[h][warp] + __popc(m[h] & ((1u << lane) - 1u));
             S.e_t[slot] = (unsigned)t[h];
