@@ -119,7 +119,11 @@ __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__res
                                                const uint8_t *__restrict__ sysid, float4 *mono, float4 *qa, float2 *qb,
                                                float2 *delta, double *shadow, float4 *cext,
                                                float4 *test, float inv_theta) {
+    // The link, level and parent in one round trip (the parent of a root
+    // is never used: a root leaf does not climb).
     uint2 link = cell_link[c];
+    int lev = cell_level[c];                         // level and parent, for the climb
+    unsigned p = cell_parent[c];
     if (!(link.y & LEAF_BIT)) return;
 
     // Leaf from its bodies in one pass: mass, first and second moments of
@@ -127,8 +131,6 @@ __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__res
     // central moments C = S - s c^T and Q = 3C - tr(C) I.  The offsets are
     // at most the cell size, so nothing cancels beyond FP32 rounding.
     unsigned b = link.x, cnt = link.y & ~LEAF_BIT;
-    int lev = cell_level[c];                         // level and parent, for the climb
-    unsigned p = lev != 0 ? cell_parent[c] : 0u;
     float4 x0 = pos4[b];
     float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
     float sxx = 0.f, syy = 0.f, szz = 0.f, sxy = 0.f, sxz = 0.f, syz = 0.f;
