@@ -338,7 +338,7 @@ k_build_scan(unsigned *blockcount, int nblocks, DevState *st) {
 // level r+1's first index: for an internal cell that is its first child, and
 // the children of a cell are the level-(r+1) cells between its cb and the
 // next cell's cb.  Leaves get their body count here.
-constexpr int WRITE_THREADS = 256;
+constexpr int WRITE_THREADS = 512;
 
 __global__ void __launch_bounds__(WRITE_THREADS)
 k_build_write(const uint4 *__restrict__ entries, int ncrit, const unsigned *__restrict__ blockcount, int nblocks,
@@ -547,25 +547,40 @@ __global__ void __launch_bounds__(PACK_THREADS)
 k_group_mark(const DevState *__restrict__ st, const uint2 *__restrict__ graw, const uint8_t *__restrict__ glvl,
              const unsigned long long *__restrict__ sk, const uint8_t *__restrict__ sysid, int ncrit,
              uint8_t *gflag, unsigned *bcount) {
+    // The chunk's groups and the 8 before it in shared memory, each with
+    // whether it is a sibling of the one before: every thread's look-back
+    // and greedy pass then run on shared memory (one round of global loads
+    // per chunk instead of one per step back).
+    constexpr int HALO = 8;
+    __shared__ unsigned s_cnt[PACK_THREADS + HALO];
+    __shared__ uint8_t s_sib[PACK_THREADS + HALO];
     if (st->status & ST_TIMEOUT) return;
     const unsigned ng = st->row_total[GROUP_ROW];
     const unsigned nchunk = (ng + PACK_THREADS - 1) / PACK_THREADS;
     for (unsigned ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
+        const long long g0 = (long long)ch * PACK_THREADS - HALO;
+        for (int i = threadIdx.x; i < PACK_THREADS + HALO; i += PACK_THREADS) {
+            const long long gg = g0 + i;
+            const bool valid = gg >= 0 && gg < (long long)ng;
+            s_cnt[i] = valid ? graw[gg].y : 0u;
+            s_sib[i] = valid && group_sibling((unsigned)gg, graw, glvl, sk, sysid) ? 1u : 0u;
+        }
+        __syncthreads();
         const unsigned g = ch * PACK_THREADS + threadIdx.x;
         bool start = false;
         if (g < ng) {
-            unsigned s = g;
-            for (int k = 0; k < 8 && group_sibling(s, graw, glvl, sk, sysid); k++) s--;
-            unsigned acc = graw[s].y;
+            int s = (int)threadIdx.x + HALO;
+            for (int k = 0; k < 8 && s_sib[s]; k++) s--;
+            unsigned acc = s_cnt[s];
             start = true;
-            for (unsigned j = s + 1; j <= g; j++) {
-                const unsigned cj = graw[j].y;
+            for (int j = s + 1; j <= (int)threadIdx.x + HALO; j++) {
+                const unsigned cj = s_cnt[j];
                 start = acc + cj > (unsigned)ncrit;
                 acc = start ? cj : acc + cj;
             }
             gflag[g] = start ? 1u : 0u;
         }
-        const int cnt = __syncthreads_count(start);
+        const int cnt = __syncthreads_count(start);   // also: the shared arrays are free again
         if (threadIdx.x == 0) bcount[ch] = (unsigned)cnt;
     }
 }
