@@ -320,7 +320,9 @@ int bonsai_multipoles(bonsai_ctx *ctx) {
     if (!ctx) return BONSAI_ERR_INVALID_ARG;
     Ctx &c = ctx->c;
     if (!c.built) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_multipoles: call bonsai_build first");
-    CK(refresh_cells_hint(c));
+    // The launch is sized from the last known cell count (a tree of the same
+    // bodies changes little); only a context without one reads it back.
+    if (c.cells_hint == 0) CK(refresh_cells_hint(c));
     CK(launch_multipoles(c));
     c.moments_ready = true;
     return BONSAI_OK;

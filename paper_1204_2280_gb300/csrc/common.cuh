@@ -221,8 +221,8 @@ __device__ __forceinline__ float rsqrt_mufu(float x) {
 __device__ __forceinline__ int key_cpl(unsigned long long a, unsigned long long b) {
     unsigned long long x = a ^ b;
     if (x == 0ull) return MAX_LEVEL;
-    int p = 63 - __clzll((long long)x);
-    return MAX_LEVEL - p / 3 - 1;
+    const unsigned p = 63u - (unsigned)__clzll((long long)x);   // highest differing bit
+    return MAX_LEVEL - (int)(p / 3u) - 1;
 }
 
 // Block time steps: a body of level k (stored as a float) takes forces at
