@@ -218,11 +218,13 @@ __device__ __forceinline__ float rsqrt_mufu(float x) {
 
 // Number of leading tree levels shared by two keys (level 0 always shared):
 // prefix_l(a) == prefix_l(b) iff l <= cpl(a, b).
+// Branch-free: with y = 2(a ^ b) + 1 the highest set bit of y is one above
+// the highest differing bit h of the keys (bit 0 when they are equal), so
+// ceil(bit / 3) is h / 3 + 1 for different keys and 0 for equal ones.
 __device__ __forceinline__ int key_cpl(unsigned long long a, unsigned long long b) {
-    unsigned long long x = a ^ b;
-    if (x == 0ull) return MAX_LEVEL;
-    const unsigned p = 63u - (unsigned)__clzll((long long)x);   // highest differing bit
-    return MAX_LEVEL - (int)(p / 3u) - 1;
+    const unsigned long long y = ((a ^ b) << 1) | 1ull;         // keys use bits 0..62
+    const unsigned hb = 63u - (unsigned)__clzll((long long)y);
+    return MAX_LEVEL - (int)((hb + 2u) / 3u);
 }
 
 // Block time steps: a body of level k (stored as a float) takes forces at

@@ -141,7 +141,8 @@ __device__ __forceinline__ unsigned window_max(const unsigned *T, int it, int w,
 
 __global__ void __launch_bounds__(BUILD_THREADS)
 k_build_mark(const unsigned long long *__restrict__ sk, const uint8_t *__restrict__ sysid, int n, int nleaf,
-             int ncrit, unsigned *blockcount, int nblocks, uint4 *entries, const DevState *__restrict__ st) {
+             int ncrit, unsigned *blockcount, int nblocks, uint4 *entries, const DevState *__restrict__ st,
+             bool multi) {
     extern __shared__ unsigned long long mark_smem[];
     MarkShared &S = *reinterpret_cast<MarkShared *>(mark_smem);
     if (st->status & ST_TIMEOUT) return;        // keys not sorted: skip the build
@@ -156,7 +157,11 @@ k_build_mark(const unsigned long long *__restrict__ sk, const uint8_t *__restric
     if (tid <= MAX_LEVEL + 1) S.cnt[tid] = 0;
     if (tid == 0) S.ngrp = 0u;
     __syncthreads();
-    auto cpl = [&](int a, int b) { return body_cpl(S.k[a - k0], S.k[b - k0], S.sy[a - k0], S.sy[b - k0]); };
+    // with one system every body shares it: no system-id compare
+    auto cpl = [&](int a, int b) {
+        return multi ? body_cpl(S.k[a - k0], S.k[b - k0], S.sy[a - k0], S.sy[b - k0])
+                     : key_cpl(S.k[a - k0], S.k[b - k0]);
+    };
     for (int i = tid; i < BTAB; i += BUILD_THREADS) {
         const int j = base - BH + i;             // table position
         int d = -1, dg = -1;
@@ -638,7 +643,7 @@ cudaError_t launch_build(Ctx &c) {
     cudaError_t e = allow_dyn_smem((const void *)k_build_mark, sizeof(MarkShared), attr_done);
     if (e != cudaSuccess) return e;
     k_build_mark<<<c.nbblocks, BUILD_THREADS, sizeof(MarkShared), c.stream>>>(
-        c.keys, c.sysid, n, c.nleaf, c.ncrit, c.blockcount, c.nbblocks, c.build_entries, c.st);
+        c.keys, c.sysid, n, c.nleaf, c.ncrit, c.blockcount, c.nbblocks, c.build_entries, c.st, c.nsys > 1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_build_scan<<<NROWS, 1024, 0, c.stream>>>(c.blockcount, c.nbblocks, c.st);
