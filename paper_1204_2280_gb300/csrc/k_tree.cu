@@ -69,47 +69,36 @@ __device__ __forceinline__ int system_end(const DevState *__restrict__ st, const
 // ---- Pass 1: which cells and groups every body starts ----------------------
 // For body t (within its system) let
 //   l0(t) = cpl(k[t-1], k[t]) + 1   the first level at which t starts a key-prefix run
-//                                   (0 for the first body of a system and past the end)
+//                                   (0 for the first body of a system)
 //   D(t)  = cpl(k[t], k[t+nleaf])   the run at level l from t has more than
 //                                   nleaf bodies iff l <= D(t)   (-1: no such body)
 //   DG(t) = cpl(k[t], k[t+ncrit])   the same for ncrit.
-// Along sorted keys the prefix two keys share is the least prefix of the
-// neighbouring pairs between them, so D(t) + 1 = min(l0[t+1 .. t+nleaf]) --
-// also at the end of a system or of the bodies, where some l0 in the window
-// is 0 -- and likewise DG.  The level-L run holding t has more than w bodies
-// iff some window of w+1 consecutive bodies containing t lies inside it,
-// i.e. iff max over i in [t-w, t] of cpl(k[i], k[i+w]) >= L.  So t starts a
-// cell on level l0 (its parent run, level l0-1, is split) iff l0 = 0 or that
-// window maximum of D reaches l0 - 1; it then starts the cells of levels
-// lo = l0 .. hi = max(l0, min(D(t) + 1, 21)), the one at hi a leaf.  Its
-// group (the cells with <= ncrit bodies whose parent has more) sits on level
-// lg = max(l0, DG(t) + 1) if lg <= hi and t starts it (lg > l0, l0 = 0, or
-// the window maximum of DG reaches l0 - 1); if lg > hi the leaf has more than
-// ncrit bodies (identical keys at level 21, or ncrit < nleaf) and is cut into
-// runs of ncrit.
+// The level-L run holding t has more than w bodies iff some window of w+1
+// consecutive bodies containing t lies inside it, i.e. iff
+//   max over i in [t-w, t] of cpl(k[i], k[i+w]) >= L.
+// So t starts a cell on level l0 (the parent run, level l0-1, is split) iff
+// l0 = 0 or that window maximum of D reaches l0 - 1; it then starts the cells
+// of levels lo = l0 .. hi = max(l0, min(D(t) + 1, 21)), the one at hi a leaf.
+// Its group (the cells with <= ncrit bodies whose parent has more) sits on
+// level lg = max(l0, DG(t) + 1) if lg <= hi and t starts it (lg > l0, l0 = 0,
+// or the window maximum of DG reaches l0 - 1); if lg > hi the leaf has more
+// than ncrit bodies (identical keys at level 21, or ncrit < nleaf) and is cut
+// into runs of ncrit.  Both window maxima come from a sparse table of
+// pairwise maxima (log2(w+1) + 1 levels) in shared memory.
 //
-// One common-prefix length per position (l0), then everything from tables
-// of l0 bytes packed four to a word: minima over 2^q positions (__vminu4;
-// offsets of one and two positions by funnel shifts, of four and eight by
-// whole words) give D + 1 and DG + 1 with overlapping lookups, and maxima
-// over 2^q positions of those give the window maxima.  The bodies that start
-// cells (about one per leaf) are compacted, in key order, into the block's
-// entry list: first body, leaf count (up to the next entry, which is the
-// first body after the leaf), group body count and the levels.  Per block:
-// cells per level (a difference array over lo..hi), groups, and entries.
+// The bodies that start cells (about one per leaf) are compacted, in key
+// order, into the block's entry list: first body, leaf count (up to the next
+// entry, which is the first body after the leaf), group body count and the
+// levels.  Per block: cells per level (a difference array over lo..hi),
+// groups, and entries.
 constexpr int BH = 64;                              // halo: max(nleaf, ncrit)
 constexpr int BB = BUILD_BODIES;                    // bodies per block (BUILD_BPT per thread)
+constexpr int BTAB = BB + BH;                       // table positions [base - BH, base + BB)
 constexpr int BKEYS = BB + 2 * BH + 1;              // keys of [base - BH - 1, base + BB + BH)
-constexpr int NLW = (BB + 2 * BH) / 4;              // l0 words: positions [base - BH, base + BB + BH)
-constexpr int NTW = (BB + BH) / 4;                  // D words: positions [base - BH, base + BB)
-constexpr int PADW = 8;                             // zero words after each array (shifted reads)
-constexpr int TW = NLW + PADW;
-static_assert(BB % 4 == 0, "bodies per block in whole words");
 
 struct MarkShared {
     unsigned long long k[BKEYS];
-    unsigned lv[5][TW];            // lv[0]: l0 bytes; lv[q]: minima over 2^q positions; later the max tables
-    unsigned dw[2][TW];            // D + 1 and DG + 1 bytes of positions [base - BH, base + BB)
+    unsigned tab[2][BTAB];         // (D + 1) | (DG + 1) << 16, then maxima over 2^q positions
     unsigned e_t[BB];              // the block's entries: first body
     unsigned e_d[BB];              //   lo | hi << 8 | lg << 16 | kind << 24
     int cnt[MAX_LEVEL + 2];        // difference array of cells per level
@@ -119,32 +108,6 @@ struct MarkShared {
 };
 
 size_t build_mark_smem_bytes() { return sizeof(MarkShared); }
-
-// Word w of table T shifted by `off` positions: the bytes of positions
-// 4w + off .. 4w + off + 3.
-__device__ __forceinline__ unsigned shifted_word(const unsigned *T, int w, int off) {
-    const int q = off >> 2, r = off & 3;
-    return r == 0 ? T[w + q] : __funnelshift_r(T[w + q], T[w + q + 1], 8 * r);
-}
-
-// Per byte of word w: minimum over positions [p + start, p + start + len)
-// from a table of minima over h = 2^q positions (h <= len), by overlapping
-// lookups.
-__device__ __forceinline__ unsigned window_min_word(const unsigned *T, int w, int start, int len, int h) {
-    unsigned m = shifted_word(T, w, start + len - h);
-    for (int o = start; o < start + len - h; o += h) m = __vminu4(m, shifted_word(T, w, o));
-    return m;
-}
-
-__device__ __forceinline__ unsigned byte_at(const unsigned *T, int p) { return (T[p >> 2] >> ((p & 3) * 8)) & 0xffu; }
-
-// Maximum over positions [p - w, p] (w + 1 >= h = 2^q) of a table of maxima
-// over h positions.
-__device__ __forceinline__ unsigned window_max_at(const unsigned *T, int p, int w, int h) {
-    unsigned m = byte_at(T, p - h + 1);
-    for (int a = p - w; a < p - h + 1; a += h) m = max(m, byte_at(T, a));
-    return m;
-}
 
 // End of the level-L run from body t (L >= 1), i.e. the first body after t
 // whose key differs from k[t] above level L: a binary search over the
@@ -167,6 +130,15 @@ __device__ __forceinline__ int run_end_local(const MarkShared &S, int k0, int ba
     return hi;
 }
 
+// Maximum of the packed (16-bit) fields over table positions [it - w, it]
+// from maxima over 2^q positions (w + 1 >= 2^q): overlapping lookups.
+__device__ __forceinline__ unsigned window_max(const unsigned *T, int it, int w, int q) {
+    const int h = 1 << q;
+    unsigned m = T[it - h + 1];
+    for (int a = it - w; a < it - h + 1; a += h) m = __vmaxu2(m, T[a]);
+    return m;
+}
+
 __global__ void __launch_bounds__(BUILD_THREADS)
 k_build_mark(const unsigned long long *__restrict__ sk, const uint8_t *__restrict__ sysid, int n, int nleaf,
              int ncrit, unsigned *blockcount, int nblocks, uint4 *entries, const DevState *__restrict__ st,
@@ -175,17 +147,13 @@ k_build_mark(const unsigned long long *__restrict__ sk, const uint8_t *__restric
     MarkShared &S = *reinterpret_cast<MarkShared *>(mark_smem);
     if (st->status & ST_TIMEOUT) return;        // keys not sorted: skip the build
     const int base = blockIdx.x * BB, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int k0 = base - BH - 1, p0 = base - BH;   // first key, first table position
+    const int k0 = base - BH - 1;
     for (int i = tid; i < BKEYS; i += BUILD_THREADS) {
         const int j = k0 + i;
         const bool in = j >= 0 && j < n;
         S.k[i] = in ? sk[j] : 0ull;
         S.sy[i] = in ? sysid[j] : 0;
     }
-    for (int i = tid; i < 5 * PADW; i += BUILD_THREADS)     // zero words after the l0 tables
-        S.lv[i / PADW][NLW + i % PADW] = 0u;
-    for (int i = tid; i < 2 * (TW - NTW); i += BUILD_THREADS) // and after the D words
-        S.dw[i / (TW - NTW)][NTW + i % (TW - NTW)] = 0u;
     if (tid <= MAX_LEVEL + 1) S.cnt[tid] = 0;
     if (tid == 0) S.ngrp = 0u;
     __syncthreads();
@@ -194,68 +162,56 @@ k_build_mark(const unsigned long long *__restrict__ sk, const uint8_t *__restric
         return multi ? body_cpl(S.k[a - k0], S.k[b - k0], S.sy[a - k0], S.sy[b - k0])
                      : key_cpl(S.k[a - k0], S.k[b - k0]);
     };
-    for (int w = tid; w < NLW; w += BUILD_THREADS) {          // l0 bytes, four per word
-        unsigned word = 0u;
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const int p = p0 + 4 * w + j;
-            const unsigned l = (p <= 0 || p >= n) ? 0u : (unsigned)(cpl(p - 1, p) + 1);
-            word |= l << (8 * j);
+    for (int i = tid; i < BTAB; i += BUILD_THREADS) {
+        const int j = base - BH + i;             // table position
+        int d = -1, dg = -1;
+        if (j >= 0 && j < n) {
+            if (j + nleaf < n) d = cpl(j, j + nleaf);
+            if (j + ncrit < n) dg = cpl(j, j + ncrit);
         }
-        S.lv[0][w] = word;
+        S.tab[0][i] = (unsigned)(d + 1) | ((unsigned)(dg + 1) << 16);
     }
     __syncthreads();
-    for (int q = 0; q < 4; q++) {                             // minima over 2, 4, 8, 16 positions
-        const unsigned *T = S.lv[q];
-        unsigned *U = S.lv[q + 1];
-        for (int w = tid; w < NLW; w += BUILD_THREADS) U[w] = __vminu4(T[w], shifted_word(T, w, 1 << q));
-        __syncthreads();
-    }
-    {
-        const int qn = min(4, 31 - __clz(nleaf)), qc = min(4, 31 - __clz(ncrit));
-        for (int w = tid; w < NTW; w += BUILD_THREADS) {      // D + 1 and DG + 1
-            S.dw[0][w] = window_min_word(S.lv[qn], w, 1, nleaf, 1 << qn);
-            S.dw[1][w] = window_min_word(S.lv[qc], w, 1, ncrit, 1 << qc);
-        }
-    }
-    __syncthreads();
-    // maxima over 2^qb positions of D + 1 (in lv[1] / lv[2]) and DG + 1 (in
-    // lv[3] / lv[4]), qb = floor(log2(min(nleaf, ncrit) + 1)) capped at 16
-    // positions
-    const int qb = min(4, 31 - __clz(min(nleaf, ncrit) + 1));
-    const unsigned *XD = S.dw[0], *XG = S.dw[1];
-    for (int q = 0; q < qb; q++) {
-        unsigned *UD = S.lv[1 + (q & 1)], *UG = S.lv[3 + (q & 1)];
-        for (int w = tid; w < NTW; w += BUILD_THREADS) {
-            UD[w] = __vmaxu4(XD[w], shifted_word(XD, w, 1 << q));
-            UG[w] = __vmaxu4(XG[w], shifted_word(XG, w, 1 << q));
-        }
-        __syncthreads();
-        XD = UD; XG = UG;
-    }
 
-    // This thread's bodies t[h] = base + tid + h * BUILD_THREADS (h < BUILD_BPT).
-    int t[BUILD_BPT];
+    // This thread's bodies t[h] = base + tid + h * BUILD_THREADS (h <
+    // BUILD_BPT): own l0, D, DG, then the window maxima from maxima over 2^qb
+    // positions, qb = floor(log2(min(nleaf, ncrit) + 1)) capped at 16 positions.
+    int t[BUILD_BPT], l0[BUILD_BPT];
+    unsigned own[BUILD_BPT];
+#pragma unroll
+    for (int h = 0; h < BUILD_BPT; h++) {
+        t[h] = base + tid + h * BUILD_THREADS;
+        own[h] = S.tab[0][t[h] - base + BH];
+        l0[h] = (t[h] <= 0 || t[h] >= n) ? 0 : cpl(t[h] - 1, t[h]) + 1;
+    }
+    const int qb = min(4, 31 - __clz(min(nleaf, ncrit) + 1));
+    int cur = 0;
+    for (int q = 0; q < qb; q++) {               // uniform over the block
+        const int hq = 1 << q;
+        const unsigned *T = S.tab[cur];
+        unsigned *U = S.tab[cur ^ 1];
+        for (int i = tid; i + 2 * hq <= BTAB; i += BUILD_THREADS) U[i] = __vmaxu2(T[i], T[i + hq]);
+        __syncthreads();
+        cur ^= 1;
+    }
     bool has[BUILD_BPT];
     unsigned desc[BUILD_BPT];
 #pragma unroll
     for (int h = 0; h < BUILD_BPT; h++) {
-        t[h] = base + tid + h * BUILD_THREADS;
-        const int pt = t[h] - p0;                              // table position
-        const int l0 = (int)byte_at(S.lv[0], pt);
-        const int winD = (int)window_max_at(XD, pt, nleaf, 1 << qb);   // 1 + max D over [t - nleaf, t]
-        has[h] = t[h] < n && l0 <= MAX_LEVEL && (l0 == 0 || winD >= l0);
+        const int it = t[h] - base + BH;
+        const int winD = (int)(window_max(S.tab[cur], it, nleaf, qb) & 0xffffu);   // 1 + max D
+        has[h] = t[h] < n && l0[h] <= MAX_LEVEL && (l0[h] == 0 || winD >= l0[h]);
         desc[h] = 0u;
         if (has[h]) {
-            const int D = (int)byte_at(S.dw[0], pt) - 1, DG = (int)byte_at(S.dw[1], pt) - 1;
-            const int hi = max(l0, min(D + 1, MAX_LEVEL));
-            const int lg = max(l0, DG + 1);
+            const int D = (int)(own[h] & 0xffffu) - 1, DG = (int)(own[h] >> 16) - 1;
+            const int hi = max(l0[h], min(D + 1, MAX_LEVEL));
+            const int lg = max(l0[h], DG + 1);
             int kind = 2;
             if (lg <= hi) {
-                const int winG = (int)window_max_at(XG, pt, ncrit, 1 << qb);   // 1 + max DG
-                kind = (lg > l0 || l0 == 0 || winG >= l0) ? 1 : 0;
+                const int winG = (int)(window_max(S.tab[cur], it, ncrit, qb) >> 16);   // 1 + max DG
+                kind = (lg > l0[h] || l0[h] == 0 || winG >= l0[h]) ? 1 : 0;
             }
-            desc[h] = (unsigned)l0 | ((unsigned)hi << 8) | ((unsigned)min(lg, 255) << 16) | ((unsigned)kind << 24);
+            desc[h] = (unsigned)l0[h] | ((unsigned)hi << 8) | ((unsigned)min(lg, 255) << 16) | ((unsigned)kind << 24);
         }
     }
     // compaction of the block's entries, in key order (slice h of the block's
