@@ -410,13 +410,19 @@ class _BlockTree:
 
 def block_cycle(pos, vel, mass, acc, dt_max: float, kmax: int, eta: float, theta: float, eps: float,
                 nleaf: int = 16, ncrit: int = 32, pack: bool = False, rebuild_every: int = 1,
-                clock: bool = False):
+                clock: bool = False, schedule: bool = False):
     """One cycle of block time steps from a synchronised state (acc: the
     acceleration at pos).  State in float64; the tree and forces see the
-    positions rounded to float32 (the stored state is float32).  Returns
-    (pos, vel, acc, pot, levels at the start, active bodies per substep),
-    with clock=True also each body's time advanced by the steps it completed
-    (dt_max for every body when the cycle ends synchronised)."""
+    positions rounded to float32 (the stored state is float32).
+
+    A substep at which no body's step ends only drifts: tree work (rebuild or
+    refit) and the walk happen at the substeps where some step ends, and a
+    rebuild scheduled for a substep without one (every rebuild_every-th
+    substep, starting with the first) is taken at the next substep that has
+    one.  Returns (pos, vel, acc, pot, levels at the start, active bodies per
+    substep), with clock=True also each body's time advanced by the steps it
+    completed (dt_max for every body when the cycle ends synchronised), with
+    schedule=True also the substeps walked and the substeps rebuilt."""
     mass = np.asarray(mass, np.float32)
     x = np.array(pos, np.float64)
     v = np.array(vel, np.float64)
@@ -430,15 +436,23 @@ def block_cycle(pos, vel, mass, acc, dt_max: float, kmax: int, eta: float, theta
     h = (1 << (kmax - lev)) * dtm / 2
     v += a * h[:, None]
     bt = None
-    nactive = []
+    due = False
+    nactive, walked, rebuilt = [], [], []
     t_done = np.zeros(x.shape[0])
     for s in range(1, nsub + 1):
         x += v * dtm
-        x32 = x.astype(np.float32)
-        if bt is None or (s - 1) % rebuild_every == 0:
-            bt = _BlockTree(x32, nleaf, ncrit, pack)
+        if (s - 1) % rebuild_every == 0:
+            due = True
         act = (s % (1 << (kmax - lev))) == 0
         nactive.append(int(act.sum()))
+        if not act.any():
+            continue
+        x32 = x.astype(np.float32)
+        if due:
+            bt = _BlockTree(x32, nleaf, ncrit, pack)
+            due = False
+            rebuilt.append(s)
+        walked.append(s)
         an, pn = bt.forces(x32, mass, theta, eps, act)
         a[act] = an[act]
         pot[act] = pn[act]
@@ -450,9 +464,12 @@ def block_cycle(pos, vel, mass, acc, dt_max: float, kmax: int, eta: float, theta
             lev[act] = new[act]
             h = (1 << (kmax - lev)) * dtm / 2
             v[act] += a[act] * h[act][:, None]
+    out = (x, v, a, pot, lev0, nactive)
     if clock:
-        return x, v, a, pot, lev0, nactive, t_done
-    return x, v, a, pot, lev0, nactive
+        out += (t_done,)
+    if schedule:
+        out += (walked, rebuilt)
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -172,3 +172,26 @@ def test_every_body_ends_the_cycle_synchronised(orc):
     assert np.all(t_done == dt)
     # every body is active at the last substep; some substeps walk a subset only
     assert nact[-1] == 3000 and min(nact) < 3000
+
+
+@pytest.mark.parametrize("rebuild", [1, 2])
+def test_an_empty_finest_level_is_the_coarser_cycle(orc, rebuild):
+    """Levels 0..2 in use and none on level 3: a cycle with max level 3 has
+    no step ending at an odd substep, so it drifts through those and must be
+    the cycle with max level 2 (same dt_max) up to the split of each drift
+    in two.  The rebuilds scheduled for its odd substeps (every 2r-th
+    substep from the first) are taken at the even ones that follow, which
+    makes them the coarse cycle's every r-th."""
+    b, a0 = start(orc, 3000, 28, 0.75, 0.01)
+    dt, eta = 1.0 / 16, 0.3
+    fine = orc.block_cycle(b.pos, b.vel, b.mass, a0, dt, 3, eta, 0.75, 0.01,
+                           rebuild_every=2 * rebuild, schedule=True)
+    coarse = orc.block_cycle(b.pos, b.vel, b.mass, a0, dt, 2, eta, 0.75, 0.01,
+                             rebuild_every=rebuild, schedule=True)
+    assert set(np.unique(fine[4]).tolist()) == {0, 1, 2}
+    assert fine[5][0::2] == [0, 0, 0, 0] and fine[5][1::2] == coarse[5]
+    assert fine[6] == [2, 4, 6, 8] and fine[7] == [2 * s for s in coarse[7]]
+    assert coarse[7] == ([1, 2, 3, 4] if rebuild == 1 else [1, 3])
+    for f, c in zip(fine[:4], coarse[:4]):
+        assert np.abs(f - c).max() <= 1e-9 * np.abs(c).max()
+    assert np.array_equal(fine[4], coarse[4])

@@ -72,6 +72,8 @@ PY_MUTATIONS = [
     ("__init__.py", "    v += a * h[:, None]\n", "    v += a * 2 * h[:, None]\n", STEP_PINS),
     ("__init__.py", "ro = open_radius(self.tree, self.skeys, self.mn, self.S, com, theta, ext)",
      "ro = open_radius(self.tree, self.skeys, self.mn, self.S, com, theta)", STEP_PINS),
+    ("__init__.py", "        if not act.any():\n            continue\n", "", STEP_PINS),
+    ("__init__.py", "            due = False\n", "", STEP_PINS),
 ]
 C_PINS = ["tests/test_oracle_keys.py", "tests/test_oracle_tree.py", "tests/test_oracle_moments.py",
           "tests/test_oracle_forces.py", "tests/test_oracle_walk.py", "tests/test_oracle_physics.py",
