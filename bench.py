@@ -667,16 +667,19 @@ def run_block(a, dev, stream):
                 bz.block_cycle(dt_max, kmax, eta, r)
             ms = timed_cycles(lambda: bz.block_cycle(dt_max, kmax, eta, r))
             act, npc, npp = B.bonsai_block_stats(bz.ctx)
+            walked, rebuilt = B.bonsai_block_substeps(bz.ctx)
             e1 = energy(bz)
             bz.sync()
             bz.close()
             out[f"eta{eta}_r{r}"] = {
                 "ms_per_cycle": ms, "body_steps_per_cycle": act, "active_fraction": act / (8 * a.n),
+                "substeps_walked": walked, "substeps_rebuilt": rebuilt,
                 "interactions_per_body_step": (npc + npp) / max(act, 1), "energy_err": (e1 - e0) / abs(e0),
                 "speedup_vs_shared": out["shared"]["ms_per_cycle"] / ms,
                 "particles_per_s_equivalent": 8 * a.n / (ms / 1e3)}
     out["what"] = ("cycle of dt_max = 8 dt: shared = 8 bonsai_steps of dt; etaE_rR = one bonsai_block_cycle "
-                   "(accuracy eta = E) with a rebuild every R substeps (refits between); "
+                   "(accuracy eta = E) with a rebuild every R substeps (refits between; substeps where no "
+                   "step ends only drift); "
                    "particles_per_s_equivalent = 8 N / cycle time")
     return out
 

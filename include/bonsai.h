@@ -132,11 +132,14 @@ int bonsai_step(bonsai_ctx *ctx, float dt);
  * float32 as 16^k >= c |a|^2, c = dt_max^4 / (eta^4 eps^2) rounded to float
  * once).  One call advances one cycle of dt_max = 2^max_level substeps of
  * dt_max / 2^max_level, all bodies synchronised at both ends: opening half
- * kicks at the start; per substep a drift of every body, a rebuild (every
- * rebuild_every-th substep, starting with the first) or a refit, a walk of
- * the bodies whose step ends (each group's box is its active bodies' box),
- * and for those the closing half kick, a new level (never coarser than the
- * substep's alignment allows) and the next opening half kick.  theta and
+ * kicks at the start; per substep a drift of every body and, if some body's
+ * step ends there, a rebuild (every rebuild_every-th substep, starting with
+ * the first; one scheduled on a substep where no step ends is taken at the
+ * next substep where one does) or a refit, a walk of the bodies whose step
+ * ends (each group's box is its active bodies' box), and for those the
+ * closing half kick, a new level (never coarser than the substep's
+ * alignment allows) and the next opening half kick.  A substep where no
+ * step ends only drifts.  theta and
  * eps are those of the last bonsai_forces / bonsai_set_params; without
  * forces yet they are computed first.  max_level = 0 is bonsai_step(dt_max).
  * One system only (BONSAI_ERR_INVALID_ARG otherwise); 0 <= max_level <= 20,
@@ -144,7 +147,9 @@ int bonsai_step(bonsai_ctx *ctx, float dt);
  * ext the half side of its build-time cube enlarged to hold its bodies'
  * current positions (a leaf from its bodies, a parent from its children), so
  * a cell that holds a walked body is always opened for that body's group.
- * No host synchronisation. */
+ * Synchronises once per walked substep: each kick leaves on the device the
+ * next substep at which some body's step ends, and the host reads it (4
+ * bytes) to schedule the next walk. */
 int bonsai_block_cycle(bonsai_ctx *ctx, float dt_max, int max_level, float eta,
                        int rebuild_every);
 
@@ -158,6 +163,12 @@ int bonsai_block_levels(bonsai_ctx *ctx, float dt_max, int max_level, float eta,
  * taken), out[1] / out[2] = body-cell / body-body interactions summed over
  * its substeps.  Synchronises. */
 int bonsai_block_stats(bonsai_ctx *ctx, long long out[3]);
+
+/* Schedule of the last block cycle (host counters, no synchronisation):
+ * out[0] = substeps walked (those where some body's step ended), out[1] =
+ * substeps rebuilt; the other substeps refitted (walked - rebuilt) or only
+ * drifted (2^max_level - walked). */
+int bonsai_block_substeps(bonsai_ctx *ctx, int32_t out[2]);
 
 /* Neighbour search and SPH density on the octree (paper Sect. 3: the tree
  * also serves neighbour search and smoothed particle hydrodynamics).  h: the

@@ -35,7 +35,7 @@ EXPORTS = ["bonsai_create", "bonsai_destroy", "bonsai_set_bodies", "bonsai_build
            "bonsai_mlp_fit_norm", "bonsai_mlp_predict", "bonsai_mlp_grad", "bonsai_mlp_train",
            "bonsai_learn_samples", "bonsai_judge", "bonsai_set_learned", "bonsai_forces_learned",
            "bonsai_get_judge", "bonsai_set_judge_interval", "bonsai_get_config", "bonsai_block_cycle",
-           "bonsai_block_levels", "bonsai_block_stats", "bonsai_sph_density", "bonsai_bench_fma",
+           "bonsai_block_levels", "bonsai_block_stats", "bonsai_block_substeps", "bonsai_sph_density", "bonsai_bench_fma",
            "bonsai_debug_hold_sort_tile"]
 
 MLP_IN, MLP_H, MLP_OUT = 12, 64, 3
@@ -103,6 +103,7 @@ def lib():
         L.bonsai_block_cycle.argtypes = [p, f, i, f, i]
         L.bonsai_block_levels.argtypes = [p, f, i, f, p]
         L.bonsai_block_stats.argtypes = [p, p]
+        L.bonsai_block_substeps.argtypes = [p, p]
         L.bonsai_sph_density.argtypes = [p, p, p, p, i]
         L.bonsai_bench_fma.argtypes = [i, i, ll, p, p]
         L.bonsai_debug_hold_sort_tile.argtypes = [p, i]
@@ -236,6 +237,13 @@ def bonsai_block_stats(ctx) -> tuple[int, int, int]:
     out = np.zeros(3, np.int64)
     _check(ctx, lib().bonsai_block_stats(ctx, out.ctypes.data))
     return int(out[0]), int(out[1]), int(out[2])
+
+
+def bonsai_block_substeps(ctx) -> tuple[int, int]:
+    """(substeps walked, substeps rebuilt) of the last block cycle."""
+    out = np.zeros(2, np.int32)
+    _check(ctx, lib().bonsai_block_substeps(ctx, out.ctypes.data))
+    return int(out[0]), int(out[1])
 
 
 def bonsai_sph_density(ctx, h, rho=None, nngb=None):

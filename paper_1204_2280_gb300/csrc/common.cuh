@@ -91,6 +91,7 @@ struct DevState {
     unsigned long long cyc_active;    // block steps, last cycle: body steps ended (forces taken)
     unsigned long long cyc_inter[2];  // block steps, last cycle: n_pc, n_pp summed over substeps
     unsigned hold_tile;               // testing aid: sort tile hold_tile - 1 never publishes (0: off)
+    unsigned blk_next;                // block steps: first substep after the last kick at which a step ends
 };
 
 struct Ctx {
@@ -164,6 +165,7 @@ struct Ctx {
     // level is vel4.w); -1 otherwise
     int block_kmax = -1;
     unsigned block_s = 0;
+    int blk_walked = 0, blk_rebuilt = 0;   // last cycle: substeps walked, substeps rebuilt
 
     // learned far-field correction (bonsai_set_learned): weights, thetas,
     // judge budget, and the judge's sample and scratch

@@ -61,6 +61,13 @@ __device__ __forceinline__ float dist_inf(float3 a, float3 b) {
 
 struct Mom32 { float M, x, y, z, q[6]; };
 
+#ifndef MOM_MINB
+#define MOM_MINB 4            // resident 256-thread blocks per SM the launch bounds ask for (5 spills)
+#endif
+#ifndef MOM_LB
+#define MOM_LB 8              // leaf bodies loaded per round trip (4: 3% slower at 2^22, 16 spills)
+#endif
+
 __device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned *p, unsigned v) {
     unsigned old;
     asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
@@ -131,15 +138,19 @@ __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__res
     // central moments C = S - s c^T and Q = 3C - tr(C) I.  The offsets are
     // at most the cell size, so nothing cancels beyond FP32 rounding.
     unsigned b = link.x, cnt = link.y & ~LEAF_BIT;
+    // The first body's key and system with its position (one round trip;
+    // loaded after the sums they cost 2% at 2^22 bodies).
+    const unsigned long long kb = sk[b];
+    const int sysb = sysid[b];
     float4 x0 = pos4[b];
     float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
     float sxx = 0.f, syy = 0.f, szz = 0.f, sxy = 0.f, sxz = 0.f, syz = 0.f;
     float3 ctr = make_float3(0.f, 0.f, 0.f);
     float ext = 0.f;
-    if (REFIT) ext = 0.5f * cell_cube(sk[b], cell_level[c], sysid[b], stc, ctr);
+    if (REFIT) ext = 0.5f * cell_cube(kb, lev, sysb, stc, ctr);
     // The bodies' loads are issued LB at a time (one round trip per LB
     // bodies instead of one per body); the sums still run in body order.
-    constexpr unsigned LB = 8;
+    constexpr unsigned LB = MOM_LB;
     for (unsigned j0 = b; j0 < b + cnt; j0 += LB) {
         float4 pb[LB];
 #pragma unroll
@@ -169,8 +180,6 @@ __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__res
     store32(c, m, mono, qa, qb);
     // The first body's key shares the key prefix of the leaf and of every
     // ancestor: it gives every geometric centre on the way up.
-    const unsigned long long kb = sk[b];
-    const int sysb = sysid[b];
     if (REFIT) {
         put_delta(c, m, make_float2(com_offset(make_float3(m.x, m.y, m.z), ctr), 2.f * ext), delta, test, inv_theta);
         cext[c] = make_float4(ctr.x, ctr.y, ctr.z, ext);
@@ -276,7 +285,7 @@ __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__res
 // last known cell count (plus an eighth) and the loop only covers a tree
 // that grew beyond it.
 template <bool REFIT>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, MOM_MINB)
 k_multipoles(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__ cell_body,
              const uint2 *__restrict__ cell_link, const uint8_t *__restrict__ cell_level,
              const uint32_t *__restrict__ cell_parent, uint32_t *cell_done,

@@ -25,6 +25,9 @@ namespace bonsai {
 #ifndef SORT_LOOKBACK
 #define SORT_LOOKBACK 8           // predecessor tiles read per look-back round trip (16: 3% slower at 2^20, 32: 9%)
 #endif
+#ifndef SORT_MATCH
+#define SORT_MATCH 0              // 1: peers of equal digit from one match.any instead of SORT_BITS ballots
+#endif
 #ifndef SORT_MIN_BLOCKS
 #define SORT_MIN_BLOCKS 2         // resident onesweep blocks per SM the register budget allows
 #endif
@@ -117,6 +120,9 @@ k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restric
     for (int it = 0; it < SORT_ITEMS; it++) {
         const int idx = wbase + it * 32 + lane;
         const unsigned d = idx < n ? (unsigned)dg[it] : R;
+#if SORT_MATCH
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+#else
         unsigned peers = __ballot_sync(0xffffffffu, d < R);
         if (d >= R) peers = ~peers;
 #pragma unroll
@@ -125,6 +131,7 @@ k_onesweep(const unsigned long long *__restrict__ kin, const uint32_t *__restric
             const unsigned bm = __ballot_sync(0xffffffffu, on);
             peers &= on ? bm : ~bm;
         }
+#endif
         pe[it] = peers;
         old[it] = (d < R && (peers & lt) == 0u) ? atomicAdd(&s_whist[warp][d], (unsigned)__popc(peers)) : 0u;
     }

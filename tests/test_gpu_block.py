@@ -156,3 +156,43 @@ def test_refit_streams_vs_oracle_and_direct_sum():
     da, _ = oracle.direct(x, s.mass, EPS)
     e = np.linalg.norm(acc - da, axis=1) / np.linalg.norm(da, axis=1)
     assert np.median(e) <= 1e-3 and np.percentile(e, 99) <= 1e-2
+
+
+@pytest.mark.parametrize("rebuild", [1, 2, 4])
+def test_empty_substeps_only_drift(rebuild):
+    """eta = 0.3 leaves level 3 empty (levels 0..2 in use): no step ends at
+    an odd substep, which then only drifts.  The GPU walks and rebuilds on
+    the oracle's schedule (rebuilds scheduled on odd substeps taken at the
+    next even one) and ends within the float32 rounding of the oracle's
+    cycle."""
+    b = W.plummer(8192, 37)
+    dt, kmax, eta = 1.0 / 16, 3, 0.3
+    with make(b) as bz:
+        acc, _ = forces(bz, b.n)
+        lev_gpu = B.bonsai_block_levels(bz.ctx, dt, kmax, eta)
+        bz.block_cycle(dt, kmax, eta, rebuild)
+        x, v = state(bz, b.n)
+        active, _, _ = B.bonsai_block_stats(bz.ctx)
+        walked, rebuilt = B.bonsai_block_substeps(bz.ctx)
+    a0 = oracle.tree_forces(b.pos, b.mass, THETA, EPS, 16, 32).acc
+    ox, ov, oa, op, lev0, nact, o_walked, o_rebuilt = oracle.block_cycle(
+        b.pos, b.vel, b.mass, a0, dt, kmax, eta, THETA, EPS, 16, 32, False, rebuild, schedule=True)
+    assert set(np.unique(lev0).tolist()) == {0, 1, 2} and nact[0::2] == [0, 0, 0, 0]
+    assert o_walked == [2, 4, 6, 8] and (walked, rebuilt) == (len(o_walked), len(o_rebuilt))
+    same = lev_gpu == lev0
+    assert same.mean() > 0.995
+    disp = np.linalg.norm(ox - b.pos, axis=1)
+    dx = np.linalg.norm(x - ox, axis=1)
+    dv = np.linalg.norm(v - ov, axis=1) / np.linalg.norm(ov - b.vel, axis=1)
+    assert np.all(dx[same] <= 3e-7 * np.linalg.norm(ox[same], axis=1) + 1e-4 * disp[same])
+    assert np.median(dv[same]) <= 1e-4 and np.percentile(dv[same], 99) <= 3e-3
+    assert np.all(dx <= 1e-2 * disp + 1e-6)
+    assert abs(active - sum(nact)) <= 0.01 * sum(nact)
+
+
+def test_every_substep_walked_when_the_finest_level_is_used():
+    b = W.plummer(12000, 33)
+    with make(b) as bz:
+        forces(bz, b.n)
+        bz.block_cycle(1.0 / 16, 2, 1e-6, 3)
+        assert B.bonsai_block_substeps(bz.ctx) == (4, 2)      # rebuilt at substeps 1 and 4
