@@ -124,12 +124,6 @@ __global__ void k_block_drift(float4 *pos, const float4 *__restrict__ vel, int n
     }
 }
 
-// Refit: the arrival counters of the multipole climb start at zero again.
-__global__ void k_block_refit_reset(const DevState *__restrict__ st, uint32_t *cell_done) {
-    const unsigned nc = st->ncells;
-    for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) cell_done[c] = 0u;
-}
-
 // The walk's interaction totals of a substep added to the cycle's; the
 // next-step-end minimum starts over for the kick that follows.
 __global__ void k_block_accum(DevState *st, int first) {
@@ -169,7 +163,6 @@ static cudaError_t block_next(Ctx &c, unsigned s, unsigned nsub, unsigned &nx) {
 static cudaError_t block_cycle(Ctx &c, float dt_max, int kmax, float eta, int rebuild) {
     const int n = (int)c.n;
     const int grid = (int)std::min<long long>((c.n + 255) / 256, (long long)c.num_sms * 8);
-    const unsigned cgrid = (unsigned)std::min<long long>((c.ccap + 255) / 256, (long long)c.num_sms * 8);
     const float dtm = ldexpf(dt_max, -kmax);
     const float cc = block_constant(dt_max, eta, c.eps);
     const unsigned nsub = 1u << kmax;
@@ -200,7 +193,6 @@ static cudaError_t block_cycle(Ctx &c, float dt_max, int kmax, float eta, int re
             c.blk_rebuilt++;
         } else {
             k_block_drift<<<grid, 256, 0, c.stream>>>(c.pos4, c.vel4, n, dtm, quiet + 1u);
-            k_block_refit_reset<<<cgrid, 256, 0, c.stream>>>(c.st, c.cell_done);
             if ((e = launch_multipoles_refit(c)) != cudaSuccess) return e;
         }
         if ((e = launch_open_radius(c, c.theta)) != cudaSuccess) return e;

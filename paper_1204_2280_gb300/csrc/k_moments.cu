@@ -7,8 +7,9 @@
 // from the first body, then from the com).  Parents combine their children
 // by the parallel-axis theorem,
 //   Q_p = sum_k [ Q_k + M_k (3 d_k d_k^T - |d_k|^2 I) ],  d_k = com_k - com_p,
-// in one launch: each thread finishing a cell bumps its parent's arrival
-// counter and the last child to arrive combines the parent (no waiting).
+// in a second launch: each thread finishing a cell counts down its parent's
+// arrival word and the last internal child to arrive combines the parent
+// (no waiting).
 // The root of each system (level 0) combines in FP64: FP64 arithmetic runs
 // at a small fraction of the FP32 rate here, so the thread finishing each
 // level-1 cell writes that cell's FP64 terms about the root cube's centre O
@@ -64,6 +65,9 @@ struct Mom32 { float M, x, y, z, q[6]; };
 #ifndef MOM_MINB
 #define MOM_MINB 4            // resident 256-thread blocks per SM the launch bounds ask for (5 spills)
 #endif
+#ifndef MOM_MINB2
+#define MOM_MINB2 4           // the same for the combine pass
+#endif
 #ifndef MOM_LB
 #define MOM_LB 8              // leaf bodies loaded per round trip (4: 3% slower at 2^22, 16 spills)
 #endif
@@ -117,44 +121,59 @@ __device__ __forceinline__ void root_terms(unsigned c, const Mom32 &m, unsigned 
 // ext_k)), stored with the centre in cext, and delta holds (|com - centre|,
 // 2 ext): the opening radius 2 ext / theta + delta then keeps every cell that
 // holds a body of a group opened for it (theta < 2 / sqrt(3)).
-template <bool REFIT>
-__device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__restrict__ stc, DevState *st,
-                                               const uint2 *__restrict__ cell_body, const uint2 *__restrict__ cell_link,
-                                               const uint8_t *__restrict__ cell_level,
-                                               const uint32_t *__restrict__ cell_parent, uint32_t *cell_done,
-                                               const float4 *__restrict__ pos4, const unsigned long long *__restrict__ sk,
-                                               const uint8_t *__restrict__ sysid, float4 *mono, float4 *qa, float2 *qb,
-                                               float2 *delta, double *shadow, float4 *cext,
-                                               float4 *test, float inv_theta) {
-    // The link, level and parent in one round trip (the parent of a root
-    // is never used: a root leaf does not climb).
-    uint2 link = cell_link[c];
-    int lev = cell_level[c];                         // level and parent, for the climb
-    unsigned p = cell_parent[c];
-    if (!(link.y & LEAF_BIT)) return;
+//
+// Two launches.  The leaf pass sums every leaf from its bodies (no atomics,
+// no fences) and gives every internal cell its arrival word, 2 x (internal
+// children) plus a start bit when it has none; leaves get 0.  The combine
+// pass starts at the internal cells with the start bit (all children leaves,
+// complete since the leaf pass) and climbs: a finished cell subtracts 2 from
+// its parent's word and the child that brings it to zero combines the
+// parent.  The start bit is never touched by the subtractions, so a cell's
+// thread can test it while its children arrive.
 
-    // Leaf from its bodies in one pass: mass, first and second moments of
-    // the offsets u = x - x0 from the first body; then with c = s/M the
-    // central moments C = S - s c^T and Q = 3C - tr(C) I.  The offsets are
-    // at most the cell size, so nothing cancels beyond FP32 rounding.
-    unsigned b = link.x, cnt = link.y & ~LEAF_BIT;
+struct MomArrays {
+    const DevState *__restrict__ stc;
+    const uint2 *__restrict__ cell_body;
+    const uint2 *__restrict__ cell_link;
+    const uint8_t *__restrict__ cell_level;
+    const uint32_t *__restrict__ cell_parent;
+    uint32_t *cell_done;
+    const float4 *__restrict__ pos4;
+    const unsigned long long *__restrict__ sk;
+    const uint8_t *__restrict__ sysid;
+    float4 *mono, *qa;
+    float2 *qb, *delta;
+    double *shadow;
+    float4 *cext, *test;
+    float inv_theta;
+    bool multi;                       // several systems (else every body is in system 0)
+};
+
+// Leaf c (level lev, bodies link.x ..) from its bodies in one pass: mass,
+// first and second moments of the offsets u = x - x0 from the first body;
+// then with c = s/M the central moments C = S - s c^T and Q = 3C - tr(C) I.
+// The offsets are at most the cell size, so nothing cancels beyond FP32
+// rounding.  A level-1 leaf also writes its FP64 root terms.
+template <bool REFIT>
+__device__ __forceinline__ void leaf_cell(unsigned c, uint2 link, int lev, const MomArrays &a) {
+    const unsigned b = link.x, cnt = link.y & ~LEAF_BIT;
     // The first body's key and system with its position (one round trip;
     // loaded after the sums they cost 2% at 2^22 bodies).
-    const unsigned long long kb = sk[b];
-    const int sysb = sysid[b];
-    float4 x0 = pos4[b];
+    const unsigned long long kb = a.sk[b];
+    const int sysb = a.multi ? a.sysid[b] : 0;
+    const float4 x0 = a.pos4[b];
     float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
     float sxx = 0.f, syy = 0.f, szz = 0.f, sxy = 0.f, sxz = 0.f, syz = 0.f;
     float3 ctr = make_float3(0.f, 0.f, 0.f);
     float ext = 0.f;
-    if (REFIT) ext = 0.5f * cell_cube(kb, lev, sysb, stc, ctr);
+    if (REFIT) ext = 0.5f * cell_cube(kb, lev, sysb, a.stc, ctr);
     // The bodies' loads are issued LB at a time (one round trip per LB
     // bodies instead of one per body); the sums still run in body order.
     constexpr unsigned LB = MOM_LB;
     for (unsigned j0 = b; j0 < b + cnt; j0 += LB) {
         float4 pb[LB];
 #pragma unroll
-        for (unsigned u = 0; u < LB; u++) pb[u] = j0 + u < b + cnt ? pos4[j0 + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (unsigned u = 0; u < LB; u++) pb[u] = j0 + u < b + cnt ? a.pos4[j0 + u] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (unsigned u = 0; u < LB; u++) {
             if (j0 + u >= b + cnt) break;
@@ -177,155 +196,194 @@ __device__ __forceinline__ void multipole_cell(unsigned c, const DevState *__res
     const float tr = Cxx + Cyy + Czz;
     m.q[0] = 3.f * Cxx - tr; m.q[1] = 3.f * Cyy - tr; m.q[2] = 3.f * Czz - tr;
     m.q[3] = 3.f * fmaf(-sx, cy, sxy); m.q[4] = 3.f * fmaf(-sx, cz, sxz); m.q[5] = 3.f * fmaf(-sy, cz, syz);
-    store32(c, m, mono, qa, qb);
-    // The first body's key shares the key prefix of the leaf and of every
-    // ancestor: it gives every geometric centre on the way up.
+    store32(c, m, a.mono, a.qa, a.qb);
     if (REFIT) {
-        put_delta(c, m, make_float2(com_offset(make_float3(m.x, m.y, m.z), ctr), 2.f * ext), delta, test, inv_theta);
-        cext[c] = make_float4(ctr.x, ctr.y, ctr.z, ext);
+        put_delta(c, m, make_float2(com_offset(make_float3(m.x, m.y, m.z), ctr), 2.f * ext), a.delta, a.test,
+                  a.inv_theta);
+        a.cext[c] = make_float4(ctr.x, ctr.y, ctr.z, ext);
     } else {
-        put_delta(c, m, cell_delta(kb, lev, sysb, make_float3(m.x, m.y, m.z), stc), delta, test, inv_theta);
+        put_delta(c, m, cell_delta(kb, lev, sysb, make_float3(m.x, m.y, m.z), a.stc), a.delta, a.test, a.inv_theta);
     }
+    if (lev == 1) root_terms(c, m, kb, sysb, a.stc, a.shadow);
+}
 
-    // Up the tree while this thread is the last child to finish (roots are
-    // the level-0 cells, one per system).  The tree is read-only here: the
-    // parent's link and level and the next parent are loaded with the
-    // arrival atomic, so only the children's moments wait for its acquire.
-    while (lev != 0) {
-        const uint2 plk = cell_link[p];          // (first child, child count) of the parent
-        const int lv = cell_level[p];
-        const unsigned gp = lv != 0 ? cell_parent[p] : 0u;
-        if (lev == 1) root_terms(c, m, kb, sysb, stc, shadow);
-        // Release: this cell's moments are visible to whoever reads the
-        // counter after this add; acquire: the last child to arrive sees
-        // every sibling's moments (each sibling's add heads a release
-        // sequence that this read-modify-write extends).
-        if (atom_add_acq_rel_gpu(&cell_done[p], 1u) != plk.y - 1u) return;
-        c = p;
-        p = gp;
-        const unsigned cb = plk.x, nch = plk.y;
-        lev = lv;
-        if (lv == 0) {
-            float3 o;
-            cell_cube(kb, 0, sysb, stc, o);
-            double t[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-            for (unsigned k = 0; k < nch; k++) {
-                const double *sk2 = shadow + 10 * (size_t)(cb + k);
+// Internal cell c (level lv, children plk.x .. plk.x + plk.y - 1, all
+// complete) from its children; kb, sysb: the key and system of a body inside
+// it (its key prefix gives the cell's centre).  A root combines the FP64
+// terms of its level-1 cells; a level-1 cell writes its own.
+template <bool REFIT>
+__device__ __forceinline__ void combine_cell(unsigned c, int lv, uint2 plk, unsigned long long kb, int sysb,
+                                             const MomArrays &a) {
+    const unsigned cb = plk.x, nch = plk.y;
+    Mom32 m;
+    if (lv == 0) {
+        float3 o;
+        cell_cube(kb, 0, sysb, a.stc, o);
+        double t[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (unsigned k = 0; k < nch; k++) {
+            const double *sk2 = a.shadow + 10 * (size_t)(cb + k);
 #pragma unroll
-                for (int i = 0; i < 10; i++) t[i] += __ldcg(sk2 + i);
-            }
-            const double inv2 = t[0] > 0 ? 1.0 / t[0] : 0.0;
-            const double sx = t[1] * inv2, sy = t[2] * inv2, sz = t[3] * inv2;   // com - O
-            const double s2 = sx * sx + sy * sy + sz * sz;
-            m.M = (float)t[0];
-            m.x = (float)(o.x + sx); m.y = (float)(o.y + sy); m.z = (float)(o.z + sz);
-            m.q[0] = (float)(t[4] - t[0] * (3 * sx * sx - s2));
-            m.q[1] = (float)(t[5] - t[0] * (3 * sy * sy - s2));
-            m.q[2] = (float)(t[6] - t[0] * (3 * sz * sz - s2));
-            m.q[3] = (float)(t[7] - t[0] * (3 * sx * sy));
-            m.q[4] = (float)(t[8] - t[0] * (3 * sx * sz));
-            m.q[5] = (float)(t[9] - t[0] * (3 * sy * sz));
-        } else {
-            // Children's moments loaded together (at most 8, unrolled): one
-            // round trip to L2 per level instead of one per child.
-            float4 mo[8];
+            for (int i = 0; i < 10; i++) t[i] += __ldcg(sk2 + i);
+        }
+        const double inv2 = t[0] > 0 ? 1.0 / t[0] : 0.0;
+        const double sx = t[1] * inv2, sy = t[2] * inv2, sz = t[3] * inv2;   // com - O
+        const double s2 = sx * sx + sy * sy + sz * sz;
+        m.M = (float)t[0];
+        m.x = (float)(o.x + sx); m.y = (float)(o.y + sy); m.z = (float)(o.z + sz);
+        m.q[0] = (float)(t[4] - t[0] * (3 * sx * sx - s2));
+        m.q[1] = (float)(t[5] - t[0] * (3 * sy * sy - s2));
+        m.q[2] = (float)(t[6] - t[0] * (3 * sz * sz - s2));
+        m.q[3] = (float)(t[7] - t[0] * (3 * sx * sy));
+        m.q[4] = (float)(t[8] - t[0] * (3 * sx * sz));
+        m.q[5] = (float)(t[9] - t[0] * (3 * sy * sz));
+    } else {
+        // Children's moments loaded together (at most 8, unrolled): one
+        // round trip to L2 per level instead of one per child.  By the
+        // parallel-axis theorem,
+        //   Q_p = sum_k [ Q_k + M_k (3 d_k d_k^T - |d_k|^2 I) ],  d_k = com_k - com_p.
+        float4 mo[8];
 #pragma unroll
-            for (int k = 0; k < 8; k++)
-                mo[k] = k < (int)nch ? __ldcg(mono + cb + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float c0x = mo[0].x, c0y = mo[0].y, c0z = mo[0].z;
-            float fM = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
+        for (int k = 0; k < 8; k++) mo[k] = k < (int)nch ? __ldcg(a.mono + cb + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float c0x = mo[0].x, c0y = mo[0].y, c0z = mo[0].z;
+        float fM = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
 #pragma unroll
-            for (int k = 0; k < 8; k++) {
-                if (k < (int)nch) {
-                    fM += mo[k].w;
-                    ax = fmaf(mo[k].w, mo[k].x - c0x, ax);
-                    ay = fmaf(mo[k].w, mo[k].y - c0y, ay);
-                    az = fmaf(mo[k].w, mo[k].z - c0z, az);
-                }
-            }
-            float inv2 = fM > 0.f ? 1.f / fM : 0.f;
-            m.M = fM; m.x = c0x + ax * inv2; m.y = c0y + ay * inv2; m.z = c0z + az * inv2;
-            for (int i = 0; i < 6; i++) m.q[i] = 0.f;
-#pragma unroll
-            for (int k = 0; k < 8; k++) {
-                if (k < (int)nch) {
-                    const float4 a = __ldcg(qa + cb + k);
-                    const float2 q2 = __ldcg(qb + cb + k);
-                    const float dx = mo[k].x - m.x, dy = mo[k].y - m.y, dz = mo[k].z - m.z;
-                    const float d2 = dx * dx + dy * dy + dz * dz;
-                    m.q[0] += -a.x + mo[k].w * (3.f * dx * dx - d2);
-                    m.q[1] += -a.y + mo[k].w * (3.f * dy * dy - d2);
-                    m.q[2] += -a.z + mo[k].w * (3.f * dz * dz - d2);
-                    m.q[3] += -a.w + mo[k].w * (3.f * dx * dy);
-                    m.q[4] += -q2.x + mo[k].w * (3.f * dx * dz);
-                    m.q[5] += -q2.y + mo[k].w * (3.f * dy * dz);
-                }
+        for (int k = 0; k < 8; k++) {
+            if (k < (int)nch) {
+                fM += mo[k].w;
+                ax = fmaf(mo[k].w, mo[k].x - c0x, ax);
+                ay = fmaf(mo[k].w, mo[k].y - c0y, ay);
+                az = fmaf(mo[k].w, mo[k].z - c0z, az);
             }
         }
-        store32(c, m, mono, qa, qb);
-        if (REFIT) {
-            float3 pc;
-            float e = 0.5f * cell_cube(kb, lv, sysb, stc, pc);
-            for (unsigned k = 0; k < nch; k++) {
-                const float4 ce = __ldcg(cext + cb + k);
-                e = fmaxf(e, dist_inf(make_float3(ce.x, ce.y, ce.z), pc) + ce.w);
+        const float inv2 = fM > 0.f ? 1.f / fM : 0.f;
+        m.M = fM; m.x = c0x + ax * inv2; m.y = c0y + ay * inv2; m.z = c0z + az * inv2;
+        for (int i = 0; i < 6; i++) m.q[i] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            if (k < (int)nch) {
+                const float4 q4 = __ldcg(a.qa + cb + k);
+                const float2 q2 = __ldcg(a.qb + cb + k);
+                const float dx = mo[k].x - m.x, dy = mo[k].y - m.y, dz = mo[k].z - m.z;
+                const float d2 = dx * dx + dy * dy + dz * dz;
+                m.q[0] += -q4.x + mo[k].w * (3.f * dx * dx - d2);
+                m.q[1] += -q4.y + mo[k].w * (3.f * dy * dy - d2);
+                m.q[2] += -q4.z + mo[k].w * (3.f * dz * dz - d2);
+                m.q[3] += -q4.w + mo[k].w * (3.f * dx * dy);
+                m.q[4] += -q2.x + mo[k].w * (3.f * dx * dz);
+                m.q[5] += -q2.y + mo[k].w * (3.f * dy * dz);
             }
-            put_delta(c, m, make_float2(com_offset(make_float3(m.x, m.y, m.z), pc), 2.f * e), delta, test, inv_theta);
-            cext[c] = make_float4(pc.x, pc.y, pc.z, e);
+        }
+    }
+    store32(c, m, a.mono, a.qa, a.qb);
+    if (REFIT) {
+        float3 pc;
+        float e = 0.5f * cell_cube(kb, lv, sysb, a.stc, pc);
+        for (unsigned k = 0; k < nch; k++) {
+            const float4 ce = __ldcg(a.cext + cb + k);
+            e = fmaxf(e, dist_inf(make_float3(ce.x, ce.y, ce.z), pc) + ce.w);
+        }
+        put_delta(c, m, make_float2(com_offset(make_float3(m.x, m.y, m.z), pc), 2.f * e), a.delta, a.test,
+                  a.inv_theta);
+        a.cext[c] = make_float4(pc.x, pc.y, pc.z, e);
+    } else {
+        put_delta(c, m, cell_delta(kb, lv, sysb, make_float3(m.x, m.y, m.z), a.stc), a.delta, a.test, a.inv_theta);
+    }
+    if (lv == 1) root_terms(c, m, kb, sysb, a.stc, a.shadow);
+}
+
+// Leaf pass: one thread per cell, from the end of the breadth-first
+// numbering.  A leaf sums its bodies; an internal cell writes its arrival
+// word from its children's leaf bits (contiguous links); a leaf's word is 0.
+template <bool REFIT>
+__global__ void __launch_bounds__(256, MOM_MINB)
+k_mom_leaves(MomArrays a) {
+    const unsigned nc = a.stc->ncells;
+    if (a.stc->status & ST_TIMEOUT) return;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+        const unsigned c = nc - 1u - i;
+        const uint2 link = a.cell_link[c];
+        const int lev = a.cell_level[c];
+        if (link.y & LEAF_BIT) {
+            a.cell_done[c] = 0u;
+            leaf_cell<REFIT>(c, link, lev, a);
         } else {
-            put_delta(c, m, cell_delta(kb, lv, sysb, make_float3(m.x, m.y, m.z), stc), delta, test, inv_theta);
+            uint2 ch[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) ch[k] = k < (int)link.y ? a.cell_link[link.x + k] : make_uint2(0u, LEAF_BIT);
+            unsigned ni = 0;
+#pragma unroll
+            for (int k = 0; k < 8; k++) ni += (ch[k].y & LEAF_BIT) ? 0u : 1u;
+            a.cell_done[c] = (ni << 1) | (ni == 0u ? 1u : 0u);
         }
     }
 }
 
-// One thread per cell (leaves do the work): leaf moments from the bodies,
-// then up the tree while it is the last child to arrive.  A thread per cell
-// keeps many climbs in flight (a grid-stride loop that serialises several
-// cells per thread measured twice as slow), so the launch is sized from the
-// last known cell count (plus an eighth) and the loop only covers a tree
-// that grew beyond it.
+// Combine pass: the internal cells with the start bit combine their
+// (leaf) children, then climb while they are the last internal child to
+// arrive.  Arrival: release (this cell's moments are visible to whoever
+// reads the word after the subtraction) and acquire (the last child sees
+// every sibling's moments: each sibling's subtraction heads a release
+// sequence that this read-modify-write extends).
 template <bool REFIT>
-__global__ void __launch_bounds__(256, MOM_MINB)
-k_multipoles(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__ cell_body,
-             const uint2 *__restrict__ cell_link, const uint8_t *__restrict__ cell_level,
-             const uint32_t *__restrict__ cell_parent, uint32_t *cell_done,
-             const float4 *__restrict__ pos4, const unsigned long long *__restrict__ sk,
-             const uint8_t *__restrict__ sysid, float4 *mono, float4 *qa, float2 *qb, float2 *delta,
-             double *shadow, float4 *cext, float4 *test, float inv_theta) {
-    // Cells are numbered breadth first, so the deepest leaves, whose climbs
-    // to the root are the longest, have the largest numbers: blocks take
-    // the cells from the end so that those climbs start in the first wave.
-    const unsigned nc = stc->ncells;
-    if (stc->status & ST_TIMEOUT) return;
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
-        multipole_cell<REFIT>(nc - 1u - i, stc, st, cell_body, cell_link, cell_level, cell_parent, cell_done, pos4, sk,
-                              sysid, mono, qa, qb, delta, shadow, cext, test, inv_theta);
+__global__ void __launch_bounds__(256, MOM_MINB2)
+k_mom_combine(MomArrays a) {
+    const unsigned nc = a.stc->ncells;
+    if (a.stc->status & ST_TIMEOUT) return;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+        unsigned c = nc - 1u - i;
+        if (!(__ldcg(a.cell_done + c) & 1u)) continue;
+        uint2 plk = a.cell_link[c];
+        int lv = a.cell_level[c];
+        unsigned p = lv != 0 ? a.cell_parent[c] : 0u;
+        // a body inside the cell: its key prefix gives the centre of the
+        // cell and of every ancestor
+        const unsigned b = a.cell_body[c].x;
+        const unsigned long long kb = a.sk[b];
+        const int sysb = a.multi ? a.sysid[b] : 0;
+        combine_cell<REFIT>(c, lv, plk, kb, sysb, a);
+        while (lv != 0) {
+            // the parent's link and level and the next parent are loaded with
+            // the arrival atomic (the tree is read-only here)
+            const uint2 pl = a.cell_link[p];
+            const int plv = a.cell_level[p];
+            const unsigned gp = plv != 0 ? a.cell_parent[p] : 0u;
+            if (atom_add_acq_rel_gpu(&a.cell_done[p], 0xfffffffeu) != 2u) break;   // subtract 2
+            c = p; plk = pl; lv = plv; p = gp;
+            combine_cell<REFIT>(c, lv, plk, kb, sysb, a);
+        }
+    }
 }
 
 // Launch size: one thread per cell of the last known cell count (plus an
-// eighth), or of a typical count for the leaf size when none is known.
+// eighth), or of a typical count for the leaf size when none is known; a
+// grid-stride loop covers a tree that grew beyond it.
 static unsigned multipole_blocks(const Ctx &c) {
     long long cells = c.cells_hint > 0 ? c.cells_hint + c.cells_hint / 8 + 1024 : 8 * c.n / c.nleaf + 1024;
     if (cells > c.ccap) cells = c.ccap;
     return (unsigned)((cells + 255) / 256);
 }
 
+static MomArrays mom_arrays(Ctx &c, float theta, bool refit) {
+    return MomArrays{c.st, c.cell_body, c.cell_link, c.cell_level, c.cell_parent, c.cell_done, c.pos4, c.keys,
+                     c.sysid, c.mono, c.quadA, c.quadB, c.delta, c.shadow, refit ? c.cext : nullptr,
+                     theta > 0.f ? c.test : nullptr, theta > 0.f ? 1.0f / theta : 0.f, c.nsys > 1};
+}
+
 // theta > 0: also the walk's MAC records for that opening angle (what
 // launch_open_radius writes), so that a step needs no separate pass.
 cudaError_t launch_multipoles(Ctx &c, float theta) {
-    k_multipoles<false><<<multipole_blocks(c), 256, 0, c.stream>>>(
-        c.st, c.st, c.cell_body, c.cell_link, c.cell_level, c.cell_parent, c.cell_done, c.pos4, c.keys, c.sysid,
-        c.mono, c.quadA, c.quadB, c.delta, c.shadow, nullptr, theta > 0.f ? c.test : nullptr,
-        theta > 0.f ? 1.0f / theta : 0.f);
+    const MomArrays a = mom_arrays(c, theta, false);
+    k_mom_leaves<false><<<multipole_blocks(c), 256, 0, c.stream>>>(a);
+    k_mom_combine<false><<<multipole_blocks(c), 256, 0, c.stream>>>(a);
     return cudaGetLastError();
 }
 
 // Moments of the existing cells at the bodies' current positions (block time
 // steps between rebuilds), with each cell's cube enlarged to hold its bodies.
 cudaError_t launch_multipoles_refit(Ctx &c) {
-    k_multipoles<true><<<multipole_blocks(c), 256, 0, c.stream>>>(
-        c.st, c.st, c.cell_body, c.cell_link, c.cell_level, c.cell_parent, c.cell_done, c.pos4, c.keys, c.sysid,
-        c.mono, c.quadA, c.quadB, c.delta, c.shadow, c.cext, nullptr, 0.f);
+    const MomArrays a = mom_arrays(c, 0.f, true);
+    k_mom_leaves<true><<<multipole_blocks(c), 256, 0, c.stream>>>(a);
+    k_mom_combine<true><<<multipole_blocks(c), 256, 0, c.stream>>>(a);
     return cudaGetLastError();
 }
 

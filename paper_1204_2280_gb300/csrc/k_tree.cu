@@ -348,7 +348,7 @@ constexpr int WRITE_THREADS = 512;
 __global__ void __launch_bounds__(WRITE_THREADS)
 k_build_write(const uint4 *__restrict__ entries, int ncrit, const unsigned *__restrict__ blockcount, int nblocks,
               long long ccap, DevState *st, uint2 *cell_body, uint2 *cell_link, uint8_t *cell_level,
-              uint32_t *cell_parent, uint32_t *cell_done, uint32_t *cell_cb, uint2 *groups, uint8_t *group_lvl) {
+              uint32_t *cell_parent, uint32_t *cell_cb, uint2 *groups, uint8_t *group_lvl) {
     constexpr int NW = WRITE_THREADS / 32;
     __shared__ unsigned s_wc[NROWS][NW];
     __shared__ unsigned s_base[NROWS];
@@ -430,7 +430,6 @@ k_build_write(const uint4 *__restrict__ entries, int ncrit, const unsigned *__re
                 const unsigned cb = r < MAX_LEVEL ? s_base[r + 1] + s_wc[r + 1][warp] + __popc(bnext & lt) : 0u;
                 cell_cb[c] = cb;
                 cell_level[c] = (uint8_t)r;
-                cell_done[c] = 0u;
                 if (r == 0) cell_parent[c] = 0xffffffffu;
                 if (r == hi) {
                     cell_body[c] = make_uint2(t, e.y);
@@ -652,7 +651,7 @@ cudaError_t launch_build(Ctx &c) {
     const bool pack = c.group_pack != 0;
     k_build_write<<<c.nbblocks, WRITE_THREADS, 0, c.stream>>>(
         c.build_entries, c.ncrit, c.blockcount, c.nbblocks, c.ccap, c.st, c.cell_body, c.cell_link, c.cell_level,
-        c.cell_parent, c.cell_done, c.cell_cb, pack ? c.groups_raw : c.groups, pack ? c.group_lvl : nullptr);
+        c.cell_parent, c.cell_cb, pack ? c.groups_raw : c.groups, pack ? c.group_lvl : nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (pack) {
