@@ -74,7 +74,7 @@ cudaError_t alloc_bodies(Ctx &c, long long n) {
     a.take(c.build_entries, (size_t)nbb * BUILD_BODIES, plan);
     a.take(c.cell_body, ccap, plan); a.take(c.cell_link, ccap, plan);
     a.take(c.cell_level, ccap, plan); a.take(c.cell_parent, ccap, plan);
-    a.take(c.cell_done, ccap, plan); a.take(c.cell_cb, ccap, plan);
+    a.take(c.cell_done, ccap, plan); a.take(c.cell_cb, ccap, plan); a.take(c.cell_start, ccap, plan);
     a.take(c.mono, ccap, plan); a.take(c.quadA, ccap, plan); a.take(c.quadB, ccap, plan);
     a.take(c.test, ccap, plan); a.take(c.delta, ccap, plan); a.take(c.cext, ccap, plan);
     a.take(c.shadow, 10 * (size_t)(ccap < 585 * MAX_SYSTEMS ? ccap : 585 * MAX_SYSTEMS), plan);   // FP64 root terms of the level-1 cells

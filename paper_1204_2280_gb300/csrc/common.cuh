@@ -92,6 +92,7 @@ struct DevState {
     unsigned long long cyc_inter[2];  // block steps, last cycle: n_pc, n_pp summed over substeps
     unsigned hold_tile;               // testing aid: sort tile hold_tile - 1 never publishes (0: off)
     unsigned blk_next;                // block steps: first substep after the last kick at which a step ends
+    unsigned mom_starts;              // multipoles: internal cells whose children are all leaves
 };
 
 struct Ctx {
@@ -126,6 +127,7 @@ struct Ctx {
     uint2 *cell_body = nullptr, *cell_link = nullptr;
     uint8_t *cell_level = nullptr;
     uint32_t *cell_parent = nullptr, *cell_done = nullptr, *cell_cb = nullptr;
+    uint32_t *cell_start = nullptr;  // multipoles: the internal cells whose children are all leaves
     float4 *mono = nullptr, *quadA = nullptr, *test = nullptr;
     float2 *quadB = nullptr;
     float2 *delta = nullptr;         // per cell: (|com - centre|, side l; after a refit 2 ext)

@@ -65,8 +65,17 @@ struct Mom32 { float M, x, y, z, q[6]; };
 #ifndef MOM_MINB
 #define MOM_MINB 4            // resident 256-thread blocks per SM the launch bounds ask for (5 spills)
 #endif
+#ifndef MOM_CTHREADS
+#define MOM_CTHREADS 128      // combine pass: threads per block
+#endif
 #ifndef MOM_MINB2
-#define MOM_MINB2 4           // the same for the combine pass
+#define MOM_MINB2 6           // combine pass: resident blocks per SM the launch bounds ask for
+#endif
+#ifndef MOM_CPASYNC
+#define MOM_CPASYNC 1         // combine: children's data through asynchronous copies to shared memory
+#endif                        // (0: register loads in two round trips, 5-11% slower at 2^20..2^22)
+#ifndef MOM_CBLOCKS
+#define MOM_CBLOCKS 6         // combine pass: blocks per SM of its persistent grid (32 KB of staging each)
 #endif
 #ifndef MOM_LB
 #define MOM_LB 8              // leaf bodies loaded per round trip (4: 3% slower at 2^22, 16 spills)
@@ -123,13 +132,19 @@ __device__ __forceinline__ void root_terms(unsigned c, const Mom32 &m, unsigned 
 // holds a body of a group opened for it (theta < 2 / sqrt(3)).
 //
 // Two launches.  The leaf pass sums every leaf from its bodies (no atomics,
-// no fences) and gives every internal cell its arrival word, 2 x (internal
-// children) plus a start bit when it has none; leaves get 0.  The combine
-// pass starts at the internal cells with the start bit (all children leaves,
-// complete since the leaf pass) and climbs: a finished cell subtracts 2 from
-// its parent's word and the child that brings it to zero combines the
-// parent.  The start bit is never touched by the subtractions, so a cell's
-// thread can test it while its children arrive.
+// no fences), gives every internal cell its arrival word (the number of its
+// internal children) and lists the internal cells without any.  The combine
+// pass starts at the listed cells (all children leaves, complete since the
+// leaf pass) and climbs: a finished cell decrements its parent's word and
+// the child that brings it to zero combines the parent.
+
+// 16-byte asynchronous copy global -> shared through L2 (zero fill when
+// !valid: nothing is read).
+__device__ __forceinline__ void cp_async16(float4 *sdst, const float4 *gsrc, bool valid) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gsrc), "r"(valid ? 16 : 0)
+                 : "memory");
+}
 
 struct MomArrays {
     const DevState *__restrict__ stc;
@@ -147,6 +162,8 @@ struct MomArrays {
     float4 *cext, *test;
     float inv_theta;
     bool multi;                       // several systems (else every body is in system 0)
+    uint32_t *starts;                 // internal cells whose children are all leaves
+    unsigned *nstart;                 // their number
 };
 
 // Leaf c (level lev, bodies link.x ..) from its bodies in one pass: mass,
@@ -213,7 +230,7 @@ __device__ __forceinline__ void leaf_cell(unsigned c, uint2 link, int lev, const
 // terms of its level-1 cells; a level-1 cell writes its own.
 template <bool REFIT>
 __device__ __forceinline__ void combine_cell(unsigned c, int lv, uint2 plk, unsigned long long kb, int sysb,
-                                             const MomArrays &a) {
+                                             const MomArrays &a, float4 *stage = nullptr) {
     const unsigned cb = plk.x, nch = plk.y;
     Mom32 m;
     if (lv == 0) {
@@ -242,8 +259,34 @@ __device__ __forceinline__ void combine_cell(unsigned c, int lv, uint2 plk, unsi
         // parallel-axis theorem,
         //   Q_p = sum_k [ Q_k + M_k (3 d_k d_k^T - |d_k|^2 I) ],  d_k = com_k - com_p.
         float4 mo[8];
+#if MOM_CPASYNC
+        // masses and centres and the quadrupoles' first four components
+        // land in shared memory by asynchronous copies (no registers held),
+        // the last two in registers: one round trip for all of it
+        float2 qq2[8];
+        if (stage) {
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const unsigned kk = k < (int)nch ? (unsigned)k : 0u;   // an address inside the arrays
+                cp_async16(stage + k * MOM_CTHREADS, a.mono + cb + kk, k < (int)nch);
+                cp_async16(stage + (8 + k) * MOM_CTHREADS, a.qa + cb + kk, k < (int)nch);
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) qq2[k] = k < (int)nch ? __ldcg(a.qb + cb + k) : make_float2(0.f, 0.f);
+        if (stage) {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+#pragma unroll
+            for (int k = 0; k < 8; k++) mo[k] = stage[k * MOM_CTHREADS];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; k++) mo[k] = k < (int)nch ? __ldcg(a.mono + cb + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#else
 #pragma unroll
         for (int k = 0; k < 8; k++) mo[k] = k < (int)nch ? __ldcg(a.mono + cb + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+#endif
         const float c0x = mo[0].x, c0y = mo[0].y, c0z = mo[0].z;
         float fM = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
 #pragma unroll
@@ -261,8 +304,13 @@ __device__ __forceinline__ void combine_cell(unsigned c, int lv, uint2 plk, unsi
 #pragma unroll
         for (int k = 0; k < 8; k++) {
             if (k < (int)nch) {
+#if MOM_CPASYNC
+                const float4 q4 = stage ? stage[(8 + k) * MOM_CTHREADS] : __ldcg(a.qa + cb + k);
+                const float2 q2 = qq2[k];
+#else
                 const float4 q4 = __ldcg(a.qa + cb + k);
                 const float2 q2 = __ldcg(a.qb + cb + k);
+#endif
                 const float dx = mo[k].x - m.x, dy = mo[k].y - m.y, dz = mo[k].z - m.z;
                 const float d2 = dx * dx + dy * dy + dz * dz;
                 m.q[0] += -q4.x + mo[k].w * (3.f * dx * dx - d2);
@@ -293,45 +341,68 @@ __device__ __forceinline__ void combine_cell(unsigned c, int lv, uint2 plk, unsi
 
 // Leaf pass: one thread per cell, from the end of the breadth-first
 // numbering.  A leaf sums its bodies; an internal cell writes its arrival
-// word from its children's leaf bits (contiguous links); a leaf's word is 0.
+// word, the number of its internal children (contiguous links), and one
+// without any is appended to the start list (one atomic per warp, lanes in
+// cell order, so the list runs roughly deepest first).
 template <bool REFIT>
 __global__ void __launch_bounds__(256, MOM_MINB)
 k_mom_leaves(MomArrays a) {
     const unsigned nc = a.stc->ncells;
     if (a.stc->status & ST_TIMEOUT) return;
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lt = (1u << lane) - 1u;
+    // every lane of a warp runs the same iterations (the ballot below)
+    for (unsigned i0 = blockIdx.x * blockDim.x; i0 < nc; i0 += gridDim.x * blockDim.x) {
+        const unsigned i = i0 + threadIdx.x;
         const unsigned c = nc - 1u - i;
-        const uint2 link = a.cell_link[c];
-        const int lev = a.cell_level[c];
-        if (link.y & LEAF_BIT) {
-            a.cell_done[c] = 0u;
-            leaf_cell<REFIT>(c, link, lev, a);
-        } else {
-            uint2 ch[8];
+        bool start = false;
+        if (i < nc) {
+            const uint2 link = a.cell_link[c];
+            const int lev = a.cell_level[c];
+            if (link.y & LEAF_BIT) {
+                leaf_cell<REFIT>(c, link, lev, a);
+            } else {
+                uint2 ch[8];
 #pragma unroll
-            for (int k = 0; k < 8; k++) ch[k] = k < (int)link.y ? a.cell_link[link.x + k] : make_uint2(0u, LEAF_BIT);
-            unsigned ni = 0;
+                for (int k = 0; k < 8; k++)
+                    ch[k] = k < (int)link.y ? a.cell_link[link.x + k] : make_uint2(0u, LEAF_BIT);
+                unsigned ni = 0;
 #pragma unroll
-            for (int k = 0; k < 8; k++) ni += (ch[k].y & LEAF_BIT) ? 0u : 1u;
-            a.cell_done[c] = (ni << 1) | (ni == 0u ? 1u : 0u);
+                for (int k = 0; k < 8; k++) ni += (ch[k].y & LEAF_BIT) ? 0u : 1u;
+                a.cell_done[c] = ni;
+                start = ni == 0u;
+            }
+        }
+        const unsigned sm = __ballot_sync(0xffffffffu, start);
+        if (sm) {
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(a.nstart, (unsigned)__popc(sm));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (start) a.starts[base + __popc(sm & lt)] = c;
         }
     }
 }
 
-// Combine pass: the internal cells with the start bit combine their
-// (leaf) children, then climb while they are the last internal child to
-// arrive.  Arrival: release (this cell's moments are visible to whoever
-// reads the word after the subtraction) and acquire (the last child sees
-// every sibling's moments: each sibling's subtraction heads a release
-// sequence that this read-modify-write extends).
+// Combine pass (persistent grid over the start list): a listed cell combines
+// its children (all leaves), then climbs while it is the last internal child
+// of its parent to arrive.  Arrival: release (this cell's moments are visible
+// to whoever reads the word after the decrement) and acquire (the last child
+// sees every sibling's moments: each sibling's decrement heads a release
+// sequence that this read-modify-write extends).  Only the list's cells
+// start, so a block is not held by climbs for cells that have nothing to do.
 template <bool REFIT>
-__global__ void __launch_bounds__(256, MOM_MINB2)
+__global__ void __launch_bounds__(MOM_CTHREADS, MOM_MINB2)
 k_mom_combine(MomArrays a) {
-    const unsigned nc = a.stc->ncells;
     if (a.stc->status & ST_TIMEOUT) return;
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
-        unsigned c = nc - 1u - i;
-        if (!(__ldcg(a.cell_done + c) & 1u)) continue;
+#if MOM_CPASYNC
+    __shared__ float4 s_stage[16 * MOM_CTHREADS];     // per thread: 8 children x (mono, qa)
+    float4 *stage = s_stage + threadIdx.x;
+#else
+    float4 *stage = nullptr;
+#endif
+    const unsigned ns = __ldcg(a.nstart);
+    for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < ns; j += gridDim.x * blockDim.x) {
+        unsigned c = __ldcg(a.starts + j);
         uint2 plk = a.cell_link[c];
         int lv = a.cell_level[c];
         unsigned p = lv != 0 ? a.cell_parent[c] : 0u;
@@ -340,16 +411,16 @@ k_mom_combine(MomArrays a) {
         const unsigned b = a.cell_body[c].x;
         const unsigned long long kb = a.sk[b];
         const int sysb = a.multi ? a.sysid[b] : 0;
-        combine_cell<REFIT>(c, lv, plk, kb, sysb, a);
+        combine_cell<REFIT>(c, lv, plk, kb, sysb, a, stage);
         while (lv != 0) {
             // the parent's link and level and the next parent are loaded with
             // the arrival atomic (the tree is read-only here)
             const uint2 pl = a.cell_link[p];
             const int plv = a.cell_level[p];
             const unsigned gp = plv != 0 ? a.cell_parent[p] : 0u;
-            if (atom_add_acq_rel_gpu(&a.cell_done[p], 0xfffffffeu) != 2u) break;   // subtract 2
+            if (atom_add_acq_rel_gpu(&a.cell_done[p], 0xffffffffu) != 1u) break;   // decrement
             c = p; plk = pl; lv = plv; p = gp;
-            combine_cell<REFIT>(c, lv, plk, kb, sysb, a);
+            combine_cell<REFIT>(c, lv, plk, kb, sysb, a, stage);
         }
     }
 }
@@ -366,25 +437,30 @@ static unsigned multipole_blocks(const Ctx &c) {
 static MomArrays mom_arrays(Ctx &c, float theta, bool refit) {
     return MomArrays{c.st, c.cell_body, c.cell_link, c.cell_level, c.cell_parent, c.cell_done, c.pos4, c.keys,
                      c.sysid, c.mono, c.quadA, c.quadB, c.delta, c.shadow, refit ? c.cext : nullptr,
-                     theta > 0.f ? c.test : nullptr, theta > 0.f ? 1.0f / theta : 0.f, c.nsys > 1};
+                     theta > 0.f ? c.test : nullptr, theta > 0.f ? 1.0f / theta : 0.f, c.nsys > 1,
+                     c.cell_start, &c.st->mom_starts};
+}
+
+// Both passes: the start list is emptied first (a memset node in a graph).
+template <bool REFIT>
+static cudaError_t launch_mom(Ctx &c, const MomArrays &a) {
+    cudaError_t e = cudaMemsetAsync(a.nstart, 0, sizeof(unsigned), c.stream);
+    if (e != cudaSuccess) return e;
+    k_mom_leaves<REFIT><<<multipole_blocks(c), 256, 0, c.stream>>>(a);
+    k_mom_combine<REFIT><<<c.num_sms * MOM_CBLOCKS, MOM_CTHREADS, 0, c.stream>>>(a);
+    return cudaGetLastError();
 }
 
 // theta > 0: also the walk's MAC records for that opening angle (what
 // launch_open_radius writes), so that a step needs no separate pass.
 cudaError_t launch_multipoles(Ctx &c, float theta) {
-    const MomArrays a = mom_arrays(c, theta, false);
-    k_mom_leaves<false><<<multipole_blocks(c), 256, 0, c.stream>>>(a);
-    k_mom_combine<false><<<multipole_blocks(c), 256, 0, c.stream>>>(a);
-    return cudaGetLastError();
+    return launch_mom<false>(c, mom_arrays(c, theta, false));
 }
 
 // Moments of the existing cells at the bodies' current positions (block time
 // steps between rebuilds), with each cell's cube enlarged to hold its bodies.
 cudaError_t launch_multipoles_refit(Ctx &c) {
-    const MomArrays a = mom_arrays(c, 0.f, true);
-    k_mom_leaves<true><<<multipole_blocks(c), 256, 0, c.stream>>>(a);
-    k_mom_combine<true><<<multipole_blocks(c), 256, 0, c.stream>>>(a);
-    return cudaGetLastError();
+    return launch_mom<true>(c, mom_arrays(c, 0.f, true));
 }
 
 // cext[c] = (geometric centre, l / 2) of every cell from its first body's

@@ -488,8 +488,7 @@ __global__ void k_build_link(const DevState *__restrict__ st, const uint32_t *__
 // ranges from the links): filled on demand for the tree getter.  A cell ends
 // where its last descendant leaf ends: descend along last children (at most
 // 21 levels).
-__global__ void k_internal_counts(const DevState *__restrict__ st, const uint32_t *__restrict__ cell_cb,
-                                  const uint8_t *__restrict__ cell_level, const uint2 *__restrict__ cell_link,
+__global__ void k_internal_counts(const DevState *__restrict__ st, const uint2 *__restrict__ cell_link,
                                   uint2 *cell_body) {
     const unsigned ncells = st->ncells;
     for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
@@ -507,7 +506,7 @@ __global__ void k_internal_counts(const DevState *__restrict__ st, const uint32_
 
 cudaError_t launch_internal_counts(Ctx &c) {
     const unsigned grid = (unsigned)min((c.ccap + 255) / 256, (long long)c.num_sms * 8);
-    k_internal_counts<<<grid, 256, 0, c.stream>>>(c.st, c.cell_cb, c.cell_level, c.cell_link, c.cell_body);
+    k_internal_counts<<<grid, 256, 0, c.stream>>>(c.st, c.cell_link, c.cell_body);
     return cudaGetLastError();
 }
 
