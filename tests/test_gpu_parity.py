@@ -99,6 +99,24 @@ def test_moments_vs_oracle():
     assert np.all(np.abs(quad - Q) <= 1e-5 * (M * l * l)[:, None])
 
 
+@pytest.mark.parametrize("n,nleaf", [(1, 16), (17, 16), (200, 16), (20000, 1), (20000, 64), (100003, 8)])
+def test_moments_vs_oracle_tree_shapes(n, nleaf):
+    """The two multipole passes over trees of every shape: a root that is a
+    leaf, a root whose children are all leaves (combined from the start
+    list), leaves of one body (every internal cell climbs), shallow trees
+    and a ragged size."""
+    b = W.plummer(n, 11)
+    res = gpu_run(b.pos, b.mass, forces=False, nleaf=nleaf, ncrit=max(nleaf, 16))
+    mn, S, k, perm, t = check_keys_tree(res, b.pos, nleaf, max(nleaf, 16))
+    M, com, Q = oracle.moments(t, b.pos[perm], b.mass[perm])
+    mono, quad = res["mono"].astype(np.float64), res["quad"].astype(np.float64)
+    l = S / 2.0 ** t.level
+    assert np.all(np.abs(mono[:, 3] - M) <= 1e-6 * M)
+    dcom = np.linalg.norm(mono[:, :3] - com, axis=1)
+    assert np.all(dcom <= 4e-7 * np.linalg.norm(com, axis=1) + 2e-6 * l)
+    assert np.all(np.abs(quad - Q) <= 1e-5 * (M * l * l)[:, None])
+
+
 @pytest.mark.parametrize("theta,ncrit", [(0.5, 32), (0.75, 32), (1.0, 32), (0.75, 64), (0.5, 64)])
 def test_forces_vs_oracle_tree(theta, ncrit):
     b = W.plummer(32768, 0)
