@@ -309,6 +309,9 @@ cudaError_t launch_domains(Ctx &c) {
 
 constexpr int KEYS_THREADS = 256;
 constexpr int KEYS_ITEMS = 8;
+#ifndef KEYS_BLOCKS_PER_SM
+#define KEYS_BLOCKS_PER_SM 16         // key blocks per SM, each flushing its 8 x 256 digit counts once
+#endif                                // (a block per 2048 bodies: 0.132 ms at 2^24; 16 per SM: 0.097 ms)
 
 // Keys of all bodies (each quantised in its own system's cube) plus the 8
 // digit histograms of the radix sort; also clears the pass-0 tile status of
@@ -325,7 +328,11 @@ k_keys(const float4 *__restrict__ p, const uint8_t *__restrict__ sysid, int n, i
         status0[i] = 0;
     __syncthreads();
     const unsigned qmax = (1u << KEY_BITS_PER_AXIS) - 1u;
-    int base = blockIdx.x * KEYS_THREADS * KEYS_ITEMS + threadIdx.x;
+    // chunks of KEYS_THREADS * KEYS_ITEMS bodies, grid-stride: a block sums
+    // its chunks in shared memory and adds each digit count to the global
+    // histograms once
+    for (int base = blockIdx.x * KEYS_THREADS * KEYS_ITEMS + threadIdx.x; base - (int)threadIdx.x < n;
+         base += gridDim.x * KEYS_THREADS * KEYS_ITEMS) {
 #pragma unroll
     for (int k = 0; k < KEYS_ITEMS; k++) {
         int i = base + k * KEYS_THREADS;
@@ -342,6 +349,7 @@ k_keys(const float4 *__restrict__ p, const uint8_t *__restrict__ sysid, int n, i
                 atomicAdd(&h[d * SORT_RADIX + (unsigned)((key >> (SORT_BITS * d)) & (SORT_RADIX - 1))], 1u);
         }
     }
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < SORT_PASSES * SORT_RADIX; i += blockDim.x)
         if (h[i]) atomicAdd(&st->hist[i], h[i]);
@@ -357,8 +365,9 @@ cudaError_t launch_keys(Ctx &c) {
     // ensemble) it starts from the alternate buffer.
     const int npass = SORT_PASSES + (c.nsys > 1 ? 1 : 0);
     unsigned long long *out = (npass & 1) ? c.keys_alt : c.keys;
-    k_keys<<<(n + per - 1) / per, KEYS_THREADS, 0, c.stream>>>(c.pos4_alt, c.sysid, n, c.nsys, c.st, out,
-                                                              c.tile_status, c.ntiles * SORT_RADIX);
+    const int grid = min((n + per - 1) / per, c.num_sms * KEYS_BLOCKS_PER_SM);
+    k_keys<<<grid, KEYS_THREADS, 0, c.stream>>>(c.pos4_alt, c.sysid, n, c.nsys, c.st, out, c.tile_status,
+                                                c.ntiles * SORT_RADIX);
     return cudaGetLastError();
 }
 
