@@ -56,10 +56,25 @@ __device__ __forceinline__ unsigned block_next_end(int k, unsigned s, int kmax) 
     return ((s >> (kmax - k)) + 1u) << (kmax - k);
 }
 
-// The minimum over a warp's bodies into st->blk_next (every lane calls).
-__device__ __forceinline__ void block_min_next(unsigned e, DevState *st) {
+// The minimum of e over the block's threads into st->blk_next and (cnt !=
+// nullptr) the sum of cnt into st->cyc_active: warp reductions, then one
+// shared-memory atomic per warp and one global atomic per block (every
+// thread of the block calls, outside divergent code).
+__device__ __forceinline__ void block_totals(unsigned e, const unsigned *cnt, DevState *st) {
+    __shared__ unsigned s_min, s_cnt;
+    if (threadIdx.x == 0) { s_min = 0xffffffffu; s_cnt = 0u; }
+    __syncthreads();
     e = __reduce_min_sync(0xffffffffu, e);
-    if ((threadIdx.x & 31) == 0 && e != 0xffffffffu) atomicMin(&st->blk_next, e);
+    const unsigned c = cnt ? __reduce_add_sync(0xffffffffu, *cnt) : 0u;
+    if ((threadIdx.x & 31) == 0) {
+        if (e != 0xffffffffu) atomicMin_block(&s_min, e);
+        if (c) atomicAdd_block(&s_cnt, c);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_min != 0xffffffffu) atomicMin(&st->blk_next, s_min);
+        if (s_cnt) atomicAdd(&st->cyc_active, (unsigned long long)s_cnt);
+    }
 }
 
 // Cycle start: every body takes its level and the opening half kick.
@@ -76,7 +91,7 @@ __global__ void k_block_open(float4 *vel, const float4 *__restrict__ acc, int n,
         vel[i] = v;
         nx = min(nx, block_next_end(k, 0u, kmax));
     }
-    block_min_next(nx, st);
+    block_totals(nx, nullptr, st);
 }
 
 // Substep s: the bodies whose step ends take the closing half kick and,
@@ -106,9 +121,7 @@ __global__ void k_block_kick(float4 *vel, const float4 *__restrict__ acc, int n,
         }
         vel[i] = v;
     }
-    cnt = __reduce_add_sync(0xffffffffu, cnt);
-    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&st->cyc_active, (unsigned long long)cnt);
-    block_min_next(nx, st);
+    block_totals(nx, &cnt, st);
 }
 
 // `times` drifts of every body by dt in place (substeps that only drift,
