@@ -86,14 +86,16 @@ def fp32_peak_tflops(local_rank: int = 0) -> float:
 
 def kernels_per_step(ncrit, group_pack=0):
     """reset, kick+drift+bbox, domains, keys, 8 sort passes, reorder, 4 build
-    (+2 for sibling packing of the groups), multipoles (which also write the
-    MAC records), walk (a second instantiation when groups may exceed 16
-    bodies: three bodies per lane for 17..24, two for more than 32), kick."""
-    return 20 + (1 if ncrit > 16 else 0) + (2 if group_pack else 0)
+    (+2 for sibling packing of the groups), multipoles in two passes (leaves,
+    then internal cells; they also write the MAC records), walk (a second
+    instantiation when groups may exceed 16 bodies: three bodies per lane for
+    17..24, two for more than 32), kick.  (The start-list reset before the
+    multipoles is a memset node, not a kernel.)"""
+    return 21 + (1 if ncrit > 16 else 0) + (2 if group_pack else 0)
 # DRAM bytes (read + write) of one step's walk (both instantiations) from
 # the ncu capture in profiles/k_walk_plummer_n2e20.md, keyed by (N, ncrit,
 # group_pack); other choices have no capture and report null.
-WALK_TRAFFIC = {(1 << 20, 32, 1): 68.77e6}
+WALK_TRAFFIC = {(1 << 20, 32, 1): 71.47e6}
 
 
 def parse():

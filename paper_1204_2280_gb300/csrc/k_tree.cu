@@ -375,8 +375,11 @@ k_build_write(const uint4 *__restrict__ entries, int ncrit, const unsigned *__re
             s_ok = (long long)run <= ccap;
             if (blockIdx.x == 0) {
                 st->level_start[MAX_LEVEL + 1] = run;
-                st->ncells = run;
-                st->ngroups = st->row_total[GROUP_ROW];
+                // over capacity (cannot happen for the arena's bound, kept as
+                // a guard): no cells and no groups, so that every later
+                // stage does nothing, and the error is reported
+                st->ncells = s_ok ? run : 0u;
+                st->ngroups = s_ok ? st->row_total[GROUP_ROW] : 0u;
                 if (!s_ok) atomicOr(&st->status, ST_CAPACITY);
             }
         }
@@ -557,7 +560,7 @@ k_group_mark(const DevState *__restrict__ st, const uint2 *__restrict__ graw, co
     constexpr int HALO = 8;
     __shared__ unsigned s_cnt[PACK_THREADS + HALO];
     __shared__ uint8_t s_sib[PACK_THREADS + HALO];
-    if (st->status & ST_TIMEOUT) return;
+    if ((st->status & ST_TIMEOUT) || st->ncells == 0u) return;   // keys unsorted, or no tree
     const unsigned ng = st->row_total[GROUP_ROW];
     const unsigned nchunk = (ng + PACK_THREADS - 1) / PACK_THREADS;
     for (unsigned ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
@@ -595,7 +598,7 @@ __global__ void __launch_bounds__(PACK_THREADS)
 k_group_pack(DevState *st, const uint2 *__restrict__ graw, const uint8_t *__restrict__ gflag,
              const unsigned *__restrict__ bcount, uint2 *groups) {
     __shared__ unsigned s_w[32];
-    if (st->status & ST_TIMEOUT) return;
+    if ((st->status & ST_TIMEOUT) || st->ncells == 0u) return;   // keys unsorted, or no tree
     const unsigned ng = st->row_total[GROUP_ROW];
     const unsigned nchunk = (ng + PACK_THREADS - 1) / PACK_THREADS;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

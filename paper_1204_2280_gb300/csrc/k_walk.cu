@@ -376,7 +376,8 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
     unsigned *stk = reinterpret_cast<unsigned *>(wbase + sizeof(WarpRings));
     // Nothing to do after a timed-out sort, or when a gate flag (the learned
     // path's fallback decision) is clear.
-    const unsigned ngroups = ((stc->status & ST_TIMEOUT) || (gate && *gate == 0u)) ? 0u : stc->ngroups;
+    const unsigned ngroups =
+        ((stc->status & ST_TIMEOUT) || (gate && *gate == 0u) || stc->ncells == 0u) ? 0u : stc->ngroups;
     const float eps2 = eps * eps;
     const float2 eps2x2 = make_float2(eps2, eps2);
     const unsigned lt = lanemask_lt_w();
