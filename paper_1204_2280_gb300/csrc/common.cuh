@@ -48,7 +48,10 @@ constexpr int MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_
 constexpr int MLP_NNORM = 2 * MLP_IN + 1;              // mu[12], sigma[12], ysig
 constexpr int FEAT_STRIDE = 12;                        // walk features per body
 constexpr int JUDGE_MAX = 4096;                        // sampled bodies of the direct-sum judge
-constexpr int JUDGE_SPLIT = 64;                        // source splits of the judge's direct sum
+#ifndef JUDGE_SPLIT_CFG
+#define JUDGE_SPLIT_CFG 128
+#endif
+constexpr int JUDGE_SPLIT = JUDGE_SPLIT_CFG;            // source splits of the judge's direct sum
 #ifndef BUILD_THREADS_CFG
 #define BUILD_THREADS_CFG 1024
 #endif

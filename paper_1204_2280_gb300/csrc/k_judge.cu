@@ -15,7 +15,10 @@
 
 namespace bonsai {
 
-constexpr int DS_THREADS = 128;        // threads per block, two targets each
+#ifndef DS_PAIRS
+#define DS_PAIRS 1                     // packed target pairs per thread (2: 3% slower at 2^22 with
+#endif                                 // twice the source splits, 21% slower with as many)
+constexpr int DS_THREADS = 128;        // threads per block, 2 DS_PAIRS targets each
 constexpr int DS_TILE = 256;           // sources per shared tile
 
 __device__ __forceinline__ void kadd(float &s, float &c, float v) {
@@ -26,25 +29,36 @@ __device__ __forceinline__ void kadd(float &s, float &c, float v) {
 }
 
 // Partial sums of split blockIdx.y over sources [chunk*y, chunk*(y+1)).
-// Each thread owns targets k and k + DS_THREADS of its block as one packed
-// FP32x2 operand; the tile holds every source twice per component ((x, x,
-// y, y), (z, z, m, m)), so two broadcast loads feed 13 packed operations.
-// Per target the arithmetic and its order are those of one scalar loop over
-// the sources.  A non-null gate that reads 0 skips the work (all kernels of
-// this file).
+// Each thread owns 2 DS_PAIRS targets, k + i DS_THREADS (i < 2 DS_PAIRS),
+// as DS_PAIRS packed FP32x2 operands; the tile holds every source twice per
+// component ((x, x, y, y), (z, z, m, m)), so two broadcast loads feed
+// 13 DS_PAIRS packed operations.  Per target the arithmetic and its order
+// are those of one scalar loop over the sources.  A non-null gate that
+// reads 0 skips the work (all kernels of this file).
 __global__ void __launch_bounds__(DS_THREADS)
 k_direct_partial(const float4 *__restrict__ pos4, int n, const uint32_t *__restrict__ targets, int ntar,
                  float eps2, int chunk, float4 *partial, const unsigned *__restrict__ gate) {
     if (gate && *gate == 0u) return;
+    constexpr int P = DS_PAIRS, TT = 2 * DS_PAIRS;
     __shared__ float4 tile[2 * DS_TILE];
-    const int k0 = blockIdx.x * 2 * DS_THREADS + threadIdx.x, k1 = k0 + DS_THREADS;
-    const bool live0 = k0 < ntar, live1 = k1 < ntar;
-    const float4 m0 = live0 ? pos4[targets[k0]] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 m1 = live1 ? pos4[targets[k1]] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float2 nx = make_float2(-m0.x, -m1.x), ny = make_float2(-m0.y, -m1.y), nz = make_float2(-m0.z, -m1.z);
+    int kk[TT];
+    bool live[TT];
+    float2 nx[P], ny[P], nz[P];
+#pragma unroll
+    for (int i = 0; i < TT; i++) {
+        kk[i] = blockIdx.x * TT * DS_THREADS + i * DS_THREADS + threadIdx.x;
+        live[i] = kk[i] < ntar;
+    }
+#pragma unroll
+    for (int q = 0; q < P; q++) {
+        const float4 m0 = live[2 * q] ? pos4[targets[kk[2 * q]]] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 m1 = live[2 * q + 1] ? pos4[targets[kk[2 * q + 1]]] : make_float4(0.f, 0.f, 0.f, 0.f);
+        nx[q] = make_float2(-m0.x, -m1.x); ny[q] = make_float2(-m0.y, -m1.y); nz[q] = make_float2(-m0.z, -m1.z);
+    }
     const float2 e2 = make_float2(eps2, eps2);
-    float ax[2] = {0.f, 0.f}, ay[2] = {0.f, 0.f}, az[2] = {0.f, 0.f}, ph[2] = {0.f, 0.f};
-    float cx[2] = {0.f, 0.f}, cy[2] = {0.f, 0.f}, cz[2] = {0.f, 0.f}, cp[2] = {0.f, 0.f};
+    float ax[TT], ay[TT], az[TT], ph[TT], cx[TT], cy[TT], cz[TT], cp[TT];
+#pragma unroll
+    for (int i = 0; i < TT; i++) ax[i] = ay[i] = az[i] = ph[i] = cx[i] = cy[i] = cz[i] = cp[i] = 0.f;
     const int s0 = blockIdx.y * chunk, s1 = min(n, s0 + chunk);
     for (int b = s0; b < s1; b += DS_TILE) {
         __syncthreads();
@@ -54,27 +68,40 @@ k_direct_partial(const float4 *__restrict__ pos4, int n, const uint32_t *__restr
             tile[2 * i + 1] = make_float4(v.z, v.z, v.w, v.w);
         }
         __syncthreads();
-        float2 px = make_float2(0.f, 0.f), py = px, pz = px, pq = px;     // pq: +sum m/r
+        float2 px[P], py[P], pz[P], pq[P];                              // pq: +sum m/r
+#pragma unroll
+        for (int q = 0; q < P; q++) px[q] = py[q] = pz[q] = pq[q] = make_float2(0.f, 0.f);
 #pragma unroll 8
         for (int j = 0; j < DS_TILE; j++) {
             const float4 u = tile[2 * j], w = tile[2 * j + 1];
-            const float2 dx = __fadd2_rn(make_float2(u.x, u.y), nx);
-            const float2 dy = __fadd2_rn(make_float2(u.z, u.w), ny);
-            const float2 dz = __fadd2_rn(make_float2(w.x, w.y), nz);
-            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, e2)));
-            const float2 rinv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-            const float2 mr = __fmul2_rn(make_float2(w.z, w.w), rinv);
-            const float2 mr3 = __fmul2_rn(__fmul2_rn(mr, rinv), rinv);
-            pq = __fadd2_rn(pq, mr);
-            px = __ffma2_rn(mr3, dx, px);
-            py = __ffma2_rn(mr3, dy, py);
-            pz = __ffma2_rn(mr3, dz, pz);
+#pragma unroll
+            for (int q = 0; q < P; q++) {
+                const float2 dx = __fadd2_rn(make_float2(u.x, u.y), nx[q]);
+                const float2 dy = __fadd2_rn(make_float2(u.z, u.w), ny[q]);
+                const float2 dz = __fadd2_rn(make_float2(w.x, w.y), nz[q]);
+                const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, e2)));
+                const float2 rinv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+                const float2 mr = __fmul2_rn(make_float2(w.z, w.w), rinv);
+                const float2 mr3 = __fmul2_rn(__fmul2_rn(mr, rinv), rinv);
+                pq[q] = __fadd2_rn(pq[q], mr);
+                px[q] = __ffma2_rn(mr3, dx, px[q]);
+                py[q] = __ffma2_rn(mr3, dy, py[q]);
+                pz[q] = __ffma2_rn(mr3, dz, pz[q]);
+            }
         }
-        kadd(ax[0], cx[0], px.x); kadd(ay[0], cy[0], py.x); kadd(az[0], cz[0], pz.x); kadd(ph[0], cp[0], -pq.x);
-        kadd(ax[1], cx[1], px.y); kadd(ay[1], cy[1], py.y); kadd(az[1], cz[1], pz.y); kadd(ph[1], cp[1], -pq.y);
+#pragma unroll
+        for (int q = 0; q < P; q++) {
+            kadd(ax[2 * q], cx[2 * q], px[q].x); kadd(ay[2 * q], cy[2 * q], py[q].x);
+            kadd(az[2 * q], cz[2 * q], pz[q].x); kadd(ph[2 * q], cp[2 * q], -pq[q].x);
+            kadd(ax[2 * q + 1], cx[2 * q + 1], px[q].y); kadd(ay[2 * q + 1], cy[2 * q + 1], py[q].y);
+            kadd(az[2 * q + 1], cz[2 * q + 1], pz[q].y); kadd(ph[2 * q + 1], cp[2 * q + 1], -pq[q].y);
+        }
     }
-    if (live0) partial[(size_t)blockIdx.y * ntar + k0] = make_float4(ax[0] - cx[0], ay[0] - cy[0], az[0] - cz[0], ph[0] - cp[0]);
-    if (live1) partial[(size_t)blockIdx.y * ntar + k1] = make_float4(ax[1] - cx[1], ay[1] - cy[1], az[1] - cz[1], ph[1] - cp[1]);
+#pragma unroll
+    for (int i = 0; i < TT; i++)
+        if (live[i])
+            partial[(size_t)blockIdx.y * ntar + kk[i]] =
+                make_float4(ax[i] - cx[i], ay[i] - cy[i], az[i] - cz[i], ph[i] - cp[i]);
 }
 
 // Sum the splits in order with Kahan compensation (FP32) and remove the
@@ -97,7 +124,7 @@ cudaError_t launch_direct(Ctx &c, const uint32_t *targets, int ntar, float eps, 
                           int nsplit, float4 *out, const unsigned *gate) {
     const int n = (int)c.n;
     const int chunk = ((n + nsplit - 1) / nsplit + DS_TILE - 1) / DS_TILE * DS_TILE;
-    dim3 grid((ntar + 2 * DS_THREADS - 1) / (2 * DS_THREADS), nsplit);
+    dim3 grid((ntar + 2 * DS_PAIRS * DS_THREADS - 1) / (2 * DS_PAIRS * DS_THREADS), nsplit);
     k_direct_partial<<<grid, DS_THREADS, 0, c.stream>>>(c.pos4, n, targets, ntar, eps * eps, chunk, partial, gate);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
