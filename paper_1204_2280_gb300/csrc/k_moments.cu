@@ -77,9 +77,6 @@ struct Mom32 { float M, x, y, z, q[6]; };
 #ifndef MOM_CBLOCKS
 #define MOM_CBLOCKS 6         // combine pass: blocks per SM of its persistent grid (32 KB of staging each)
 #endif
-#ifndef MOM_LANES
-#define MOM_LANES 1           // leaf pass: lanes per cell (bodies spread over them, shuffle sums);
-#endif                        // 2, 4, 8 lanes: 13%, 29%, 2x slower at 2^22 (fewer leaves in flight)
 #ifndef MOM_LB
 #define MOM_LB 8              // leaf bodies loaded per round trip (4: 3% slower at 2^22, 16 spills)
 #endif
@@ -400,100 +397,6 @@ k_mom_leaves(MomArrays a) {
     }
 }
 
-#if MOM_LANES > 1
-// The leaf pass with MOM_LANES lanes per cell: the lanes of a leaf take its
-// bodies in turn (strided, coalesced) and their sums are added by xor
-// shuffles inside the lane group; the group's first lane finishes the leaf,
-// or counts an internal cell's internal children.
-template <bool REFIT>
-__global__ void __launch_bounds__(256, MOM_MINB)
-k_mom_leaves_g(MomArrays a) {
-    constexpr unsigned G = MOM_LANES, PER = 256 / G;
-    const unsigned nc = a.stc->ncells;
-    if (a.stc->status & ST_TIMEOUT) return;
-    const unsigned lane = threadIdx.x & 31u, r = threadIdx.x & (G - 1u);
-    const unsigned lt = (1u << lane) - 1u;
-    for (unsigned i0 = blockIdx.x * PER; i0 < nc; i0 += gridDim.x * PER) {
-        const unsigned i = i0 + threadIdx.x / G;
-        const unsigned c = nc - 1u - i;
-        const bool valid = i < nc;
-        uint2 link = make_uint2(0u, 0u);
-        int lev = 0;
-        if (valid) { link = a.cell_link[c]; lev = a.cell_level[c]; }
-        const bool leaf = valid && (link.y & LEAF_BIT);
-        float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
-        float sxx = 0.f, syy = 0.f, szz = 0.f, sxy = 0.f, sxz = 0.f, syz = 0.f;
-        float ext = 0.f;
-        float3 ctr = make_float3(0.f, 0.f, 0.f);
-        float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f);
-        unsigned long long kb = 0ull;
-        int sysb = 0;
-        if (leaf) {
-            const unsigned b = link.x, cnt = link.y & ~LEAF_BIT;
-            kb = a.sk[b];
-            sysb = a.multi ? a.sysid[b] : 0;
-            x0 = a.pos4[b];
-            if (REFIT) ext = 0.5f * cell_cube(kb, lev, sysb, a.stc, ctr);
-            constexpr unsigned LB = (MOM_LB + G - 1) / G;
-            for (unsigned j0 = b + r; j0 < b + cnt; j0 += LB * G) {
-                float4 pb[LB];
-#pragma unroll
-                for (unsigned u = 0; u < LB; u++)
-                    pb[u] = j0 + u * G < b + cnt ? a.pos4[j0 + u * G] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (unsigned u = 0; u < LB; u++) {
-                    if (j0 + u * G >= b + cnt) break;
-                    const float4 p = pb[u];
-                    if (REFIT) ext = fmaxf(ext, dist_inf(make_float3(p.x, p.y, p.z), ctr));
-                    const float ux = p.x - x0.x, uy = p.y - x0.y, uz = p.z - x0.z;
-                    const float wx = p.w * ux, wy = p.w * uy, wz = p.w * uz;
-                    M += p.w;
-                    sx += wx; sy += wy; sz += wz;
-                    sxx = fmaf(wx, ux, sxx); syy = fmaf(wy, uy, syy); szz = fmaf(wz, uz, szz);
-                    sxy = fmaf(wx, uy, sxy); sxz = fmaf(wx, uz, sxz); syz = fmaf(wy, uz, syz);
-                }
-            }
-        }
-#pragma unroll
-        for (unsigned o = G / 2; o > 0; o >>= 1) {
-            M += __shfl_xor_sync(0xffffffffu, M, o);
-            sx += __shfl_xor_sync(0xffffffffu, sx, o);
-            sy += __shfl_xor_sync(0xffffffffu, sy, o);
-            sz += __shfl_xor_sync(0xffffffffu, sz, o);
-            sxx += __shfl_xor_sync(0xffffffffu, sxx, o);
-            syy += __shfl_xor_sync(0xffffffffu, syy, o);
-            szz += __shfl_xor_sync(0xffffffffu, szz, o);
-            sxy += __shfl_xor_sync(0xffffffffu, sxy, o);
-            sxz += __shfl_xor_sync(0xffffffffu, sxz, o);
-            syz += __shfl_xor_sync(0xffffffffu, syz, o);
-            if (REFIT) ext = fmaxf(ext, __shfl_xor_sync(0xffffffffu, ext, o));
-        }
-        bool start = false;
-        if (valid && r == 0u) {
-            if (leaf) {
-                leaf_finish<REFIT>(c, lev, kb, sysb, x0, M, sx, sy, sz, sxx, syy, szz, sxy, sxz, syz, ctr, ext, a);
-            } else {
-                uint2 ch[8];
-#pragma unroll
-                for (int k = 0; k < 8; k++)
-                    ch[k] = k < (int)link.y ? a.cell_link[link.x + k] : make_uint2(0u, LEAF_BIT);
-                unsigned ni = 0;
-#pragma unroll
-                for (int k = 0; k < 8; k++) ni += (ch[k].y & LEAF_BIT) ? 0u : 1u;
-                a.cell_done[c] = ni;
-                start = ni == 0u;
-            }
-        }
-        const unsigned sm = __ballot_sync(0xffffffffu, start);
-        if (sm) {
-            unsigned base = 0;
-            if (lane == 0) base = atomicAdd(a.nstart, (unsigned)__popc(sm));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (start) a.starts[base + __popc(sm & lt)] = c;
-        }
-    }
-}
-#endif
 
 // Combine pass (persistent grid over the start list): a listed cell combines
 // its children (all leaves), then climbs while it is the last internal child
@@ -558,11 +461,7 @@ template <bool REFIT>
 static cudaError_t launch_mom(Ctx &c, const MomArrays &a) {
     cudaError_t e = cudaMemsetAsync(a.nstart, 0, sizeof(unsigned), c.stream);
     if (e != cudaSuccess) return e;
-#if MOM_LANES > 1
-    k_mom_leaves_g<REFIT><<<multipole_blocks(c) * MOM_LANES, 256, 0, c.stream>>>(a);
-#else
     k_mom_leaves<REFIT><<<multipole_blocks(c), 256, 0, c.stream>>>(a);
-#endif
     k_mom_combine<REFIT><<<c.num_sms * MOM_CBLOCKS, MOM_CTHREADS, 0, c.stream>>>(a);
     return cudaGetLastError();
 }
