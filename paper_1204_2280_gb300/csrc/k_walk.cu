@@ -345,14 +345,6 @@ __device__ __forceinline__ void walk_pop(const unsigned *stk, int &sp, int lane,
 #ifndef WALK_MAXNREG1
 #define WALK_MAXNREG1 0             // > 0: register cap of the one-body-per-lane walk
 #endif
-#ifndef WALK_PREFETCH
-#define WALK_PREFETCH 0             // 1: an opened cell prefetches its children's records into L1
-#endif
-
-// Fire-and-forget L1 prefetch of the cache line holding p.
-__device__ __forceinline__ void prefetch_l1(const void *p) {
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
 #if WALK_MAXNREG1 > 0
 #define WALK_ATTRS __launch_bounds__(256) __maxnreg__(BPL == 1 ? WALK_MAXNREG1 : BPL == 2 ? 255 : 128)
 #else
@@ -531,11 +523,6 @@ k_walk(const DevState *__restrict__ stc, DevState *st, const uint2 *__restrict__
             } else {
                 if (open && !isleaf) {
                     stk[sp + __popc(im & lt)] = (lk.x << 3) | ((lk.y - 1u) & 7u);
-                    if (WALK_PREFETCH) {
-                        // the children (contiguous, popped soon): MAC records, links, moments
-                        prefetch_l1(test + lk.x); prefetch_l1(link + lk.x); prefetch_l1(mono + lk.x);
-                        prefetch_l1(quadA + lk.x); prefetch_l1(quadB + lk.x);
-                    }
                 }
                 sp += np;
             }
