@@ -80,7 +80,9 @@ void bonsai_destroy(bonsai_ctx *ctx);
 
 /* Load N bodies: pos (N x 3, xyz interleaved), mass (N), vel (N x 3, or
  * NULL for zero velocities).  Invalidates the tree and the forces.
- * N must be in [1, 2^26]. */
+ * N must be in [1, 2^26].  Host buffers (on_device = 0) are read before the
+ * call returns: page-locked ones directly by a kernel through their device
+ * address, others through a copy to the context's staging area. */
 int bonsai_set_bodies(bonsai_ctx *ctx, const float *pos, const float *mass,
                       const float *vel, long long n, int on_device);
 

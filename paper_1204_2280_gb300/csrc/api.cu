@@ -249,7 +249,23 @@ int bonsai_set_bodies(bonsai_ctx *ctx, const float *pos, const float *mass, cons
     if (n != c.n) c.cells_hint = 0;
     c.n = n;
     const float *p = pos, *m = mass, *v = vel;
-    if (!on_device) {
+    // Page-locked host buffers (cudaHostAlloc / cudaHostRegister) are read by
+    // the pack kernel directly over the host link, through the device
+    // address the runtime reports for them: no staging copies.  Any other
+    // host buffer is copied to the staging area first.
+    auto mapped = [](const float *q, const float *&d) {
+        d = q;
+        if (!q) return true;
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, q) != cudaSuccess) { cudaGetLastError(); return false; }
+        if (at.type != cudaMemoryTypeHost || !at.devicePointer) return false;
+        d = static_cast<const float *>(at.devicePointer);
+        return true;
+    };
+    const float *dp, *dm, *dv;
+    if (!on_device && mapped(pos, dp) && mapped(mass, dm) && mapped(vel, dv)) {
+        p = dp; m = dm; v = dv;
+    } else if (!on_device) {
         float *s = c.stage;
         CK(cudaMemcpyAsync(s, pos, 12 * (size_t)n, cudaMemcpyHostToDevice, c.stream));
         CK(cudaMemcpyAsync(s + 3 * n, mass, 4 * (size_t)n, cudaMemcpyHostToDevice, c.stream));
