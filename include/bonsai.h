@@ -96,6 +96,12 @@ int bonsai_set_bodies(bonsai_ctx *ctx, const float *pos, const float *mass,
  * (bonsai_set_bodies resets to a single system). */
 int bonsai_set_systems(bonsai_ctx *ctx, const long long *offsets, int nsys);
 
+/* bonsai_build, bonsai_multipoles and bonsai_forces run their launches
+ * directly the first time a configuration is seen (size, systems, tuning
+ * knobs, theta and eps), capture them into a CUDA graph the second time and
+ * replay that graph while the configuration holds (use_graph = -1: always
+ * direct launches); the results are the same bit for bit. */
+
 /* Sect. 2 "sorting", "moving", "tree-construction": domain cube, 63-bit
  * Morton keys (21 bits per axis, x in the lowest bit of each triple), stable
  * LSD radix sort, body reorder, octree (cells with more than nleaf bodies

@@ -49,8 +49,14 @@ struct Arena {
     }
 };
 
+void drop_graph(CallGraph &g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = CallGraph{};
+}
+
 void free_bodies(Ctx &c) {
     if (c.step_graph) { cudaGraphExecDestroy(c.step_graph); c.step_graph = nullptr; }
+    drop_graph(c.build_graph); drop_graph(c.mom_graph); drop_graph(c.forces_graph);
     if (c.pos4) cudaFree(c.pos4);
     c.pos4 = nullptr;
     c.ncap = 0;
@@ -91,6 +97,7 @@ cudaError_t alloc_bodies(Ctx &c, long long n) {
     if (e != cudaSuccess) return e;
     for (auto &p : plan) *p.first = base + p.second;
     c.ncap = n;
+    c.arena_gen++;
     c.stage_floats = stage_floats;
     c.ntiles = (int)ntiles;
     c.nbblocks = (int)nbb;
@@ -111,6 +118,45 @@ cudaError_t refresh_cells_hint(Ctx &c) {
 
 // keys -> sort -> reorder -> build; the domain accumulators must hold the
 // bounding box of the pre-sort positions.
+// The launches of body() on the context's stream: direct the first time a
+// key is seen, captured into a graph the second time, replayed from then on
+// while the key holds (the first run also sets up what the launches cache:
+// function attributes, occupancy).  A capture that fails falls back to
+// direct launches for that key.
+template <class F>
+cudaError_t run_cached(Ctx &c, CallGraph &g, const long long *key, int nkey, F body) {
+    if (!c.use_graph) return body();
+    bool same = g.nkey == nkey;
+    for (int i = 0; same && i < nkey; i++) same = g.key[i] == key[i];
+    if (same && g.exec) return cudaGraphLaunch(g.exec, c.stream);
+    if (same && !g.failed) {
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const cudaError_t e1 = body();
+            e = cudaStreamEndCapture(c.stream, &graph);
+            if (e1 != cudaSuccess) e = e1;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e == cudaSuccess) return cudaGraphLaunch(g.exec, c.stream);
+        cudaGetLastError();
+        g.exec = nullptr;
+        g.failed = true;
+        return body();
+    }
+    drop_graph(g);
+    for (int i = 0; i < nkey; i++) g.key[i] = key[i];
+    g.nkey = nkey;
+    return body();
+}
+
+long long fbits(float x) {
+    unsigned u;
+    std::memcpy(&u, &x, sizeof u);
+    return (long long)u;
+}
+
 cudaError_t pipeline_tree(Ctx &c) {
     cudaError_t e;
     if ((e = launch_keys(c)) != cudaSuccess) return e;
@@ -318,15 +364,23 @@ int bonsai_build(bonsai_ctx *ctx) {
     if (!ctx) return BONSAI_ERR_INVALID_ARG;
     Ctx &c = ctx->c;
     if (!c.have_bodies) return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_build: no bodies");
-    if (c.built) {
-        // rebuild from the current (sorted) state: copy it to the pre-sort arrays
-        CK(cudaMemcpyAsync(c.pos4_alt, c.pos4, 16 * (size_t)c.n, cudaMemcpyDeviceToDevice, c.stream));
-        CK(cudaMemcpyAsync(c.vel4_alt, c.vel4, 16 * (size_t)c.n, cudaMemcpyDeviceToDevice, c.stream));
-        CK(cudaMemcpyAsync(c.id_alt, c.id, 4 * (size_t)c.n, cudaMemcpyDeviceToDevice, c.stream));
-    }
-    CK(launch_reset(c));
-    CK(launch_bbox(c));
-    CK(pipeline_tree(c));
+    const bool again = c.built;
+    const long long key[] = {c.n, c.arena_gen, c.nsys, c.nleaf, c.ncrit, c.group_pack, c.max_spin, again};
+    CK(run_cached(c, c.build_graph, key, (int)(sizeof key / sizeof key[0]), [&]() -> cudaError_t {
+        cudaError_t e;
+        if (again) {
+            // rebuild from the current (sorted) state: copy it to the pre-sort arrays
+            if ((e = cudaMemcpyAsync(c.pos4_alt, c.pos4, 16 * (size_t)c.n, cudaMemcpyDeviceToDevice, c.stream)))
+                return e;
+            if ((e = cudaMemcpyAsync(c.vel4_alt, c.vel4, 16 * (size_t)c.n, cudaMemcpyDeviceToDevice, c.stream)))
+                return e;
+            if ((e = cudaMemcpyAsync(c.id_alt, c.id, 4 * (size_t)c.n, cudaMemcpyDeviceToDevice, c.stream)))
+                return e;
+        }
+        if ((e = launch_reset(c)) != cudaSuccess) return e;
+        if ((e = launch_bbox(c)) != cudaSuccess) return e;
+        return pipeline_tree(c);
+    }));
     c.built = c.tree_fresh = true;
     c.moments_ready = c.have_acc = false;
     return BONSAI_OK;
@@ -339,7 +393,8 @@ int bonsai_multipoles(bonsai_ctx *ctx) {
     // The launch is sized from the last known cell count (a tree of the same
     // bodies changes little); only a context without one reads it back.
     if (c.cells_hint == 0) CK(refresh_cells_hint(c));
-    CK(launch_multipoles(c));
+    const long long key[] = {c.n, c.arena_gen, c.nsys, c.cells_hint};
+    CK(run_cached(c, c.mom_graph, key, (int)(sizeof key / sizeof key[0]), [&]() { return launch_multipoles(c); }));
     c.moments_ready = true;
     return BONSAI_OK;
 }
@@ -368,8 +423,12 @@ int bonsai_forces(bonsai_ctx *ctx, float theta, float eps, float *acc, float *po
         return fail(ctx, BONSAI_ERR_NOT_READY, "bonsai_forces: call bonsai_build and bonsai_multipoles first");
     c.theta = theta;
     c.eps = eps;
-    CK(launch_reset(c));
-    CK(pipeline_forces(c, theta, eps));
+    const long long key[] = {c.n, c.arena_gen, c.nsys, c.ncrit, c.group_pack, c.walk_warps, c.list_capacity,
+                             c.max_spin, fbits(theta), fbits(eps), c.block_kmax};
+    CK(run_cached(c, c.forces_graph, key, (int)(sizeof key / sizeof key[0]), [&]() -> cudaError_t {
+        const cudaError_t e = launch_reset(c);
+        return e != cudaSuccess ? e : pipeline_forces(c, theta, eps);
+    }));
     c.have_acc = true;
     if (acc || pot) {
         if (on_device) {

@@ -98,6 +98,16 @@ struct DevState {
     unsigned mom_starts;              // multipoles: internal cells whose children are all leaves
 };
 
+// The launches of one entry point captured into a CUDA graph and replayed
+// while the parameters they were captured with (key) stay the same.
+struct CallGraph {
+    static constexpr int KEYS = 12;
+    cudaGraphExec_t exec = nullptr;
+    long long key[KEYS] = {};
+    int nkey = 0;              // 0: no call recorded yet
+    bool failed = false;       // capture or instantiation failed for this key: direct launches
+};
+
 struct Ctx {
     // configuration
     int nleaf = 16, ncrit = 64, walk_warps = 4, list_capacity = 256, use_graph = 1;
@@ -157,6 +167,8 @@ struct Ctx {
     bool tree_fresh = false;         // the tree was built from the current positions (no refit since)
     float theta = 0.75f, eps = 0.01f;
     cudaGraphExec_t step_graph = nullptr;
+    CallGraph build_graph, mom_graph, forces_graph;   // bonsai_build / _multipoles / _forces
+    long long arena_gen = 0;         // bumped whenever the arena is reallocated
     static constexpr int NSTAGE = 8;
     cudaEvent_t ev[NSTAGE + 1] = {};
     bool timed_step = false;         // the last bonsai_step recorded stage events

@@ -112,6 +112,36 @@ def test_page_locked_host_inputs_match_device_inputs():
     assert np.all(out[4][2] == 0)
 
 
+def test_repeated_calls_replay_graphs_bit_identically():
+    """bonsai_build / _multipoles / _forces run directly the first time a
+    configuration is seen, are captured into graphs the second time and
+    replayed after that: over new bodies of the same size, a change of theta
+    and a rebuild from the sorted state, the forces equal those of a context
+    that never uses graphs, bit for bit."""
+    import torch
+    rng = np.random.default_rng(13)
+    ctxs = [B.Bonsai(B.Config(nleaf=16, ncrit=32, group_pack=1)),
+            B.Bonsai(B.Config(nleaf=16, ncrit=32, group_pack=1, use_graph=-1))]
+    try:
+        for it, theta in enumerate([0.75, 0.75, 0.75, 0.75, 0.6, 0.6, 0.6]):
+            b = W.plummer(20000, 100 + it)
+            accs = []
+            for bz in ctxs:
+                acc = torch.zeros((20000, 3), dtype=torch.float32, device="cuda")
+                bz.set_bodies(b.pos, b.mass, b.vel).build().multipoles().forces(theta, 0.01, acc)
+                if it % 2:                                # rebuild from the sorted state
+                    bz.build().multipoles().forces(theta, 0.01, acc)
+                bz.sync()
+                accs.append(acc.cpu().numpy())
+            assert np.array_equal(accs[0], accs[1]), it
+        tf = oracle.tree_forces(b.pos, b.mass, 0.6, 0.01, 16, 32, TAU_ABS, TAU_REL, pack=True)
+        ok = ~tf.borderline
+        assert rel_err(accs[0], tf.acc)[ok].max() <= 1e-5
+    finally:
+        for bz in ctxs:
+            bz.close()
+
+
 def test_moments_vs_oracle():
     b = edge_bodies(32768, 1)
     res = gpu_run(b.pos, b.mass, forces=False)
