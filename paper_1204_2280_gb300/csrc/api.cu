@@ -122,10 +122,16 @@ cudaError_t refresh_cells_hint(Ctx &c) {
 // key is seen, captured into a graph the second time, replayed from then on
 // while the key holds (the first run also sets up what the launches cache:
 // function attributes, occupancy).  A capture that fails falls back to
-// direct launches for that key.
+// direct launches for that key; while the stream is being captured by the
+// caller, the launches go into the caller's graph.
 template <class F>
 cudaError_t run_cached(Ctx &c, CallGraph &g, const long long *key, int nkey, F body) {
     if (!c.use_graph) return body();
+    // inside a capture of the caller's own: the launches join that graph
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t ec = cudaStreamIsCapturing(c.stream, &cs);
+    if (ec != cudaSuccess) return ec;
+    if (cs != cudaStreamCaptureStatusNone) return body();
     bool same = g.nkey == nkey;
     for (int i = 0; same && i < nkey; i++) same = g.key[i] == key[i];
     if (same && g.exec) return cudaGraphLaunch(g.exec, c.stream);
