@@ -333,17 +333,30 @@ k_keys(const float4 *__restrict__ p, const uint8_t *__restrict__ sysid, int n, i
     // histograms once
     for (int base = blockIdx.x * KEYS_THREADS * KEYS_ITEMS + threadIdx.x; base - (int)threadIdx.x < n;
          base += gridDim.x * KEYS_THREADS * KEYS_ITEMS) {
+    // all of the chunk's loads first (KEYS_ITEMS in flight per thread), then
+    // the keys and the shared-memory histogram atomics
+    float4 qs[KEYS_ITEMS];
+    uint8_t ss[KEYS_ITEMS];
+#pragma unroll
+    for (int k = 0; k < KEYS_ITEMS; k++) {
+        const int i = base + k * KEYS_THREADS;
+        qs[k] = i < n ? p[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        ss[k] = i < n ? sysid[i] : (uint8_t)0;
+    }
 #pragma unroll
     for (int k = 0; k < KEYS_ITEMS; k++) {
         int i = base + k * KEYS_THREADS;
         if (i < n) {
-            float4 q = p[i];
-            const float4 dm = s_dom[sysid[i]];
+            const float4 q = qs[k];
+            const float4 dm = s_dom[ss[k]];
             unsigned qx = min((unsigned)(__fsub_rd(q.x, dm.x) * dm.w), qmax);
             unsigned qy = min((unsigned)(__fsub_rd(q.y, dm.y) * dm.w), qmax);
             unsigned qz = min((unsigned)(__fsub_rd(q.z, dm.z) * dm.w), qmax);
             unsigned long long key = spread3(qx) | (spread3(qy) << 1) | (spread3(qz) << 2);
             keys[i] = key;
+            // one shared-memory atomic per digit (counting the digits a warp
+            // shares with one atomic per warp measured slower: 23.7 against
+            // 18.2 us at 2^20)
 #pragma unroll
             for (int d = 0; d < SORT_PASSES; d++)
                 atomicAdd(&h[d * SORT_RADIX + (unsigned)((key >> (SORT_BITS * d)) & (SORT_RADIX - 1))], 1u);
