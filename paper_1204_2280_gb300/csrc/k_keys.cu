@@ -212,6 +212,9 @@ __device__ __forceinline__ void block_bbox_atomics(float (&v)[6], DevState *st) 
     }
 }
 
+#ifndef KD_ITEMS
+#define KD_ITEMS 4                    // bodies per thread and pass of the fused kick-drift-bbox (1: 6% slower)
+#endif
 __global__ void __launch_bounds__(256)
 k_kick_drift_bbox1(const float4 *__restrict__ pos, const float4 *__restrict__ vel, const float4 *__restrict__ acc,
                    const uint32_t *__restrict__ id, int n, float dt, float4 *pos_o, float4 *vel_o, uint32_t *id_o,
@@ -219,17 +222,34 @@ k_kick_drift_bbox1(const float4 *__restrict__ pos, const float4 *__restrict__ ve
     float v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
     bool bad = false;
     const float h = 0.5f * dt;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        float4 u = vel[i], x = pos[i];
-        if (acc) {                         // acc NULL: drift only
-            const float4 a = acc[i];
-            u.x = fmaf(a.x, h, u.x); u.y = fmaf(a.y, h, u.y); u.z = fmaf(a.z, h, u.z);
+    // KD_ITEMS bodies per thread and pass, all loads issued first
+    constexpr int KD = KD_ITEMS;
+    for (int i0 = blockIdx.x * blockDim.x * KD + threadIdx.x; i0 < n; i0 += gridDim.x * blockDim.x * KD) {
+        float4 uu[KD], xx[KD], aa[KD];
+        uint32_t dd[KD];
+#pragma unroll
+        for (int k = 0; k < KD; k++) {
+            const int i = i0 + k * (int)blockDim.x;
+            if (i < n) {
+                uu[k] = vel[i]; xx[k] = pos[i]; dd[k] = id[i];
+                aa[k] = acc ? acc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         }
-        x.x = fmaf(u.x, dt, x.x); x.y = fmaf(u.y, dt, x.y); x.z = fmaf(u.z, dt, x.z);
-        bad |= !(isfinite(x.x) && isfinite(x.y) && isfinite(x.z));
-        pos_o[i] = x; vel_o[i] = u; id_o[i] = id[i];
-        v[0] = fminf(v[0], x.x); v[1] = fminf(v[1], x.y); v[2] = fminf(v[2], x.z);
-        v[3] = fmaxf(v[3], x.x); v[4] = fmaxf(v[4], x.y); v[5] = fmaxf(v[5], x.z);
+#pragma unroll
+        for (int k = 0; k < KD; k++) {
+            const int i = i0 + k * (int)blockDim.x;
+            if (i >= n) break;
+            float4 u = uu[k], x = xx[k];
+            if (acc) {                     // acc NULL: drift only
+                const float4 a = aa[k];
+                u.x = fmaf(a.x, h, u.x); u.y = fmaf(a.y, h, u.y); u.z = fmaf(a.z, h, u.z);
+            }
+            x.x = fmaf(u.x, dt, x.x); x.y = fmaf(u.y, dt, x.y); x.z = fmaf(u.z, dt, x.z);
+            bad |= !(isfinite(x.x) && isfinite(x.y) && isfinite(x.z));
+            pos_o[i] = x; vel_o[i] = u; id_o[i] = dd[k];
+            v[0] = fminf(v[0], x.x); v[1] = fminf(v[1], x.y); v[2] = fminf(v[2], x.z);
+            v[3] = fmaxf(v[3], x.x); v[4] = fmaxf(v[4], x.y); v[5] = fmaxf(v[5], x.z);
+        }
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&st->status, ST_NAN);
     block_bbox_atomics(v, st);
@@ -239,7 +259,7 @@ k_kick_drift_bbox1(const float4 *__restrict__ pos, const float4 *__restrict__ ve
 // (one system): the input of a rebuild during block time steps.
 cudaError_t launch_drift_bbox(Ctx &c, float dt) {
     const int n = (int)c.n;
-    const int grid = min((n + 255) / 256, c.num_sms * 8);
+    const int grid = min((n + 256 * KD_ITEMS - 1) / (256 * KD_ITEMS), c.num_sms * 8);
     k_kick_drift_bbox1<<<grid, 256, 0, c.stream>>>(c.pos4, c.vel4, nullptr, c.id, n, dt, c.pos4_alt, c.vel4_alt,
                                                     c.id_alt, c.st);
     return cudaGetLastError();
@@ -248,7 +268,7 @@ cudaError_t launch_drift_bbox(Ctx &c, float dt) {
 cudaError_t launch_kick_drift_bbox(Ctx &c, float dt) {
     int n = (int)c.n;
     if (c.nsys == 1) {
-        const int grid = min((n + 255) / 256, c.num_sms * 8);
+        const int grid = min((n + 256 * KD_ITEMS - 1) / (256 * KD_ITEMS), c.num_sms * 8);
         k_kick_drift_bbox1<<<grid, 256, 0, c.stream>>>(c.pos4, c.vel4, c.acc4, c.id, n, dt, c.pos4_alt,
                                                         c.vel4_alt, c.id_alt, c.st);
         return cudaGetLastError();
