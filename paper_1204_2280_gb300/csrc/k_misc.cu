@@ -5,17 +5,32 @@
 namespace bonsai {
 
 // Second half of the kick-drift-kick step: v += a dt/2 (sorted order).
+#ifndef KK_ITEMS
+#define KK_ITEMS 2                    // bodies per thread of the kick, loads first (1 or 4: 0.012 ms at 2^20, 2: 0.010)
+#endif
 __global__ void k_kick(float4 *vel, const float4 *__restrict__ acc, int n, float h) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float4 v = vel[i], a = acc[i];
-    v.x = fmaf(a.x, h, v.x); v.y = fmaf(a.y, h, v.y); v.z = fmaf(a.z, h, v.z);
-    vel[i] = v;
+    const int i0 = blockIdx.x * blockDim.x * KK_ITEMS + threadIdx.x;
+    float4 vv[KK_ITEMS], aa[KK_ITEMS];
+#pragma unroll
+    for (int k = 0; k < KK_ITEMS; k++) {
+        const int i = i0 + k * (int)blockDim.x;
+        if (i < n) { vv[k] = vel[i]; aa[k] = acc[i]; }
+    }
+#pragma unroll
+    for (int k = 0; k < KK_ITEMS; k++) {
+        const int i = i0 + k * (int)blockDim.x;
+        if (i < n) {
+            float4 v = vv[k];
+            const float4 a = aa[k];
+            v.x = fmaf(a.x, h, v.x); v.y = fmaf(a.y, h, v.y); v.z = fmaf(a.z, h, v.z);
+            vel[i] = v;
+        }
+    }
 }
 
 cudaError_t launch_kick(Ctx &c, float dt) {
     int n = (int)c.n;
-    k_kick<<<(n + 255) / 256, 256, 0, c.stream>>>(c.vel4, c.acc4, n, 0.5f * dt);
+    k_kick<<<(n + 256 * KK_ITEMS - 1) / (256 * KK_ITEMS), 256, 0, c.stream>>>(c.vel4, c.acc4, n, 0.5f * dt);
     return cudaGetLastError();
 }
 
